@@ -1,0 +1,342 @@
+"""Pins for the FP64 oracle: each check is fixed by the paper or by mathematics, not by the
+oracle's own formulas (closed forms, library special cases, invariants, finite
+differences and dense brute force on tiny problems)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_01767_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def tiny_problem(loss=oracle.LOSS_GAUSSIAN, n=10, m=4, seed=0, noiseless=True, b=1e-8):
+    """N = 10^2, M = 4^2, K = 6 positions (brute-force size)."""
+    rng = np.random.default_rng(seed)
+    O = synth.object_texture(n, seed=seed, sigma=1.0)
+    P = synth.random_complex((m, m), seed=seed + 10, scale=0.7)
+    pos = np.array([[0, 0], [0, 3], [0, 6], [3, 1], [6, 4], [5, 6]], np.int32)
+    pb = oracle.Problem((n, n), P, pos, None, loss, b)
+    h = oracle.intensity(pb, O)
+    if noiseless:
+        y = h.copy()
+    else:
+        y = rng.poisson(h * 50.0) / 50.0
+    pb.y = np.ascontiguousarray(y, np.float64)
+    return pb, O
+
+
+def rdot(a, b):
+    return float(np.sum(a.real * b.real + a.imag * b.imag))
+
+
+# ----------------------------------------------------------------------------- transforms
+def test_dft_closed_forms():
+    """A delta transforms to the constant M^{-1/2}; a pure exponential to a scaled delta."""
+    my, mx = 8, 4
+    x = np.zeros((my, mx), complex)
+    x[0, 0] = 1
+    X = oracle.dft2(x)
+    np.testing.assert_allclose(X, np.full((my, mx), 1 / math.sqrt(my * mx)), atol=1e-15)
+    uy, ux = 3, 1
+    yy, xx = np.mgrid[0:my, 0:mx]
+    e = np.exp(2j * np.pi * (uy * yy / my + ux * xx / mx))
+    X = oracle.dft2(e)  # forward sign -1 picks out frequency (uy, ux)
+    ref = np.zeros((my, mx), complex)
+    ref[uy, ux] = math.sqrt(my * mx)
+    np.testing.assert_allclose(X, ref, atol=1e-12)
+    # inverse undoes forward
+    z = synth.random_complex((my, mx), seed=5)
+    np.testing.assert_allclose(oracle.dft2(oracle.dft2(z), inverse=True), z, atol=1e-13)
+
+
+@pytest.mark.parametrize("shape", [(32, 32), (16, 8), (64, 64), (128, 128)])
+def test_fft_matches_direct_dft_and_numpy(shape):
+    z = synth.random_complex(shape, seed=7)
+    F = oracle.fft2(z)
+    np.testing.assert_allclose(F, np.fft.fft2(z, norm="ortho"), atol=1e-11, rtol=0)
+    if shape[0] * shape[1] <= 1024:
+        np.testing.assert_allclose(F, oracle.dft2(z), atol=1e-11, rtol=0)
+    np.testing.assert_allclose(oracle.fft2(F, inverse=True), z, atol=1e-12)
+    # Parseval for the orthonormal transform
+    assert abs(np.vdot(F, F).real - np.vdot(z, z).real) <= 1e-10 * np.vdot(z, z).real
+
+
+# ----------------------------------------------------------------------------- forward model
+def test_forward_matches_library_fft_and_parseval():
+    n, m = 48, 16
+    O = synth.object_texture(n, seed=0)
+    P = synth.probe_disk_defocus(m, 5.0)
+    pos, _ = synth.raster_positions(n, m, 4, 9, 1, seed=1)
+    pb = oracle.Problem((n, n), P, pos, None, 0, 1e-8)
+    ph, h = oracle.forward(pb, O)
+    for k, (r, c) in enumerate(pos):
+        psi = P * O[r:r + m, c:c + m]
+        np.testing.assert_allclose(ph[k], np.fft.fft2(psi, norm="ortho"), atol=1e-12)
+        # Parseval: sum_m h = ||psi||^2 + M b
+        assert abs(h[k].sum() - (np.vdot(psi, psi).real + m * m * 1e-8)) < 1e-10 * h[k].sum()
+
+
+def test_forward_translation_and_phase_invariance():
+    n, m = 40, 8
+    O = synth.object_texture(n, seed=3)
+    P = synth.random_complex((m, m), seed=4)
+    pos = np.array([[0, 0], [5, 7], [20, 3]], np.int32)
+    pb = oracle.Problem((n, n), P, pos, None, 0, 1e-8)
+    h = oracle.intensity(pb, O)
+    # global phase leaves h unchanged (Sec. 2 ambiguity)
+    np.testing.assert_allclose(oracle.intensity(pb, O * np.exp(0.7j)), h, rtol=1e-12)
+    # shifting the object and the scan together leaves h unchanged
+    O2 = np.roll(O, (4, 6), axis=(0, 1))
+    pb2 = oracle.Problem((n, n), P, pos + np.array([4, 6], np.int32), None, 0, 1e-8)
+    np.testing.assert_allclose(oracle.intensity(pb2, O2), h, rtol=1e-12)
+
+
+# ----------------------------------------------------------------------------- error metric
+@pytest.mark.parametrize("loss", [0, 1])
+def test_ell_derivatives_by_finite_differences(loss):
+    rng = np.random.default_rng(0)
+    zeta = rng.uniform(0.3, 3.0, 50)
+    y = rng.uniform(0.0, 5.0, 50)
+    y[:5] = 0.0
+    l, d1, d2 = oracle.ell_terms(loss, zeta, y)
+    e = 1e-5
+    lp, d1p, _ = oracle.ell_terms(loss, zeta + e, y)
+    lm, d1m, _ = oracle.ell_terms(loss, zeta - e, y)
+    np.testing.assert_allclose((lp - lm) / (2 * e), d1, rtol=1e-7, atol=1e-9)
+    np.testing.assert_allclose((d1p - d1m) / (2 * e), d2, rtol=1e-7, atol=1e-9)
+    # closed values of Eq. ell_magnitude at a few points
+    if loss == 0:
+        np.testing.assert_allclose(l, 0.5 * (zeta - np.sqrt(y)) ** 2, rtol=1e-14)
+    else:
+        np.testing.assert_allclose(l[:5], zeta[:5] ** 2, rtol=1e-14)  # 0 log 0 = 0
+
+
+def test_noiseless_truth_zero_loss_and_gradient():
+    """Gaussian metric: f = 0 and grad f = 0 at the truth of noiseless data (b included)."""
+    pb, O = tiny_problem(0)
+    f = oracle.loss(pb, O)
+    assert abs(f) < 1e-20
+    g = oracle.gradient(pb, O)
+    assert np.abs(g).max() < 1e-12
+
+
+def test_poisson_truth_value_and_stationarity():
+    """Poisson metric at the truth with y = h: f = sum (y - y log y), grad f = 0."""
+    pb, O = tiny_problem(1)
+    y = pb.y
+    f = oracle.loss(pb, O)
+    ref = float(np.sum(y - np.where(y > 0, y * np.log(np.where(y > 0, y, 1)), 0)))
+    assert abs(f - ref) <= 1e-12 * max(1.0, abs(ref))
+    g = oracle.gradient(pb, O)
+    assert np.abs(g).max() < 1e-9
+
+
+# ----------------------------------------------------------------------------- derivatives
+@pytest.mark.parametrize("loss", [0, 1])
+def test_gradient_by_central_differences(loss):
+    pb, O_true = tiny_problem(loss, noiseless=False)
+    O = O_true + synth.random_complex(O_true.shape, seed=11, scale=0.05)
+    g = oracle.gradient(pb, O)
+    v = synth.random_complex(O.shape, seed=12)
+    e = 1e-6
+    fd = (oracle.loss(pb, O + e * v) - oracle.loss(pb, O - e * v)) / (2 * e)
+    assert abs(fd - rdot(g, v)) <= 1e-7 * abs(fd) + 1e-9
+
+
+def test_probe_gradient_by_central_differences():
+    pb, O_true = tiny_problem(1, noiseless=False)
+    O = O_true + synth.random_complex(O_true.shape, seed=13, scale=0.05)
+    P = pb.P
+    gO, gP = oracle.gradient(pb, O, probe_part=True)
+    v = synth.random_complex(P.shape, seed=14)
+    e = 1e-6
+    fd = (oracle.loss(pb, O, P + e * v) - oracle.loss(pb, O, P - e * v)) / (2 * e)
+    assert abs(fd - rdot(gP, v)) <= 1e-7 * abs(fd) + 1e-9
+
+
+def zeta_of(pb, O, P=None):
+    if P is not None:
+        pb = oracle.Problem((pb.ny, pb.nx), P, pb.pos, pb.y, pb.loss, pb.b)
+    return np.sqrt(oracle.intensity(pb, O))
+
+
+def test_jvp_by_finite_differences_object_and_probe():
+    pb, O = tiny_problem(0)
+    vO = synth.random_complex(O.shape, seed=20)
+    vP = synth.random_complex(pb.P.shape, seed=21)
+    e = 1e-6
+    fd = (zeta_of(pb, O + e * vO, pb.P + e * vP) - zeta_of(pb, O - e * vO, pb.P - e * vP)) / (2 * e)
+    jv = oracle.jvp(pb, O, vO, vP=vP)
+    np.testing.assert_allclose(jv, fd, rtol=1e-6, atol=1e-8)
+
+
+def test_adjoint_identity():
+    """<J v, w> = <v, J^T w> in real coordinates (object + probe), to 1e-12."""
+    pb, O = tiny_problem(1, noiseless=False)
+    vO = synth.random_complex(O.shape, seed=30)
+    vP = synth.random_complex(pb.P.shape, seed=31)
+    w = synth.random_real((pb.K, pb.my, pb.mx), seed=32)
+    lhs = float(np.sum(oracle.jvp(pb, O, vO, vP=vP) * w))
+    tO, tP = oracle.jtvp(pb, O, w, probe_part=True)
+    rhs = rdot(vO, tO) + rdot(vP, tP)
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+
+
+def dense_jacobian(pb, O, e=1e-6):
+    """Dense real-coordinate Jacobian of zeta (K*M x 2N) by central differences of the
+    forward model, column by column (brute force)."""
+    N = O.size
+    cols = []
+    for part in (1.0, 1j):
+        for n in range(N):
+            d = np.zeros(N, complex)
+            d[n] = part * e
+            d = d.reshape(O.shape)
+            cols.append(((zeta_of(pb, O + d) - zeta_of(pb, O - d)) / (2 * e)).ravel())
+    return np.stack(cols, axis=1)
+
+
+def to_real(z):
+    z = np.asarray(z).ravel()
+    return np.concatenate([z.real, z.imag])
+
+
+def from_real(x, shape):
+    n = x.size // 2
+    return (x[:n] + 1j * x[n:]).reshape(shape)
+
+
+@pytest.mark.parametrize("loss", [0, 1])
+def test_ggn_matvec_equals_dense_brute_force(loss):
+    pb, O_true = tiny_problem(loss, noiseless=False)
+    O = O_true + synth.random_complex(O_true.shape, seed=40, scale=0.05)
+    J = dense_jacobian(pb, O)
+    zeta = zeta_of(pb, O).ravel()
+    _, dl, d2l = oracle.ell_terms(loss, zeta, pb.y.ravel())
+    G = J.T @ (d2l[:, None] * J)
+    g_dense = J.T @ dl
+    np.testing.assert_allclose(to_real(oracle.gradient(pb, O)), g_dense, rtol=1e-6, atol=1e-7)
+    v = synth.random_complex(O.shape, seed=41)
+    lam = 0.37
+    out = oracle.ggn_matvec(pb, O, v, lam=lam)
+    ref = G @ to_real(v) + lam * to_real(v)
+    np.testing.assert_allclose(to_real(out), ref, rtol=1e-6, atol=1e-6 * np.abs(ref).max())
+
+
+def test_ggn_symmetric_psd_and_gauss_identity():
+    pb, O_true = tiny_problem(0, noiseless=False)
+    O = O_true + synth.random_complex(O_true.shape, seed=50, scale=0.1)
+    u = synth.random_complex(O.shape, seed=51)
+    v = synth.random_complex(O.shape, seed=52)
+    Gu = oracle.ggn_matvec(pb, O, u)
+    Gv = oracle.ggn_matvec(pb, O, v)
+    assert abs(rdot(u, Gv) - rdot(Gu, v)) <= 1e-12 * abs(rdot(u, Gv))
+    assert rdot(v, Gv) >= 0
+    jv = oracle.jvp(pb, O, v)
+    assert abs(rdot(v, Gv) - float(np.sum(jv * jv))) <= 1e-12 * rdot(v, Gv)
+
+
+def test_global_phase_null_direction():
+    """J (i O) = 0 and G (i O) = 0: the global-phase ambiguity (Sec. 2)."""
+    pb, O_true = tiny_problem(1, noiseless=False)
+    O = O_true + synth.random_complex(O_true.shape, seed=60, scale=0.05)
+    Gv = oracle.ggn_matvec(pb, O, 1j * O)
+    Gu = oracle.ggn_matvec(pb, O, synth.random_complex(O.shape, seed=61))
+    assert np.abs(Gv).max() <= 1e-12 * np.abs(Gu).max()
+    g1 = oracle.gradient(pb, O)
+    g2 = oracle.gradient(pb, O * np.exp(0.4j))
+    np.testing.assert_allclose(g2, g1 * np.exp(0.4j), atol=1e-12 * np.abs(g1).max())
+    assert abs(oracle.loss(pb, O) - oracle.loss(pb, O * np.exp(0.4j))) < 1e-12 * abs(oracle.loss(pb, O))
+
+
+def test_blind_scale_null_direction():
+    """J (O, -P) = 0: the object/probe scale ambiguity of the blind problem (Sec. 2)."""
+    pb, O = tiny_problem(0, noiseless=False)
+    jv = oracle.jvp(pb, O, O, vP=-pb.P)
+    assert np.abs(jv).max() < 1e-12 * np.abs(oracle.jvp(pb, O, O)).max()
+
+
+def test_ggn_equals_hessian_at_noiseless_truth():
+    """At the truth of noiseless Gaussian data the residual term of Eq. ggn_approximation
+    vanishes, so G v equals the Hessian-vector product (central differences of grad f)."""
+    pb, O = tiny_problem(0)
+    v = synth.random_complex(O.shape, seed=70)
+    e = 1e-5
+    hv = (oracle.gradient(pb, O + e * v) - oracle.gradient(pb, O - e * v)) / (2 * e)
+    gv = oracle.ggn_matvec(pb, O, v)
+    np.testing.assert_allclose(gv, hv, rtol=1e-6, atol=1e-7 * np.abs(gv).max())
+
+
+@pytest.mark.parametrize("loss", [0, 1])
+def test_ggn_diag_closed_form_vs_dense(loss):
+    """App. B: the closed-form diagonal equals the mean of the exact Re/Im diagonals of the
+    dense G when tr_k uses the exact weights |psihat|^2/h (the printed form approximates
+    h ~ |psihat|^2, a difference of order b)."""
+    pb, O_true = tiny_problem(loss, noiseless=False, b=1e-12)
+    O = O_true + synth.random_complex(O_true.shape, seed=80, scale=0.05)
+    J = dense_jacobian(pb, O)
+    zeta = zeta_of(pb, O).ravel()
+    _, _, d2l = oracle.ell_terms(loss, zeta, pb.y.ravel())
+    G = J.T @ (d2l[:, None] * J)
+    N = O.size
+    dg = np.diag(G)
+    mean_diag = 0.5 * (dg[:N] + dg[N:])
+    D_O, _ = oracle.ggn_diag(pb, O)
+    np.testing.assert_allclose(D_O.ravel(), mean_diag, rtol=2e-6, atol=1e-9 * mean_diag.max())
+
+
+def test_cg_matches_dense_solve():
+    pb, O_true = tiny_problem(0, noiseless=False)
+    O = O_true + synth.random_complex(O_true.shape, seed=90, scale=0.05)
+    g = oracle.gradient(pb, O)
+    lam = 0.05
+    J = dense_jacobian(pb, O)
+    G = J.T @ J
+    A = G + lam * np.eye(G.shape[0])
+    x_ref = np.linalg.solve(A, -to_real(g))
+    x, r, it, conv = oracle.cg(pb, O, g, lam, eta=1e-12, max_iter=400)
+    assert conv
+    np.testing.assert_allclose(to_real(x), x_ref, rtol=1e-5, atol=1e-7 * np.abs(x_ref).max())
+    # residual returned is -g - A x
+    np.testing.assert_allclose(to_real(r), -to_real(g) - A @ to_real(x), atol=1e-8)
+
+
+def test_object_error_phase_invariance():
+    O = synth.object_texture(32, seed=1)
+    assert oracle.object_error(O * np.exp(1.3j), O) < 1e-14
+    assert abs(oracle.object_error(1.1 * O, O) - 0.1) < 1e-12
+
+
+def test_paper_lm_parameters_fixture():
+    """The LM constants of Sec. 5 (tests/golden/lm_parameters.txt) are the oracle defaults."""
+    vals = {}
+    with open(os.path.join(GOLDEN, "lm_parameters.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                k, v = line.split("=")
+                vals[k.strip()] = float(v)
+    d = oracle.DEFAULT_LM
+    for k in ("mu0", "mu_min", "nu", "rho_min", "kappa"):
+        assert d[k] == vals[k]
+
+
+def test_lm_converges_on_small_noiseless_workload():
+    """Algorithm 1 on the 128^2 / 32^2 / 64-position noiseless workload from a flat start
+    reaches 1e-3 object error against the truth (the solution is exact up to phase)."""
+    w = synth.SMALL
+    O_true = synth.to_c64(synth.object_texture(w.n, seed=0))
+    P = synth.to_c64(synth.probe_disk_defocus(w.m, w.radius))
+    pos, _ = synth.raster_positions(w.n, w.m, w.grid, w.step, w.jitter, seed=1)
+    pb = oracle.Problem((w.n, w.n), P, pos, None, 0, 1e-8)
+    pb.y = synth.to_f32(oracle.intensity(pb, O_true))
+    mask = synth.illumination_mask(w.n, P, pos, 0.1)
+    O, info = oracle.lm_solve(pb, synth.flat_object(w.n), O_ref=O_true, mask=mask,
+                              max_outer=60, target_err=1e-3)
+    assert info["status"] == 0
+    assert info["err"][-1] <= 1e-3, info
+    assert info["n_outer"] < 60
