@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""GGN matvecs/s of the matrix-free LM ptychography solver on one GB300 (or N replicas).
+
+Workload: object 1024x1024, probe 128x128 (defocused disk, radius 40 px), 60x60 jittered
+raster (3600 positions, step 15 px: the requested 16 px would carry patches past the
+object edge), Poisson counts at 1e3 photons peak, Poisson error metric, complex64 data
+with FP64 LM/CG scalars.  Inputs are synthetic and seeded (paper_2103_01767_gb300.synth);
+the measurements are simulated with the library's own forward model.
+
+One "step" is one outer iteration of Algorithm 1 through the C-ABI's lm_solve with a fixed
+number of CG iterations: linearise (forward + cache + gradient), CG iterations (GGN matvec
++ FP64 dots + vector updates), trial loss, gain ratio and damping update.  `value` counts
+the GGN matvecs actually executed (CG iterations plus each solve's initial residual) per
+second of device time.  The 472 MB frequency cache streamed by every matvec is larger
+than L2, so no L2 flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle (the method's plain restatement) on the host
+cores instead, on a bounded sample of positions of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2103_01767_gb300 import synth  # noqa: E402
+
+METRIC = "GGN matvecs/s (1024^2 obj, 3600 pos, 128^2 probe)"
+UNIT = "matvec/s"
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+HBM_FALLBACK_GBS = 6800.0
+PROFILE_FILE = os.path.join(ROOT, "profiles", "ggn_matvec_obj1024_probe128_pos3600.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2103_01767_gb300", "csrc", f)
+                  for f in ("team_fft.cuh", "ptycho_kernels.cu", "kernels.h")]
+
+
+def fft_flops(M):
+    return 5.0 * M * math.log2(M)
+
+
+def matvec_flops(K, M):
+    """Algorithmic FP32 flops of one GGN matvec: a forward and an inverse M-point 2D FFT per
+    position (5 M log2 M each, the usual FFT count) plus 24 flops per pixel of elementwise
+    work (probe multiply, frequency stage, conj-probe multiply, scatter add)."""
+    return K * (2.0 * fft_flops(M) + 24.0 * M)
+
+
+def matvec_bytes(K, M, N):
+    """Algorithmic DRAM bytes of one GGN matvec: the cache a (8 K M), the vector v and the
+    output written and read-modify-written (3 x 8 N), the probe (8 M)."""
+    return 8.0 * K * M + 24.0 * N + 8.0 * M
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as fh:
+                d = json.load(fh)
+            return float(d.get("hbm_gbs") or d.get("hbm_GBs") or HBM_FALLBACK_GBS), "measured"
+        except Exception:
+            pass
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+def recorded_traffic():
+    """dram bytes per matvec launch recorded from an ncu capture of the current kernel
+    source (profiles/...md line 'traffic_bytes_per_launch: X kernel_hash: H'); None if the
+    kernels changed since."""
+    if not os.path.exists(PROFILE_FILE):
+        return None
+    want = kernel_hash()
+    with open(PROFILE_FILE) as fh:
+        for line in fh:
+            if line.startswith("traffic_bytes_per_launch:"):
+                parts = line.split()
+                try:
+                    val = float(parts[1])
+                    hsh = parts[3]
+                except (IndexError, ValueError):
+                    return None
+                return val if hsh == want else None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, p[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+# CPU legs: the FP64 oracle on a bounded sample of positions
+# ---------------------------------------------------------------------------------------
+def oracle_sample_problem(w, n_pos, seed=0):
+    import oracle
+    O_true = synth.to_c64(synth.object_texture(w.n, seed=0))
+    P = synth.probe_disk_defocus(w.m, w.radius)
+    pos, _ = synth.raster_positions(w.n, w.m, w.grid, w.step, w.jitter, seed=1)
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(pos.shape[0], size=min(n_pos, pos.shape[0]), replace=False))
+    pos = pos[idx]
+    pb = oracle.Problem((w.n, w.n), P, pos, None, w.loss, 1e-8)
+    h = oracle.intensity(pb, O_true)
+    if w.peak > 0:
+        P = P * np.sqrt(w.peak / h.max())
+        pb = oracle.Problem((w.n, w.n), P, pos, None, w.loss, 1e-8)
+        h = oracle.intensity(pb, O_true)
+        y = synth.poisson_counts(h, seed=2)
+    else:
+        y = h
+    pb.y = np.ascontiguousarray(y, np.float64)
+    O = synth.to_c64(synth.flat_object(w.n) * np.mean(np.abs(O_true)))
+    v = synth.random_complex((w.n, w.n), seed=3)
+    return pb, O, v
+
+
+def time_oracle_matvec(w, budget_s=15.0):
+    """Times oracle.ggn_matvec on a position sample sized for about budget_s seconds.
+    Returns (matvecs/s scaled to the full K, seconds, positions, threads)."""
+    import oracle
+    oracle.build()
+    n_try = 16
+    pb, O, v = oracle_sample_problem(w, n_try)
+    t0 = time.perf_counter()
+    oracle.ggn_matvec(pb, O, v, lam=1e-3)
+    dt = time.perf_counter() - t0
+    n = int(min(w.K, max(n_try, n_try * budget_s / max(dt, 1e-6))))
+    pb, O, v = oracle_sample_problem(w, n)
+    t0 = time.perf_counter()
+    oracle.ggn_matvec(pb, O, v, lam=1e-3)
+    dt = time.perf_counter() - t0
+    return (n / w.K) / dt, dt, n, oracle.num_threads()
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    threads = oracle.num_threads()
+    # size one step at ~4 s of CPU work so warmup+steps finish within a few minutes
+    n_try = 8
+    pb, O, v = oracle_sample_problem(w, n_try)
+    t0 = time.perf_counter()
+    oracle.ggn_matvec(pb, O, v, lam=1e-3)
+    per_pos = (time.perf_counter() - t0) / n_try
+    n = int(min(w.K, max(n_try, 4.0 / max(per_pos, 1e-6))))
+    pb, O, v = oracle_sample_problem(w, n)
+    for _ in range(args.warmup):
+        oracle.ggn_matvec(pb, O, v, lam=1e-3)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.ggn_matvec(pb, O, v, lam=1e-3)
+    dt = time.perf_counter() - t0
+    value = args.steps * (n / w.K) / dt
+    sample = f"{n} of {w.K} positions per step, one FP64 GGN matvec each, scaled by {n}/{w.K}"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w.name},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------------------
+def setup_workload(ptylm, torch, w, dev, stream):
+    O_true = torch.from_numpy(synth.object_texture(w.n, seed=0).astype(np.complex64)).to(dev)
+    P = torch.from_numpy(synth.probe_disk_defocus(w.m, w.radius).astype(np.complex64)).to(dev)
+    pos_np, step_used = synth.raster_positions(w.n, w.m, w.grid, w.step, w.jitter, seed=1)
+    pos = torch.from_numpy(pos_np).to(dev)
+    y = torch.empty((pos_np.shape[0], w.m, w.m), dtype=torch.float32, device=dev)
+    ctx = ptylm.lm_init(w.n, w.n, w.m, w.m, pos, y, w.loss, 1e-8, stream=stream)
+    ptylm.forward_intensity(ctx, O_true, P, y)
+    torch.cuda.synchronize(dev)
+    if w.peak > 0:
+        P *= math.sqrt(w.peak / float(y.max()))
+        ptylm.forward_intensity(ctx, O_true, P, y)
+        counts = synth.poisson_counts(y.cpu().numpy(), seed=2).astype(np.float32)
+        y.copy_(torch.from_numpy(counts))
+    torch.cuda.synchronize(dev)
+    O0 = torch.full((w.n, w.n), complex(float(O_true.abs().mean()), 0.0), dtype=torch.complex64, device=dev)
+    return ctx, O0, P, y, pos, step_used
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cg-per-step", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--workload", default=synth.LARGE.name, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    # CPU baseline first (before any GPU work, so no forked process ever follows a CUDA call).
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, secs, n, threads = time_oracle_matvec(w)
+        cpu = {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"one FP64 GGN matvec over {n} of {w.K} positions ({secs:.1f} s), "
+                         f"scaled by {n}/{w.K}"}
+
+    from paper_2103_01767_gb300 import build as _build
+    _build.build()
+    from paper_2103_01767_gb300 import ptylm
+
+    stream = torch.cuda.current_stream(dev)
+    ctx, O0, P, y, pos, step_used = setup_workload(ptylm, torch, w, dev, stream)
+    O = O0.clone()
+    params = ptylm.default_lm_params(w.loss)
+    params.max_outer = 1
+    params.fixed_cg = args.cg_per_step
+
+    def step(Obuf, Pbuf):
+        st, info = ptylm.lm_solve(ctx, Obuf, Pbuf, params)
+        return info["matvecs"]
+
+    for _ in range(args.warmup):
+        step(O, P)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ptylm.ptylm_profile(ctx, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    matvecs = 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            matvecs += step(O, P)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    mv_ms, mv_n = ptylm.ptylm_profile_read(ctx, ptylm.KERNEL_GGN_MATVEC)
+    _, launches = ptylm.ptylm_profile_read(ctx, -1)
+    ptylm.ptylm_profile(ctx, False)
+    if world > 1:
+        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t)
+        m = torch.tensor([matvecs], dtype=torch.float64, device=dev)
+        dist.all_reduce(m, op=dist.ReduceOp.SUM)
+        total_matvecs = float(m)
+    else:
+        total_matvecs = float(matvecs)
+    value = total_matvecs / elapsed
+
+    # End to end through the C-ABI with pinned host buffers: H2D of O and P, D2H of O.
+    O_h = O.cpu().pin_memory()
+    P_h = P.cpu().pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e2e_mv = 0
+    for _ in range(args.e2e_steps):
+        e2e_mv += step(O_h, P_h)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t)
+        m = torch.tensor([e2e_mv], dtype=torch.float64, device=dev)
+        dist.all_reduce(m, op=dist.ReduceOp.SUM)
+        e2e_mv = float(m)
+    N, M, K = w.n * w.n, w.m * w.m, int(pos.shape[0])
+
+    clocks = clk.summary()
+    avg_mv_s = (mv_ms / 1e3) / max(mv_n, 1)
+    flops = matvec_flops(K, M)
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_fp32 = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / avg_mv_s / 1e12
+    hbm_peak, hbm_kind = measured_peaks()
+    hbm_achieved = matvec_bytes(K, M, N) / avg_mv_s / 1e9
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "object": w.n, "probe": w.m, "positions": K,
+                       "raster_step_used": step_used, "loss": "poisson", "peak_photons": w.peak,
+                       "cg_iters_per_step": args.cg_per_step, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2: 472 MB cache streamed per matvec"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                         "frac": achieved / peak_fp32, "traffic": recorded_traffic(),
+                         "kernel": "k_ggn_matvec<7>", "avg_launch_us": avg_mv_s * 1e6,
+                         "launches": mv_n, "flops_per_launch": flops,
+                         "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                         "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": hbm_achieved / hbm_peak, "peak_kind": hbm_kind,
+                                 "bytes_per_launch": matvec_bytes(K, M, N)}},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_mv / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * N + 8 * M,
+                    "d2h_bytes_per_step": 8 * N},
+            "clocks": clocks,
+            "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    ptylm.lm_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

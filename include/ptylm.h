@@ -1,0 +1,207 @@
+/*
+ * ptylm.h -- C-ABI of the GB300 (sm_103a) matrix-free Levenberg-Marquardt ptychography
+ * library, after arXiv 2103.01767 ("A matrix-free Levenberg-Marquardt algorithm for
+ * efficient ptychographic phase retrieval").
+ *
+ * Model (Sec. 2, Eqs. exit_wave and expected_count):
+ *     psi_k = diag(P) S_k O,   psihat_k = F psi_k,   h_k = |psihat_k|^2 + b,
+ *     zeta = h^(1/2)           (Sec. 4.1, Eq. magnitude)
+ * Error metric (Sec. 4.1, Eq. ell_magnitude), summed over positions k and pixels m:
+ *     Gaussian  l = (zeta - y^(1/2))^2 / 2          Poisson  l = zeta^2 - y log zeta^2
+ * LM system (Sec. 4.1, Eq. lma_magnitude):  (G + lambda D) dz = -J^T grad_zeta l,
+ *     G = J^T Hess_zeta(l) J  (Eq. ggn_magnitude), applied matrix-free (App. A).
+ *
+ * Conventions shared by every entry point
+ *   - Complex arrays are interleaved single precision (ptylm_c64, 8 bytes).  Object O is
+ *     row-major [ny][nx], probe P row-major [my][mx], per-position arrays [K][my][mx].
+ *   - A complex vector stands for the real coordinates [Re; Im] of Sec. 3: inner products
+ *     are sum(re*re + im*im) and gradients are dRe + i dIm (twice the Wirtinger form).
+ *   - F is the orthonormal 2D DFT with forward sign -1.
+ *   - Positions are int32 [K][2] = (row, col) of each patch's top-left corner; every
+ *     position must satisfy 0 <= row <= ny-my and 0 <= col <= nx-mx.
+ *   - Supported sizes: square probes with my = mx in {32, 64, 128}; any ny, nx >= my.
+ *   - Pointers are device pointers unless an entry point says "host or device"; there the
+ *     library detects host memory (pageable or pinned) and stages it through buffers it
+ *     owns.  All memory passed in stays owned by the caller; the library never frees it.
+ *   - Work is issued on the stream given to lm_init.  Entry points that return host
+ *     scalars (f_host, stats) synchronise that stream before returning.
+ *   - Errors are reported by return code only; nothing is thrown across the ABI.  A
+ *     failed call leaves outputs unspecified.  ptylm_last_error() gives a thread-local
+ *     message for the most recent failure on the calling thread.
+ *   - A context is not thread-safe: one thread at a time may call into it.
+ */
+#ifndef PTYLM_H
+#define PTYLM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { float re, im; } ptylm_c64;
+
+typedef struct ptylm_ctx ptylm_ctx;
+
+typedef enum {
+    PTYLM_OK = 0,
+    PTYLM_ERR_ARG = 1,        /* invalid argument, size or position; nothing launched   */
+    PTYLM_ERR_NOMEM = 2,      /* device allocation failed or workspace budget exceeded  */
+    PTYLM_ERR_CUDA = 3,       /* a CUDA runtime call failed                              */
+    PTYLM_ERR_NAN = 4,        /* a reduction produced NaN or Inf                         */
+    PTYLM_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up                      */
+    PTYLM_ERR_STALLED = 6,    /* LM damping overflowed (mu > mu_max) without progress   */
+    PTYLM_ERR_STATE = 7,      /* call needs a linearisation point (forward_loss cache=1) */
+    PTYLM_WARN_CG_MAXIT = 16  /* a CG solve hit max_cg; the step was still used         */
+} ptylm_status;
+
+typedef enum { PTYLM_LOSS_GAUSSIAN = 0, PTYLM_LOSS_POISSON = 1 } ptylm_loss;
+
+typedef struct {
+    int ny, nx;               /* object rows, columns                                    */
+    int my, mx;               /* probe / detector rows, columns (my == mx, 32/64/128)    */
+    int K;                    /* number of scan positions (>= 0)                         */
+    int loss;                 /* ptylm_loss                                              */
+    float background;         /* b > 0, added to every detector pixel (Eq. expected_count) */
+    int joint;                /* 0: object only (SPR, Eq. cdp); 1: object + probe (BPR)  */
+    size_t workspace_budget;  /* max bytes the context may allocate; 0 = unlimited       */
+} ptylm_desc;
+
+/* Parameters of Algorithm 1 (Sec. 4.2; values used in the paper: Sec. 5). */
+typedef struct {
+    double mu0;        /* initial damping multiplier (paper: 1e-5)                         */
+    double mu_min;     /* lower bound of mu (1e-8)                                         */
+    double kappa;      /* mu growth/shrink factor (4)                                      */
+    double nu;         /* exponent in lambda = mu ||grad_zeta l||^nu (1)                   */
+    double rho_min;    /* acceptance threshold of the gain ratio (1e-4)                    */
+    double beta;       /* CG forcing bound, Eq. lma_termination_eta (0.1 Gauss, 0.9 Poisson) */
+    double mu_max;     /* give up (PTYLM_ERR_STALLED) when mu exceeds this (1e16)          */
+    int max_outer;     /* outer LM iterations                                              */
+    int max_cg;        /* CG iterations per solve (PTYLM_WARN_CG_MAXIT when reached)       */
+    int fixed_cg;      /* > 0: run exactly this many CG iterations per solve (benchmarking) */
+    double target_err; /* stop once the object error <= target_err (needs O_ref)           */
+    const ptylm_c64* O_ref; /* optional device reference object for the error metric       */
+    const uint8_t* mask;    /* optional device [ny][nx] mask of pixels the error compares   */
+} ptylm_lm_params;
+
+/* Per-call results of lm_solve.  hist_* point to host arrays of hist_len entries (or are
+ * NULL); entry t describes outer iteration t. */
+typedef struct {
+    int n_outer;          /* outer iterations run                                         */
+    int cg_total;         /* CG iterations (GGN matvecs inside CG) summed over the run    */
+    int matvecs_total;    /* all GGN matvecs, including each solve's initial residual     */
+    double f_final;       /* error metric at the returned iterate                         */
+    double err_final;     /* object error at the returned iterate (NaN without O_ref)     */
+    int hist_len;
+    double* hist_f;       /* f at the linearisation point of iteration t                  */
+    double* hist_gnorm;   /* ||grad f|| there                                             */
+    double* hist_mu;      /* mu after iteration t                                         */
+    int* hist_cg;         /* CG iterations in iteration t                                 */
+    double* hist_err;     /* object error after iteration t (NaN without O_ref)           */
+} ptylm_lm_stats;
+
+/* Create a context for one reconstruction problem (Sec. 2).
+ *   positions_dev: device int32 [K][2], copied into the context (validated on the host:
+ *                  out-of-range positions return PTYLM_ERR_ARG with nothing launched).
+ *   y_dev:         device float [K][my][mx] measured intensities (y >= 0), NOT copied: it
+ *                  must stay valid and unchanged until lm_destroy.
+ *   stream:        cudaStream_t (NULL = legacy default stream) all work is issued on.
+ * Allocates the frequency-domain cache (8*K*M bytes) and small workspaces within
+ * desc->workspace_budget, else PTYLM_ERR_NOMEM. */
+ptylm_status lm_init(ptylm_ctx** ctx, const ptylm_desc* desc, const int32_t* positions_dev,
+                     const float* y_dev, void* stream);
+
+/* Error metric f = sum_k sum_m l(zeta_km, y_km) at (O, P)  (Eq. error_metric_magnitude).
+ *   O: device [ny][nx]; P: device [my][mx].
+ *   f_host: host double receiving f (accumulated in FP64).
+ *   dl_norm2_host: optional host double receiving ||grad_zeta l||^2 (Algorithm 1's lambda).
+ *   cache = 1 makes (O, P) the linearisation point of later jvp / jtvp / ggn_matvec /
+ *   gradient calls: it copies O and P into the context, stores the per-pixel factor
+ *   a = psihat (Hess_zeta l)^(1/2) / zeta used by ggn_matvec, and computes
+ *   grad f = J^T grad_zeta l (App. A step 1) fused in the same kernel.
+ *   cache = 0 evaluates f only (Algorithm 1's trial point) and changes no state. */
+ptylm_status forward_loss(ptylm_ctx* ctx, const ptylm_c64* O, const ptylm_c64* P,
+                          double* f_host, double* dl_norm2_host, int cache);
+
+/* grad f = J^T grad_zeta l at the linearisation point (App. A step 1; Eq. grad_f_obj in
+ * real coordinates).  gO: device [ny][nx]; gP: device [my][mx] or NULL.  The probe part is
+ * only available for joint contexts (else PTYLM_ERR_ARG when gP != NULL). */
+ptylm_status gradient(ptylm_ctx* ctx, ptylm_c64* gO, ptylm_c64* gP);
+
+/* Jacobian-vector product at the linearisation point (App. A Eqs. jvp_step_1..3; computed
+ * in forward mode from App. B Eq. jac_ampl):
+ *     out_km = Re( conj(psihat_km) [F (P . S_k vO + vP . S_k O)]_m ) / zeta_km
+ *   vO: device [ny][nx]; vP: device [my][mx] or NULL (= 0); out: device float [K][my][mx].
+ * Recomputes psihat from the stored (O, P); does not read the ggn_matvec cache. */
+ptylm_status jvp(ptylm_ctx* ctx, const ptylm_c64* vO, const ptylm_c64* vP, float* out);
+
+/* Transposed-Jacobian product at the linearisation point (App. A Eq. arbitrary_jtvp_sequence):
+ *     outO = sum_k S_k^T [conj(P) . F^H(psihat_k w_k / zeta_k)]
+ *     outP = sum_k conj(S_k O) . F^H(psihat_k w_k / zeta_k)         (joint contexts)
+ *   w: device float [K][my][mx]; outO: device [ny][nx] (overwritten); outP: device [my][mx]
+ *   or NULL. */
+ptylm_status jtvp(ptylm_ctx* ctx, const float* w, ptylm_c64* outO, ptylm_c64* outP);
+
+/* Damped GGN-vector product, the hot path (App. A steps 2-4, Eq. ggn_magnitude_appendix_2):
+ *     outO = J^T( Hess_zeta l . J vO ) + lambda D vO
+ * One fused kernel per call: patch gather x P, 2D FFT, frequency stage with the cached a
+ * (t = Re(conj(a) dpsihat), chihat = a t), inverse 2D FFT, x conj(P), overlap scatter-add.
+ *   vO, outO: host or device [ny][nx]; outO is overwritten.
+ *   D: device float [ny][nx] diagonal scaling, or NULL for the identity.
+ *   vP / outP: reserved for joint contexts; must be NULL in object-only contexts.
+ * Needs a linearisation point (PTYLM_ERR_STATE otherwise). */
+ptylm_status ggn_matvec(ptylm_ctx* ctx, const ptylm_c64* vO, const ptylm_c64* vP, double lambda,
+                        const float* D, ptylm_c64* outO, ptylm_c64* outP);
+
+/* Truncated matrix-free LM, Algorithm 1 (Sec. 4.2) for the object (SPR) problem with
+ * D = I and lambda = mu ||grad_zeta l||^nu; inner truncated CG stopped by
+ * Eqs. lma_termination_magnitude / lma_termination_eta with eta = min(beta, ||grad f||^(1/2)),
+ * warm-started from the previous step.  CG vectors are FP32; dot products, lambda, mu,
+ * the gain ratio and f are FP64 on the device.
+ *   O_inout: host or device [ny][nx]; initial guess in, final iterate out.
+ *   P_inout: host or device [my][mx] probe (read only for object-only contexts).
+ *   prm: host parameters; stats: host results (may be NULL).
+ * Returns PTYLM_OK, PTYLM_WARN_CG_MAXIT (some solve hit max_cg), or an error. */
+ptylm_status lm_solve(ptylm_ctx* ctx, ptylm_c64* O_inout, ptylm_c64* P_inout,
+                      const ptylm_lm_params* prm, ptylm_lm_stats* stats);
+
+/* Expected intensities h = |F diag(P) S_k O|^2 + b for every position (Sec. 2,
+ * Eq. expected_count), used to simulate measurements.  O: device [ny][nx]; P: device
+ * [my][mx]; h_out: device float [K][my][mx] (it may be the y buffer given to lm_init).
+ * Changes no context state. */
+ptylm_status forward_intensity(ptylm_ctx* ctx, const ptylm_c64* O, const ptylm_c64* P, float* h_out);
+
+/* Instrumentation (no counterpart in the paper).  ptylm_profile(ctx, 1) resets the
+ * counters and starts timing every launch of the per-position kernels with CUDA events on
+ * the context stream; ptylm_profile(ctx, 0) stops.  ptylm_profile_read synchronises the
+ * stream and returns, for kernel id `kernel` (PTYLM_KERNEL_*), the summed device time in
+ * milliseconds and the number of timed launches; kernel = -1 returns 0 ms and the number
+ * of launches of all the library's kernels (vector kernels included) since the reset. */
+enum {
+    PTYLM_KERNEL_FORWARD_LOSS = 0,
+    PTYLM_KERNEL_FORWARD_CACHE = 1,
+    PTYLM_KERNEL_GGN_MATVEC = 2,
+    PTYLM_KERNEL_JTVP = 3,
+    PTYLM_KERNEL_JVP = 4,
+    PTYLM_KERNEL_FORWARD_INTENSITY = 5
+};
+ptylm_status ptylm_profile(ptylm_ctx* ctx, int enable);
+ptylm_status ptylm_profile_read(ptylm_ctx* ctx, int kernel, double* total_ms, long long* launches);
+
+/* Free the context and everything it allocated (NULL is accepted). */
+ptylm_status lm_destroy(ptylm_ctx* ctx);
+
+/* Static description of a status code. */
+const char* ptylm_strerror(ptylm_status s);
+
+/* Thread-local message of the most recent failed call on this thread ("" if none). */
+const char* ptylm_last_error(void);
+
+/* Fill prm with the paper's Algorithm 1 defaults (Sec. 5) for the given loss. */
+void ptylm_default_lm_params(ptylm_lm_params* prm, int loss);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTYLM_H */

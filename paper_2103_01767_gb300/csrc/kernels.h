@@ -1,0 +1,44 @@
+// kernels.h -- internal interface between the C-ABI host code and the FFT kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace ptylm {
+
+// Arguments shared by the per-position kernels.  Pointers not used by a kernel are NULL.
+struct PtyArgs {
+    const float2* O;       // object (forward, jtvp, jvp linearisation point) or vector (matvec)
+    const float2* V;       // second gathered array: the direction vO of jvp
+    const float2* P;       // probe [S][S]
+    const int2* pos;       // positions [K] as (row, col)
+    const float* y;        // measurements [K][S][S]
+    const float* w;        // jtvp weights [K][S][S]
+    float2* a_cache;       // [K][M] per-pixel factor a, team-register order
+    float2* out;           // scatter-add target [ny][nx] (gradient, matvec, jtvp)
+    float* out_real;       // jvp output [K][S][S]
+    float2* scratch;       // jvp: one M-sized slot per team
+    double* partials;      // per-CTA FP64 partial sums [gridDim.x][2]
+    const float2* tw;      // twiddles W_S^j = exp(-2 pi i j / S), j < S
+    int K;
+    int nx;
+    float b;               // background
+    int loss;              // 0 Gaussian, 1 Poisson
+};
+
+enum KernelId {
+    KID_FWD_LOSS = 0, KID_FWD_CACHE = 1, KID_MATVEC = 2, KID_JTVP = 3, KID_JVP = 4, KID_FWD_INTENSITY = 5,
+    KID_COUNT = 6
+};
+
+// Threads per CTA and teams (positions in flight) per CTA for a patch side 2^LS.
+int cta_threads(int LS);
+int cta_teams(int LS);
+size_t cta_smem_bytes(int LS);
+
+// Opt in to the kernel's dynamic shared memory and report how many CTAs fit on one SM.
+cudaError_t kernel_prepare(int LS, int kid, int* ctas_per_sm);
+
+// Launch kernel `kid` for patch side 2^LS on `grid` CTAs.
+cudaError_t kernel_launch(int LS, int kid, const PtyArgs& a, int grid, cudaStream_t stream);
+
+}  // namespace ptylm

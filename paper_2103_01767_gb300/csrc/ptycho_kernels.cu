@@ -1,0 +1,330 @@
+// ptycho_kernels.cu -- per-scan-position kernels of the far-field ptychography model and
+// its matrix-free derivatives (arXiv 2103.01767), for sm_103a.
+//
+// Every kernel is persistent over scan positions: a team of T = S*S/32 threads owns one
+// position at a time, gathers its S x S object patch straight into registers, runs the
+// team FFT of team_fft.cuh, applies an elementwise frequency-domain stage in registers
+// and (except the loss-only kernel) runs the inverse FFT and scatter-adds the conj(P)
+// weighted result into an object-sized array with vector float2 reductions in L2.
+//
+//   KID_FWD_LOSS   f = sum l(zeta, y)                        (Sec. 4.1, Eq. ell_magnitude)
+//   KID_FWD_INTENSITY  h = |psihat|^2 + b in natural order   (Sec. 2, Eq. expected_count)
+//   KID_FWD_CACHE  f, ||grad_zeta l||^2, the cache a = psihat (d2l)^(1/2) / zeta and
+//                  grad f = J^T grad_zeta l                  (App. A step 1)
+//   KID_MATVEC     J^T( Hess l . J v )  with the cache a     (App. A steps 2-4)
+//   KID_JTVP       J^T w                                     (App. A Eq. arbitrary_jtvp_sequence)
+//   KID_JVP        J v                                       (App. B Eq. jac_ampl, forward mode)
+#include "kernels.h"
+#include "team_fft.cuh"
+
+namespace ptylm {
+
+__device__ __forceinline__ void red_add_c64(float2* addr, float2 v) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// Per-element error metric l(zeta, y) of Eq. ell_magnitude and its first two zeta-derivatives.
+struct EllTerms {
+    float l, dl, d2l;
+};
+__device__ __forceinline__ EllTerms ell_terms(int loss, float h, float zeta, float y) {
+    EllTerms t;
+    if (loss == 0) {  // Gaussian: (zeta - sqrt y)^2 / 2
+        const float d = zeta - sqrtf(y);
+        t.l = 0.5f * d * d;
+        t.dl = d;
+        t.d2l = 1.0f;
+    } else {          // Poisson: zeta^2 - y log zeta^2, with 0 log 0 = 0
+        t.l = h - (y > 0.0f ? y * logf(h) : 0.0f);
+        t.dl = 2.0f * zeta - 2.0f * y / zeta;
+        t.d2l = 2.0f + 2.0f * y / h;
+    }
+    return t;
+}
+
+// Block-wide FP64 sum of two per-thread values; thread 0 writes partials[blockIdx.x*2 + {0,1}].
+__device__ void block_reduce2_store(double s0, double s1, double* partials) {
+    __shared__ double red[2][32];
+    for (int off = 16; off > 0; off >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, off);
+        s1 += __shfl_down_sync(0xffffffffu, s1, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = s0;
+        red[1][warp] = s1;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        s0 = lane < nw ? red[0][lane] : 0.0;
+        s1 = lane < nw ? red[1][lane] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) {
+            s0 += __shfl_down_sync(0xffffffffu, s0, off);
+            s1 += __shfl_down_sync(0xffffffffu, s1, off);
+        }
+        if (lane == 0) {
+            partials[2 * blockIdx.x] = s0;
+            partials[2 * blockIdx.x + 1] = s1;
+        }
+    }
+}
+
+// Common prologue: twiddles into shared memory, team and thread indices.
+template <class G>
+struct TeamCtx {
+    float2* tw;
+    float2* sm;
+    int team, tid;
+};
+
+template <class G>
+__device__ __forceinline__ TeamCtx<G> team_setup(const float2* tw_g) {
+    extern __shared__ float4 dyn_smem_f4[];
+    float2* dyn = reinterpret_cast<float2*>(dyn_smem_f4);
+    TeamCtx<G> c;
+    c.tw = dyn;
+    for (int i = threadIdx.x; i < G::S; i += blockDim.x) c.tw[i] = tw_g[i];
+    c.team = threadIdx.x / G::T;
+    c.tid = threadIdx.x % G::T;
+    c.sm = dyn + G::S + c.team * G::M;
+    __syncthreads();
+    return c;
+}
+
+// Pass-1 gather: v[ax] = P[y][x] * A[r0 + y][c0 + x],  x = BX*ax + bx, thread = y*BX + bx.
+template <class G>
+__device__ __forceinline__ void gather_times_probe(float2* v, const float2* __restrict__ A,
+                                                   const float2* __restrict__ P, int nx, int r0,
+                                                   int c0, int tid) {
+    const int yrow = tid / G::BX, bx = tid % G::BX;
+    const float2* src = A + (size_t)(r0 + yrow) * nx + c0 + bx;
+    const float2* pr = P + yrow * G::S + bx;
+#pragma unroll
+    for (int ax = 0; ax < 32; ++ax) v[ax] = cmul(__ldg(pr + G::BX * ax), __ldg(src + G::BX * ax));
+}
+
+// Pass-1 scatter: out[r0 + y][c0 + x] += conj(P[y][x]) * v[ax].
+template <class G>
+__device__ __forceinline__ void scatter_times_conj_probe(const float2* v, float2* out,
+                                                         const float2* __restrict__ P, int nx,
+                                                         int r0, int c0, int tid) {
+    const int yrow = tid / G::BX, bx = tid % G::BX;
+    float2* dst = out + (size_t)(r0 + yrow) * nx + c0 + bx;
+    const float2* pr = P + yrow * G::S + bx;
+#pragma unroll
+    for (int ax = 0; ax < 32; ++ax) red_add_c64(dst + G::BX * ax, cmulc(v[ax], __ldg(pr + G::BX * ax)));
+}
+
+// ---------------------------------------------------------------------------------------
+// Forward model + error metric (+ cache and gradient when CACHE; intensities only when
+// INTENSITY).
+// ---------------------------------------------------------------------------------------
+template <int LS, bool CACHE, bool INTENSITY = false>
+__global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
+k_forward(PtyArgs a) {
+    using G = Geo<LS>;
+    TeamCtx<G> c = team_setup<G>(a.tw);
+    const float invS = 1.0f / G::S;
+    double acc_l = 0.0, acc_d = 0.0;
+    float2 v[32];
+    for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
+        const int2 rc = a.pos[k];
+        gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
+        team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
+        const int kx = freq_kx<G>(c.tid);
+        const float* yk = a.y + (size_t)k * G::M;
+        float sl = 0.0f, sd = 0.0f;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            const int ky = freq_ky<G>(c.tid, e);
+            const float2 ps = v[e] * invS;                      // orthonormal psihat
+            const float h = ps.x * ps.x + ps.y * ps.y + a.b;    // Eq. expected_count
+            if constexpr (INTENSITY) {
+                a.out_real[(size_t)k * G::M + ky * G::S + kx] = h;
+                continue;
+            }
+            const float zeta = sqrtf(h);                        // Eq. magnitude
+            const EllTerms t = ell_terms(a.loss, h, zeta, __ldg(yk + ky * G::S + kx));
+            sl += t.l;
+            if constexpr (CACHE) {
+                sd += t.dl * t.dl;
+                const float inv_zeta = 1.0f / zeta;
+                a.a_cache[(size_t)k * G::M + e * G::T + c.tid] = ps * (sqrtf(t.d2l) * inv_zeta);
+                v[e] = ps * (t.dl * inv_zeta * invS);  // psihat grad l / zeta, inverse 1/S folded in
+            }
+        }
+        acc_l += (double)sl;
+        acc_d += (double)sd;
+        if constexpr (CACHE) {
+            team_fft_inv<G>(v, c.sm, c.tw, c.tid);
+            scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
+        }
+        team_sync<G>();
+    }
+    block_reduce2_store(acc_l, acc_d, a.partials);
+}
+
+// ---------------------------------------------------------------------------------------
+// GGN-vector product: out += J^T (Hess l . J v), with t = Re(conj(a) F(P S_k v)),
+// chihat = a t (App. A steps 2-4; the closed-form diagonal Hessian of step 3(ii) is folded
+// into a).  out must hold lambda D v (or zero) on entry.
+// ---------------------------------------------------------------------------------------
+template <int LS>
+__global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
+k_ggn_matvec(PtyArgs a) {
+    using G = Geo<LS>;
+    TeamCtx<G> c = team_setup<G>(a.tw);
+    const float invM = 1.0f / G::M;
+    float2 v[32];
+    for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
+        const int2 rc = a.pos[k];
+        gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
+        team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
+        const float2* ak = a.a_cache + (size_t)k * G::M + c.tid;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            const float2 av = __ldcs(ak + e * G::T);
+            const float t = (av.x * v[e].x + av.y * v[e].y) * invM;
+            v[e] = av * t;
+        }
+        team_fft_inv<G>(v, c.sm, c.tw, c.tid);
+        scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
+        team_sync<G>();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// J^T w: chihat = psihat w / zeta, recomputing psihat from (O, P).  out += result.
+// ---------------------------------------------------------------------------------------
+template <int LS>
+__global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
+k_jtvp(PtyArgs a) {
+    using G = Geo<LS>;
+    TeamCtx<G> c = team_setup<G>(a.tw);
+    const float invS = 1.0f / G::S;
+    float2 v[32];
+    for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
+        const int2 rc = a.pos[k];
+        gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
+        team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
+        const int kx = freq_kx<G>(c.tid);
+        const float* wk = a.w + (size_t)k * G::M;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            const int ky = freq_ky<G>(c.tid, e);
+            const float2 ps = v[e] * invS;
+            const float zeta = sqrtf(ps.x * ps.x + ps.y * ps.y + a.b);
+            v[e] = ps * (__ldg(wk + ky * G::S + kx) / zeta * invS);
+        }
+        team_fft_inv<G>(v, c.sm, c.tw, c.tid);
+        scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
+        team_sync<G>();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// J v = Re(conj(psihat) F(P S_k v)) / zeta, written in natural [K][S][S] order.  psihat is
+// recomputed and parked in a per-team global scratch slot while the direction is transformed.
+// ---------------------------------------------------------------------------------------
+template <int LS>
+__global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
+k_jvp(PtyArgs a) {
+    using G = Geo<LS>;
+    TeamCtx<G> c = team_setup<G>(a.tw);
+    const float invS = 1.0f / G::S;
+    float2* slot = a.scratch + (size_t)(blockIdx.x * G::TEAMS + c.team) * G::M + c.tid;
+    float2 v[32];
+    for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
+        const int2 rc = a.pos[k];
+        gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
+        team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) slot[e * G::T] = v[e];
+        team_sync<G>();
+        gather_times_probe<G>(v, a.V, a.P, a.nx, rc.x, rc.y, c.tid);
+        team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
+        const int kx = freq_kx<G>(c.tid);
+        float* ok = a.out_real + (size_t)k * G::M;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            const int ky = freq_ky<G>(c.tid, e);
+            const float2 ps = slot[e * G::T] * invS;
+            const float2 dps = v[e] * invS;
+            const float zeta = sqrtf(ps.x * ps.x + ps.y * ps.y + a.b);
+            ok[ky * G::S + kx] = (ps.x * dps.x + ps.y * dps.y) / zeta;
+        }
+        team_sync<G>();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host-side dispatch.
+// ---------------------------------------------------------------------------------------
+int cta_threads(int LS) {
+    switch (LS) {
+        case 5: return Geo<5>::THREADS;
+        case 6: return Geo<6>::THREADS;
+        case 7: return Geo<7>::THREADS;
+    }
+    return 0;
+}
+
+int cta_teams(int LS) {
+    switch (LS) {
+        case 5: return Geo<5>::TEAMS;
+        case 6: return Geo<6>::TEAMS;
+        case 7: return Geo<7>::TEAMS;
+    }
+    return 0;
+}
+
+size_t cta_smem_bytes(int LS) {
+    switch (LS) {
+        case 5: return sizeof(float2) * (Geo<5>::S + Geo<5>::TEAMS * Geo<5>::M);
+        case 6: return sizeof(float2) * (Geo<6>::S + Geo<6>::TEAMS * Geo<6>::M);
+        case 7: return sizeof(float2) * (Geo<7>::S + Geo<7>::TEAMS * Geo<7>::M);
+    }
+    return 0;
+}
+
+template <int LS>
+static const void* kernel_ptr(int kid) {
+    switch (kid) {
+        case KID_FWD_LOSS: return (const void*)k_forward<LS, false>;
+        case KID_FWD_CACHE: return (const void*)k_forward<LS, true>;
+        case KID_MATVEC: return (const void*)k_ggn_matvec<LS>;
+        case KID_JTVP: return (const void*)k_jtvp<LS>;
+        case KID_JVP: return (const void*)k_jvp<LS>;
+        case KID_FWD_INTENSITY: return (const void*)k_forward<LS, false, true>;
+    }
+    return nullptr;
+}
+
+static const void* kernel_for(int LS, int kid) {
+    switch (LS) {
+        case 5: return kernel_ptr<5>(kid);
+        case 6: return kernel_ptr<6>(kid);
+        case 7: return kernel_ptr<7>(kid);
+    }
+    return nullptr;
+}
+
+cudaError_t kernel_prepare(int LS, int kid, int* ctas_per_sm) {
+    const void* fn = kernel_for(LS, kid);
+    if (!fn) return cudaErrorInvalidValue;
+    const size_t smem = cta_smem_bytes(LS);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, cta_threads(LS), smem);
+}
+
+cudaError_t kernel_launch(int LS, int kid, const PtyArgs& a, int grid, cudaStream_t stream) {
+    const void* fn = kernel_for(LS, kid);
+    if (!fn || grid <= 0) return cudaErrorInvalidValue;
+    PtyArgs copy = a;
+    void* args[] = {&copy};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(cta_threads(LS)), args, cta_smem_bytes(LS), stream);
+}
+
+}  // namespace ptylm

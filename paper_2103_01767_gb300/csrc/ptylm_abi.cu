@@ -1,0 +1,872 @@
+// ptylm_abi.cu -- C-ABI entry points (include/ptylm.h), context management, the CG and
+// LM vector kernels with FP64 reductions, and the truncated LM driver (Algorithm 1 of
+// arXiv 2103.01767, Sec. 4.2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ptylm.h"
+#include "kernels.h"
+
+using namespace ptylm;
+
+// ---------------------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static ptylm_status fail(ptylm_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define CUDA_TRY(expr)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (expr);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(PTYLM_ERR_CUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                               \
+    } while (0)
+
+#define STATUS_TRY(expr)                      \
+    do {                                      \
+        ptylm_status s_ = (expr);             \
+        if (s_ != PTYLM_OK) return s_;        \
+    } while (0)
+
+// ---------------------------------------------------------------------------------------
+// Device scalar slots (FP64) and reduction kernels
+// ---------------------------------------------------------------------------------------
+enum Slot {
+    S_F = 0, S_DL2 = 1,           // forward: f, ||grad_zeta l||^2
+    S_RR = 2, S_PQ = 3, S_ALPHA = 4, S_RRNEW = 5, S_BETA = 6,
+    S_GG = 7,                     // ||g||^2
+    S_DD = 8, S_DG = 9, S_DR = 10, // step dots for the predicted reduction
+    S_ER = 11, S_EI = 12, S_NO = 13, S_NR = 14,  // error metric sums
+    S_TMP = 15,
+    S_COUNT = 24
+};
+enum FinalOp { OP_NONE = 0, OP_ALPHA = 1, OP_BETA = 2 };
+
+static constexpr int VEC_THREADS = 256;
+static constexpr int MAX_PART_WIDTH = 4;
+
+// Real-coordinate inner products sum(a.re*b.re + a.im*b.im) accumulate in FP64.
+__device__ __forceinline__ double rdot(float2 a, float2 b) {
+    return (double)a.x * (double)b.x + (double)a.y * (double)b.y;
+}
+
+// Block sum of up to 4 FP64 values -> part[blockIdx.x * W + c].
+template <int W>
+__device__ void block_sum_store(double (&s)[W], double* part) {
+    __shared__ double red[W][VEC_THREADS / 32];
+#pragma unroll
+    for (int c = 0; c < W; ++c)
+        for (int off = 16; off > 0; off >>= 1) s[c] += __shfl_down_sync(0xffffffffu, s[c], off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < W; ++c) red[c][warp] = s[c];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            double t = 0.0;
+            for (int w = 0; w < VEC_THREADS / 32; ++w) t += red[c][w];
+            part[blockIdx.x * W + c] = t;
+        }
+    }
+}
+
+// Sum columns of part[nb][W] in a fixed order into s[dst + c]; then apply `op`.
+__global__ void k_finalize(const double* __restrict__ part, int nb, int W, double* s, int dst, int op) {
+    __shared__ double red[MAX_PART_WIDTH][VEC_THREADS];
+    for (int c = 0; c < W; ++c) {
+        double t = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) t += part[b * W + c];
+        red[c][threadIdx.x] = t;
+    }
+    __syncthreads();
+    for (int half = blockDim.x / 2; half > 0; half >>= 1) {
+        if ((int)threadIdx.x < half)
+            for (int c = 0; c < W; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + half];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < W; ++c) s[dst + c] = red[c][0];
+        if (op == OP_ALPHA) {
+            s[S_ALPHA] = s[S_RR] / s[S_PQ];
+        } else if (op == OP_BETA) {
+            s[S_BETA] = s[S_RRNEW] / s[S_RR];
+            s[S_RR] = s[S_RRNEW];
+        }
+    }
+}
+
+// out = lambda * D * v   (D == NULL: identity).  Initialises the matvec accumulator.
+__global__ void k_damping_init(const float2* __restrict__ v, const float* __restrict__ D, float lambda,
+                               float2* __restrict__ out, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float d = lambda * (D ? D[i] : 1.0f);
+        const float2 x = v[i];
+        out[i] = make_float2(d * x.x, d * x.y);
+    }
+}
+
+// partials of (a.b, c.d, e.f) -- any of the pairs may be unused (W picks how many).
+template <int W>
+__global__ void k_dots(const float2* __restrict__ a0, const float2* __restrict__ b0,
+                       const float2* __restrict__ a1, const float2* __restrict__ b1,
+                       const float2* __restrict__ a2, const float2* __restrict__ b2, long n,
+                       double* part) {
+    double s[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) s[c] = 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        s[0] += rdot(a0[i], b0[i]);
+        if constexpr (W > 1) s[1] += rdot(a1[i], b1[i]);
+        if constexpr (W > 2) s[2] += rdot(a2[i], b2[i]);
+    }
+    block_sum_store<W>(s, part);
+}
+
+// CG start: r = -g - q, p = r; partial r.r
+__global__ void k_cg_start(const float2* __restrict__ g, const float2* __restrict__ q, float2* __restrict__ r,
+                           float2* __restrict__ p, long n, double* part) {
+    double s[1] = {0.0};
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float2 gi = g[i], qi = q[i];
+        const float2 ri = make_float2(-gi.x - qi.x, -gi.y - qi.y);
+        r[i] = ri;
+        p[i] = ri;
+        s[0] += rdot(ri, ri);
+    }
+    block_sum_store<1>(s, part);
+}
+
+// x += alpha p, r -= alpha q; partial r.r   (alpha read from the device scalar slot)
+__global__ void k_cg_update(float2* __restrict__ x, float2* __restrict__ r, const float2* __restrict__ p,
+                            const float2* __restrict__ q, const double* __restrict__ sc, long n, double* part) {
+    const float alpha = (float)sc[S_ALPHA];
+    double s[1] = {0.0};
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float2 pi = p[i], qi = q[i];
+        float2 xi = x[i], ri = r[i];
+        xi.x += alpha * pi.x;
+        xi.y += alpha * pi.y;
+        ri.x -= alpha * qi.x;
+        ri.y -= alpha * qi.y;
+        x[i] = xi;
+        r[i] = ri;
+        s[0] += rdot(ri, ri);
+    }
+    block_sum_store<1>(s, part);
+}
+
+// p = r + beta p;  q = lambda D p  (the damping term that starts the next matvec)
+__global__ void k_cg_direction(const float2* __restrict__ r, float2* __restrict__ p, float2* __restrict__ q,
+                               const float* __restrict__ D, float lambda, const double* __restrict__ sc, long n) {
+    const float beta = (float)sc[S_BETA];
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float2 ri = r[i], pi = p[i];
+        const float2 pn = make_float2(ri.x + beta * pi.x, ri.y + beta * pi.y);
+        p[i] = pn;
+        const float d = lambda * (D ? D[i] : 1.0f);
+        q[i] = make_float2(d * pn.x, d * pn.y);
+    }
+}
+
+// z = x + d
+__global__ void k_add(const float2* __restrict__ x, const float2* __restrict__ d, float2* __restrict__ z, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float2 a = x[i], b = d[i];
+        z[i] = make_float2(a.x + b.x, a.y + b.y);
+    }
+}
+
+// Object-error sums over a mask: <O, O_ref> (re, im), ||O||^2, ||O_ref||^2.
+__global__ void k_err_sums(const float2* __restrict__ O, const float2* __restrict__ R,
+                           const uint8_t* __restrict__ mask, long n, double* part) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        if (mask && !mask[i]) continue;
+        const float2 o = O[i], r = R[i];
+        s[0] += (double)o.x * r.x + (double)o.y * r.y;   // Re conj(O) R
+        s[1] += (double)o.x * r.y - (double)o.y * r.x;   // Im conj(O) R
+        s[2] += (double)o.x * o.x + (double)o.y * o.y;
+        s[3] += (double)r.x * r.x + (double)r.y * r.y;
+    }
+    block_sum_store<4>(s, part);
+}
+
+// ---------------------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------------------
+struct ptylm_ctx {
+    ptylm_desc d;
+    int LS = 0, S = 0, M = 0;
+    long N = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    int grid[KID_COUNT] = {0};
+    int vec_grid = 0;
+    size_t allocated = 0;
+    std::vector<void*> allocations;
+
+    int2* pos = nullptr;
+    const float* y = nullptr;
+    float2* tw = nullptr;
+    float2* a_cache = nullptr;
+    float2* grad = nullptr;
+    float2* O_lin = nullptr;
+    float2* P_lin = nullptr;
+    double* partials = nullptr;
+    int partials_cap = 0;
+    double* scal = nullptr;        // device FP64 scalars [S_COUNT]
+    double* scal_host = nullptr;   // pinned mirror
+    float2* jvp_scratch = nullptr;
+    bool has_lin = false;
+    double f_lin = 0.0, dl2_lin = 0.0;
+
+    // CG / LM vectors (allocated on first use)
+    float2 *cg_x = nullptr, *cg_r = nullptr, *cg_p = nullptr, *cg_q = nullptr, *trial = nullptr;
+    // staging for host pointers
+    float2 *stage_a = nullptr, *stage_b = nullptr, *stage_P = nullptr;
+
+    // instrumentation
+    long long launches = 0;
+    bool prof_on = false;
+    struct Rec { int kid; cudaEvent_t a, b; };
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<Rec> recs;
+    double prof_ms[KID_COUNT] = {0};
+    long long prof_n[KID_COUNT] = {0};
+};
+
+// Accumulate the elapsed time of every recorded launch (synchronises the stream).
+static ptylm_status prof_flush(ptylm_ctx* c) {
+    if (c->recs.empty()) return PTYLM_OK;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (auto& r : c->recs) {
+        float ms = 0.0f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+        c->prof_ms[r.kid] += ms;
+        c->prof_n[r.kid] += 1;
+        c->ev_free.push_back(r.a);
+        c->ev_free.push_back(r.b);
+    }
+    c->recs.clear();
+    return PTYLM_OK;
+}
+
+static ptylm_status take_event(ptylm_ctx* c, cudaEvent_t* e) {
+    if (c->ev_free.empty()) {
+        CUDA_TRY(cudaEventCreate(e));
+        return PTYLM_OK;
+    }
+    *e = c->ev_free.back();
+    c->ev_free.pop_back();
+    return PTYLM_OK;
+}
+
+// Launch a per-position kernel, timing it with events when profiling is on.
+static ptylm_status launch(ptylm_ctx* c, int kid, const PtyArgs& a) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->prof_on) {
+        if (c->recs.size() >= 2048) STATUS_TRY(prof_flush(c));
+        STATUS_TRY(take_event(c, &e0));
+        STATUS_TRY(take_event(c, &e1));
+        CUDA_TRY(cudaEventRecord(e0, c->stream));
+    }
+    CUDA_TRY(kernel_launch(c->LS, kid, a, c->grid[kid], c->stream));
+    ++c->launches;
+    if (c->prof_on) {
+        CUDA_TRY(cudaEventRecord(e1, c->stream));
+        c->recs.push_back({kid, e0, e1});
+    }
+    return PTYLM_OK;
+}
+
+// Count a vector-kernel launch and check it was accepted.
+static ptylm_status vec_launched(ptylm_ctx* c) {
+    ++c->launches;
+    CUDA_TRY(cudaGetLastError());
+    return PTYLM_OK;
+}
+
+static ptylm_status ctx_alloc(ptylm_ctx* c, void** p, size_t bytes, const char* what) {
+    if (c->d.workspace_budget && c->allocated + bytes > c->d.workspace_budget)
+        return fail(PTYLM_ERR_NOMEM, "workspace budget %zu bytes exceeded allocating %s (%zu bytes, %zu in use)",
+                    c->d.workspace_budget, what, bytes, c->allocated);
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PTYLM_ERR_NOMEM, "cudaMalloc(%zu) for %s failed: %s", bytes, what, cudaGetErrorString(e));
+    }
+    c->allocated += bytes;
+    c->allocations.push_back(*p);
+    return PTYLM_OK;
+}
+
+template <class T>
+static ptylm_status ctx_alloc_t(ptylm_ctx* c, T** p, size_t count, const char* what) {
+    void* q = nullptr;
+    ptylm_status s = ctx_alloc(c, &q, count * sizeof(T), what);
+    *p = static_cast<T*>(q);
+    return s;
+}
+
+static void ctx_free_all(ptylm_ctx* c) {
+    for (auto& r : c->recs) {
+        c->ev_free.push_back(r.a);
+        c->ev_free.push_back(r.b);
+    }
+    c->recs.clear();
+    for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
+    c->ev_free.clear();
+    for (void* p : c->allocations) cudaFree(p);
+    c->allocations.clear();
+    if (c->scal_host) cudaFreeHost(c->scal_host);
+    c->scal_host = nullptr;
+}
+
+static bool is_host_pointer(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return attr.type == cudaMemoryTypeHost || attr.type == cudaMemoryTypeUnregistered;
+}
+
+static int vec_blocks(const ptylm_ctx* c) { return c->vec_grid; }
+
+// Sum the width-W partials of `nb` blocks into scalar slots [dst, dst+W).
+static ptylm_status finalize(ptylm_ctx* c, int nb, int W, int dst, int op) {
+    k_finalize<<<1, VEC_THREADS, 0, c->stream>>>(c->partials, nb, W, c->scal, dst, op);
+    STATUS_TRY(vec_launched(c));
+    return PTYLM_OK;
+}
+
+static ptylm_status read_scalars(ptylm_ctx* c, int first, int count) {
+    CUDA_TRY(cudaMemcpyAsync(c->scal_host + first, c->scal + first, sizeof(double) * count,
+                             cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return PTYLM_OK;
+}
+
+static ptylm_status dots(ptylm_ctx* c, int W, const float2* a0, const float2* b0, const float2* a1,
+                         const float2* b1, const float2* a2, const float2* b2, int dst, int op = OP_NONE) {
+    const int nb = vec_blocks(c);
+    if (W == 1) k_dots<1><<<nb, VEC_THREADS, 0, c->stream>>>(a0, b0, a1, b1, a2, b2, c->N, c->partials);
+    else if (W == 2) k_dots<2><<<nb, VEC_THREADS, 0, c->stream>>>(a0, b0, a1, b1, a2, b2, c->N, c->partials);
+    else k_dots<3><<<nb, VEC_THREADS, 0, c->stream>>>(a0, b0, a1, b1, a2, b2, c->N, c->partials);
+    STATUS_TRY(vec_launched(c));
+    return finalize(c, nb, W, dst, op);
+}
+
+static PtyArgs base_args(const ptylm_ctx* c) {
+    PtyArgs a;
+    memset(&a, 0, sizeof a);
+    a.pos = c->pos;
+    a.y = c->y;
+    a.tw = c->tw;
+    a.K = c->d.K;
+    a.nx = c->d.nx;
+    a.b = c->d.background;
+    a.loss = c->d.loss;
+    a.partials = c->partials;
+    return a;
+}
+
+// ---------------------------------------------------------------------------------------
+// Internal operations on device pointers
+// ---------------------------------------------------------------------------------------
+
+// Forward model + loss; cache=1 also stores a, the linearisation point and grad f.
+static ptylm_status op_forward(ptylm_ctx* c, const float2* O, const float2* P, int cache) {
+    const int kid = cache ? KID_FWD_CACHE : KID_FWD_LOSS;
+    if (cache) {
+        if (O != c->O_lin) CUDA_TRY(cudaMemcpyAsync(c->O_lin, O, sizeof(float2) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+        if (P != c->P_lin) CUDA_TRY(cudaMemcpyAsync(c->P_lin, P, sizeof(float2) * c->M, cudaMemcpyDeviceToDevice, c->stream));
+        CUDA_TRY(cudaMemsetAsync(c->grad, 0, sizeof(float2) * c->N, c->stream));
+        c->has_lin = false;
+    }
+    if (c->d.K == 0) {
+        CUDA_TRY(cudaMemsetAsync(c->scal + S_F, 0, 2 * sizeof(double), c->stream));
+    } else {
+        PtyArgs a = base_args(c);
+        a.O = cache ? c->O_lin : O;
+        a.P = cache ? c->P_lin : P;
+        a.a_cache = c->a_cache;
+        a.out = c->grad;
+        STATUS_TRY(launch(c, kid, a));
+        STATUS_TRY(finalize(c, c->grid[kid], 2, S_F, OP_NONE));
+    }
+    if (cache) c->has_lin = true;
+    return PTYLM_OK;
+}
+
+// out = (G + lambda D) v at the linearisation point (device pointers).
+static ptylm_status op_matvec(ptylm_ctx* c, const float2* v, double lambda, const float* D, float2* out) {
+    const int nb = vec_blocks(c);
+    k_damping_init<<<nb, VEC_THREADS, 0, c->stream>>>(v, D, (float)lambda, out, c->N);
+    STATUS_TRY(vec_launched(c));
+    if (c->d.K == 0) return PTYLM_OK;
+    PtyArgs a = base_args(c);
+    a.O = v;
+    a.P = c->P_lin;
+    a.a_cache = c->a_cache;
+    a.out = out;
+    STATUS_TRY(launch(c, KID_MATVEC, a));
+    return PTYLM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// C-ABI
+// ---------------------------------------------------------------------------------------
+extern "C" {
+
+const char* ptylm_strerror(ptylm_status s) {
+    switch (s) {
+        case PTYLM_OK: return "success";
+        case PTYLM_ERR_ARG: return "invalid argument";
+        case PTYLM_ERR_NOMEM: return "out of device memory or workspace budget";
+        case PTYLM_ERR_CUDA: return "CUDA runtime error";
+        case PTYLM_ERR_NAN: return "non-finite value in a reduction";
+        case PTYLM_ERR_TIMEOUT: return "bounded device wait timed out";
+        case PTYLM_ERR_STALLED: return "LM damping overflowed without an accepted step";
+        case PTYLM_ERR_STATE: return "no linearisation point (call forward_loss with cache=1)";
+        case PTYLM_WARN_CG_MAXIT: return "CG reached its iteration limit";
+    }
+    return "unknown status";
+}
+
+const char* ptylm_last_error(void) { return g_last_error.c_str(); }
+
+void ptylm_default_lm_params(ptylm_lm_params* p, int loss) {
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->mu0 = 1e-5;
+    p->mu_min = 1e-8;
+    p->kappa = 4.0;
+    p->nu = 1.0;
+    p->rho_min = 1e-4;
+    p->beta = loss == PTYLM_LOSS_POISSON ? 0.9 : 0.1;
+    p->mu_max = 1e16;
+    p->max_outer = 50;
+    p->max_cg = 100;
+    p->fixed_cg = 0;
+    p->target_err = 0.0;
+}
+
+ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* positions_dev,
+                     const float* y_dev, void* stream) {
+    g_last_error.clear();
+    if (!out || !desc) return fail(PTYLM_ERR_ARG, "ctx and desc must be non-NULL");
+    *out = nullptr;
+    const ptylm_desc& d = *desc;
+    if (d.my != d.mx) return fail(PTYLM_ERR_ARG, "probe must be square (my=%d, mx=%d)", d.my, d.mx);
+    int LS = 0;
+    if (d.my == 32) LS = 5;
+    else if (d.my == 64) LS = 6;
+    else if (d.my == 128) LS = 7;
+    else return fail(PTYLM_ERR_ARG, "probe side %d unsupported (32, 64 or 128)", d.my);
+    if (d.ny < d.my || d.nx < d.mx) return fail(PTYLM_ERR_ARG, "object %dx%d smaller than probe %dx%d", d.ny, d.nx, d.my, d.mx);
+    if (d.K < 0) return fail(PTYLM_ERR_ARG, "K must be >= 0");
+    if (d.loss != PTYLM_LOSS_GAUSSIAN && d.loss != PTYLM_LOSS_POISSON) return fail(PTYLM_ERR_ARG, "unknown loss %d", d.loss);
+    if (!(d.background > 0.0f) || !std::isfinite(d.background)) return fail(PTYLM_ERR_ARG, "background must be finite and > 0");
+    if (d.joint != 0) return fail(PTYLM_ERR_ARG, "joint object+probe contexts are not available in this build");
+    if (d.K > 0 && (!positions_dev || !y_dev)) return fail(PTYLM_ERR_ARG, "positions and y must be non-NULL when K > 0");
+    if ((long)d.ny * d.nx > (1L << 31)) return fail(PTYLM_ERR_ARG, "object too large");
+
+    // Validate positions on the host before anything is allocated or launched.
+    std::vector<int32_t> hpos((size_t)d.K * 2);
+    if (d.K > 0) {
+        cudaError_t e = cudaMemcpy(hpos.data(), positions_dev, sizeof(int32_t) * 2 * d.K, cudaMemcpyDefault);
+        if (e != cudaSuccess) return fail(PTYLM_ERR_CUDA, "reading positions: %s", cudaGetErrorString(e));
+        for (int k = 0; k < d.K; ++k) {
+            const int r = hpos[2 * k], cc = hpos[2 * k + 1];
+            if (r < 0 || cc < 0 || r > d.ny - d.my || cc > d.nx - d.mx)
+                return fail(PTYLM_ERR_ARG, "position %d = (%d, %d) outside [0, %d] x [0, %d]", k, r, cc,
+                            d.ny - d.my, d.nx - d.mx);
+        }
+    }
+
+    ptylm_ctx* c = new ptylm_ctx();
+    c->d = d;
+    c->LS = LS;
+    c->S = 1 << LS;
+    c->M = c->S * c->S;
+    c->N = (long)d.ny * d.nx;
+    c->stream = static_cast<cudaStream_t>(stream);
+    auto bail = [&](ptylm_status s) {
+        ctx_free_all(c);
+        delete c;
+        return s;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(PTYLM_ERR_CUDA, "no usable CUDA device"));
+    }
+    const int teams = cta_teams(LS);
+    for (int kid = 0; kid < KID_COUNT; ++kid) {
+        int per_sm = 0;
+        cudaError_t e = kernel_prepare(LS, kid, &per_sm);
+        if (e != cudaSuccess || per_sm <= 0)
+            return bail(fail(PTYLM_ERR_CUDA, "kernel %d for side %d cannot launch: %s", kid, c->S,
+                             e != cudaSuccess ? cudaGetErrorString(e) : "zero occupancy"));
+        const int need = std::max(1, (d.K + teams - 1) / teams);
+        c->grid[kid] = std::min(per_sm * c->num_sms, need);
+    }
+    c->vec_grid = std::min<long>(c->num_sms * 8L, std::max<long>(1, (c->N + VEC_THREADS - 1) / VEC_THREADS));
+    c->partials_cap = std::max(c->vec_grid, *std::max_element(c->grid, c->grid + KID_COUNT));
+
+    ptylm_status s;
+    if ((s = ctx_alloc_t(c, &c->pos, std::max(1, d.K), "positions")) != PTYLM_OK) return bail(s);
+    if ((s = ctx_alloc_t(c, &c->tw, c->S, "twiddles")) != PTYLM_OK) return bail(s);
+    if ((s = ctx_alloc_t(c, &c->a_cache, (size_t)d.K * c->M, "frequency cache")) != PTYLM_OK) return bail(s);
+    if ((s = ctx_alloc_t(c, &c->grad, c->N, "gradient")) != PTYLM_OK) return bail(s);
+    if ((s = ctx_alloc_t(c, &c->O_lin, c->N, "object linearisation point")) != PTYLM_OK) return bail(s);
+    if ((s = ctx_alloc_t(c, &c->P_lin, c->M, "probe linearisation point")) != PTYLM_OK) return bail(s);
+    if ((s = ctx_alloc_t(c, &c->partials, (size_t)c->partials_cap * MAX_PART_WIDTH, "partials")) != PTYLM_OK) return bail(s);
+    if ((s = ctx_alloc_t(c, &c->scal, S_COUNT, "scalars")) != PTYLM_OK) return bail(s);
+    if (cudaMallocHost((void**)&c->scal_host, sizeof(double) * S_COUNT) != cudaSuccess) {
+        cudaGetLastError();
+        c->scal_host = nullptr;
+        return bail(fail(PTYLM_ERR_NOMEM, "pinned scalar buffer"));
+    }
+
+    // Twiddles W_S^j = exp(-2 pi i j / S) in FP64, rounded once to FP32.
+    std::vector<float2> htw(c->S);
+    for (int j = 0; j < c->S; ++j) {
+        const double ang = 2.0 * M_PI * (double)j / (double)c->S;
+        htw[j] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+    }
+    std::vector<int2> hp((size_t)std::max(1, d.K));
+    for (int k = 0; k < d.K; ++k) hp[k] = make_int2(hpos[2 * k], hpos[2 * k + 1]);
+    if (cudaMemcpyAsync(c->tw, htw.data(), sizeof(float2) * c->S, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(c->pos, hp.data(), sizeof(int2) * std::max(1, d.K), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->scal, 0, sizeof(double) * S_COUNT, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        return bail(fail(PTYLM_ERR_CUDA, "uploading context tables: %s", cudaGetErrorString(e)));
+    }
+    c->y = y_dev;
+    *out = c;
+    return PTYLM_OK;
+}
+
+ptylm_status forward_intensity(ptylm_ctx* c, const ptylm_c64* O, const ptylm_c64* P, float* h_out) {
+    g_last_error.clear();
+    if (!c || !O || !P || !h_out) return fail(PTYLM_ERR_ARG, "ctx, O, P and h_out must be non-NULL");
+    if (c->d.K == 0) return PTYLM_OK;
+    PtyArgs a = base_args(c);
+    a.O = reinterpret_cast<const float2*>(O);
+    a.P = reinterpret_cast<const float2*>(P);
+    a.out_real = h_out;
+    STATUS_TRY(launch(c, KID_FWD_INTENSITY, a));
+    return PTYLM_OK;
+}
+
+ptylm_status ptylm_profile(ptylm_ctx* c, int enable) {
+    if (!c) return fail(PTYLM_ERR_ARG, "ctx must be non-NULL");
+    if (enable) {
+        STATUS_TRY(prof_flush(c));
+        for (int k = 0; k < KID_COUNT; ++k) {
+            c->prof_ms[k] = 0.0;
+            c->prof_n[k] = 0;
+        }
+        c->launches = 0;
+    }
+    c->prof_on = enable != 0;
+    return PTYLM_OK;
+}
+
+ptylm_status ptylm_profile_read(ptylm_ctx* c, int kernel, double* total_ms, long long* launches) {
+    if (!c) return fail(PTYLM_ERR_ARG, "ctx must be non-NULL");
+    if (kernel < -1 || kernel >= KID_COUNT) return fail(PTYLM_ERR_ARG, "unknown kernel id %d", kernel);
+    STATUS_TRY(prof_flush(c));
+    if (kernel == -1) {
+        if (total_ms) *total_ms = 0.0;
+        if (launches) *launches = c->launches;
+    } else {
+        if (total_ms) *total_ms = c->prof_ms[kernel];
+        if (launches) *launches = c->prof_n[kernel];
+    }
+    return PTYLM_OK;
+}
+
+ptylm_status lm_destroy(ptylm_ctx* c) {
+    if (!c) return PTYLM_OK;
+    cudaStreamSynchronize(c->stream);
+    ctx_free_all(c);
+    delete c;
+    return PTYLM_OK;
+}
+
+ptylm_status forward_loss(ptylm_ctx* c, const ptylm_c64* O, const ptylm_c64* P, double* f_host,
+                          double* dl_norm2_host, int cache) {
+    g_last_error.clear();
+    if (!c || !O || !P) return fail(PTYLM_ERR_ARG, "ctx, O and P must be non-NULL");
+    STATUS_TRY(op_forward(c, reinterpret_cast<const float2*>(O), reinterpret_cast<const float2*>(P), cache));
+    STATUS_TRY(read_scalars(c, S_F, 2));
+    const double f = c->scal_host[S_F], dl2 = c->scal_host[S_DL2];
+    if (cache) {
+        c->f_lin = f;
+        c->dl2_lin = dl2;
+    }
+    if (f_host) *f_host = f;
+    if (dl_norm2_host) *dl_norm2_host = dl2;
+    if (!std::isfinite(f) || !std::isfinite(dl2)) return fail(PTYLM_ERR_NAN, "loss is not finite (f=%g)", f);
+    return PTYLM_OK;
+}
+
+ptylm_status gradient(ptylm_ctx* c, ptylm_c64* gO, ptylm_c64* gP) {
+    g_last_error.clear();
+    if (!c || !gO) return fail(PTYLM_ERR_ARG, "ctx and gO must be non-NULL");
+    if (gP) return fail(PTYLM_ERR_ARG, "probe gradient needs a joint context");
+    if (!c->has_lin) return fail(PTYLM_ERR_STATE, "no linearisation point");
+    CUDA_TRY(cudaMemcpyAsync(gO, c->grad, sizeof(float2) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    return PTYLM_OK;
+}
+
+ptylm_status jvp(ptylm_ctx* c, const ptylm_c64* vO, const ptylm_c64* vP, float* out) {
+    g_last_error.clear();
+    if (!c || !vO || !out) return fail(PTYLM_ERR_ARG, "ctx, vO and out must be non-NULL");
+    if (vP) return fail(PTYLM_ERR_ARG, "probe direction needs a joint context");
+    if (!c->has_lin) return fail(PTYLM_ERR_STATE, "no linearisation point");
+    if (c->d.K == 0) return PTYLM_OK;
+    if (!c->jvp_scratch)
+        STATUS_TRY(ctx_alloc_t(c, &c->jvp_scratch, (size_t)c->grid[KID_JVP] * cta_teams(c->LS) * c->M, "jvp scratch"));
+    PtyArgs a = base_args(c);
+    a.O = c->O_lin;
+    a.V = reinterpret_cast<const float2*>(vO);
+    a.P = c->P_lin;
+    a.out_real = out;
+    a.scratch = c->jvp_scratch;
+    STATUS_TRY(launch(c, KID_JVP, a));
+    return PTYLM_OK;
+}
+
+ptylm_status jtvp(ptylm_ctx* c, const float* w, ptylm_c64* outO, ptylm_c64* outP) {
+    g_last_error.clear();
+    if (!c || !w || !outO) return fail(PTYLM_ERR_ARG, "ctx, w and outO must be non-NULL");
+    if (outP) return fail(PTYLM_ERR_ARG, "probe part needs a joint context");
+    if (!c->has_lin) return fail(PTYLM_ERR_STATE, "no linearisation point");
+    CUDA_TRY(cudaMemsetAsync(outO, 0, sizeof(float2) * c->N, c->stream));
+    if (c->d.K == 0) return PTYLM_OK;
+    PtyArgs a = base_args(c);
+    a.O = c->O_lin;
+    a.P = c->P_lin;
+    a.w = w;
+    a.out = reinterpret_cast<float2*>(outO);
+    STATUS_TRY(launch(c, KID_JTVP, a));
+    return PTYLM_OK;
+}
+
+ptylm_status ggn_matvec(ptylm_ctx* c, const ptylm_c64* vO, const ptylm_c64* vP, double lambda,
+                        const float* D, ptylm_c64* outO, ptylm_c64* outP) {
+    g_last_error.clear();
+    if (!c || !vO || !outO) return fail(PTYLM_ERR_ARG, "ctx, vO and outO must be non-NULL");
+    if (vP || outP) return fail(PTYLM_ERR_ARG, "probe blocks need a joint context");
+    if (!c->has_lin) return fail(PTYLM_ERR_STATE, "no linearisation point");
+    if (!std::isfinite(lambda)) return fail(PTYLM_ERR_ARG, "lambda must be finite");
+    const bool host_in = is_host_pointer(vO), host_out = is_host_pointer(outO);
+    const float2* v = reinterpret_cast<const float2*>(vO);
+    float2* o = reinterpret_cast<float2*>(outO);
+    if (host_in || host_out) {
+        if (!c->stage_a) STATUS_TRY(ctx_alloc_t(c, &c->stage_a, c->N, "staging (vector)"));
+        if (!c->stage_b) STATUS_TRY(ctx_alloc_t(c, &c->stage_b, c->N, "staging (result)"));
+    }
+    if (host_in) {
+        CUDA_TRY(cudaMemcpyAsync(c->stage_a, vO, sizeof(float2) * c->N, cudaMemcpyHostToDevice, c->stream));
+        v = c->stage_a;
+    }
+    if (host_out) o = c->stage_b;
+    STATUS_TRY(op_matvec(c, v, lambda, D, o));
+    if (host_out) {
+        CUDA_TRY(cudaMemcpyAsync(outO, o, sizeof(float2) * c->N, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    return PTYLM_OK;
+}
+
+ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, const ptylm_lm_params* prm,
+                      ptylm_lm_stats* stats) {
+    g_last_error.clear();
+    if (!c || !O_inout || !P_inout || !prm) return fail(PTYLM_ERR_ARG, "ctx, O, P and params must be non-NULL");
+    if (prm->max_outer < 0 || prm->max_cg < 0 || !(prm->kappa > 1.0) || !(prm->mu0 > 0.0))
+        return fail(PTYLM_ERR_ARG, "invalid LM parameters");
+    const long N = c->N;
+    const size_t nbytes = sizeof(float2) * N;
+    if (!c->cg_x) {
+        STATUS_TRY(ctx_alloc_t(c, &c->cg_x, N, "CG x"));
+        STATUS_TRY(ctx_alloc_t(c, &c->cg_r, N, "CG r"));
+        STATUS_TRY(ctx_alloc_t(c, &c->cg_p, N, "CG p"));
+        STATUS_TRY(ctx_alloc_t(c, &c->cg_q, N, "CG q"));
+        STATUS_TRY(ctx_alloc_t(c, &c->trial, N, "trial point"));
+    }
+    if (!c->stage_a) STATUS_TRY(ctx_alloc_t(c, &c->stage_a, N, "iterate"));
+    if (!c->stage_P) STATUS_TRY(ctx_alloc_t(c, &c->stage_P, c->M, "probe"));
+    const bool host_O = is_host_pointer(O_inout), host_P = is_host_pointer(P_inout);
+    // The iterate lives in stage_a throughout (the caller's buffer is read once, written once).
+    CUDA_TRY(cudaMemcpyAsync(c->stage_a, O_inout, nbytes, host_O ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->stage_P, P_inout, sizeof(float2) * c->M,
+                             host_P ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+    float2* O = c->stage_a;
+    const float2* P = c->stage_P;
+    float2 *x = c->cg_x, *r = c->cg_r, *p = c->cg_p, *q = c->cg_q, *trial = c->trial;
+    const int nb = vec_blocks(c);
+    CUDA_TRY(cudaMemsetAsync(x, 0, nbytes, c->stream));
+
+    double mu = prm->mu0;
+    int cg_total = 0, matvecs = 0, t = 0;
+    bool hit_maxit = false;
+    ptylm_status status = PTYLM_OK;
+    double f_cur = NAN, err = NAN;
+    auto object_error = [&](double* e_out) -> ptylm_status {
+        k_err_sums<<<nb, VEC_THREADS, 0, c->stream>>>(O, reinterpret_cast<const float2*>(prm->O_ref), prm->mask, N, c->partials);
+        STATUS_TRY(vec_launched(c));
+        STATUS_TRY(finalize(c, nb, 4, S_ER, OP_NONE));
+        STATUS_TRY(read_scalars(c, S_ER, 4));
+        const double ac = std::hypot(c->scal_host[S_ER], c->scal_host[S_EI]);
+        const double e2 = std::max(0.0, c->scal_host[S_NO] + c->scal_host[S_NR] - 2.0 * ac);
+        *e_out = std::sqrt(e2 / c->scal_host[S_NR]);
+        return PTYLM_OK;
+    };
+
+    for (t = 0; t < prm->max_outer; ++t) {
+        // Linearise: f, ||grad_zeta l||^2, cache a, grad f (Algorithm 1, first step of the loop).
+        STATUS_TRY(op_forward(c, O, P, 1));
+        STATUS_TRY(dots(c, 1, c->grad, c->grad, nullptr, nullptr, nullptr, nullptr, S_GG));
+        STATUS_TRY(read_scalars(c, S_F, S_GG - S_F + 1));
+        const double f = c->scal_host[S_F], dl2 = c->scal_host[S_DL2], gg = c->scal_host[S_GG];
+        if (!std::isfinite(f) || !std::isfinite(gg)) {
+            status = fail(PTYLM_ERR_NAN, "non-finite loss or gradient at outer iteration %d", t);
+            break;
+        }
+        f_cur = f;
+        const double gnorm = std::sqrt(gg);
+        const double eta = std::min(prm->beta, std::sqrt(gnorm));  // Eq. lma_termination_eta
+        const double tol = eta * gnorm;                              // Eq. lma_termination_magnitude
+        if (stats && stats->hist_len > t) {
+            if (stats->hist_f) stats->hist_f[t] = f;
+            if (stats->hist_gnorm) stats->hist_gnorm[t] = gnorm;
+        }
+        double rho = 0.0;
+        int cg_this = 0;
+        bool stalled = false;
+        while (!(rho > prm->rho_min)) {
+            const double lambda = mu * std::pow(std::sqrt(dl2), prm->nu);
+            // ---- truncated CG on (G + lambda I) x = -g, warm-started from x ----
+            STATUS_TRY(op_matvec(c, x, lambda, nullptr, q));
+            ++matvecs;
+            k_cg_start<<<nb, VEC_THREADS, 0, c->stream>>>(c->grad, q, r, p, N, c->partials);
+            STATUS_TRY(vec_launched(c));
+            STATUS_TRY(finalize(c, nb, 1, S_RR, OP_NONE));
+            int it = 0;
+            bool converged = false;
+            for (;;) {
+                if (prm->fixed_cg > 0) {
+                    if (it >= prm->fixed_cg) break;
+                } else {
+                    STATUS_TRY(read_scalars(c, S_RR, 1));
+                    if (std::sqrt(c->scal_host[S_RR]) <= tol) { converged = true; break; }
+                    if (it >= prm->max_cg) break;
+                }
+                // q = lambda p was written by the previous direction update (or below at it=0)
+                if (it == 0) {
+                    k_damping_init<<<nb, VEC_THREADS, 0, c->stream>>>(p, nullptr, (float)lambda, q, N);
+                    STATUS_TRY(vec_launched(c));
+                }
+                if (c->d.K > 0) {
+                    PtyArgs a = base_args(c);
+                    a.O = p;
+                    a.P = c->P_lin;
+                    a.a_cache = c->a_cache;
+                    a.out = q;
+                    STATUS_TRY(launch(c, KID_MATVEC, a));
+                }
+                ++matvecs;
+                STATUS_TRY(dots(c, 1, p, q, nullptr, nullptr, nullptr, nullptr, S_PQ, OP_ALPHA));
+                k_cg_update<<<nb, VEC_THREADS, 0, c->stream>>>(x, r, p, q, c->scal, N, c->partials);
+                STATUS_TRY(vec_launched(c));
+                STATUS_TRY(finalize(c, nb, 1, S_RRNEW, OP_BETA));
+                k_cg_direction<<<nb, VEC_THREADS, 0, c->stream>>>(r, p, q, nullptr, (float)lambda, c->scal, N);
+                STATUS_TRY(vec_launched(c));
+                ++it;
+            }
+            cg_this += it;
+            if (!converged && prm->fixed_cg <= 0 && it >= prm->max_cg) hit_maxit = true;
+            // ---- trial point and gain ratio (Algorithm 1) ----
+            k_add<<<nb, VEC_THREADS, 0, c->stream>>>(O, x, trial, N);
+            STATUS_TRY(vec_launched(c));
+            STATUS_TRY(op_forward(c, trial, P, 0));
+            STATUS_TRY(dots(c, 3, x, x, x, c->grad, x, r, S_DD));
+            STATUS_TRY(read_scalars(c, S_F, S_DR - S_F + 1));
+            const double f_trial = c->scal_host[S_F];
+            const double dd = c->scal_host[S_DD], dg = c->scal_host[S_DG], dr = c->scal_host[S_DR];
+            const double dfa = f - f_trial;
+            const double dfp = 0.5 * (lambda * dd - dg) + 0.5 * dr;  // -(g.d + d.G.d/2)
+            rho = (dfp > 0.0 && std::isfinite(f_trial)) ? dfa / dfp : -1.0;
+            if (rho > 0.75) mu = std::max(mu / prm->kappa, prm->mu_min);
+            else if (rho > 0.25) { /* keep mu */ }
+            else mu = prm->kappa * mu;
+            if (rho > prm->rho_min) {
+                CUDA_TRY(cudaMemcpyAsync(O, trial, nbytes, cudaMemcpyDeviceToDevice, c->stream));
+                f_cur = f_trial;
+            } else if (mu > prm->mu_max) {
+                stalled = true;
+                break;
+            }
+        }
+        cg_total += cg_this;
+        if (stats && stats->hist_len > t) {
+            if (stats->hist_mu) stats->hist_mu[t] = mu;
+            if (stats->hist_cg) stats->hist_cg[t] = cg_this;
+        }
+        if (stalled) {
+            status = fail(PTYLM_ERR_STALLED, "mu exceeded %g at outer iteration %d", prm->mu_max, t);
+            ++t;
+            break;
+        }
+        if (prm->O_ref) {
+            STATUS_TRY(object_error(&err));
+            if (stats && stats->hist_len > t && stats->hist_err) stats->hist_err[t] = err;
+            if (err <= prm->target_err) {
+                ++t;
+                break;
+            }
+        } else if (stats && stats->hist_len > t && stats->hist_err) {
+            stats->hist_err[t] = NAN;
+        }
+    }
+    CUDA_TRY(cudaMemcpyAsync(O_inout, O, nbytes, host_O ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (stats) {
+        stats->n_outer = t;
+        stats->cg_total = cg_total;
+        stats->matvecs_total = matvecs;
+        stats->f_final = f_cur;
+        stats->err_final = err;
+    }
+    if (status != PTYLM_OK) return status;
+    return hit_maxit ? PTYLM_WARN_CG_MAXIT : PTYLM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,257 @@
+"""Thin ctypes binding over the C-ABI of libptylm.so (include/ptylm.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels.  Arrays may be CUDA torch tensors (device pointers) or, where the C-ABI accepts
+host memory, numpy arrays / CPU tensors.  The binding raises if the shared library is
+missing; there is no fallback implementation.
+
+Names follow the C-ABI: lm_init, forward_loss, gradient, jvp, jtvp, ggn_matvec, lm_solve,
+lm_destroy, ptylm_strerror.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libptylm.so")
+
+PTYLM_OK = 0
+PTYLM_ERR_ARG = 1
+PTYLM_ERR_NOMEM = 2
+PTYLM_ERR_CUDA = 3
+PTYLM_ERR_NAN = 4
+PTYLM_ERR_TIMEOUT = 5
+PTYLM_ERR_STALLED = 6
+PTYLM_ERR_STATE = 7
+PTYLM_WARN_CG_MAXIT = 16
+
+LOSS_GAUSSIAN = 0
+LOSS_POISSON = 1
+
+
+class PtylmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"[{status}] {msg}")
+        self.status = status
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("ny", ctypes.c_int), ("nx", ctypes.c_int), ("my", ctypes.c_int),
+                ("mx", ctypes.c_int), ("K", ctypes.c_int), ("loss", ctypes.c_int),
+                ("background", ctypes.c_float), ("joint", ctypes.c_int),
+                ("workspace_budget", ctypes.c_size_t)]
+
+
+class LMParams(ctypes.Structure):
+    _fields_ = [("mu0", ctypes.c_double), ("mu_min", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("nu", ctypes.c_double),
+                ("rho_min", ctypes.c_double), ("beta", ctypes.c_double),
+                ("mu_max", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("max_cg", ctypes.c_int), ("fixed_cg", ctypes.c_int),
+                ("target_err", ctypes.c_double), ("O_ref", ctypes.c_void_p),
+                ("mask", ctypes.c_void_p)]
+
+
+class LMStats(ctypes.Structure):
+    _fields_ = [("n_outer", ctypes.c_int), ("cg_total", ctypes.c_int),
+                ("matvecs_total", ctypes.c_int), ("f_final", ctypes.c_double),
+                ("err_final", ctypes.c_double), ("hist_len", ctypes.c_int),
+                ("hist_f", ctypes.c_void_p), ("hist_gnorm", ctypes.c_void_p),
+                ("hist_mu", ctypes.c_void_p), ("hist_cg", ctypes.c_void_p),
+                ("hist_err", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library():
+    """Load libptylm.so (it must have been built: paper_2103_01767_gb300.build.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                                   "(run paper_2103_01767_gb300/build.py)")
+            lib = ctypes.CDLL(LIB_PATH)
+            vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+            lib.lm_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Desc), vp, vp, vp]
+            lib.forward_loss.argtypes = [vp, vp, vp, ctypes.POINTER(d), ctypes.POINTER(d), i]
+            lib.gradient.argtypes = [vp, vp, vp]
+            lib.jvp.argtypes = [vp, vp, vp, vp]
+            lib.jtvp.argtypes = [vp, vp, vp, vp]
+            lib.ggn_matvec.argtypes = [vp, vp, vp, d, vp, vp, vp]
+            lib.lm_solve.argtypes = [vp, vp, vp, ctypes.POINTER(LMParams), ctypes.POINTER(LMStats)]
+            lib.lm_destroy.argtypes = [vp]
+            lib.forward_intensity.argtypes = [vp, vp, vp, vp]
+            lib.ptylm_profile.argtypes = [vp, i]
+            lib.ptylm_profile_read.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
+            lib.ptylm_strerror.argtypes = [i]
+            lib.ptylm_strerror.restype = ctypes.c_char_p
+            lib.ptylm_last_error.restype = ctypes.c_char_p
+            lib.ptylm_default_lm_params.argtypes = [ctypes.POINTER(LMParams), i]
+            for name in ("lm_init", "forward_loss", "gradient", "jvp", "jtvp", "ggn_matvec",
+                         "lm_solve", "lm_destroy", "forward_intensity", "ptylm_profile",
+                         "ptylm_profile_read"):
+                getattr(lib, name).restype = i
+            _lib = lib
+    return _lib
+
+
+def ptylm_strerror(status: int) -> str:
+    return load_library().ptylm_strerror(int(status)).decode()
+
+
+def _check(status, allow=()):
+    if status != PTYLM_OK and status not in allow:
+        lib = load_library()
+        raise PtylmError(status, f"{lib.ptylm_strerror(status).decode()}: "
+                                 f"{lib.ptylm_last_error().decode()}")
+    return status
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"unsupported array type {type(x)!r}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Context:
+    """Owns one C context (lm_init ... lm_destroy).  Keeps references to the arrays the C
+    side borrows (positions are copied; y is borrowed)."""
+
+    def __init__(self, handle, desc, y_ref):
+        self.handle = handle
+        self.desc = desc
+        self._y_ref = y_ref
+
+    def close(self):
+        if self.handle:
+            lm_destroy(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lm_init(ny, nx, my, mx, positions, y, loss=LOSS_GAUSSIAN, background=1e-8, joint=0,
+            workspace_budget=0, stream=None) -> Context:
+    """positions: device int32 [K, 2]; y: device float32 [K, my, mx] (borrowed)."""
+    lib = load_library()
+    K = 0 if positions is None else int(positions.shape[0])
+    desc = Desc(int(ny), int(nx), int(my), int(mx), K, int(loss), float(background), int(joint),
+                int(workspace_budget))
+    h = ctypes.c_void_p()
+    _check(lib.lm_init(ctypes.byref(h), ctypes.byref(desc), _ptr(positions), _ptr(y),
+                       _stream_ptr(stream)))
+    return Context(h.value, desc, y)
+
+
+def lm_destroy(ctx: Context) -> None:
+    if ctx.handle:
+        _check(load_library().lm_destroy(ctx.handle))
+        ctx.handle = None
+
+
+def forward_loss(ctx: Context, O, P, cache: int = 0):
+    """Returns (f, ||grad_zeta l||^2) as Python floats."""
+    f, n2 = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().forward_loss(ctx.handle, _ptr(O), _ptr(P), ctypes.byref(f),
+                                       ctypes.byref(n2), int(cache)))
+    return f.value, n2.value
+
+
+def gradient(ctx: Context, gO, gP=None) -> None:
+    _check(load_library().gradient(ctx.handle, _ptr(gO), _ptr(gP)))
+
+
+def jvp(ctx: Context, vO, out, vP=None) -> None:
+    _check(load_library().jvp(ctx.handle, _ptr(vO), _ptr(vP), _ptr(out)))
+
+
+def jtvp(ctx: Context, w, outO, outP=None) -> None:
+    _check(load_library().jtvp(ctx.handle, _ptr(w), _ptr(outO), _ptr(outP)))
+
+
+def ggn_matvec(ctx: Context, vO, outO, lam: float = 0.0, D=None, vP=None, outP=None) -> None:
+    _check(load_library().ggn_matvec(ctx.handle, _ptr(vO), _ptr(vP), ctypes.c_double(lam), _ptr(D),
+                                     _ptr(outO), _ptr(outP)))
+
+
+def forward_intensity(ctx: Context, O, P, h_out) -> None:
+    _check(load_library().forward_intensity(ctx.handle, _ptr(O), _ptr(P), _ptr(h_out)))
+
+
+KERNEL_FORWARD_LOSS = 0
+KERNEL_FORWARD_CACHE = 1
+KERNEL_GGN_MATVEC = 2
+KERNEL_JTVP = 3
+KERNEL_JVP = 4
+KERNEL_FORWARD_INTENSITY = 5
+
+
+def ptylm_profile(ctx: Context, enable: bool) -> None:
+    _check(load_library().ptylm_profile(ctx.handle, int(bool(enable))))
+
+
+def ptylm_profile_read(ctx: Context, kernel: int):
+    """(total device ms, launches) for one kernel id; kernel=-1 -> (0, all launches)."""
+    ms, n = ctypes.c_double(), ctypes.c_longlong()
+    _check(load_library().ptylm_profile_read(ctx.handle, int(kernel), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def default_lm_params(loss: int) -> LMParams:
+    p = LMParams()
+    load_library().ptylm_default_lm_params(ctypes.byref(p), int(loss))
+    return p
+
+
+def lm_solve(ctx: Context, O, P, params: LMParams | None = None, hist_len: int = 0,
+             O_ref=None, mask=None, **overrides):
+    """Run Algorithm 1 in place on O.  Returns (status, stats dict)."""
+    p = default_lm_params(ctx.desc.loss) if params is None else params
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    if O_ref is not None:
+        p.O_ref = _ptr(O_ref)
+    if mask is not None:
+        p.mask = _ptr(mask)
+    L = int(hist_len)
+    hf, hg, hmu, herr = (np.full(max(L, 1), math.nan) for _ in range(4))
+    hcg = np.zeros(max(L, 1), np.int32)
+    st = LMStats(0, 0, 0, 0.0, 0.0, L, hf.ctypes.data, hg.ctypes.data, hmu.ctypes.data,
+                 hcg.ctypes.data, herr.ctypes.data)
+    status = _check(load_library().lm_solve(ctx.handle, _ptr(O), _ptr(P), ctypes.byref(p),
+                                            ctypes.byref(st)), allow=(PTYLM_WARN_CG_MAXIT,))
+    n = min(st.n_outer, L)
+    return status, dict(n_outer=st.n_outer, cg_total=st.cg_total, matvecs=st.matvecs_total,
+                        f_final=st.f_final, err_final=st.err_final, f=hf[:n].copy(),
+                        gnorm=hg[:n].copy(), mu=hmu[:n].copy(), cg=hcg[:n].copy(),
+                        err=herr[:n].copy())
