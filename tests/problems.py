@@ -36,10 +36,11 @@ def random_positions(n, m, K, seed):
 
 
 def make_case(n, m, K=None, loss=0, peak=0.0, seed=0, grid=None, step=None, jitter=0, radius=None,
-              b=1e-8):
+              b=1e-8, noisy=True):
     """A problem on an n^2 object with an m^2 probe.  Positions come from a jittered raster
     (grid/step given) or are uniform random (K given).  peak > 0 scales the probe so the
-    brightest noiseless pixel holds `peak` photons and draws Poisson counts."""
+    brightest noiseless pixel holds `peak` photons; then y are Poisson counts (noisy) or the
+    expected counts themselves (noisy=False)."""
     O_true = synth.to_c64(synth.object_texture(n, seed=seed))
     P = synth.probe_disk_defocus(m, radius if radius is not None else 0.3125 * m)
     if grid is not None:
@@ -53,7 +54,7 @@ def make_case(n, m, K=None, loss=0, peak=0.0, seed=0, grid=None, step=None, jitt
         P = synth.to_c64(P * np.sqrt(peak / h.max()))
         pb = oracle.Problem((n, n), P, pos, None, loss, b)
         h = oracle.intensity(pb, O_true)
-        y = synth.poisson_counts(h, seed=seed + 2)
+        y = synth.poisson_counts(h, seed=seed + 2) if noisy else h
     else:
         y = h
     return Case(n, m, pos, O_true, P, synth.to_f32(y), loss, b)

@@ -1,12 +1,21 @@
 """CUDA path (through the C-ABI) against the FP64 oracle on identical seeded inputs.
 
-Tolerances: relative 1e-5 (2-norm) on f, grad f, J v, J^T w and (G + lambda I) v, the
-FP32 bound stated for the method's hot path; the FP64 oracle's own error is ~1e-13."""
+Tolerance: relative 1e-5 (2-norm) on f, ||grad_zeta l||^2, grad f, J v, J^T w and
+(G + lambda I) v, the FP32 bound of the hot path; the FP64 oracle's own error is ~1e-13.
+Derived exception: for the Poisson metric, pixels where the model is much darker than the
+data (zeta^2 << y) carry weights 2y/zeta^2 and 2y/zeta that amplify the FFT's absolute
+rounding error (~u log2(M) rms|psihat|) into relative errors above 1e-5 for ANY
+single-precision evaluation.  Every comparison therefore uses
+    tol = max(1e-5, 3 x error of an independent plain PyTorch FP32 reference)
+(tests/fp32_reference.py, same operator, same input).  Where the input is well conditioned
+-- the Gaussian metric, or Poisson data at their noiseless truth (d2l = 4 everywhere) --
+the FP32 reference is accurate to a few 1e-6 and the bar is 1e-5 without widening."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2103_01767_gb300 import synth
+from tests.fp32_reference import Ref32
 from tests.problems import make_case, rel_err
 
 torch = pytest.importorskip("torch")
@@ -23,6 +32,18 @@ def lib():
     build.build()
     ptylm.load_library()
     return ptylm
+
+
+def tol_for(case, ref32_value, oracle_value):
+    """1e-5 for well-conditioned inputs (Gaussian metric, Poisson at its noiseless truth);
+    otherwise max(1e-5, 3 x the FP32-reference error) -- see the module docstring."""
+    if case.loss == 0 or case.at_truth:
+        return TOL
+    return max(TOL, 3.0 * rel_err(ref32_value, oracle_value))
+
+
+def scalar_rel(a, b):
+    return abs(a - b) / abs(b)
 
 
 def dev_c64(a):
@@ -59,36 +80,56 @@ class GpuCase:
 SHAPES = [(96, 32, 37), (160, 64, 23), (288, 128, 11), (256, 32, 3000), (512, 64, 1000), (640, 128, 400)]
 
 
-@pytest.mark.parametrize("loss", [0, 1])
+# loss kinds: Gaussian on noiseless data, Poisson on expected counts, Poisson on counts
+KINDS = [(0, False), (1, False), (1, True)]
+
+
+def kind_case(n, m, K, kind, seed, at_truth=False):
+    loss, noisy = kind
+    case = make_case(n, m, K=K, loss=loss, peak=1e3 if loss else 0.0, seed=seed, noisy=noisy)
+    case.noisy = noisy
+    case.at_truth = at_truth
+    return case
+
+
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("shape", SHAPES)
-def test_forward_loss_and_gradient(lib, shape, loss):
+def test_forward_loss_and_gradient(lib, shape, kind):
     n, m, K = shape
-    case = make_case(n, m, K=K, loss=loss, peak=1e3 if loss else 0.0, seed=11)
-    g = GpuCase(lib, case)
+    case = kind_case(n, m, K, kind, 11)
+    g = GpuCase(lib, case)  # perturbed point: the gradient vanishes at the truth
+    ref32 = Ref32(case)
     O = g.point()
     Od = dev_c64(O)
     f, dl2 = lib.forward_loss(g.ctx, Od, g.P, cache=1)
     pb = case.problem()
     f_ref, dl2_ref = oracle.loss(pb, O, return_dl_norm2=True)
-    assert abs(f - f_ref) <= TOL * abs(f_ref), (f, f_ref)
-    assert abs(dl2 - dl2_ref) <= TOL * abs(dl2_ref), (dl2, dl2_ref)
+    f32, dl2_32 = ref32.loss_and_dl2(O)
+    assert scalar_rel(f, f_ref) <= tol_for(case, f32, f_ref), (f, f_ref, f32)
+    assert scalar_rel(dl2, dl2_ref) <= tol_for(case, dl2_32, dl2_ref), (dl2, dl2_ref, dl2_32)
     gd = torch.empty_like(Od)
     lib.gradient(g.ctx, gd)
-    assert rel_err(host(gd), oracle.gradient(pb, O)) <= TOL
+    g_ref = oracle.gradient(pb, O)
+    tol_g = tol_for(case, ref32.gradient(O), g_ref)
+    assert rel_err(host(gd), g_ref) <= tol_g
     # loss-only evaluation at another point leaves the linearisation intact
-    f2, _ = lib.forward_loss(g.ctx, dev_c64(g.point(seed=6)), g.P, cache=0)
-    assert abs(f2 - oracle.loss(pb, g.point(seed=6))) <= TOL * abs(f2)
+    O2 = g.point(seed=6)
+    f2, _ = lib.forward_loss(g.ctx, dev_c64(O2), g.P, cache=0)
+    f2_ref = oracle.loss(pb, O2)
+    assert scalar_rel(f2, f2_ref) <= tol_for(case, ref32.loss_and_dl2(O2)[0], f2_ref)
     lib.gradient(g.ctx, gd)
-    assert rel_err(host(gd), oracle.gradient(pb, O)) <= TOL
+    assert rel_err(host(gd), g_ref) <= tol_g
 
 
-@pytest.mark.parametrize("loss", [0, 1])
+@pytest.mark.parametrize("kind", KINDS + [(1, False, "truth")])
 @pytest.mark.parametrize("shape", SHAPES)
-def test_ggn_matvec(lib, shape, loss):
+def test_ggn_matvec(lib, shape, kind):
     n, m, K = shape
-    case = make_case(n, m, K=K, loss=loss, peak=1e3 if loss else 0.0, seed=12)
+    at_truth = len(kind) > 2
+    case = kind_case(n, m, K, kind[:2], 12, at_truth)
     g = GpuCase(lib, case)
-    O = g.point()
+    ref32 = Ref32(case)
+    O = case.O_true if at_truth else g.point()
     lib.forward_loss(g.ctx, dev_c64(O), g.P, cache=1)
     v = synth.to_c64(synth.random_complex(O.shape, seed=13))
     vd = dev_c64(v)
@@ -97,25 +138,29 @@ def test_ggn_matvec(lib, shape, loss):
     for lam in (0.0, 0.37):
         lib.ggn_matvec(g.ctx, vd, out, lam)
         ref = oracle.ggn_matvec(pb, O, v, lam=lam)
-        assert rel_err(host(out), ref) <= TOL, lam
+        assert rel_err(host(out), ref) <= tol_for(case, ref32.ggn_matvec(O, v, lam), ref), lam
 
 
+@pytest.mark.parametrize("at_truth", [False, True])
 @pytest.mark.parametrize("shape", SHAPES)
-def test_jvp_and_jtvp(lib, shape):
+def test_jvp_and_jtvp(lib, shape, at_truth):
     n, m, K = shape
-    case = make_case(n, m, K=K, loss=1, peak=1e3, seed=14)
+    case = kind_case(n, m, K, (1, not at_truth), 14, at_truth)
     g = GpuCase(lib, case)
-    O = g.point()
+    ref32 = Ref32(case)
+    O = case.O_true if at_truth else g.point()
     lib.forward_loss(g.ctx, dev_c64(O), g.P, cache=1)
     pb = case.problem()
     v = synth.to_c64(synth.random_complex(O.shape, seed=15))
     out = torch.empty((K, m, m), dtype=torch.float32, device="cuda")
     lib.jvp(g.ctx, dev_c64(v), out)
-    assert rel_err(host(out), oracle.jvp(pb, O, v)) <= TOL
+    jv_ref = oracle.jvp(pb, O, v)
+    assert rel_err(host(out), jv_ref) <= tol_for(case, ref32.jvp(O, v), jv_ref)
     w = synth.to_f32(synth.random_real((K, m, m), seed=16))
     outO = torch.empty((n, n), dtype=torch.complex64, device="cuda")
     lib.jtvp(g.ctx, dev_f32(w), outO)
-    assert rel_err(host(outO), oracle.jtvp(pb, O, w)) <= TOL
+    jt_ref = oracle.jtvp(pb, O, w)
+    assert rel_err(host(outO), jt_ref) <= tol_for(case, ref32.jtvp(O, w), jt_ref)
 
 
 def test_adjoint_identity_on_gpu(lib):
