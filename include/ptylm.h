@@ -104,13 +104,20 @@ typedef struct {
 /* Create a context for one reconstruction problem (Sec. 2).
  *   positions_dev: device int32 [K][2], copied into the context (validated on the host:
  *                  out-of-range positions return PTYLM_ERR_ARG with nothing launched).
- *   y_dev:         device float [K][my][mx] measured intensities (y >= 0), NOT copied: it
- *                  must stay valid and unchanged until lm_destroy.
+ *   y_dev:         device float [K][my][mx] measured intensities (y >= 0) in natural DFT
+ *                  order (zero frequency at [0][0]); copied into the context's internal
+ *                  order, so the caller's buffer may be reused once lm_init returns.
  *   stream:        cudaStream_t (NULL = legacy default stream) all work is issued on.
- * Allocates the frequency-domain cache (8*K*M bytes) and small workspaces within
- * desc->workspace_budget, else PTYLM_ERR_NOMEM. */
+ * Allocates the frequency-domain cache (8*K*M bytes), the measurement copy (4*K*M bytes)
+ * and small workspaces within desc->workspace_budget, else PTYLM_ERR_NOMEM. */
 ptylm_status lm_init(ptylm_ctx** ctx, const ptylm_desc* desc, const int32_t* positions_dev,
                      const float* y_dev, void* stream);
+
+/* Replace the measurements y (Sec. 2: the recorded data y_k) with y_dev, device float
+ * [K][my][mx] in natural order, copied like in lm_init.  Invalidates the linearisation
+ * point (a later jvp / jtvp / ggn_matvec / gradient returns PTYLM_ERR_STATE until
+ * forward_loss(cache=1) runs again). */
+ptylm_status ptylm_set_measurements(ptylm_ctx* ctx, const float* y_dev);
 
 /* Error metric f = sum_k sum_m l(zeta_km, y_km) at (O, P)  (Eq. error_metric_magnitude).
  *   O: device [ny][nx]; P: device [my][mx].
@@ -168,8 +175,7 @@ ptylm_status lm_solve(ptylm_ctx* ctx, ptylm_c64* O_inout, ptylm_c64* P_inout,
 
 /* Expected intensities h = |F diag(P) S_k O|^2 + b for every position (Sec. 2,
  * Eq. expected_count), used to simulate measurements.  O: device [ny][nx]; P: device
- * [my][mx]; h_out: device float [K][my][mx] (it may be the y buffer given to lm_init).
- * Changes no context state. */
+ * [my][mx]; h_out: device float [K][my][mx] in natural order.  Changes no context state. */
 ptylm_status forward_intensity(ptylm_ctx* ctx, const ptylm_c64* O, const ptylm_c64* P, float* h_out);
 
 /* Instrumentation (no counterpart in the paper).  ptylm_profile(ctx, 1) resets the

@@ -92,28 +92,49 @@ __device__ __forceinline__ TeamCtx<G> team_setup(const float2* tw_g) {
     return c;
 }
 
-// Pass-1 gather: v[ax] = P[y][x] * A[r0 + y][c0 + x],  x = BX*ax + bx, thread = y*BX + bx.
+// Pass-1 gather: thread t = x + S*b holds rows y = BX*a + b of column x:
+//   v[a] = P[y][x] * A[r0 + y][c0 + x].
+// Lanes are consecutive columns: each warp load reads 256 contiguous bytes of one row.
 template <class G>
 __device__ __forceinline__ void gather_times_probe(float2* v, const float2* __restrict__ A,
                                                    const float2* __restrict__ P, int nx, int r0,
                                                    int c0, int tid) {
-    const int yrow = tid / G::BX, bx = tid % G::BX;
-    const float2* src = A + (size_t)(r0 + yrow) * nx + c0 + bx;
-    const float2* pr = P + yrow * G::S + bx;
+    const int x = tid & (G::S - 1), b = tid >> G::LOG_S;
+    const float2* src = A + (size_t)(r0 + b) * nx + c0 + x;
+    const float2* pr = P + b * G::S + x;
+    const size_t row_step = (size_t)G::BX * nx;
 #pragma unroll
-    for (int ax = 0; ax < 32; ++ax) v[ax] = cmul(__ldg(pr + G::BX * ax), __ldg(src + G::BX * ax));
+    for (int a0 = 0; a0 < 32; a0 += 8) {
+        float2 pv[8], av[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            pv[i] = pr[G::BX * G::S * (a0 + i)];  // plain load: an __ldg is hoisted out of the position loop
+            av[i] = __ldg(src + row_step * (a0 + i));
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[a0 + i] = cmul(pv[i], av[i]);
+        sched_fence();
+    }
 }
 
-// Pass-1 scatter: out[r0 + y][c0 + x] += conj(P[y][x]) * v[ax].
+// Pass-1 scatter: out[r0 + y][c0 + x] += conj(P[y][x]) * v[a], same thread layout.
 template <class G>
 __device__ __forceinline__ void scatter_times_conj_probe(const float2* v, float2* out,
                                                          const float2* __restrict__ P, int nx,
                                                          int r0, int c0, int tid) {
-    const int yrow = tid / G::BX, bx = tid % G::BX;
-    float2* dst = out + (size_t)(r0 + yrow) * nx + c0 + bx;
-    const float2* pr = P + yrow * G::S + bx;
+    const int x = tid & (G::S - 1), b = tid >> G::LOG_S;
+    float2* dst = out + (size_t)(r0 + b) * nx + c0 + x;
+    const float2* pr = P + b * G::S + x;
+    const size_t row_step = (size_t)G::BX * nx;
 #pragma unroll
-    for (int ax = 0; ax < 32; ++ax) red_add_c64(dst + G::BX * ax, cmulc(v[ax], __ldg(pr + G::BX * ax)));
+    for (int a0 = 0; a0 < 32; a0 += 8) {
+        float2 pv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) pv[i] = pr[G::BX * G::S * (a0 + i)];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) red_add_c64(dst + row_step * (a0 + i), cmulc(v[a0 + i], pv[i]));
+        sched_fence();
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -127,39 +148,47 @@ k_forward(PtyArgs a) {
     TeamCtx<G> c = team_setup<G>(a.tw);
     const float invS = 1.0f / G::S;
     double acc_l = 0.0, acc_d = 0.0;
+    const int ky = freq_ky<G>(c.tid);
     float2 v[32];
     for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
         const int2 rc = a.pos[k];
-        gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
-        team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
-        const int kx = freq_kx<G>(c.tid);
-        const float* yk = a.y + (size_t)k * G::M;
+        const float* yk = a.y + (size_t)k * G::M + c.tid;  // measurements in team-register order
         float sl = 0.0f, sd = 0.0f;
+        gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
+        if constexpr (CACHE) {
+            float2* ak = a.a_cache + (size_t)k * G::M + c.tid;
+            team_fft_roundtrip<G>(v, c.sm, c.tw, c.tid, [&](float2* g, int j) {
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-            const int ky = freq_ky<G>(c.tid, e);
-            const float2 ps = v[e] * invS;                      // orthonormal psihat
-            const float h = ps.x * ps.x + ps.y * ps.y + a.b;    // Eq. expected_count
-            if constexpr (INTENSITY) {
-                a.out_real[(size_t)k * G::M + ky * G::S + kx] = h;
-                continue;
-            }
-            const float zeta = sqrtf(h);                        // Eq. magnitude
-            const EllTerms t = ell_terms(a.loss, h, zeta, __ldg(yk + ky * G::S + kx));
-            sl += t.l;
-            if constexpr (CACHE) {
-                sd += t.dl * t.dl;
-                const float inv_zeta = 1.0f / zeta;
-                a.a_cache[(size_t)k * G::M + e * G::T + c.tid] = ps * (sqrtf(t.d2l) * inv_zeta);
-                v[e] = ps * (t.dl * inv_zeta * invS);  // psihat grad l / zeta, inverse 1/S folded in
+                for (int k2y = 0; k2y < G::BY; ++k2y) {
+                    const int e = j * G::BY + k2y;
+                    const float2 ps = g[k2y] * invS;                    // orthonormal psihat
+                    const float h = ps.x * ps.x + ps.y * ps.y + a.b;    // Eq. expected_count
+                    const float zeta = sqrtf(h);                        // Eq. magnitude
+                    const EllTerms t = ell_terms(a.loss, h, zeta, __ldg(yk + e * G::T));
+                    sl += t.l;
+                    sd += t.dl * t.dl;
+                    const float inv_zeta = 1.0f / zeta;
+                    ak[e * G::T] = ps * (sqrtf(t.d2l) * inv_zeta);
+                    g[k2y] = ps * (t.dl * inv_zeta * invS);  // psihat grad l / zeta, inverse 1/S folded in
+                }
+            });
+            scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
+        } else {
+            team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const float2 ps = v[e] * invS;
+                const float h = ps.x * ps.x + ps.y * ps.y + a.b;
+                if constexpr (INTENSITY) {
+                    a.out_real[(size_t)k * G::M + ky * G::S + freq_kx<G>(c.tid, e)] = h;
+                } else {
+                    const float zeta = sqrtf(h);
+                    sl += ell_terms(a.loss, h, zeta, __ldg(yk + e * G::T)).l;
+                }
             }
         }
         acc_l += (double)sl;
         acc_d += (double)sd;
-        if constexpr (CACHE) {
-            team_fft_inv<G>(v, c.sm, c.tw, c.tid);
-            scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
-        }
         team_sync<G>();
     }
     block_reduce2_store(acc_l, acc_d, a.partials);
@@ -180,15 +209,17 @@ k_ggn_matvec(PtyArgs a) {
     for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
         const int2 rc = a.pos[k];
         gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
-        team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
         const float2* ak = a.a_cache + (size_t)k * G::M + c.tid;
+        team_fft_roundtrip<G>(v, c.sm, c.tw, c.tid, [&](float2* g, int j) {
+            float2 av[G::BY];
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-            const float2 av = __ldcs(ak + e * G::T);
-            const float t = (av.x * v[e].x + av.y * v[e].y) * invM;
-            v[e] = av * t;
-        }
-        team_fft_inv<G>(v, c.sm, c.tw, c.tid);
+            for (int k2y = 0; k2y < G::BY; ++k2y) av[k2y] = __ldcs(ak + (j * G::BY + k2y) * G::T);
+#pragma unroll
+            for (int k2y = 0; k2y < G::BY; ++k2y) {
+                const float t = (av[k2y].x * g[k2y].x + av[k2y].y * g[k2y].y) * invM;
+                g[k2y] = av[k2y] * t;
+            }
+        });
         scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
         team_sync<G>();
     }
@@ -203,21 +234,21 @@ k_jtvp(PtyArgs a) {
     using G = Geo<LS>;
     TeamCtx<G> c = team_setup<G>(a.tw);
     const float invS = 1.0f / G::S;
+    const int ky = freq_ky<G>(c.tid);
     float2 v[32];
     for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
         const int2 rc = a.pos[k];
         gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
-        team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
-        const int kx = freq_kx<G>(c.tid);
-        const float* wk = a.w + (size_t)k * G::M;
+        const float* wk = a.w + (size_t)k * G::M + ky * G::S;
+        team_fft_roundtrip<G>(v, c.sm, c.tw, c.tid, [&](float2* g, int j) {
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-            const int ky = freq_ky<G>(c.tid, e);
-            const float2 ps = v[e] * invS;
-            const float zeta = sqrtf(ps.x * ps.x + ps.y * ps.y + a.b);
-            v[e] = ps * (__ldg(wk + ky * G::S + kx) / zeta * invS);
-        }
-        team_fft_inv<G>(v, c.sm, c.tw, c.tid);
+            for (int k2y = 0; k2y < G::BY; ++k2y) {
+                const int kx = freq_kx<G>(c.tid, j * G::BY + k2y);
+                const float2 ps = g[k2y] * invS;
+                const float zeta = sqrtf(ps.x * ps.x + ps.y * ps.y + a.b);
+                g[k2y] = ps * (__ldg(wk + kx) / zeta * invS);
+            }
+        });
         scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
         team_sync<G>();
     }
@@ -244,18 +275,44 @@ k_jvp(PtyArgs a) {
         team_sync<G>();
         gather_times_probe<G>(v, a.V, a.P, a.nx, rc.x, rc.y, c.tid);
         team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
-        const int kx = freq_kx<G>(c.tid);
-        float* ok = a.out_real + (size_t)k * G::M;
+        float* ok = a.out_real + (size_t)k * G::M + freq_ky<G>(c.tid) * G::S;
 #pragma unroll
         for (int e = 0; e < 32; ++e) {
-            const int ky = freq_ky<G>(c.tid, e);
+            const int kx = freq_kx<G>(c.tid, e);
             const float2 ps = slot[e * G::T] * invS;
             const float2 dps = v[e] * invS;
             const float zeta = sqrtf(ps.x * ps.x + ps.y * ps.y + a.b);
-            ok[ky * G::S + kx] = (ps.x * dps.x + ps.y * dps.y) / zeta;
+            ok[kx] = (ps.x * dps.x + ps.y * dps.y) / zeta;
         }
         team_sync<G>();
     }
+}
+
+// ---------------------------------------------------------------------------------------
+// Measurements from natural [K][S][S] order to the kernels' team-register order
+// y_perm[k][e*T + t] = y[k][ky(t)][kx(t, e)].
+// ---------------------------------------------------------------------------------------
+template <int LS>
+__global__ void k_permute_measurements(const float* __restrict__ y, float* __restrict__ y_perm, long total) {
+    using G = Geo<LS>;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const long k = i / G::M;
+        const int r = (int)(i - k * G::M);
+        const int e = r / G::T, t = r % G::T;
+        y_perm[i] = y[k * G::M + freq_ky<G>(t) * G::S + freq_kx<G>(t, e)];
+    }
+}
+
+cudaError_t permute_measurements(int LS, const float* y, float* y_perm, int K, int blocks, cudaStream_t stream) {
+    const long total = (long)K << (2 * LS);
+    if (total == 0) return cudaSuccess;
+    switch (LS) {
+        case 5: k_permute_measurements<5><<<blocks, 256, 0, stream>>>(y, y_perm, total); break;
+        case 6: k_permute_measurements<6><<<blocks, 256, 0, stream>>>(y, y_perm, total); break;
+        case 7: k_permute_measurements<7><<<blocks, 256, 0, stream>>>(y, y_perm, total); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------

@@ -225,7 +225,7 @@ struct ptylm_ctx {
     std::vector<void*> allocations;
 
     int2* pos = nullptr;
-    const float* y = nullptr;
+    float* y_perm = nullptr;       // measurements in the kernels' team-register order
     float2* tw = nullptr;
     float2* a_cache = nullptr;
     float2* grad = nullptr;
@@ -382,7 +382,7 @@ static PtyArgs base_args(const ptylm_ctx* c) {
     PtyArgs a;
     memset(&a, 0, sizeof a);
     a.pos = c->pos;
-    a.y = c->y;
+    a.y = c->y_perm;
     a.tw = c->tw;
     a.K = c->d.K;
     a.nx = c->d.nx;
@@ -540,6 +540,7 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
     if ((s = ctx_alloc_t(c, &c->pos, std::max(1, d.K), "positions")) != PTYLM_OK) return bail(s);
     if ((s = ctx_alloc_t(c, &c->tw, c->S, "twiddles")) != PTYLM_OK) return bail(s);
     if ((s = ctx_alloc_t(c, &c->a_cache, (size_t)d.K * c->M, "frequency cache")) != PTYLM_OK) return bail(s);
+    if ((s = ctx_alloc_t(c, &c->y_perm, (size_t)d.K * c->M, "measurements")) != PTYLM_OK) return bail(s);
     if ((s = ctx_alloc_t(c, &c->grad, c->N, "gradient")) != PTYLM_OK) return bail(s);
     if ((s = ctx_alloc_t(c, &c->O_lin, c->N, "object linearisation point")) != PTYLM_OK) return bail(s);
     if ((s = ctx_alloc_t(c, &c->P_lin, c->M, "probe linearisation point")) != PTYLM_OK) return bail(s);
@@ -566,8 +567,23 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
         cudaError_t e = cudaGetLastError();
         return bail(fail(PTYLM_ERR_CUDA, "uploading context tables: %s", cudaGetErrorString(e)));
     }
-    c->y = y_dev;
+    if (d.K > 0) {
+        cudaError_t e = permute_measurements(LS, y_dev, c->y_perm, d.K, c->vec_grid, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return bail(fail(PTYLM_ERR_CUDA, "copying measurements: %s", cudaGetErrorString(e)));
+    }
     *out = c;
+    return PTYLM_OK;
+}
+
+ptylm_status ptylm_set_measurements(ptylm_ctx* c, const float* y_dev) {
+    g_last_error.clear();
+    if (!c) return fail(PTYLM_ERR_ARG, "ctx must be non-NULL");
+    if (c->d.K > 0 && !y_dev) return fail(PTYLM_ERR_ARG, "y must be non-NULL when K > 0");
+    c->has_lin = false;
+    if (c->d.K == 0) return PTYLM_OK;
+    CUDA_TRY(permute_measurements(c->LS, y_dev, c->y_perm, c->d.K, c->vec_grid, c->stream));
+    ++c->launches;
     return PTYLM_OK;
 }
 

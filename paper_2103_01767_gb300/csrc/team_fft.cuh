@@ -3,26 +3,30 @@
 // The far-field propagator of the model (Sec. 2, Eq. expected_count) is an S x S 2D DFT
 // applied independently at every scan position.  A "team" of T = S*S/32 threads owns one
 // patch; every thread holds 32 complex values in registers and the 2D transform runs as
-// three register passes separated by two shared-memory exchanges:
+// three register passes separated by two shared-memory exchanges.  The first transformed
+// dimension (d1) is the patch row index y, the second (d2) the column index x:
 //
-//   x = BX*ax + bx  (AX = 32, BX = S/32)     y = BY*ay + by  (AY = 32/BX, BY = S/AY)
-//   pass 1   DFT_32 over ax          -> k1x, twiddle W_S^(bx*k1x)        thread (y, bx)
-//   pass 2   DFT_BX over bx -> k2x;  DFT_AY over ay -> k1y,
-//            twiddle W_S^(by*k1y)                                       thread (k1x, by)
-//   pass 3   DFT_BY over by          -> k2y                              thread (kx, k1y)
-//   frequency index (ky, kx) = (k1y + AY*k2y, k1x + 32*k2x)
+//   d1 = BX*a1 + b1  (32 x BX = S)           d2 = BY*ay + by  (AY x BY = S, AY = 32/BX)
+//   pass 1   DFT_32 over a1          -> k1, twiddle W_S^(b1*k1)     thread t1 = d2 + S*b1
+//   pass 2   DFT_BX over b1 -> k2;  DFT_AY over ay -> k1y,
+//            twiddle W_S^(by*k1y)                                  thread t2 = k1 + 32*by
+//   pass 3   DFT_BY over by          -> k2y                         thread (kd1, k1y)
+//   frequency index (k_d1, k_d2) = (k1 + 32*k2, k1y + AY*k2y)
+//
+// In pass 1 the 32 lanes of a warp hold 32 consecutive columns of one row, so the patch
+// gather and the scatter-add touch 256 contiguous bytes per warp instruction.
 //
 // The inverse runs the same passes backwards with conjugate twiddles, so a forward
 // transform, an elementwise frequency-domain stage and an inverse transform need four
 // exchanges and no transposition back to natural order: the frequency stage sees its
-// elements in the "pass-3" layout and computes their (ky, kx) index instead.
+// elements in the "pass-3" layout and computes their frequency index instead.
 //
 // Exchange layouts (units of 8-byte complex words):
-//   ex1 (pass 1 <-> pass 2):  slot(t1, k1x) = t1*32 + (k1x ^ (t1 & 31)),  t1 = y*BX + bx
-//        writers vary t1 across lanes, readers vary k1x: the XOR swizzle keeps both
+//   ex1 (pass 1 <-> pass 2):  slot(t1, k1) = t1*32 + (k1 ^ (t1 & 31))
+//        writers vary t1 across lanes, readers vary k1: the XOR swizzle keeps both
 //        conflict-free.
-//   ex2 (pass 2 <-> pass 3):  slot = ((k2x*AY + k1y)*BY + by)*32 + k1x
-//        both sides have lanes = k1x, so plain row-major is conflict-free.
+//   ex2 (pass 2 <-> pass 3):  slot = ((k2*AY + k1y)*BY + by)*32 + k1
+//        both sides have lanes = k1, so plain row-major is conflict-free.
 //
 // Unnormalised transforms: forward then inverse multiplies by S*S; callers fold the
 // orthonormal 1/S factors into their frequency-domain stage.
@@ -174,14 +178,26 @@ __device__ __forceinline__ void team_sync() {
     else __syncthreads();
 }
 
-// ---- pass 1: thread t1 = y*BX + bx holds v[ax] = element (y, BX*ax + bx) ----------------
+// ---- pass 1: thread t1 = d2 + S*b1 holds v[a1] = element (d1 = BX*a1 + b1, d2) ----------
+// Compiler scheduling fence: keeps loads from being hoisted across it, which bounds the
+// registers held by loads in flight (the 32 data values already take 64 registers).
+__device__ __forceinline__ void sched_fence() { asm volatile("" ::: "memory"); }
+
 template <class G>
 __device__ __forceinline__ void pass1_fwd(float2* v, const float2* tw, int t1) {
     RegDFT<32, false>::run(v);
     if constexpr (G::BX > 1) {
-        const int bx = t1 & (G::BX - 1);
+        const int bx = t1 >> G::LOG_S;
 #pragma unroll
-        for (int k = 1; k < 32; ++k) v[k] = cmul(v[k], tw[bx * k]);
+        for (int k0 = 0; k0 < 32; k0 += 8) {
+            float2 w[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w[i] = tw[bx * (k0 + i)];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (k0 + i > 0) v[k0 + i] = cmul(v[k0 + i], w[i]);
+            sched_fence();
+        }
     }
 }
 
@@ -211,7 +227,7 @@ __device__ __forceinline__ void ex1_load_to_p2(const float2* sm, float2* v, int 
     for (int ay = 0; ay < G::AY; ++ay)
 #pragma unroll
         for (int bx = 0; bx < G::BX; ++bx) {
-            const int t1 = (G::BY * ay + by) * G::BX + bx;
+            const int t1 = (G::BY * ay + by) + G::S * bx;
             v[ay * G::BX + bx] = sm[t1 * 32 + (k1x ^ (t1 & 31))];
         }
 }
@@ -222,7 +238,7 @@ __device__ __forceinline__ void ex1_store_from_p2(float2* sm, const float2* v, i
     for (int ay = 0; ay < G::AY; ++ay)
 #pragma unroll
         for (int bx = 0; bx < G::BX; ++bx) {
-            const int t1 = (G::BY * ay + by) * G::BX + bx;
+            const int t1 = (G::BY * ay + by) + G::S * bx;
             sm[t1 * 32 + (k1x ^ (t1 & 31))] = v[ay * G::BX + bx];
         }
 }
@@ -326,11 +342,12 @@ __device__ __forceinline__ void pass3_inv(float2* v) {
     for (int j = 0; j < G::G3; ++j) dft_strided<G::BY, 1, true>(v, j * G::BY);
 }
 
-// Frequency index of register element e in the pass-3 layout of thread t3.
+// Frequency index (row ky, column kx) of register element e in the pass-3 layout of
+// thread t3: the row frequency comes from the first transformed dimension.
 template <class G>
-__device__ __forceinline__ int freq_kx(int t3) { return t3 & (G::S - 1); }
+__device__ __forceinline__ int freq_ky(int t3) { return t3 & (G::S - 1); }
 template <class G>
-__device__ __forceinline__ int freq_ky(int t3, int e) {
+__device__ __forceinline__ int freq_kx(int t3, int e) {
     const int j = e / G::BY, k2y = e % G::BY;
     return (t3 >> G::LOG_S) + G::BX * j + G::AY * k2y;
 }
@@ -365,6 +382,52 @@ __device__ __forceinline__ void team_fft_inv(float2* v, float2* sm, const float2
         team_sync<G>();
         ex2_load_to_p2<G>(sm, v, tid);
         team_sync<G>();  // all ex2 reads done before ex1 overwrites
+    }
+    pass2_inv<G>(v, tw, tid);
+    ex1_store_from_p2<G>(sm, v, tid);
+    team_sync<G>();
+    ex1_load_to_p1<G>(sm, v, tid);
+    pass1_inv<G>(v);
+}
+
+// Forward transform, an elementwise spectral stage and the inverse transform in one go
+// (v: pass-1 layout in and out).  Pass 3 runs one group of BY values at a time straight
+// from / back to the thread's own exchange slots, so the spectral stage only holds one
+// group (2*BY registers) plus whatever it loads: `stage(g, j)` receives the group's BY
+// spectral values g[k2y] (element e = j*BY + k2y of the pass-3 layout) and overwrites them
+// with the values to transform back.
+template <class G, class Stage>
+__device__ __forceinline__ void team_fft_roundtrip(float2* v, float2* sm, const float2* tw, int tid,
+                                                   Stage&& stage) {
+    pass1_fwd<G>(v, tw, tid);
+    ex1_store_from_p1<G>(sm, v, tid);
+    team_sync<G>();
+    ex1_load_to_p2<G>(sm, v, tid);
+    pass2_fwd<G>(v, tw, tid);
+    if constexpr (G::BY > 1) {
+        team_sync<G>();  // all ex1 reads done before ex2 overwrites
+        ex2_store_from_p2<G>(sm, v, tid);
+        team_sync<G>();
+        const int k1x = tid & 31, k2x = (tid & (G::S - 1)) >> 5, k1y0 = tid >> G::LOG_S;
+#pragma unroll 1
+        for (int j = 0; j < G::G3; ++j) {
+            float2 g[G::BY];
+            const int base = ex2_slot<G>(k2x, k1y0 + G::BX * j, 0, k1x);
+#pragma unroll
+            for (int by = 0; by < G::BY; ++by) g[by] = sm[base + by * 32];
+            RegDFT<G::BY, false>::run(g);
+            stage(g, j);
+            RegDFT<G::BY, true>::run(g);
+#pragma unroll
+            for (int by = 0; by < G::BY; ++by) sm[base + by * 32] = g[by];
+        }
+        team_sync<G>();
+        ex2_load_to_p2<G>(sm, v, tid);
+        team_sync<G>();  // all ex2 reads done before ex1 overwrites
+    } else {
+        // BY == 1: the pass-2 registers already hold the spectrum, one value per group.
+#pragma unroll
+        for (int j = 0; j < G::G3; ++j) stage(v + j, j);
     }
     pass2_inv<G>(v, tw, tid);
     ex1_store_from_p2<G>(sm, v, tid);

@@ -89,6 +89,7 @@ def load_library():
             lib.lm_solve.argtypes = [vp, vp, vp, ctypes.POINTER(LMParams), ctypes.POINTER(LMStats)]
             lib.lm_destroy.argtypes = [vp]
             lib.forward_intensity.argtypes = [vp, vp, vp, vp]
+            lib.ptylm_set_measurements.argtypes = [vp, vp]
             lib.ptylm_profile.argtypes = [vp, i]
             lib.ptylm_profile_read.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
             lib.ptylm_strerror.argtypes = [i]
@@ -96,7 +97,8 @@ def load_library():
             lib.ptylm_last_error.restype = ctypes.c_char_p
             lib.ptylm_default_lm_params.argtypes = [ctypes.POINTER(LMParams), i]
             for name in ("lm_init", "forward_loss", "gradient", "jvp", "jtvp", "ggn_matvec",
-                         "lm_solve", "lm_destroy", "forward_intensity", "ptylm_profile",
+                         "lm_solve", "lm_destroy", "forward_intensity", "ptylm_set_measurements",
+                         "ptylm_profile",
                          "ptylm_profile_read"):
                 getattr(lib, name).restype = i
             _lib = lib
@@ -141,13 +143,11 @@ def _stream_ptr(stream):
 
 
 class Context:
-    """Owns one C context (lm_init ... lm_destroy).  Keeps references to the arrays the C
-    side borrows (positions are copied; y is borrowed)."""
+    """Owns one C context (lm_init ... lm_destroy); positions and y are copied by the C side."""
 
-    def __init__(self, handle, desc, y_ref):
+    def __init__(self, handle, desc):
         self.handle = handle
         self.desc = desc
-        self._y_ref = y_ref
 
     def close(self):
         if self.handle:
@@ -162,7 +162,7 @@ class Context:
 
 def lm_init(ny, nx, my, mx, positions, y, loss=LOSS_GAUSSIAN, background=1e-8, joint=0,
             workspace_budget=0, stream=None) -> Context:
-    """positions: device int32 [K, 2]; y: device float32 [K, my, mx] (borrowed)."""
+    """positions: device int32 [K, 2]; y: device float32 [K, my, mx] (copied)."""
     lib = load_library()
     K = 0 if positions is None else int(positions.shape[0])
     desc = Desc(int(ny), int(nx), int(my), int(mx), K, int(loss), float(background), int(joint),
@@ -170,7 +170,7 @@ def lm_init(ny, nx, my, mx, positions, y, loss=LOSS_GAUSSIAN, background=1e-8, j
     h = ctypes.c_void_p()
     _check(lib.lm_init(ctypes.byref(h), ctypes.byref(desc), _ptr(positions), _ptr(y),
                        _stream_ptr(stream)))
-    return Context(h.value, desc, y)
+    return Context(h.value, desc)
 
 
 def lm_destroy(ctx: Context) -> None:
@@ -202,6 +202,10 @@ def jtvp(ctx: Context, w, outO, outP=None) -> None:
 def ggn_matvec(ctx: Context, vO, outO, lam: float = 0.0, D=None, vP=None, outP=None) -> None:
     _check(load_library().ggn_matvec(ctx.handle, _ptr(vO), _ptr(vP), ctypes.c_double(lam), _ptr(D),
                                      _ptr(outO), _ptr(outP)))
+
+
+def ptylm_set_measurements(ctx: Context, y) -> None:
+    _check(load_library().ptylm_set_measurements(ctx.handle, _ptr(y)))
 
 
 def forward_intensity(ctx: Context, O, P, h_out) -> None:
