@@ -23,6 +23,24 @@ __device__ __forceinline__ void red_add_c64(float2* addr, float2 v) {
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
 
+// Asynchronous bulk prefetch of `bytes` (multiple of 16, 16-byte aligned) into L2.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// One thread per 16 KB chunk starts pulling a position's M-element cache tile toward L2,
+// so the spectral stage later finds it there instead of waiting on DRAM.
+template <class G>
+__device__ __forceinline__ void prefetch_tile(const float2* tile, int tid) {
+    constexpr unsigned kChunk = 16384;
+    constexpr int kChunks = (int)(sizeof(float2) * G::M / kChunk);
+    if constexpr (kChunks > 0) {
+        if (tid < kChunks) prefetch_l2(reinterpret_cast<const char*>(tile) + (size_t)tid * kChunk, kChunk);
+    } else {
+        if (tid == 0) prefetch_l2(tile, sizeof(float2) * G::M);
+    }
+}
+
 // Per-element error metric l(zeta, y) of Eq. ell_magnitude and its first two zeta-derivatives.
 struct EllTerms {
     float l, dl, d2l;
@@ -208,6 +226,7 @@ k_ggn_matvec(PtyArgs a) {
     float2 v[32];
     for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
         const int2 rc = a.pos[k];
+        prefetch_tile<G>(a.a_cache + (size_t)k * G::M, c.tid);
         gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
         const float2* ak = a.a_cache + (size_t)k * G::M + c.tid;
         team_fft_roundtrip<G>(v, c.sm, c.tw, c.tid, [&](float2* g, int j) {
@@ -221,7 +240,8 @@ k_ggn_matvec(PtyArgs a) {
             }
         });
         scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
-        team_sync<G>();
+        // No barrier before the next position: its first shared-memory writes go to the
+        // slots this same thread read last (team_fft_roundtrip).
     }
 }
 
@@ -250,7 +270,8 @@ k_jtvp(PtyArgs a) {
             }
         });
         scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
-        team_sync<G>();
+        // No barrier before the next position: its first shared-memory writes go to the
+        // slots this same thread read last (team_fft_roundtrip).
     }
 }
 

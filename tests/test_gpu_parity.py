@@ -2,22 +2,23 @@
 
 Tolerance: relative 1e-5 (2-norm) on f, ||grad_zeta l||^2, grad f, J v, J^T w and
 (G + lambda I) v, the FP32 bound of the hot path; the FP64 oracle's own error is ~1e-13.
-Derived exception: for the Poisson metric, pixels where the model is much darker than the
-data (zeta^2 << y) carry weights 2y/zeta^2 and 2y/zeta that amplify the FFT's absolute
-rounding error (~u log2(M) rms|psihat|) into relative errors above 1e-5 for ANY
-single-precision evaluation; how large depends on a handful of dark pixels and on the
-FFT's radix and twiddle scheme (an O(1) factor between two correct FP32 FFTs).  Every
-comparison therefore uses
-    tol = max(1e-5, 10 x error of an independent plain PyTorch FP32 reference)
-(tests/fp32_reference.py, same operator, same input).  Where the input is well conditioned
--- the Gaussian metric, or Poisson data at their noiseless truth (d2l = 4 everywhere) --
-the FP32 reference is accurate to a few 1e-6 and the bar is 1e-5 without widening."""
+Derived exception for ill-conditioned inputs: for the Poisson metric, pixels where the
+model is much darker than the data (zeta^2 << y) carry weights 2y/zeta^2 and 2y/zeta that
+amplify the FFT's absolute rounding error into relative errors above 1e-5 for ANY
+single-precision evaluation (the paper computes in single precision throughout, Sec. 5).
+A single-precision FFT's rounding error has RMS about u sqrt(log2 M) times the RMS of the
+transform (u = 2^-24); an equivalent perturbation of the FFT inputs by that relative amount
+gives the quantity's FP32 conditioning, measured with the FP64 oracle itself
+(fp32_conditioning).  Those cases use tol = max(1e-5, 2 x conditioning).  Well-conditioned
+inputs -- the Gaussian metric, Poisson data at their noiseless truth (d2l = 4 everywhere) --
+are held to 1e-5 without widening."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2103_01767_gb300 import synth
-from tests.fp32_reference import Ref32
+import math
+
 from tests.problems import make_case, rel_err
 
 torch = pytest.importorskip("torch")
@@ -36,12 +37,32 @@ def lib():
     return ptylm
 
 
-def tol_for(case, ref32_value, oracle_value):
-    """1e-5 for well-conditioned inputs (Gaussian metric, Poisson at its noiseless truth);
-    otherwise max(1e-5, 10 x the FP32-reference error) -- see the module docstring."""
+U32 = 2.0 ** -24
+
+
+def _perturb(A, m, seed):
+    rng = np.random.default_rng(seed)
+    s = U32 * math.sqrt(math.log2(m * m))
+    noise = (rng.standard_normal(A.shape) + 1j * rng.standard_normal(A.shape)) / math.sqrt(2)
+    return A * (1 + s * noise)
+
+
+def fp32_conditioning(fn, m, *arrays, trials=2):
+    """Largest relative change of fn(*arrays) (FP64 oracle) when every complex input that
+    the method Fourier-transforms is perturbed elementwise by a relative N(0, u^2 log2 M)."""
+    base = fn(*arrays)
+    worst = 0.0
+    for t in range(trials):
+        out = fn(*[_perturb(A, m, 1000 * t + i) for i, A in enumerate(arrays)])
+        worst = max(worst, rel_err(out, base) if np.ndim(base) else abs(out - base) / abs(base))
+    return worst
+
+
+def tol_for(case, fn, *arrays):
+    """1e-5 for well-conditioned inputs, else max(1e-5, 2 x FP32 conditioning)."""
     if case.loss == 0 or case.at_truth:
         return TOL
-    return max(TOL, 10.0 * rel_err(ref32_value, oracle_value))
+    return max(TOL, 2.0 * fp32_conditioning(fn, case.m, *arrays))
 
 
 def scalar_rel(a, b):
@@ -100,25 +121,24 @@ def test_forward_loss_and_gradient(lib, shape, kind):
     n, m, K = shape
     case = kind_case(n, m, K, kind, 11)
     g = GpuCase(lib, case)  # perturbed point: the gradient vanishes at the truth
-    ref32 = Ref32(case)
     O = g.point()
     Od = dev_c64(O)
     f, dl2 = lib.forward_loss(g.ctx, Od, g.P, cache=1)
     pb = case.problem()
     f_ref, dl2_ref = oracle.loss(pb, O, return_dl_norm2=True)
-    f32, dl2_32 = ref32.loss_and_dl2(O)
-    assert scalar_rel(f, f_ref) <= tol_for(case, f32, f_ref), (f, f_ref, f32)
-    assert scalar_rel(dl2, dl2_ref) <= tol_for(case, dl2_32, dl2_ref), (dl2, dl2_ref, dl2_32)
+    assert scalar_rel(f, f_ref) <= tol_for(case, lambda A: oracle.loss(pb, A), O), (f, f_ref)
+    tol_d = tol_for(case, lambda A: oracle.loss(pb, A, return_dl_norm2=True)[1], O)
+    assert scalar_rel(dl2, dl2_ref) <= tol_d, (dl2, dl2_ref, tol_d)
     gd = torch.empty_like(Od)
     lib.gradient(g.ctx, gd)
     g_ref = oracle.gradient(pb, O)
-    tol_g = tol_for(case, ref32.gradient(O), g_ref)
+    tol_g = tol_for(case, lambda A: oracle.gradient(pb, A), O)
     assert rel_err(host(gd), g_ref) <= tol_g
     # loss-only evaluation at another point leaves the linearisation intact
     O2 = g.point(seed=6)
     f2, _ = lib.forward_loss(g.ctx, dev_c64(O2), g.P, cache=0)
     f2_ref = oracle.loss(pb, O2)
-    assert scalar_rel(f2, f2_ref) <= tol_for(case, ref32.loss_and_dl2(O2)[0], f2_ref)
+    assert scalar_rel(f2, f2_ref) <= tol_for(case, lambda A: oracle.loss(pb, A), O2)
     lib.gradient(g.ctx, gd)
     assert rel_err(host(gd), g_ref) <= tol_g
 
@@ -130,7 +150,6 @@ def test_ggn_matvec(lib, shape, kind):
     at_truth = len(kind) > 2
     case = kind_case(n, m, K, kind[:2], 12, at_truth)
     g = GpuCase(lib, case)
-    ref32 = Ref32(case)
     O = case.O_true if at_truth else g.point()
     lib.forward_loss(g.ctx, dev_c64(O), g.P, cache=1)
     v = synth.to_c64(synth.random_complex(O.shape, seed=13))
@@ -140,7 +159,8 @@ def test_ggn_matvec(lib, shape, kind):
     for lam in (0.0, 0.37):
         lib.ggn_matvec(g.ctx, vd, out, lam)
         ref = oracle.ggn_matvec(pb, O, v, lam=lam)
-        assert rel_err(host(out), ref) <= tol_for(case, ref32.ggn_matvec(O, v, lam), ref), lam
+        tol = tol_for(case, lambda A, B: oracle.ggn_matvec(pb, A, B, lam=lam), O, v)
+        assert rel_err(host(out), ref) <= tol, (lam, tol)
 
 
 @pytest.mark.parametrize("at_truth", [False, True])
@@ -149,7 +169,6 @@ def test_jvp_and_jtvp(lib, shape, at_truth):
     n, m, K = shape
     case = kind_case(n, m, K, (1, not at_truth), 14, at_truth)
     g = GpuCase(lib, case)
-    ref32 = Ref32(case)
     O = case.O_true if at_truth else g.point()
     lib.forward_loss(g.ctx, dev_c64(O), g.P, cache=1)
     pb = case.problem()
@@ -157,12 +176,12 @@ def test_jvp_and_jtvp(lib, shape, at_truth):
     out = torch.empty((K, m, m), dtype=torch.float32, device="cuda")
     lib.jvp(g.ctx, dev_c64(v), out)
     jv_ref = oracle.jvp(pb, O, v)
-    assert rel_err(host(out), jv_ref) <= tol_for(case, ref32.jvp(O, v), jv_ref)
+    assert rel_err(host(out), jv_ref) <= tol_for(case, lambda A, B: oracle.jvp(pb, A, B), O, v)
     w = synth.to_f32(synth.random_real((K, m, m), seed=16))
     outO = torch.empty((n, n), dtype=torch.complex64, device="cuda")
     lib.jtvp(g.ctx, dev_f32(w), outO)
     jt_ref = oracle.jtvp(pb, O, w)
-    assert rel_err(host(outO), jt_ref) <= tol_for(case, ref32.jtvp(O, w), jt_ref)
+    assert rel_err(host(outO), jt_ref) <= tol_for(case, lambda A: oracle.jtvp(pb, A, w), O)
 
 
 def test_adjoint_identity_on_gpu(lib):
