@@ -11,13 +11,15 @@ struct PtyArgs {
     const float2* V;       // second gathered array: the direction vO of jvp
     const float2* P;       // probe [S][S]
     const int2* pos;       // positions [K] as (row, col)
-    const float* y;        // measurements [K][M] in team-register order (permute_measurements)
+    const float* y;        // measurements [K][M] in team-register order: sqrt(y) (Gaussian) or y (Poisson)
     const float* w;        // jtvp weights [K][S][S]
     float2* a_cache;       // [K][M] per-pixel factor a, team-register order
     float2* out;           // scatter-add target [ny][nx] (gradient, matvec, jtvp)
     float* out_real;       // jvp output [K][S][S]
     float2* scratch;       // jvp: one M-sized slot per team
-    double* partials;      // per-CTA FP64 partial sums [gridDim.x][2]
+    double* partials;      // per-CTA FP64 partial sums [gridDim.x][<=4] (grid_reduce scratch)
+    unsigned* counter;     // grid_reduce counter (zero between launches)
+    double* scal;          // FP64 scalar slots (reduce.cuh Slot)
     const float2* tw;      // twiddles W_S^j = exp(-2 pi i j / S), j < S
     int K;
     int nx;
@@ -38,8 +40,10 @@ size_t cta_smem_bytes(int LS);
 // Opt in to the kernel's dynamic shared memory and report how many CTAs fit on one SM.
 cudaError_t kernel_prepare(int LS, int kid, int* ctas_per_sm);
 
-// Copy measurements from natural [K][S][S] order into the kernels' team-register order.
-cudaError_t permute_measurements(int LS, const float* y, float* y_perm, int K, int blocks, cudaStream_t stream);
+// Copy measurements from natural [K][S][S] order into the kernels' team-register order
+// (square roots when take_sqrt: the Gaussian metric only uses sqrt(y)).
+cudaError_t permute_measurements(int LS, const float* y, float* y_perm, int K, int take_sqrt, int blocks,
+                                 cudaStream_t stream);
 
 // Launch kernel `kid` for patch side 2^LS on `grid` CTAs.
 cudaError_t kernel_launch(int LS, int kid, const PtyArgs& a, int grid, cudaStream_t stream);

@@ -15,6 +15,7 @@
 //   KID_JTVP       J^T w                                     (App. A Eq. arbitrary_jtvp_sequence)
 //   KID_JVP        J v                                       (App. B Eq. jac_ampl, forward mode)
 #include "kernels.h"
+#include "reduce.cuh"
 #include "team_fft.cuh"
 
 namespace ptylm {
@@ -41,51 +42,36 @@ __device__ __forceinline__ void prefetch_tile(const float2* tile, int tid) {
     }
 }
 
-// Per-element error metric l(zeta, y) of Eq. ell_magnitude and its first two zeta-derivatives.
-struct EllTerms {
-    float l, dl, d2l;
+// Per-pixel error-metric terms of Sec. 4.1 Eq. ell_magnitude, from h = |psihat|^2 + b and
+// the stored measurement term ym (sqrt(y) for the Gaussian metric, y for Poisson):
+//   Gaussian  l = (zeta - sqrt y)^2 / 2,   dl = zeta - sqrt y,     d2l = 1
+//   Poisson   l = zeta^2 - y log zeta^2,   dl = 2 zeta - 2 y/zeta, d2l = 2 + 2 y/zeta^2
+// returned as the combinations the kernels use: l, dl, dl/zeta and sqrt(d2l)/zeta.  With
+// r = h^(-1/2) (so zeta = h r, 1/zeta = r) the Poisson ratios are dl/zeta = 2 (h - y) r^2
+// and sqrt(d2l)/zeta = sqrt(2 (h + y)) r^2: no division or IEEE square root per pixel.
+struct PixelTerms {
+    float l, dl, dl_over_zeta, sqrt_d2l_over_zeta;
 };
-__device__ __forceinline__ EllTerms ell_terms(int loss, float h, float zeta, float y) {
-    EllTerms t;
-    if (loss == 0) {  // Gaussian: (zeta - sqrt y)^2 / 2
-        const float d = zeta - sqrtf(y);
-        t.l = 0.5f * d * d;
+template <bool WANT_L>
+__device__ __forceinline__ PixelTerms pixel_terms(int loss, float h, float ym) {
+    PixelTerms t;
+    const float r = rsqrtf(h);
+    const float zeta = h * r;
+    if (loss == 0) {
+        const float d = zeta - ym;
+        t.l = WANT_L ? 0.5f * d * d : 0.0f;
         t.dl = d;
-        t.d2l = 1.0f;
-    } else {          // Poisson: zeta^2 - y log zeta^2, with 0 log 0 = 0
-        t.l = h - (y > 0.0f ? y * logf(h) : 0.0f);
-        t.dl = 2.0f * zeta - 2.0f * y / zeta;
-        t.d2l = 2.0f + 2.0f * y / h;
+        t.dl_over_zeta = d * r;
+        t.sqrt_d2l_over_zeta = r;
+    } else {
+        t.l = WANT_L ? h - (ym > 0.0f ? ym * logf(h) : 0.0f) : 0.0f;
+        const float hy = h - ym;
+        t.dl = 2.0f * hy * r;
+        t.dl_over_zeta = 2.0f * hy * r * r;
+        const float s = 2.0f * (h + ym);
+        t.sqrt_d2l_over_zeta = s * rsqrtf(s) * r * r;
     }
     return t;
-}
-
-// Block-wide FP64 sum of two per-thread values; thread 0 writes partials[blockIdx.x*2 + {0,1}].
-__device__ void block_reduce2_store(double s0, double s1, double* partials) {
-    __shared__ double red[2][32];
-    for (int off = 16; off > 0; off >>= 1) {
-        s0 += __shfl_down_sync(0xffffffffu, s0, off);
-        s1 += __shfl_down_sync(0xffffffffu, s1, off);
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        red[0][warp] = s0;
-        red[1][warp] = s1;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        s0 = lane < nw ? red[0][lane] : 0.0;
-        s1 = lane < nw ? red[1][lane] : 0.0;
-        for (int off = 16; off > 0; off >>= 1) {
-            s0 += __shfl_down_sync(0xffffffffu, s0, off);
-            s1 += __shfl_down_sync(0xffffffffu, s1, off);
-        }
-        if (lane == 0) {
-            partials[2 * blockIdx.x] = s0;
-            partials[2 * blockIdx.x + 1] = s1;
-        }
-    }
 }
 
 // Common prologue: twiddles into shared memory, team and thread indices.
@@ -181,13 +167,11 @@ k_forward(PtyArgs a) {
                     const int e = j * G::BY + k2y;
                     const float2 ps = g[k2y] * invS;                    // orthonormal psihat
                     const float h = ps.x * ps.x + ps.y * ps.y + a.b;    // Eq. expected_count
-                    const float zeta = sqrtf(h);                        // Eq. magnitude
-                    const EllTerms t = ell_terms(a.loss, h, zeta, __ldg(yk + e * G::T));
+                    const PixelTerms t = pixel_terms<true>(a.loss, h, __ldg(yk + e * G::T));
                     sl += t.l;
                     sd += t.dl * t.dl;
-                    const float inv_zeta = 1.0f / zeta;
-                    ak[e * G::T] = ps * (sqrtf(t.d2l) * inv_zeta);
-                    g[k2y] = ps * (t.dl * inv_zeta * invS);  // psihat grad l / zeta, inverse 1/S folded in
+                    ak[e * G::T] = ps * t.sqrt_d2l_over_zeta;
+                    g[k2y] = ps * (t.dl_over_zeta * invS);  // psihat grad l / zeta, inverse 1/S folded in
                 }
             });
             scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
@@ -200,8 +184,7 @@ k_forward(PtyArgs a) {
                 if constexpr (INTENSITY) {
                     a.out_real[(size_t)k * G::M + ky * G::S + freq_kx<G>(c.tid, e)] = h;
                 } else {
-                    const float zeta = sqrtf(h);
-                    sl += ell_terms(a.loss, h, zeta, __ldg(yk + e * G::T)).l;
+                    sl += pixel_terms<true>(a.loss, h, __ldg(yk + e * G::T)).l;
                 }
             }
         }
@@ -209,7 +192,8 @@ k_forward(PtyArgs a) {
         acc_d += (double)sd;
         team_sync<G>();
     }
-    block_reduce2_store(acc_l, acc_d, a.partials);
+    double sums[2] = {acc_l, acc_d};
+    if constexpr (!INTENSITY) grid_reduce<2>(sums, a.partials, a.counter, a.scal, S_F, OP_STORE, 1.0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -265,8 +249,8 @@ k_jtvp(PtyArgs a) {
             for (int k2y = 0; k2y < G::BY; ++k2y) {
                 const int kx = freq_kx<G>(c.tid, j * G::BY + k2y);
                 const float2 ps = g[k2y] * invS;
-                const float zeta = sqrtf(ps.x * ps.x + ps.y * ps.y + a.b);
-                g[k2y] = ps * (__ldg(wk + kx) / zeta * invS);
+                const float inv_zeta = rsqrtf(ps.x * ps.x + ps.y * ps.y + a.b);
+                g[k2y] = ps * (__ldg(wk + kx) * inv_zeta * invS);
             }
         });
         scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
@@ -302,8 +286,8 @@ k_jvp(PtyArgs a) {
             const int kx = freq_kx<G>(c.tid, e);
             const float2 ps = slot[e * G::T] * invS;
             const float2 dps = v[e] * invS;
-            const float zeta = sqrtf(ps.x * ps.x + ps.y * ps.y + a.b);
-            ok[kx] = (ps.x * dps.x + ps.y * dps.y) / zeta;
+            const float inv_zeta = rsqrtf(ps.x * ps.x + ps.y * ps.y + a.b);
+            ok[kx] = (ps.x * dps.x + ps.y * dps.y) * inv_zeta;
         }
         team_sync<G>();
     }
@@ -311,26 +295,30 @@ k_jvp(PtyArgs a) {
 
 // ---------------------------------------------------------------------------------------
 // Measurements from natural [K][S][S] order to the kernels' team-register order
-// y_perm[k][e*T + t] = y[k][ky(t)][kx(t, e)].
+// y_perm[k][e*T + t] = y[k][ky(t)][kx(t, e)] (its square root for the Gaussian metric,
+// whose terms only use sqrt(y)).
 // ---------------------------------------------------------------------------------------
 template <int LS>
-__global__ void k_permute_measurements(const float* __restrict__ y, float* __restrict__ y_perm, long total) {
+__global__ void k_permute_measurements(const float* __restrict__ y, float* __restrict__ y_perm, long total,
+                                       int take_sqrt) {
     using G = Geo<LS>;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
         const long k = i / G::M;
         const int r = (int)(i - k * G::M);
         const int e = r / G::T, t = r % G::T;
-        y_perm[i] = y[k * G::M + freq_ky<G>(t) * G::S + freq_kx<G>(t, e)];
+        const float v = y[k * G::M + freq_ky<G>(t) * G::S + freq_kx<G>(t, e)];
+        y_perm[i] = take_sqrt ? sqrtf(v) : v;
     }
 }
 
-cudaError_t permute_measurements(int LS, const float* y, float* y_perm, int K, int blocks, cudaStream_t stream) {
+cudaError_t permute_measurements(int LS, const float* y, float* y_perm, int K, int take_sqrt, int blocks,
+                                 cudaStream_t stream) {
     const long total = (long)K << (2 * LS);
     if (total == 0) return cudaSuccess;
     switch (LS) {
-        case 5: k_permute_measurements<5><<<blocks, 256, 0, stream>>>(y, y_perm, total); break;
-        case 6: k_permute_measurements<6><<<blocks, 256, 0, stream>>>(y, y_perm, total); break;
-        case 7: k_permute_measurements<7><<<blocks, 256, 0, stream>>>(y, y_perm, total); break;
+        case 5: k_permute_measurements<5><<<blocks, 256, 0, stream>>>(y, y_perm, total, take_sqrt); break;
+        case 6: k_permute_measurements<6><<<blocks, 256, 0, stream>>>(y, y_perm, total, take_sqrt); break;
+        case 7: k_permute_measurements<7><<<blocks, 256, 0, stream>>>(y, y_perm, total, take_sqrt); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -13,6 +13,7 @@
 
 #include "../../include/ptylm.h"
 #include "kernels.h"
+#include "reduce.cuh"
 
 using namespace ptylm;
 
@@ -46,121 +47,71 @@ static ptylm_status fail(ptylm_status s, const char* fmt, ...) {
     } while (0)
 
 // ---------------------------------------------------------------------------------------
-// Device scalar slots (FP64) and reduction kernels
+// Vector kernels of the truncated CG and of Algorithm 1.  Products are formed in FP32 and
+// summed per thread over its few grid-stride elements, then reduced in FP64 by
+// grid_reduce (reduce.cuh), whose last CTA also updates the FP64 scalars (alpha, beta,
+// ||p||^2, ...): a CG iteration is the matvec plus two launches, with no host round trip.
 // ---------------------------------------------------------------------------------------
-enum Slot {
-    S_F = 0, S_DL2 = 1,           // forward: f, ||grad_zeta l||^2
-    S_RR = 2, S_PQ = 3, S_ALPHA = 4, S_RRNEW = 5, S_BETA = 6,
-    S_GG = 7,                     // ||g||^2
-    S_DD = 8, S_DG = 9, S_DR = 10, // step dots for the predicted reduction
-    S_ER = 11, S_EI = 12, S_NO = 13, S_NR = 14,  // error metric sums
-    S_TMP = 15,
-    S_COUNT = 24
-};
-enum FinalOp { OP_NONE = 0, OP_ALPHA = 1, OP_BETA = 2 };
-
 static constexpr int VEC_THREADS = 256;
-static constexpr int MAX_PART_WIDTH = 4;
 
-// Real-coordinate inner products sum(a.re*b.re + a.im*b.im) accumulate in FP64.
-__device__ __forceinline__ double rdot(float2 a, float2 b) {
-    return (double)a.x * (double)b.x + (double)a.y * (double)b.y;
-}
+__device__ __forceinline__ float rdotf(float2 a, float2 b) { return a.x * b.x + a.y * b.y; }
 
-// Block sum of up to 4 FP64 values -> part[blockIdx.x * W + c].
-template <int W>
-__device__ void block_sum_store(double (&s)[W], double* part) {
-    __shared__ double red[W][VEC_THREADS / 32];
-#pragma unroll
-    for (int c = 0; c < W; ++c)
-        for (int off = 16; off > 0; off >>= 1) s[c] += __shfl_down_sync(0xffffffffu, s[c], off);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0)
-#pragma unroll
-        for (int c = 0; c < W; ++c) red[c][warp] = s[c];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int c = 0; c < W; ++c) {
-            double t = 0.0;
-            for (int w = 0; w < VEC_THREADS / 32; ++w) t += red[c][w];
-            part[blockIdx.x * W + c] = t;
-        }
-    }
-}
-
-// Sum columns of part[nb][W] in a fixed order into s[dst + c]; then apply `op`.
-__global__ void k_finalize(const double* __restrict__ part, int nb, int W, double* s, int dst, int op) {
-    __shared__ double red[MAX_PART_WIDTH][VEC_THREADS];
-    for (int c = 0; c < W; ++c) {
-        double t = 0.0;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) t += part[b * W + c];
-        red[c][threadIdx.x] = t;
-    }
-    __syncthreads();
-    for (int half = blockDim.x / 2; half > 0; half >>= 1) {
-        if ((int)threadIdx.x < half)
-            for (int c = 0; c < W; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + half];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        for (int c = 0; c < W; ++c) s[dst + c] = red[c][0];
-        if (op == OP_ALPHA) {
-            s[S_ALPHA] = s[S_RR] / s[S_PQ];
-        } else if (op == OP_BETA) {
-            s[S_BETA] = s[S_RRNEW] / s[S_RR];
-            s[S_RR] = s[S_RRNEW];
-        }
-    }
-}
+#define GRID_STRIDE(i, n) \
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (n); i += (long)gridDim.x * blockDim.x)
 
 // out = lambda * D * v   (D == NULL: identity).  Initialises the matvec accumulator.
 __global__ void k_damping_init(const float2* __restrict__ v, const float* __restrict__ D, float lambda,
                                float2* __restrict__ out, long n) {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    GRID_STRIDE(i, n) {
         const float d = lambda * (D ? D[i] : 1.0f);
         const float2 x = v[i];
         out[i] = make_float2(d * x.x, d * x.y);
     }
 }
 
-// partials of (a.b, c.d, e.f) -- any of the pairs may be unused (W picks how many).
+// Up to three real-coordinate dot products a_i . b_i into slots [dst, dst + W).
 template <int W>
 __global__ void k_dots(const float2* __restrict__ a0, const float2* __restrict__ b0,
                        const float2* __restrict__ a1, const float2* __restrict__ b1,
                        const float2* __restrict__ a2, const float2* __restrict__ b2, long n,
-                       double* part) {
+                       double* part, unsigned* counter, double* sc, int dst, int op) {
+    float f[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) f[c] = 0.0f;
+    GRID_STRIDE(i, n) {
+        f[0] += rdotf(a0[i], b0[i]);
+        if constexpr (W > 1) f[1] += rdotf(a1[i], b1[i]);
+        if constexpr (W > 2) f[2] += rdotf(a2[i], b2[i]);
+    }
     double s[W];
 #pragma unroll
-    for (int c = 0; c < W; ++c) s[c] = 0.0;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        s[0] += rdot(a0[i], b0[i]);
-        if constexpr (W > 1) s[1] += rdot(a1[i], b1[i]);
-        if constexpr (W > 2) s[2] += rdot(a2[i], b2[i]);
-    }
-    block_sum_store<W>(s, part);
+    for (int c = 0; c < W; ++c) s[c] = f[c];
+    grid_reduce<W>(s, part, counter, sc, dst, op, 1.0);
 }
 
-// CG start: r = -g - q, p = r; partial r.r
-__global__ void k_cg_start(const float2* __restrict__ g, const float2* __restrict__ q, float2* __restrict__ r,
-                           float2* __restrict__ p, long n, double* part) {
-    double s[1] = {0.0};
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+// CG start: r = -g - q, p = r, q = lambda p; r.r (= p.p) into the slots.
+__global__ void k_cg_start(const float2* __restrict__ g, float2* __restrict__ q, float2* __restrict__ r,
+                           float2* __restrict__ p, float lambda, long n, double* part, unsigned* counter,
+                           double* sc) {
+    float f = 0.0f;
+    GRID_STRIDE(i, n) {
         const float2 gi = g[i], qi = q[i];
         const float2 ri = make_float2(-gi.x - qi.x, -gi.y - qi.y);
         r[i] = ri;
         p[i] = ri;
-        s[0] += rdot(ri, ri);
+        q[i] = make_float2(lambda * ri.x, lambda * ri.y);
+        f += rdotf(ri, ri);
     }
-    block_sum_store<1>(s, part);
+    double s[1] = {f};
+    grid_reduce<1>(s, part, counter, sc, 0, OP_START, 1.0);
 }
 
-// x += alpha p, r -= alpha q; partial r.r   (alpha read from the device scalar slot)
+// x += alpha p, r -= alpha q; new r.r -> beta (alpha read from the slots).
 __global__ void k_cg_update(float2* __restrict__ x, float2* __restrict__ r, const float2* __restrict__ p,
-                            const float2* __restrict__ q, const double* __restrict__ sc, long n, double* part) {
+                            const float2* __restrict__ q, long n, double* part, unsigned* counter, double* sc) {
     const float alpha = (float)sc[S_ALPHA];
-    double s[1] = {0.0};
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    float f = 0.0f;
+    GRID_STRIDE(i, n) {
         const float2 pi = p[i], qi = q[i];
         float2 xi = x[i], ri = r[i];
         xi.x += alpha * pi.x;
@@ -169,16 +120,17 @@ __global__ void k_cg_update(float2* __restrict__ x, float2* __restrict__ r, cons
         ri.y -= alpha * qi.y;
         x[i] = xi;
         r[i] = ri;
-        s[0] += rdot(ri, ri);
+        f += rdotf(ri, ri);
     }
-    block_sum_store<1>(s, part);
+    double s[1] = {f};
+    grid_reduce<1>(s, part, counter, sc, 0, OP_BETA, 1.0);
 }
 
-// p = r + beta p;  q = lambda D p  (the damping term that starts the next matvec)
+// p = r + beta p;  q = lambda D p (starts the next matvec's accumulator).
 __global__ void k_cg_direction(const float2* __restrict__ r, float2* __restrict__ p, float2* __restrict__ q,
-                               const float* __restrict__ D, float lambda, const double* __restrict__ sc, long n) {
+                               const float* __restrict__ D, float lambda, long n, const double* __restrict__ sc) {
     const float beta = (float)sc[S_BETA];
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    GRID_STRIDE(i, n) {
         const float2 ri = r[i], pi = p[i];
         const float2 pn = make_float2(ri.x + beta * pi.x, ri.y + beta * pi.y);
         p[i] = pn;
@@ -189,7 +141,7 @@ __global__ void k_cg_direction(const float2* __restrict__ r, float2* __restrict_
 
 // z = x + d
 __global__ void k_add(const float2* __restrict__ x, const float2* __restrict__ d, float2* __restrict__ z, long n) {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    GRID_STRIDE(i, n) {
         const float2 a = x[i], b = d[i];
         z[i] = make_float2(a.x + b.x, a.y + b.y);
     }
@@ -197,17 +149,19 @@ __global__ void k_add(const float2* __restrict__ x, const float2* __restrict__ d
 
 // Object-error sums over a mask: <O, O_ref> (re, im), ||O||^2, ||O_ref||^2.
 __global__ void k_err_sums(const float2* __restrict__ O, const float2* __restrict__ R,
-                           const uint8_t* __restrict__ mask, long n, double* part) {
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+                           const uint8_t* __restrict__ mask, long n, double* part, unsigned* counter,
+                           double* sc) {
+    float f[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    GRID_STRIDE(i, n) {
         if (mask && !mask[i]) continue;
         const float2 o = O[i], r = R[i];
-        s[0] += (double)o.x * r.x + (double)o.y * r.y;   // Re conj(O) R
-        s[1] += (double)o.x * r.y - (double)o.y * r.x;   // Im conj(O) R
-        s[2] += (double)o.x * o.x + (double)o.y * o.y;
-        s[3] += (double)r.x * r.x + (double)r.y * r.y;
+        f[0] += o.x * r.x + o.y * r.y;   // Re conj(O) R
+        f[1] += o.x * r.y - o.y * r.x;   // Im conj(O) R
+        f[2] += o.x * o.x + o.y * o.y;
+        f[3] += r.x * r.x + r.y * r.y;
     }
-    block_sum_store<4>(s, part);
+    double s[4] = {f[0], f[1], f[2], f[3]};
+    grid_reduce<4>(s, part, counter, sc, S_ER, OP_STORE, 1.0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -233,6 +187,7 @@ struct ptylm_ctx {
     float2* P_lin = nullptr;
     double* partials = nullptr;
     int partials_cap = 0;
+    unsigned* counters = nullptr;  // grid_reduce counters [CNT_COUNT]
     double* scal = nullptr;        // device FP64 scalars [S_COUNT]
     double* scal_host = nullptr;   // pinned mirror
     float2* jvp_scratch = nullptr;
@@ -354,13 +309,6 @@ static bool is_host_pointer(const void* p) {
 
 static int vec_blocks(const ptylm_ctx* c) { return c->vec_grid; }
 
-// Sum the width-W partials of `nb` blocks into scalar slots [dst, dst+W).
-static ptylm_status finalize(ptylm_ctx* c, int nb, int W, int dst, int op) {
-    k_finalize<<<1, VEC_THREADS, 0, c->stream>>>(c->partials, nb, W, c->scal, dst, op);
-    STATUS_TRY(vec_launched(c));
-    return PTYLM_OK;
-}
-
 static ptylm_status read_scalars(ptylm_ctx* c, int first, int count) {
     CUDA_TRY(cudaMemcpyAsync(c->scal_host + first, c->scal + first, sizeof(double) * count,
                              cudaMemcpyDeviceToHost, c->stream));
@@ -369,13 +317,13 @@ static ptylm_status read_scalars(ptylm_ctx* c, int first, int count) {
 }
 
 static ptylm_status dots(ptylm_ctx* c, int W, const float2* a0, const float2* b0, const float2* a1,
-                         const float2* b1, const float2* a2, const float2* b2, int dst, int op = OP_NONE) {
+                         const float2* b1, const float2* a2, const float2* b2, int dst, int op = OP_STORE) {
     const int nb = vec_blocks(c);
-    if (W == 1) k_dots<1><<<nb, VEC_THREADS, 0, c->stream>>>(a0, b0, a1, b1, a2, b2, c->N, c->partials);
-    else if (W == 2) k_dots<2><<<nb, VEC_THREADS, 0, c->stream>>>(a0, b0, a1, b1, a2, b2, c->N, c->partials);
-    else k_dots<3><<<nb, VEC_THREADS, 0, c->stream>>>(a0, b0, a1, b1, a2, b2, c->N, c->partials);
-    STATUS_TRY(vec_launched(c));
-    return finalize(c, nb, W, dst, op);
+    unsigned* cnt = c->counters + CNT_VEC;
+    if (W == 1) k_dots<1><<<nb, VEC_THREADS, 0, c->stream>>>(a0, b0, a1, b1, a2, b2, c->N, c->partials, cnt, c->scal, dst, op);
+    else if (W == 2) k_dots<2><<<nb, VEC_THREADS, 0, c->stream>>>(a0, b0, a1, b1, a2, b2, c->N, c->partials, cnt, c->scal, dst, op);
+    else k_dots<3><<<nb, VEC_THREADS, 0, c->stream>>>(a0, b0, a1, b1, a2, b2, c->N, c->partials, cnt, c->scal, dst, op);
+    return vec_launched(c);
 }
 
 static PtyArgs base_args(const ptylm_ctx* c) {
@@ -389,6 +337,7 @@ static PtyArgs base_args(const ptylm_ctx* c) {
     a.b = c->d.background;
     a.loss = c->d.loss;
     a.partials = c->partials;
+    a.scal = c->scal;
     return a;
 }
 
@@ -413,18 +362,15 @@ static ptylm_status op_forward(ptylm_ctx* c, const float2* O, const float2* P, i
         a.P = cache ? c->P_lin : P;
         a.a_cache = c->a_cache;
         a.out = c->grad;
+        a.counter = c->counters + CNT_FWD;
         STATUS_TRY(launch(c, kid, a));
-        STATUS_TRY(finalize(c, c->grid[kid], 2, S_F, OP_NONE));
     }
     if (cache) c->has_lin = true;
     return PTYLM_OK;
 }
 
-// out = (G + lambda D) v at the linearisation point (device pointers).
-static ptylm_status op_matvec(ptylm_ctx* c, const float2* v, double lambda, const float* D, float2* out) {
-    const int nb = vec_blocks(c);
-    k_damping_init<<<nb, VEC_THREADS, 0, c->stream>>>(v, D, (float)lambda, out, c->N);
-    STATUS_TRY(vec_launched(c));
+// out += G v at the linearisation point (out already holds the damping term).
+static ptylm_status op_matvec_accumulate(ptylm_ctx* c, const float2* v, float2* out) {
     if (c->d.K == 0) return PTYLM_OK;
     PtyArgs a = base_args(c);
     a.O = v;
@@ -433,6 +379,14 @@ static ptylm_status op_matvec(ptylm_ctx* c, const float2* v, double lambda, cons
     a.out = out;
     STATUS_TRY(launch(c, KID_MATVEC, a));
     return PTYLM_OK;
+}
+
+// out = (G + lambda D) v at the linearisation point (device pointers).
+static ptylm_status op_matvec(ptylm_ctx* c, const float2* v, double lambda, const float* D, float2* out) {
+    const int nb = vec_blocks(c);
+    k_damping_init<<<nb, VEC_THREADS, 0, c->stream>>>(v, D, (float)lambda, out, c->N);
+    STATUS_TRY(vec_launched(c));
+    return op_matvec_accumulate(c, v, out);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -544,7 +498,8 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
     if ((s = ctx_alloc_t(c, &c->grad, c->N, "gradient")) != PTYLM_OK) return bail(s);
     if ((s = ctx_alloc_t(c, &c->O_lin, c->N, "object linearisation point")) != PTYLM_OK) return bail(s);
     if ((s = ctx_alloc_t(c, &c->P_lin, c->M, "probe linearisation point")) != PTYLM_OK) return bail(s);
-    if ((s = ctx_alloc_t(c, &c->partials, (size_t)c->partials_cap * MAX_PART_WIDTH, "partials")) != PTYLM_OK) return bail(s);
+    if ((s = ctx_alloc_t(c, &c->partials, (size_t)c->partials_cap * kMaxReduceWidth, "partials")) != PTYLM_OK) return bail(s);
+    if ((s = ctx_alloc_t(c, &c->counters, CNT_COUNT, "reduction counters")) != PTYLM_OK) return bail(s);
     if ((s = ctx_alloc_t(c, &c->scal, S_COUNT, "scalars")) != PTYLM_OK) return bail(s);
     if (cudaMallocHost((void**)&c->scal_host, sizeof(double) * S_COUNT) != cudaSuccess) {
         cudaGetLastError();
@@ -563,12 +518,13 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
     if (cudaMemcpyAsync(c->tw, htw.data(), sizeof(float2) * c->S, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
         cudaMemcpyAsync(c->pos, hp.data(), sizeof(int2) * std::max(1, d.K), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->scal, 0, sizeof(double) * S_COUNT, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->counters, 0, sizeof(unsigned) * CNT_COUNT, c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess) {
         cudaError_t e = cudaGetLastError();
         return bail(fail(PTYLM_ERR_CUDA, "uploading context tables: %s", cudaGetErrorString(e)));
     }
     if (d.K > 0) {
-        cudaError_t e = permute_measurements(LS, y_dev, c->y_perm, d.K, c->vec_grid, c->stream);
+        cudaError_t e = permute_measurements(LS, y_dev, c->y_perm, d.K, d.loss == PTYLM_LOSS_GAUSSIAN, c->vec_grid, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return bail(fail(PTYLM_ERR_CUDA, "copying measurements: %s", cudaGetErrorString(e)));
     }
@@ -582,7 +538,7 @@ ptylm_status ptylm_set_measurements(ptylm_ctx* c, const float* y_dev) {
     if (c->d.K > 0 && !y_dev) return fail(PTYLM_ERR_ARG, "y must be non-NULL when K > 0");
     c->has_lin = false;
     if (c->d.K == 0) return PTYLM_OK;
-    CUDA_TRY(permute_measurements(c->LS, y_dev, c->y_perm, c->d.K, c->vec_grid, c->stream));
+    CUDA_TRY(permute_measurements(c->LS, y_dev, c->y_perm, c->d.K, c->d.loss == PTYLM_LOSS_GAUSSIAN, c->vec_grid, c->stream));
     ++c->launches;
     return PTYLM_OK;
 }
@@ -728,6 +684,7 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
     if (!c || !O_inout || !P_inout || !prm) return fail(PTYLM_ERR_ARG, "ctx, O, P and params must be non-NULL");
     if (prm->max_outer < 0 || prm->max_cg < 0 || !(prm->kappa > 1.0) || !(prm->mu0 > 0.0))
         return fail(PTYLM_ERR_ARG, "invalid LM parameters");
+    if (c->d.K == 0) return fail(PTYLM_ERR_ARG, "lm_solve needs at least one scan position");
     const long N = c->N;
     const size_t nbytes = sizeof(float2) * N;
     if (!c->cg_x) {
@@ -748,6 +705,7 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
     const float2* P = c->stage_P;
     float2 *x = c->cg_x, *r = c->cg_r, *p = c->cg_p, *q = c->cg_q, *trial = c->trial;
     const int nb = vec_blocks(c);
+    unsigned* cnt = c->counters + CNT_VEC;
     CUDA_TRY(cudaMemsetAsync(x, 0, nbytes, c->stream));
 
     double mu = prm->mu0;
@@ -756,9 +714,9 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
     ptylm_status status = PTYLM_OK;
     double f_cur = NAN, err = NAN;
     auto object_error = [&](double* e_out) -> ptylm_status {
-        k_err_sums<<<nb, VEC_THREADS, 0, c->stream>>>(O, reinterpret_cast<const float2*>(prm->O_ref), prm->mask, N, c->partials);
+        k_err_sums<<<nb, VEC_THREADS, 0, c->stream>>>(O, reinterpret_cast<const float2*>(prm->O_ref), prm->mask, N,
+                                                      c->partials, cnt, c->scal);
         STATUS_TRY(vec_launched(c));
-        STATUS_TRY(finalize(c, nb, 4, S_ER, OP_NONE));
         STATUS_TRY(read_scalars(c, S_ER, 4));
         const double ac = std::hypot(c->scal_host[S_ER], c->scal_host[S_EI]);
         const double e2 = std::max(0.0, c->scal_host[S_NO] + c->scal_host[S_NR] - 2.0 * ac);
@@ -789,12 +747,12 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
         bool stalled = false;
         while (!(rho > prm->rho_min)) {
             const double lambda = mu * std::pow(std::sqrt(dl2), prm->nu);
+            const float lam32 = (float)lambda;
             // ---- truncated CG on (G + lambda I) x = -g, warm-started from x ----
-            STATUS_TRY(op_matvec(c, x, lambda, nullptr, q));
+            STATUS_TRY(op_matvec(c, x, lambda, nullptr, q));                      // q = (G + lambda I) x
             ++matvecs;
-            k_cg_start<<<nb, VEC_THREADS, 0, c->stream>>>(c->grad, q, r, p, N, c->partials);
-            STATUS_TRY(vec_launched(c));
-            STATUS_TRY(finalize(c, nb, 1, S_RR, OP_NONE));
+            k_cg_start<<<nb, VEC_THREADS, 0, c->stream>>>(c->grad, q, r, p, lam32, N, c->partials, cnt, c->scal);
+            STATUS_TRY(vec_launched(c));                                          // r = p = -g - q, q = lambda p
             int it = 0;
             bool converged = false;
             for (;;) {
@@ -805,26 +763,13 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
                     if (std::sqrt(c->scal_host[S_RR]) <= tol) { converged = true; break; }
                     if (it >= prm->max_cg) break;
                 }
-                // q = lambda p was written by the previous direction update (or below at it=0)
-                if (it == 0) {
-                    k_damping_init<<<nb, VEC_THREADS, 0, c->stream>>>(p, nullptr, (float)lambda, q, N);
-                    STATUS_TRY(vec_launched(c));
-                }
-                if (c->d.K > 0) {
-                    PtyArgs a = base_args(c);
-                    a.O = p;
-                    a.P = c->P_lin;
-                    a.a_cache = c->a_cache;
-                    a.out = q;
-                    STATUS_TRY(launch(c, KID_MATVEC, a));
-                }
+                STATUS_TRY(op_matvec_accumulate(c, p, q));                        // q += G p
                 ++matvecs;
-                STATUS_TRY(dots(c, 1, p, q, nullptr, nullptr, nullptr, nullptr, S_PQ, OP_ALPHA));
-                k_cg_update<<<nb, VEC_THREADS, 0, c->stream>>>(x, r, p, q, c->scal, N, c->partials);
-                STATUS_TRY(vec_launched(c));
-                STATUS_TRY(finalize(c, nb, 1, S_RRNEW, OP_BETA));
-                k_cg_direction<<<nb, VEC_THREADS, 0, c->stream>>>(r, p, q, nullptr, (float)lambda, c->scal, N);
-                STATUS_TRY(vec_launched(c));
+                STATUS_TRY(dots(c, 1, p, q, nullptr, nullptr, nullptr, nullptr, S_PAP, OP_ALPHA));  // alpha
+                k_cg_update<<<nb, VEC_THREADS, 0, c->stream>>>(x, r, p, q, N, c->partials, cnt, c->scal);
+                STATUS_TRY(vec_launched(c));                                      // x, r; beta
+                k_cg_direction<<<nb, VEC_THREADS, 0, c->stream>>>(r, p, q, nullptr, lam32, N, c->scal);
+                STATUS_TRY(vec_launched(c));                                      // p, q = lambda p
                 ++it;
             }
             cg_this += it;
