@@ -29,17 +29,13 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// One thread per 16 KB chunk starts pulling a position's M-element cache tile toward L2,
-// so the spectral stage later finds it there instead of waiting on DRAM.
-template <class G>
-__device__ __forceinline__ void prefetch_tile(const float2* tile, int tid) {
+// Threads 0, 1, ... each start pulling one 16 KB chunk of a position's tile (`bytes`, a
+// multiple of 16) toward L2, so the spectral stage later finds it there instead of waiting
+// on DRAM.
+__device__ __forceinline__ void prefetch_tile_l2(const void* tile, unsigned bytes, int tid) {
     constexpr unsigned kChunk = 16384;
-    constexpr int kChunks = (int)(sizeof(float2) * G::M / kChunk);
-    if constexpr (kChunks > 0) {
-        if (tid < kChunks) prefetch_l2(reinterpret_cast<const char*>(tile) + (size_t)tid * kChunk, kChunk);
-    } else {
-        if (tid == 0) prefetch_l2(tile, sizeof(float2) * G::M);
-    }
+    const unsigned off = (unsigned)tid * kChunk;
+    if (off < bytes) prefetch_l2(reinterpret_cast<const char*>(tile) + off, min(kChunk, bytes - off));
 }
 
 // Per-pixel error-metric terms of Sec. 4.1 Eq. ell_magnitude, from h = |psihat|^2 + b and
@@ -157,6 +153,7 @@ k_forward(PtyArgs a) {
     for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
         const int2 rc = a.pos[k];
         const float* yk = a.y + (size_t)k * G::M + c.tid;  // measurements in team-register order
+        if constexpr (!INTENSITY) prefetch_tile_l2(a.y + (size_t)k * G::M, sizeof(float) * G::M, c.tid);
         float sl = 0.0f, sd = 0.0f;
         gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
         if constexpr (CACHE) {
@@ -210,7 +207,7 @@ k_ggn_matvec(PtyArgs a) {
     float2 v[32];
     for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
         const int2 rc = a.pos[k];
-        prefetch_tile<G>(a.a_cache + (size_t)k * G::M, c.tid);
+        prefetch_tile_l2(a.a_cache + (size_t)k * G::M, sizeof(float2) * G::M, c.tid);
         gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
         const float2* ak = a.a_cache + (size_t)k * G::M + c.tid;
         team_fft_roundtrip<G>(v, c.sm, c.tw, c.tid, [&](float2* g, int j) {
