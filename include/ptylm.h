@@ -195,6 +195,33 @@ enum {
 ptylm_status ptylm_profile(ptylm_ctx* ctx, int enable);
 ptylm_status ptylm_profile_read(ptylm_ctx* ctx, int kernel, double* total_ms, long long* launches);
 
+/* Allocation-free error metric (the paper has no counterpart: this serves callers that
+ * cannot allocate device memory -- code that issues work while its stream is being
+ * captured into a CUDA graph, where cudaMalloc is not allowed; steady-state loops that
+ * forbid allocation after start-up; hosts whose device memory is owned by another
+ * allocator).  Computes the same f = sum_k sum_m l(zeta_km, y_km) and ||grad_zeta l||^2 as
+ * forward_loss(cache = 0), without a context and without allocating: the caller passes
+ * all inputs and the output, and the only scratch (twiddle tables, FP64 partial sums, a
+ * counter, an error flag) is a file-scope device array of PTYLM_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits.
+ *   ny, nx: object size; m: probe side (32, 64 or 128; larger sizes are rejected with
+ *   PTYLM_ERR_ARG); K >= 0; loss, background: as in ptylm_desc.
+ *   O [ny][nx], P [m][m], positions int32 [K][2] (8-byte aligned), y float [K][m][m] in
+ *   natural order: device pointers.  out_dev: device double[2] <- (f, ||grad_zeta l||^2).
+ *   stream: cudaStream_t.
+ * At most PTYLM_NOALLOC_MAX_CTAS CTAs run (fewer positions in flight, same result).
+ * The first call on a device sets up that device's scratch (symbol address, twiddle
+ * upload): make it before any stream capture.  Every call shares the scratch, which keeps
+ * the last call's contents; the counter and flag are cleared at the start of each call.
+ * Calls whose work overlaps on the GPU (other streams, other threads) race and give wrong
+ * results.  The call synchronises `stream` to read the error flag: positions outside the
+ * object return PTYLM_ERR_ARG. */
+#define PTYLM_NOALLOC_MAX_CTAS 2048
+#define PTYLM_NOALLOC_SCRATCH_BYTES 35328
+ptylm_status ptylm_forward_loss_noalloc(int ny, int nx, int m, int K, int loss, float background,
+                                        const ptylm_c64* O, const ptylm_c64* P, const int32_t* positions,
+                                        const float* y, double* out_dev, void* stream);
+
 /* Free the context and everything it allocated (NULL is accepted). */
 ptylm_status lm_destroy(ptylm_ctx* ctx);
 

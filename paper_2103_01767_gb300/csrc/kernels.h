@@ -45,6 +45,9 @@ cudaError_t kernel_prepare(int LS, int kid, int* ctas_per_sm);
 cudaError_t permute_measurements(int LS, const float* y, float* y_perm, int K, int take_sqrt, int blocks,
                                  cudaStream_t stream);
 
+// Record the thread-local message that ptylm_last_error() returns (shared by all entry points).
+void set_last_error(const char* msg);
+
 // Launch kernel `kid` for patch side 2^LS on `grid` CTAs.
 cudaError_t kernel_launch(int LS, int kid, const PtyArgs& a, int grid, cudaStream_t stream);
 

@@ -15,127 +15,11 @@
 //   KID_JTVP       J^T w                                     (App. A Eq. arbitrary_jtvp_sequence)
 //   KID_JVP        J v                                       (App. B Eq. jac_ampl, forward mode)
 #include "kernels.h"
+#include "ptycho_device.cuh"
 #include "reduce.cuh"
 #include "team_fft.cuh"
 
 namespace ptylm {
-
-__device__ __forceinline__ void red_add_c64(float2* addr, float2 v) {
-    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(v.x), "f"(v.y) : "memory");
-}
-
-// Asynchronous bulk prefetch of `bytes` (multiple of 16, 16-byte aligned) into L2.
-__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-// Threads 0, 1, ... each start pulling one 16 KB chunk of a position's tile (`bytes`, a
-// multiple of 16) toward L2, so the spectral stage later finds it there instead of waiting
-// on DRAM.
-__device__ __forceinline__ void prefetch_tile_l2(const void* tile, unsigned bytes, int tid) {
-    constexpr unsigned kChunk = 16384;
-    const unsigned off = (unsigned)tid * kChunk;
-    if (off < bytes) prefetch_l2(reinterpret_cast<const char*>(tile) + off, min(kChunk, bytes - off));
-}
-
-// Per-pixel error-metric terms of Sec. 4.1 Eq. ell_magnitude, from h = |psihat|^2 + b and
-// the stored measurement term ym (sqrt(y) for the Gaussian metric, y for Poisson):
-//   Gaussian  l = (zeta - sqrt y)^2 / 2,   dl = zeta - sqrt y,     d2l = 1
-//   Poisson   l = zeta^2 - y log zeta^2,   dl = 2 zeta - 2 y/zeta, d2l = 2 + 2 y/zeta^2
-// returned as the combinations the kernels use: l, dl, dl/zeta and sqrt(d2l)/zeta.  With
-// r = h^(-1/2) (so zeta = h r, 1/zeta = r) the Poisson ratios are dl/zeta = 2 (h - y) r^2
-// and sqrt(d2l)/zeta = sqrt(2 (h + y)) r^2: no division or IEEE square root per pixel.
-struct PixelTerms {
-    float l, dl, dl_over_zeta, sqrt_d2l_over_zeta;
-};
-template <bool WANT_L>
-__device__ __forceinline__ PixelTerms pixel_terms(int loss, float h, float ym) {
-    PixelTerms t;
-    const float r = rsqrtf(h);
-    const float zeta = h * r;
-    if (loss == 0) {
-        const float d = zeta - ym;
-        t.l = WANT_L ? 0.5f * d * d : 0.0f;
-        t.dl = d;
-        t.dl_over_zeta = d * r;
-        t.sqrt_d2l_over_zeta = r;
-    } else {
-        t.l = WANT_L ? h - (ym > 0.0f ? ym * logf(h) : 0.0f) : 0.0f;
-        const float hy = h - ym;
-        t.dl = 2.0f * hy * r;
-        t.dl_over_zeta = 2.0f * hy * r * r;
-        const float s = 2.0f * (h + ym);
-        t.sqrt_d2l_over_zeta = s * rsqrtf(s) * r * r;
-    }
-    return t;
-}
-
-// Common prologue: twiddles into shared memory, team and thread indices.
-template <class G>
-struct TeamCtx {
-    float2* tw;
-    float2* sm;
-    int team, tid;
-};
-
-template <class G>
-__device__ __forceinline__ TeamCtx<G> team_setup(const float2* tw_g) {
-    extern __shared__ float4 dyn_smem_f4[];
-    float2* dyn = reinterpret_cast<float2*>(dyn_smem_f4);
-    TeamCtx<G> c;
-    c.tw = dyn;
-    for (int i = threadIdx.x; i < G::S; i += blockDim.x) c.tw[i] = tw_g[i];
-    c.team = threadIdx.x / G::T;
-    c.tid = threadIdx.x % G::T;
-    c.sm = dyn + G::S + c.team * G::M;
-    __syncthreads();
-    return c;
-}
-
-// Pass-1 gather: thread t = x + S*b holds rows y = BX*a + b of column x:
-//   v[a] = P[y][x] * A[r0 + y][c0 + x].
-// Lanes are consecutive columns: each warp load reads 256 contiguous bytes of one row.
-template <class G>
-__device__ __forceinline__ void gather_times_probe(float2* v, const float2* __restrict__ A,
-                                                   const float2* __restrict__ P, int nx, int r0,
-                                                   int c0, int tid) {
-    const int x = tid & (G::S - 1), b = tid >> G::LOG_S;
-    const float2* src = A + (size_t)(r0 + b) * nx + c0 + x;
-    const float2* pr = P + b * G::S + x;
-    const size_t row_step = (size_t)G::BX * nx;
-#pragma unroll
-    for (int a0 = 0; a0 < 32; a0 += 8) {
-        float2 pv[8], av[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            pv[i] = pr[G::BX * G::S * (a0 + i)];  // plain load: an __ldg is hoisted out of the position loop
-            av[i] = __ldg(src + row_step * (a0 + i));
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[a0 + i] = cmul(pv[i], av[i]);
-        sched_fence();
-    }
-}
-
-// Pass-1 scatter: out[r0 + y][c0 + x] += conj(P[y][x]) * v[a], same thread layout.
-template <class G>
-__device__ __forceinline__ void scatter_times_conj_probe(const float2* v, float2* out,
-                                                         const float2* __restrict__ P, int nx,
-                                                         int r0, int c0, int tid) {
-    const int x = tid & (G::S - 1), b = tid >> G::LOG_S;
-    float2* dst = out + (size_t)(r0 + b) * nx + c0 + x;
-    const float2* pr = P + b * G::S + x;
-    const size_t row_step = (size_t)G::BX * nx;
-#pragma unroll
-    for (int a0 = 0; a0 < 32; a0 += 8) {
-        float2 pv[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) pv[i] = pr[G::BX * G::S * (a0 + i)];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) red_add_c64(dst + row_step * (a0 + i), cmulc(v[a0 + i], pv[i]));
-        sched_fence();
-    }
-}
 
 // ---------------------------------------------------------------------------------------
 // Forward model + error metric (+ cache and gradient when CACHE; intensities only when

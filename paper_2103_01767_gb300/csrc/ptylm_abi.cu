@@ -32,6 +32,8 @@ static ptylm_status fail(ptylm_status s, const char* fmt, ...) {
     return s;
 }
 
+void ptylm::set_last_error(const char* msg) { g_last_error = msg; }
+
 #define CUDA_TRY(expr)                                                                     \
     do {                                                                                   \
         cudaError_t e_ = (expr);                                                           \

@@ -90,6 +90,7 @@ def load_library():
             lib.lm_destroy.argtypes = [vp]
             lib.forward_intensity.argtypes = [vp, vp, vp, vp]
             lib.ptylm_set_measurements.argtypes = [vp, vp]
+            lib.ptylm_forward_loss_noalloc.argtypes = [i, i, i, i, i, ctypes.c_float, vp, vp, vp, vp, vp, vp]
             lib.ptylm_profile.argtypes = [vp, i]
             lib.ptylm_profile_read.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
             lib.ptylm_strerror.argtypes = [i]
@@ -98,6 +99,7 @@ def load_library():
             lib.ptylm_default_lm_params.argtypes = [ctypes.POINTER(LMParams), i]
             for name in ("lm_init", "forward_loss", "gradient", "jvp", "jtvp", "ggn_matvec",
                          "lm_solve", "lm_destroy", "forward_intensity", "ptylm_set_measurements",
+                         "ptylm_forward_loss_noalloc",
                          "ptylm_profile",
                          "ptylm_profile_read"):
                 getattr(lib, name).restype = i
@@ -206,6 +208,15 @@ def ggn_matvec(ctx: Context, vO, outO, lam: float = 0.0, D=None, vP=None, outP=N
 
 def ptylm_set_measurements(ctx: Context, y) -> None:
     _check(load_library().ptylm_set_measurements(ctx.handle, _ptr(y)))
+
+
+def ptylm_forward_loss_noalloc(ny, nx, m, positions, y, O, P, out, loss=LOSS_GAUSSIAN,
+                               background=1e-8, stream=None) -> None:
+    """Context-free, allocation-free (f, ||grad_zeta l||^2) into device double[2] `out`."""
+    K = 0 if positions is None else int(positions.shape[0])
+    _check(load_library().ptylm_forward_loss_noalloc(int(ny), int(nx), int(m), K, int(loss), float(background),
+                                                     _ptr(O), _ptr(P), _ptr(positions), _ptr(y), _ptr(out),
+                                                     _stream_ptr(stream)))
 
 
 def forward_intensity(ctx: Context, O, P, h_out) -> None:
