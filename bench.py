@@ -156,6 +156,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def workload_config(w, cg_per_step, world):
+    _, step_used = synth.raster_positions(w.n, w.m, w.grid, w.step, w.jitter, seed=1)
+    return {"workload": w.name, "object": w.n, "probe": w.m, "positions": w.K,
+            "raster_step_used": step_used, "loss": "poisson" if w.loss else "amplitude",
+            "peak_photons": w.peak, "cg_iters_per_step": cg_per_step, "parallelism": f"replicas{world}",
+            "l2": "inputs larger than L2: 8 K M byte cache streamed per matvec"}
+
+
+def reduce_over_ranks(elapsed_s, count, device):
+    """Whole-job figures of N independent replicas (one process per GPU): the slowest
+    rank's time and the summed work.  Single-process runs return the inputs unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(elapsed_s), float(count)
+    t = torch.tensor([float(elapsed_s), float(count)], dtype=torch.float64, device=device)
+    tmax, tsum = t.clone(), t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[1])
+
+
 # ---------------------------------------------------------------------------------------
 # CPU legs: the FP64 oracle on a bounded sample of positions
 # ---------------------------------------------------------------------------------------
@@ -227,7 +249,7 @@ def run_reference(args, w):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": w.name},
+        "data": "synthetic", "config": workload_config(w, args.cg_per_step, args.gpus),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -328,15 +350,7 @@ def main():
     mv_ms, mv_n = ptylm.ptylm_profile_read(ctx, ptylm.KERNEL_GGN_MATVEC)
     _, launches = ptylm.ptylm_profile_read(ctx, -1)
     ptylm.ptylm_profile(ctx, False)
-    if world > 1:
-        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t)
-        m = torch.tensor([matvecs], dtype=torch.float64, device=dev)
-        dist.all_reduce(m, op=dist.ReduceOp.SUM)
-        total_matvecs = float(m)
-    else:
-        total_matvecs = float(matvecs)
+    elapsed, total_matvecs = reduce_over_ranks(elapsed, matvecs, dev)
     value = total_matvecs / elapsed
 
     # End to end through the C-ABI with pinned host buffers: H2D of O and P, D2H of O.
@@ -349,13 +363,7 @@ def main():
     for _ in range(args.e2e_steps):
         e2e_mv += step(O_h, P_h, O0_h)
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t)
-        m = torch.tensor([e2e_mv], dtype=torch.float64, device=dev)
-        dist.all_reduce(m, op=dist.ReduceOp.SUM)
-        e2e_mv = float(m)
+    e2e_s, e2e_mv = reduce_over_ranks(e2e_s, e2e_mv, dev)
     N, M, K = w.n * w.n, w.m * w.m, int(pos.shape[0])
 
     clocks = clk.summary()
@@ -374,10 +382,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": w.name, "object": w.n, "probe": w.m, "positions": K,
-                       "raster_step_used": step_used, "loss": "poisson", "peak_photons": w.peak,
-                       "cg_iters_per_step": args.cg_per_step, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2: 472 MB cache streamed per matvec"},
+            "config": workload_config(w, args.cg_per_step, world),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
                          "frac": achieved / peak_fp32, "traffic": recorded_traffic(),
                          "kernel": "k_ggn_matvec<7>", "avg_launch_us": avg_mv_s * 1e6,
@@ -387,7 +392,7 @@ def main():
                                  "frac": hbm_achieved / hbm_peak, "peak_kind": hbm_kind,
                                  "bytes_per_launch": matvec_bytes(K, M, N)}},
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_mv / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * N + 8 * M,
+            "e2e": {"value": e2e_mv / e2e_s if e2e_s > 0 else 0.0, "unit": UNIT, "h2d_bytes_per_step": 8 * N + 8 * M,
                     "d2h_bytes_per_step": 8 * N},
             "clocks": clocks,
             "gpu_launches": int(launches),

@@ -65,7 +65,9 @@ k_forward(PtyArgs a) {
                 if constexpr (INTENSITY) {
                     a.out_real[(size_t)k * G::M + ky * G::S + freq_kx<G>(c.tid, e)] = h;
                 } else {
-                    sl += pixel_terms<true>(a.loss, h, __ldg(yk + e * G::T)).l;
+                    const PixelTerms t = pixel_terms<true>(a.loss, h, __ldg(yk + e * G::T));
+                    sl += t.l;
+                    sd += t.dl * t.dl;
                 }
             }
         }

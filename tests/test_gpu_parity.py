@@ -136,9 +136,10 @@ def test_forward_loss_and_gradient(lib, shape, kind):
     assert rel_err(host(gd), g_ref) <= tol_g
     # loss-only evaluation at another point leaves the linearisation intact
     O2 = g.point(seed=6)
-    f2, _ = lib.forward_loss(g.ctx, dev_c64(O2), g.P, cache=0)
-    f2_ref = oracle.loss(pb, O2)
+    f2, dl2_2 = lib.forward_loss(g.ctx, dev_c64(O2), g.P, cache=0)
+    f2_ref, dl2_2_ref = oracle.loss(pb, O2, return_dl_norm2=True)
     assert scalar_rel(f2, f2_ref) <= tol_for(case, lambda A: oracle.loss(pb, A), O2)
+    assert scalar_rel(dl2_2, dl2_2_ref) <= tol_for(case, lambda A: oracle.loss(pb, A, return_dl_norm2=True)[1], O2)
     lib.gradient(g.ctx, gd)
     assert rel_err(host(gd), g_ref) <= tol_g
 
