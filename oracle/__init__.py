@@ -290,3 +290,125 @@ def lm_solve(pb: Problem, O0, O_ref=None, mask=None, beta=None, **kw):
     n = n_outer.value
     return O, dict(status=st, n_outer=n, cg_total=cg_total.value, f=hf[:n], gnorm=hg[:n],
                    mu=hmu[:n], cg=hcg[:n], err=herr[:n])
+
+
+# ---------------------------------------------------------------------------------------
+# Scaled / joint / projected LM (PLM, PLM-J with Algorithm 2)
+# ---------------------------------------------------------------------------------------
+class _LM2Params(ctypes.Structure):
+    _fields_ = [("mu0", ctypes.c_double), ("mu_min", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("nu", ctypes.c_double),
+                ("rho_min", ctypes.c_double), ("beta", ctypes.c_double),
+                ("mu_max", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("max_cg", ctypes.c_int), ("target_err", ctypes.c_double),
+                ("scaled", ctypes.c_int), ("joint", ctypes.c_int), ("projected", ctypes.c_int),
+                ("radius_O", ctypes.c_double), ("radius_P", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("tau_s", ctypes.c_double), ("p_s", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("max_ls", ctypes.c_int), ("diag_floor", ctypes.c_double),
+                ("f_min", ctypes.c_double)]
+
+
+def _z(pb, O, P=None):
+    O = _c(O)
+    return O if P is None else np.concatenate([O.ravel(), _c(P).ravel()])
+
+
+def ggn_matvec_z(pb: Problem, O, v, lam=0.0, D=None, P=None, joint=False):
+    """(G + lambda D) v on the z = [O; P] vector (joint) or O alone; v, D flat of length N(+M)."""
+    z = _z(pb, O, P if joint else None)
+    v = _c(v).ravel()
+    out = np.empty_like(v)
+    Pf = pb.P if P is None else _c(P)
+    D = None if D is None else _r(D).ravel()
+    g = pb.geom()
+    _load().orc_ggn_matvec_z(ctypes.byref(g), _p(z), _p(Pf), _p(pb.pos), _p(pb.y), int(joint), _p(v),
+                             ctypes.c_double(lam), _p(D), _p(out))
+    return out
+
+
+def pcg(pb: Problem, O, grad, lam, D, eta, max_iter, P=None, joint=False, x0=None):
+    """Truncated PCG for (G + lambda D) x = -grad with the Jacobi preconditioner (1+lambda) D
+    (D None: plain CG, D = I).  Vectors flat over z.  Returns (x, r, iterations, converged)."""
+    z = _z(pb, O, P if joint else None)
+    grad = _c(grad).ravel()
+    x = np.zeros_like(grad) if x0 is None else _c(x0).ravel().copy()
+    r = np.empty_like(x)
+    D = None if D is None else _r(D).ravel()
+    conv = ctypes.c_int(0)
+    Pf = pb.P if P is None else _c(P)
+    g = pb.geom()
+    lib = _load()
+    lib.orc_pcg.restype = ctypes.c_int
+    it = lib.orc_pcg(ctypes.byref(g), _p(z), _p(Pf), _p(pb.pos), _p(pb.y), int(joint), _p(grad),
+                     ctypes.c_double(lam), _p(D), ctypes.c_double(eta), int(max_iter), _p(x), _p(r),
+                     ctypes.byref(conv))
+    return x, r, it, bool(conv.value)
+
+
+def project(v, radius):
+    """Radial projection onto {|v_i| <= radius} (Eq. constraints)."""
+    v = _c(v).copy()
+    _load().orc_project(ctypes.c_long(v.size), _p(v), ctypes.c_double(radius))
+    return v
+
+
+def poisson_f_min(y):
+    """sum(y - y log y): the Poisson metric's value at h = y (its minimum over h)."""
+    y = np.asarray(y, np.float64)
+    return float(np.sum(y - np.where(y > 0, y * np.log(np.where(y > 0, y, 1.0)), 0.0)))
+
+
+DEFAULT_LM2 = dict(DEFAULT_LM, scaled=1, joint=0, projected=0, radius_O=1.0, radius_P=1e8, gamma=1e-6,
+                   tau_s=1e-8, p_s=2.1, sigma=1e-4, max_ls=30, diag_floor=1e-6)
+
+
+def lm_solve2(pb: Problem, O0, P0=None, O_ref=None, mask=None, beta=None, **kw):
+    """Algorithm 1 with D = Dg(G) and Jacobi PCG (scaled), the joint state (joint) and the
+    Algorithm 2 plug-in (projected).  Returns (O, P, info)."""
+    prm = dict(DEFAULT_LM2)
+    prm.update(kw)
+    if beta is None:
+        beta = 0.1 if pb.loss == LOSS_GAUSSIAN else 0.9
+    f_min = poisson_f_min(pb.y) if pb.loss == LOSS_POISSON else 0.0
+    p = _LM2Params(prm["mu0"], prm["mu_min"], prm["kappa"], prm["nu"], prm["rho_min"], beta, prm["mu_max"],
+                   int(prm["max_outer"]), int(prm["max_cg"]), prm["target_err"], int(prm["scaled"]),
+                   int(prm["joint"]), int(prm["projected"]), prm["radius_O"], prm["radius_P"], prm["gamma"],
+                   prm["tau_s"], prm["p_s"], prm["sigma"], int(prm["max_ls"]), prm["diag_floor"], f_min)
+    O = _c(O0).copy()
+    P = (pb.P if P0 is None else _c(P0)).copy()
+    L = int(prm["max_outer"])
+    hf, hg, hmu, herr = (np.full(L, np.nan) for _ in range(4))
+    hcg = np.zeros(L, np.int32)
+    n_outer, cg_total = ctypes.c_int(0), ctypes.c_int(0)
+    Oref = None if O_ref is None else _c(O_ref)
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    g = pb.geom()
+    lib = _load()
+    lib.orc_lm_solve2.restype = ctypes.c_int
+    st = lib.orc_lm_solve2(ctypes.byref(g), _p(O), _p(P), _p(pb.pos), _p(pb.y), ctypes.byref(p), _p(Oref),
+                           _p(m), ctypes.byref(n_outer), ctypes.byref(cg_total), _p(hf), _p(hg), _p(hmu),
+                           _p(hcg), _p(herr), L)
+    n = n_outer.value
+    return O, P, dict(status=st, n_outer=n, cg_total=cg_total.value, f=hf[:n], gnorm=hg[:n], mu=hmu[:n],
+                      cg=hcg[:n], err=herr[:n])
+
+
+def object_error_blind(O, O_ref, mask=None, ramp_iterations=3):
+    """Object error for the blind problem (Sec. 2: its solutions are unique only up to a
+    complex scale and a linear phase ramp): min over c in C and a ramp exp(i(a0 + a1 y + a2 x))
+    of ||c e^{i ramp} O - O_ref|| / ||O_ref|| on the mask.  The ramp is fitted by weighted
+    least squares on the phase difference, repeated so that wrapped phases settle; then the
+    closed-form c = <O', O_ref>/||O'||^2."""
+    O = np.asarray(O, np.complex128)
+    R = np.asarray(O_ref, np.complex128)
+    mk = np.ones(O.shape, bool) if mask is None else np.asarray(mask, bool)
+    yy, xx = np.nonzero(mk)
+    o, r = O[mk], R[mk]
+    A = np.stack([np.ones_like(yy), yy, xx], axis=1).astype(np.float64)
+    for _ in range(ramp_iterations):
+        w = np.abs(o) * np.abs(r)
+        ph = np.angle(r * np.conj(o))
+        coef, *_ = np.linalg.lstsq(A * w[:, None], ph * w, rcond=None)
+        o = o * np.exp(1j * (A @ coef))
+    c = np.vdot(o, r) / np.vdot(o, o)
+    return float(np.linalg.norm(c * o - r) / np.linalg.norm(r))

@@ -588,3 +588,243 @@ void orc_set_threads(int n)
     (void)n;
 #endif
 }
+
+/* ====================================================================================
+ * Scaled / joint / projected LM (the paper's PLM and PLM-J, Secs. 3.3 and 4.2-4.5).
+ * The state is z = [O; P] (P present only for the joint problem); vectors over z are
+ * stored as N (+ M) complex values and all inner products are real-coordinate ones.
+ * ==================================================================================== */
+
+/* z -> (O, P) views. */
+typedef struct {
+    const orc_geom* g;
+    const int32_t* pos;
+    const double* y;
+    int joint;
+    const dc* P_fixed;   /* probe when not joint */
+} orc_problem;
+
+static long zlen(const orc_problem* pb) {
+    return (long)pb->g->ny * pb->g->nx + (pb->joint ? (long)pb->g->my * pb->g->mx : 0);
+}
+static const dc* zP(const orc_problem* pb, const dc* z) {
+    return pb->joint ? z + (long)pb->g->ny * pb->g->nx : pb->P_fixed;
+}
+
+/* (G + lambda D) v for the z-vector v (D NULL = identity), at the point z. */
+static void z_matvec(const orc_problem* pb, const dc* z, const dc* v, double lambda, const double* D, dc* out)
+{
+    const long N = (long)pb->g->ny * pb->g->nx;
+    orc_ggn_matvec(pb->g, z, zP(pb, z), pb->pos, pb->y, v, pb->joint ? v + N : NULL, lambda,
+                   D, D ? D + N : NULL, out, pb->joint ? out + N : NULL);
+}
+
+static void z_gradient(const orc_problem* pb, const dc* z, dc* gz)
+{
+    const long N = (long)pb->g->ny * pb->g->nx;
+    orc_gradient(pb->g, z, zP(pb, z), pb->pos, pb->y, gz, pb->joint ? gz + N : NULL);
+}
+
+static double z_loss(const orc_problem* pb, const dc* z, double* dl2)
+{
+    return orc_loss(pb->g, z, zP(pb, z), pb->pos, pb->y, dl2);
+}
+
+/* Closed-form Dg(G) over z with the relative floor (App. B, Eq. ggn_joint_diag). */
+static void z_diag(const orc_problem* pb, const dc* z, double floor_rel, double* D)
+{
+    const long N = (long)pb->g->ny * pb->g->nx;
+    const int M = pb->g->my * pb->g->mx;
+    if (pb->joint) {
+        orc_ggn_diag(pb->g, z, zP(pb, z), pb->pos, pb->y, floor_rel, D, D + N);
+    } else {
+        double* dp = (double*)malloc(sizeof(double) * M);
+        orc_ggn_diag(pb->g, z, zP(pb, z), pb->pos, pb->y, floor_rel, D, dp);
+        free(dp);
+    }
+}
+
+/* Radial projections of Eq. constraints: |O| <= rO, |P| <= rP (separable, Sec. 4.3). */
+static void z_project(const orc_problem* pb, dc* z, double rO, double rP)
+{
+    const long N = (long)pb->g->ny * pb->g->nx;
+    const long L = zlen(pb);
+    for (long i = 0; i < L; ++i) {
+        const double r = i < N ? rO : rP;
+        const double a = cabs(z[i]);
+        if (r > 0.0 && a > r) z[i] *= r / a;
+    }
+}
+
+void orc_project(long n, dc* v, double radius)
+{
+    for (long i = 0; i < n; ++i) {
+        double a = cabs(v[i]);
+        if (radius > 0.0 && a > radius) v[i] *= radius / a;
+    }
+}
+
+/* Truncated PCG for (G + lambda D) x = -g with the Jacobi preconditioner
+ * Dg(G + lambda D) = (1 + lambda) D when D = Dg(G) (Sec. 3.3), or no preconditioner when
+ * D is NULL (D = I).  Stopping rule Eq. lma_termination_magnitude on the unpreconditioned
+ * residual.  x: warm start in, step out; r: final residual -g - (G + lambda D) x. */
+static int z_pcg(const orc_problem* pb, const dc* z, const dc* grad, double lambda, const double* D, double eta,
+                 int max_iter, dc* x, dc* r, int* conv_out)
+{
+    const long L = zlen(pb);
+    dc* p = (dc*)malloc(sizeof(dc) * L);
+    dc* q = (dc*)malloc(sizeof(dc) * L);
+    dc* zz = (dc*)malloc(sizeof(dc) * L);
+    z_matvec(pb, z, x, lambda, D, q);
+    for (long i = 0; i < L; ++i) r[i] = -grad[i] - q[i];
+    const double tol = eta * sqrt(rdot(grad, grad, L));
+    for (long i = 0; i < L; ++i) zz[i] = D ? r[i] / ((1.0 + lambda) * D[i]) : r[i];
+    for (long i = 0; i < L; ++i) p[i] = zz[i];
+    double rz = rdot(r, zz, L), rr = rdot(r, r, L);
+    int it = 0, conv = 0;
+    while (1) {
+        if (sqrt(rr) <= tol) { conv = 1; break; }
+        if (it >= max_iter) break;
+        z_matvec(pb, z, p, lambda, D, q);
+        double pq = rdot(p, q, L);
+        if (!(pq > 0.0)) break;
+        double alpha = rz / pq;
+        for (long i = 0; i < L; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+        for (long i = 0; i < L; ++i) zz[i] = D ? r[i] / ((1.0 + lambda) * D[i]) : r[i];
+        double rz_new = rdot(r, zz, L);
+        rr = rdot(r, r, L);
+        double beta = rz_new / rz;
+        rz = rz_new;
+        for (long i = 0; i < L; ++i) p[i] = zz[i] + beta * p[i];
+        ++it;
+    }
+    if (conv_out) *conv_out = conv;
+    free(p); free(q); free(zz);
+    return it;
+}
+
+/* Public PCG on z-vectors (tests). */
+int orc_pcg(const orc_geom* g, const dc* z, const dc* P_fixed, const int32_t* pos, const double* y, int joint,
+            const dc* grad, double lambda, const double* D, double eta, int max_iter, dc* x, dc* r,
+            int* converged_out)
+{
+    orc_problem pb = {g, pos, y, joint, P_fixed};
+    return z_pcg(&pb, z, grad, lambda, D, eta, max_iter, x, r, converged_out);
+}
+
+void orc_ggn_matvec_z(const orc_geom* g, const dc* z, const dc* P_fixed, const int32_t* pos, const double* y,
+                      int joint, const dc* v, double lambda, const double* D, dc* out)
+{
+    orc_problem pb = {g, pos, y, joint, P_fixed};
+    z_matvec(&pb, z, v, lambda, D, out);
+}
+
+typedef struct {
+    double mu0, mu_min, kappa, nu, rho_min, beta, mu_max;
+    int max_outer, max_cg;
+    double target_err;
+    int scaled;          /* D = Dg(G) with lambda = mu and Jacobi PCG (PLM), else D = I (LM) */
+    int joint;           /* z = (O, P) (BPR), else O only (SPR) */
+    int projected;       /* Algorithm 2 with the radial constraints below */
+    double radius_O, radius_P;      /* Eq. constraints: 1 and 1e8 */
+    double gamma, tau_s, p_s, sigma;  /* Algorithm 2 / Eq. armijo_criterion */
+    int max_ls;
+    double diag_floor;   /* D >= diag_floor * max D */
+    double f_min;        /* subtracted from f in Algorithm 2's tests (Poisson: sum y - y log y) */
+} orc_lm2_params;
+
+/* Algorithm 1 with scaling, the joint state and the Algorithm 2 plug-in.
+ * O_inout [N], P_inout [M] (updated when joint).  History as in orc_lm_solve. */
+int orc_lm_solve2(const orc_geom* g, dc* O_inout, dc* P_inout, const int32_t* pos, const double* y,
+                  const orc_lm2_params* prm, const dc* O_ref, const unsigned char* mask,
+                  int* n_outer_out, int* cg_total_out, double* hist_f, double* hist_gnorm, double* hist_mu,
+                  int* hist_cg, double* hist_err, int hist_len)
+{
+    orc_problem pb = {g, pos, y, prm->joint, P_inout};
+    const long N = (long)g->ny * g->nx;
+    const int M = g->my * g->mx;
+    const long L = zlen(&pb);
+    dc* z = (dc*)malloc(sizeof(dc) * L);
+    dc* grad = (dc*)malloc(sizeof(dc) * L);
+    dc* delta = (dc*)calloc((size_t)L, sizeof(dc));
+    dc* r = (dc*)malloc(sizeof(dc) * L);
+    dc* trial = (dc*)malloc(sizeof(dc) * L);
+    dc* s = (dc*)malloc(sizeof(dc) * L);
+    double* D = prm->scaled ? (double*)malloc(sizeof(double) * L) : NULL;
+    memcpy(z, O_inout, sizeof(dc) * N);
+    if (prm->joint) memcpy(z + N, P_inout, sizeof(dc) * M);
+    double mu = prm->mu0;
+    int cg_total = 0, status = 0, t;
+    for (t = 0; t < prm->max_outer; ++t) {
+        double dl2 = 0.0;
+        const double f = z_loss(&pb, z, &dl2);
+        z_gradient(&pb, z, grad);
+        const double gnorm = sqrt(rdot(grad, grad, L));
+        const double eta = fmin(prm->beta, sqrt(gnorm));
+        if (D) z_diag(&pb, z, prm->diag_floor, D);
+        if (hist_f && t < hist_len) hist_f[t] = f;
+        if (hist_gnorm && t < hist_len) hist_gnorm[t] = gnorm;
+        double rho = 0.0;
+        int cg_this = 0;
+        while (!(rho > prm->rho_min)) {
+            const double lambda = D ? mu : mu * pow(sqrt(dl2), prm->nu);
+            int conv = 0;
+            cg_this += z_pcg(&pb, z, grad, lambda, D, eta, prm->max_cg, delta, r, &conv);
+            for (long i = 0; i < L; ++i) trial[i] = z[i] + delta[i];
+            const double f_trial = z_loss(&pb, trial, NULL);
+            double dd = 0.0;
+            for (long i = 0; i < L; ++i) dd += (D ? D[i] : 1.0) * creal(delta[i] * conj(delta[i]));
+            const double dfp = 0.5 * (lambda * dd - rdot(delta, grad, L)) + 0.5 * rdot(delta, r, L);
+            rho = dfp > 0.0 ? (f - f_trial) / dfp : -1.0;
+            if (rho > 0.75) mu = fmax(mu / prm->kappa, prm->mu_min);
+            else if (rho > 0.25) { /* keep */ }
+            else mu = prm->kappa * mu;
+            if (rho > prm->rho_min) {
+                if (!prm->projected) {
+                    memcpy(z, trial, sizeof(dc) * L);
+                } else {
+                    /* Algorithm 2: projected step, descent test, Armijo backtracking. */
+                    z_project(&pb, trial, prm->radius_O, prm->radius_P);
+                    const double fp = z_loss(&pb, trial, NULL);
+                    if (fp - prm->f_min < prm->gamma * (f - prm->f_min)) {
+                        memcpy(z, trial, sizeof(dc) * L);
+                    } else {
+                        for (long i = 0; i < L; ++i) s[i] = trial[i] - z[i];
+                        const double ss = rdot(s, s, L);
+                        const int descent = rdot(grad, s, L) <= -prm->tau_s * pow(sqrt(ss), prm->p_s);
+                        if (!descent) {
+                            for (long i = 0; i < L; ++i) s[i] = -grad[i];
+                        }
+                        const double sn2 = rdot(s, s, L);
+                        double alpha = 1.0;
+                        int found = 0;
+                        for (int ls = 0; ls < prm->max_ls; ++ls, alpha *= 0.5) {
+                            for (long i = 0; i < L; ++i) trial[i] = z[i] + alpha * s[i];
+                            z_project(&pb, trial, prm->radius_O, prm->radius_P);
+                            if (z_loss(&pb, trial, NULL) <= f - prm->sigma * alpha * sn2) { found = 1; break; }
+                        }
+                        if (found) memcpy(z, trial, sizeof(dc) * L);
+                    }
+                }
+            } else if (mu > prm->mu_max) {
+                status = 6;
+                break;
+            }
+        }
+        cg_total += cg_this;
+        if (hist_mu && t < hist_len) hist_mu[t] = mu;
+        if (hist_cg && t < hist_len) hist_cg[t] = cg_this;
+        if (status) { ++t; break; }
+        if (O_ref) {
+            double e = orc_object_error(N, z, O_ref, mask);
+            if (hist_err && t < hist_len) hist_err[t] = e;
+            if (e <= prm->target_err) { ++t; break; }
+        }
+    }
+    memcpy(O_inout, z, sizeof(dc) * N);
+    if (prm->joint) memcpy(P_inout, z + N, sizeof(dc) * M);
+    if (n_outer_out) *n_outer_out = t;
+    if (cg_total_out) *cg_total_out = cg_total;
+    free(z); free(grad); free(delta); free(r); free(trial); free(s); free(D);
+    return status;
+}

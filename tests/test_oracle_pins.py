@@ -340,3 +340,135 @@ def test_lm_converges_on_small_noiseless_workload():
     assert info["status"] == 0
     assert info["err"][-1] <= 1e-3, info
     assert info["n_outer"] < 60
+
+
+# ----------------------------------------------------------------------------- joint / PLM
+def dense_jacobian_joint(pb, O, P, e=1e-6):
+    """Dense real-coordinate Jacobian of zeta w.r.t. z = [O; P] (K*M x 2(N+M)) by central
+    differences of the forward model: columns ordered Re O, Re P, Im O, Im P."""
+    N, M = O.size, P.size
+
+    def zeta_at(Ov, Pv):
+        return zeta_of(pb, Ov, Pv).ravel()
+
+    cols = []
+    for part in (1.0, 1j):
+        for n in range(N):
+            d = np.zeros(N, complex)
+            d[n] = part * e
+            d = d.reshape(O.shape)
+            cols.append((zeta_at(O + d, P) - zeta_at(O - d, P)) / (2 * e))
+        for m in range(M):
+            d = np.zeros(M, complex)
+            d[m] = part * e
+            d = d.reshape(P.shape)
+            cols.append((zeta_at(O, P + d) - zeta_at(O, P - d)) / (2 * e))
+    return np.stack(cols, axis=1)
+
+
+def z_real(z):
+    return np.concatenate([z.real, z.imag])
+
+
+@pytest.mark.parametrize("loss", [0, 1])
+def test_joint_ggn_matvec_and_diag_vs_dense(loss):
+    pb, O_true = tiny_problem(loss, noiseless=False, b=1e-12)
+    O = O_true + synth.random_complex(O_true.shape, seed=100, scale=0.05)
+    P = pb.P * 1.1 + synth.random_complex(pb.P.shape, seed=101, scale=0.05)
+    J = dense_jacobian_joint(pb, O, P)
+    zeta = zeta_of(pb, O, P).ravel()
+    _, _, d2l = oracle.ell_terms(loss, zeta, pb.y.ravel())
+    G = J.T @ (d2l[:, None] * J)
+    L = O.size + P.size
+    v = synth.random_complex(L, seed=102)
+    D = np.abs(synth.random_real(L, seed=103)) + 0.5
+    lam = 0.3
+    out = oracle.ggn_matvec_z(pb, O, v, lam=lam, D=D, P=P, joint=True)
+    ref = G @ z_real(v) + lam * np.concatenate([D, D]) * z_real(v)
+    np.testing.assert_allclose(z_real(out), ref, rtol=1e-6, atol=1e-6 * np.abs(ref).max())
+    # closed-form diagonal of both blocks (App. B, Eq. ggn_joint_diag) = mean of Re/Im diagonals
+    D_O, D_P = oracle.ggn_diag(pb, O, P)
+    dg = np.diag(G)
+    mean_diag = 0.5 * (dg[:L] + dg[L:])
+    np.testing.assert_allclose(np.concatenate([D_O.ravel(), D_P.ravel()]), mean_diag, rtol=2e-6,
+                               atol=1e-9 * mean_diag.max())
+
+
+def test_jacobi_pcg_matches_dense_solve_joint():
+    pb, O_true = tiny_problem(0, noiseless=False)
+    O = O_true + synth.random_complex(O_true.shape, seed=110, scale=0.05)
+    P = pb.P
+    gO, gP = oracle.gradient(pb, O, P, probe_part=True)
+    g = np.concatenate([gO.ravel(), gP.ravel()])
+    D_O, D_P = oracle.ggn_diag(pb, O, P, floor_rel=1e-6)
+    D = np.concatenate([D_O.ravel(), D_P.ravel()])
+    lam = 0.05
+    J = dense_jacobian_joint(pb, O, P)
+    A = J.T @ J + lam * np.diag(np.concatenate([D, D]))
+    x_ref = np.linalg.solve(A, -z_real(g))
+    x, r, it, conv = oracle.pcg(pb, O, g, lam, D, eta=1e-12, max_iter=800, P=P, joint=True)
+    assert conv
+    np.testing.assert_allclose(z_real(x), x_ref, rtol=1e-5, atol=1e-7 * np.abs(x_ref).max())
+    # the preconditioned solve needs far fewer iterations than plain CG on the same system
+    _, _, it_plain, _ = oracle.pcg(pb, O, g, lam, None, eta=1e-6, max_iter=800, P=P, joint=True)
+    _, _, it_pcg, _ = oracle.pcg(pb, O, g, lam, D, eta=1e-6, max_iter=800, P=P, joint=True)
+    assert it_pcg <= it_plain
+
+
+def test_projection_is_the_nearest_feasible_point():
+    v = synth.random_complex(500, seed=120, scale=2.0)
+    p = oracle.project(v, 1.0)
+    assert np.abs(p).max() <= 1.0 + 1e-15
+    np.testing.assert_allclose(oracle.project(p, 1.0), p)           # idempotent
+    inside = np.abs(v) <= 1.0
+    np.testing.assert_allclose(p[inside], v[inside])                # feasible points unchanged
+    # no feasible point is closer: compare with random points of the unit disk
+    rng = np.random.default_rng(121)
+    q = np.sqrt(rng.uniform(0, 1, (200, 500))) * np.exp(2j * np.pi * rng.uniform(0, 1, (200, 500)))
+    assert np.all(np.abs(v - p)[None, :] <= np.abs(v[None, :] - q) + 1e-12)
+
+
+def test_plm_scaled_converges_on_small_workload():
+    """PLM (D = Dg(G), lambda = mu, Jacobi PCG) on the 128^2 noiseless workload reaches 1e-3."""
+    w = synth.SMALL
+    O_true = synth.to_c64(synth.object_texture(w.n, seed=0))
+    P = synth.to_c64(synth.probe_disk_defocus(w.m, w.radius))
+    pos, _ = synth.raster_positions(w.n, w.m, w.grid, w.step, w.jitter, seed=1)
+    pb = oracle.Problem((w.n, w.n), P, pos, None, 0, 1e-8)
+    pb.y = synth.to_f32(oracle.intensity(pb, O_true))
+    mask = synth.illumination_mask(w.n, P, pos, 0.1)
+    O, _, info = oracle.lm_solve2(pb, synth.flat_object(w.n), O_ref=O_true, mask=mask, max_outer=60,
+                                  target_err=1e-3, scaled=1)
+    assert info["status"] == 0 and info["err"][-1] <= 1e-3, info
+
+
+def test_plm_joint_projected_blind_reconstruction_improves():
+    """PLM-J with Algorithm 2 on a small noiseless blind problem: the object error falls by an
+    order of magnitude from a flat start with a wrong (unphased) probe, and the iterate
+    satisfies the constraints |O| <= 1 (Eq. constraints)."""
+    n, m = 96, 32
+    O_true = synth.to_c64(synth.object_texture(n, seed=4))
+    P_true = synth.to_c64(synth.probe_disk_defocus(m, 10.0))
+    pos, _ = synth.raster_positions(n, m, 8, 8, 1, seed=5)
+    pb = oracle.Problem((n, n), P_true, pos, None, 0, 1e-8)
+    pb.y = synth.to_f32(oracle.intensity(pb, O_true))
+    mask = synth.illumination_mask(n, P_true, pos, 0.3)
+    P0 = synth.to_c64(synth.probe_disk_defocus(m, 10.0, phased=False))
+    O0 = synth.flat_object(n) * 0.9
+    e0 = oracle.object_error_blind(O0, O_true, mask)
+    O, P, info = oracle.lm_solve2(pb, O0, P0, max_outer=40, scaled=1, joint=1, projected=1)
+    assert info["status"] == 0
+    assert np.abs(O).max() <= 1.0 + 1e-12
+    e = oracle.object_error_blind(O, O_true, mask)
+    assert e <= 0.05 * e0, (e0, e)
+    assert info["f"][-1] < 1e-3 * info["f"][0]
+
+
+def test_blind_error_metric_invariances():
+    """The blind-problem error is zero under a complex scale and a linear phase ramp of the
+    reference (the ambiguities of Sec. 2) and positive otherwise."""
+    O = synth.object_texture(48, seed=9)
+    yy, xx = np.mgrid[0:48, 0:48]
+    Ot = (0.7 - 0.4j) * O * np.exp(1j * (0.3 + 0.05 * yy - 0.02 * xx))
+    assert oracle.object_error_blind(Ot, O) < 1e-10
+    assert oracle.object_error_blind(O + 0.1 * synth.random_complex(O.shape, seed=8), O) > 0.05
