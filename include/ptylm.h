@@ -83,6 +83,17 @@ typedef struct {
     double target_err; /* stop once the object error <= target_err (needs O_ref)           */
     const ptylm_c64* O_ref; /* optional device reference object for the error metric       */
     const uint8_t* mask;    /* optional device [ny][nx] mask of pixels the error compares   */
+    int scaled;        /* 1: D = Dg(G) (closed form, App. B), lambda = mu, Jacobi PCG with
+                          Dg(G + lambda D) (Sec. 3.3, "PLM"); 0: D = I, lambda = mu ||grad l||^nu */
+    int projected;     /* 1: Algorithm 2 after each accepted step (Sec. 4.3)                */
+    double radius_O;   /* constraint |O| <= radius_O (Eq. constraints: 1)                   */
+    double radius_P;   /* constraint |P| <= radius_P (Eq. constraints: 1e8)                 */
+    double gamma;      /* Algorithm 2: accept Pi(z + dz) if f(Pi) - f_min < gamma (f - f_min) (1e-6) */
+    double tau_s;      /* Algorithm 2: descent test g.s <= -tau_s ||s||^p_s (1e-8)          */
+    double p_s;        /* (2.1)                                                              */
+    double sigma;      /* Armijo constant, Eq. armijo_criterion (1e-4)                       */
+    int max_ls;        /* Armijo halvings before giving up the move (30)                    */
+    double diag_floor; /* Dg(G) is raised to diag_floor * max Dg(G) (1e-6)                  */
 } ptylm_lm_params;
 
 /* Per-call results of lm_solve.  hist_* point to host arrays of hist_len entries (or are
@@ -139,7 +150,8 @@ ptylm_status gradient(ptylm_ctx* ctx, ptylm_c64* gO, ptylm_c64* gP);
 /* Jacobian-vector product at the linearisation point (App. A Eqs. jvp_step_1..3; computed
  * in forward mode from App. B Eq. jac_ampl):
  *     out_km = Re( conj(psihat_km) [F (P . S_k vO + vP . S_k O)]_m ) / zeta_km
- *   vO: device [ny][nx]; vP: device [my][mx] or NULL (= 0); out: device float [K][my][mx].
+ *   vO: device [ny][nx]; vP: device [my][mx] (joint contexts only) or NULL (= 0);
+ *   out: device float [K][my][mx], natural order.
  * Recomputes psihat from the stored (O, P); does not read the ggn_matvec cache. */
 ptylm_status jvp(ptylm_ctx* ctx, const ptylm_c64* vO, const ptylm_c64* vP, float* out);
 
@@ -147,7 +159,7 @@ ptylm_status jvp(ptylm_ctx* ctx, const ptylm_c64* vO, const ptylm_c64* vP, float
  *     outO = sum_k S_k^T [conj(P) . F^H(psihat_k w_k / zeta_k)]
  *     outP = sum_k conj(S_k O) . F^H(psihat_k w_k / zeta_k)         (joint contexts)
  *   w: device float [K][my][mx]; outO: device [ny][nx] (overwritten); outP: device [my][mx]
- *   or NULL. */
+ *   (joint contexts only) or NULL. */
 ptylm_status jtvp(ptylm_ctx* ctx, const float* w, ptylm_c64* outO, ptylm_c64* outP);
 
 /* Damped GGN-vector product, the hot path (App. A steps 2-4, Eq. ggn_magnitude_appendix_2):
@@ -155,19 +167,34 @@ ptylm_status jtvp(ptylm_ctx* ctx, const float* w, ptylm_c64* outO, ptylm_c64* ou
  * One fused kernel per call: patch gather x P, 2D FFT, frequency stage with the cached a
  * (t = Re(conj(a) dpsihat), chihat = a t), inverse 2D FFT, x conj(P), overlap scatter-add.
  *   vO, outO: host or device [ny][nx]; outO is overwritten.
- *   D: device float [ny][nx] diagonal scaling, or NULL for the identity.
- *   vP / outP: reserved for joint contexts; must be NULL in object-only contexts.
+ *   vP, outP: joint contexts: device [my][mx] probe blocks (the joint GGN of Eq. ggn_joint_diag's
+ *   block structure, z = (O, P)); both NULL in object-only contexts.
+ *   D: device float diagonal scaling over z -- [ny*nx] (object only) or [ny*nx + my*mx]
+ *   (object then probe) -- or NULL for the identity.
  * Needs a linearisation point (PTYLM_ERR_STATE otherwise). */
+
+/* Closed-form diagonal of the GGN in real coordinates at the linearisation point (App. B,
+ * Eqs. ggn_diag_elem_final, ggn_diag_mat, ggn_joint_diag; the paper's h ~ |psihat|^2
+ * approximation):  D_O[n] = sum_{k: n in patch k} |P[n - r_k]|^2 tr_k / (2M),
+ *                  D_P[m] = sum_k |O[r_k + m]|^2 tr_k / (2M),   tr_k = sum_m d2l_km.
+ *   D_out: device float [ny*nx] or, for joint contexts, [ny*nx + my*mx].
+ *   floor_rel: entries of each block below floor_rel * (that block's max) are raised to
+ *   it (0 disables). */
+ptylm_status ggn_diag(ptylm_ctx* ctx, float* D_out, double floor_rel);
 ptylm_status ggn_matvec(ptylm_ctx* ctx, const ptylm_c64* vO, const ptylm_c64* vP, double lambda,
                         const float* D, ptylm_c64* outO, ptylm_c64* outP);
 
-/* Truncated matrix-free LM, Algorithm 1 (Sec. 4.2) for the object (SPR) problem with
- * D = I and lambda = mu ||grad_zeta l||^nu; inner truncated CG stopped by
- * Eqs. lma_termination_magnitude / lma_termination_eta with eta = min(beta, ||grad f||^(1/2)),
- * warm-started from the previous step.  CG vectors are FP32; dot products, lambda, mu,
- * the gain ratio and f are FP64 on the device.
+/* Truncated matrix-free LM, Algorithm 1 (Sec. 4.2), on z = O (object-only contexts, the
+ * SPR problem) or z = (O, P) (joint contexts, the BPR problem).  prm->scaled selects D = I
+ * with lambda = mu ||grad_zeta l||^nu ("LM") or D = Dg(G) with lambda = mu and the Jacobi
+ * preconditioner Dg(G + lambda D) ("PLM", Sec. 3.3); prm->projected adds Algorithm 2
+ * (Sec. 4.3) with the radial constraints of Eq. constraints.  The inner truncated (P)CG is
+ * stopped by Eqs. lma_termination_magnitude / lma_termination_eta with
+ * eta = min(beta, ||grad f||^(1/2)) and warm-started from the previous step.  CG vectors are
+ * FP32; dot products, lambda, mu, the gain ratio and f are FP64 on the device.
  *   O_inout: host or device [ny][nx]; initial guess in, final iterate out.
- *   P_inout: host or device [my][mx] probe (read only for object-only contexts).
+ *   P_inout: host or device [my][mx] probe: read only for object-only contexts, updated
+ *   in place for joint contexts.
  *   prm: host parameters; stats: host results (may be NULL).
  * Returns PTYLM_OK, PTYLM_WARN_CG_MAXIT (some solve hit max_cg), or an error. */
 ptylm_status lm_solve(ptylm_ctx* ctx, ptylm_c64* O_inout, ptylm_c64* P_inout,

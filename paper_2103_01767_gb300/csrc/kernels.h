@@ -25,12 +25,23 @@ struct PtyArgs {
     int nx;
     float b;               // background
     int loss;              // 0 Gaussian, 1 Poisson
+    const float2* VP;      // joint: probe part of the direction (matvec, jvp)
+    const float2* Olin;    // joint: object at the linearisation point (matvec)
+    float2* outP_part;     // joint: per-team probe accumulators [grid * TEAMS][M]
+    float* trp;            // optional: per-thread sums of d2l [K][T] (forward + cache)
 };
 
 enum KernelId {
     KID_FWD_LOSS = 0, KID_FWD_CACHE = 1, KID_MATVEC = 2, KID_JTVP = 3, KID_JVP = 4, KID_FWD_INTENSITY = 5,
-    KID_COUNT = 6
+    KID_FWD_CACHE_J = 6, KID_MATVEC_J = 7, KID_JTVP_J = 8, KID_JVP_J = 9,
+    KID_COUNT = 10
 };
+
+// Closed-form GGN diagonal (App. B, Eqs. ggn_diag_mat and ggn_joint_diag) from the per-thread
+// d2l sums of the last linearisation: D_O += |P|^2 tr_k / (2M) over each patch (one CTA per
+// position, D_O zeroed first) and, when D_P != NULL, D_P[m] = sum_k |O[r_k + m]|^2 tr_k / (2M).
+cudaError_t launch_ggn_diag(int LS, const float* trp, const int2* pos, int K, const float2* O,
+                            const float2* P, int nx, float* D_O, float* D_P, float* tr, cudaStream_t stream);
 
 // Threads per CTA and teams (positions in flight) per CTA for a patch side 2^LS.
 int cta_threads(int LS);

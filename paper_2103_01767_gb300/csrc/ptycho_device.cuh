@@ -34,7 +34,7 @@ __device__ __forceinline__ void prefetch_tile_l2(const void* tile, unsigned byte
 // r = h^(-1/2) (so zeta = h r, 1/zeta = r) the Poisson ratios are dl/zeta = 2 (h - y) r^2
 // and sqrt(d2l)/zeta = sqrt(2 (h + y)) r^2: no division or IEEE square root per pixel.
 struct PixelTerms {
-    float l, dl, dl_over_zeta, sqrt_d2l_over_zeta;
+    float l, dl, dl_over_zeta, sqrt_d2l_over_zeta, d2l;
 };
 template <bool WANT_L>
 __device__ __forceinline__ PixelTerms pixel_terms(int loss, float h, float ym) {
@@ -47,6 +47,7 @@ __device__ __forceinline__ PixelTerms pixel_terms(int loss, float h, float ym) {
         t.dl = d;
         t.dl_over_zeta = d * r;
         t.sqrt_d2l_over_zeta = r;
+        t.d2l = 1.0f;
     } else {
         t.l = WANT_L ? h - (ym > 0.0f ? ym * logf(h) : 0.0f) : 0.0f;
         const float hy = h - ym;
@@ -54,6 +55,7 @@ __device__ __forceinline__ PixelTerms pixel_terms(int loss, float h, float ym) {
         t.dl_over_zeta = 2.0f * hy * r * r;
         const float s = 2.0f * (h + ym);
         t.sqrt_d2l_over_zeta = s * rsqrtf(s) * r * r;
+        t.d2l = s * r * r;
     }
     return t;
 }
@@ -121,6 +123,56 @@ __device__ __forceinline__ void scatter_times_conj_probe(const float2* v, float2
         for (int i = 0; i < 8; ++i) pv[i] = pr[G::BX * G::S * (a0 + i)];
 #pragma unroll
         for (int i = 0; i < 8; ++i) red_add_c64(dst + row_step * (a0 + i), cmulc(v[a0 + i], pv[i]));
+        sched_fence();
+    }
+}
+
+// Joint gather (Eq. jac_ampl with both blocks): v[a] = P[y][x] A[r0+y][c0+x] + B[y][x] C[r0+y][c0+x],
+// i.e. P . S_k dO + dP . S_k O for the direction (A, B) = (dO, dP) at the object C.
+template <class G>
+__device__ __forceinline__ void gather_joint(float2* v, const float2* __restrict__ A, const float2* __restrict__ P,
+                                             const float2* __restrict__ B, const float2* __restrict__ C, int nx,
+                                             int r0, int c0, int tid) {
+    const int x = tid & (G::S - 1), b = tid >> G::LOG_S;
+    const size_t off = (size_t)(r0 + b) * nx + c0 + x;
+    const int poff = b * G::S + x;
+    const size_t row_step = (size_t)G::BX * nx;
+#pragma unroll
+    for (int a0 = 0; a0 < 32; a0 += 8) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int a = a0 + i;
+            const float2 p = P[poff + G::BX * G::S * a];
+            const float2 dp = B[poff + G::BX * G::S * a];
+            const float2 da = __ldg(A + off + row_step * a);
+            const float2 o = __ldg(C + off + row_step * a);
+            const float2 t0 = cmul(p, da), t1 = cmul(dp, o);
+            v[a] = make_float2(t0.x + t1.x, t0.y + t1.y);
+        }
+        sched_fence();
+    }
+}
+
+// Probe block of the adjoint: part[y][x] += conj(C[r0+y][c0+x]) * v[a] in the team's own
+// accumulator row (each element has one owner thread within the team: no atomics).
+template <class G>
+__device__ __forceinline__ void accumulate_probe_adjoint(const float2* v, float2* part, const float2* __restrict__ C,
+                                                         int nx, int r0, int c0, int tid) {
+    const int x = tid & (G::S - 1), b = tid >> G::LOG_S;
+    const size_t off = (size_t)(r0 + b) * nx + c0 + x;
+    const int poff = b * G::S + x;
+    const size_t row_step = (size_t)G::BX * nx;
+#pragma unroll
+    for (int a0 = 0; a0 < 32; a0 += 8) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int a = a0 + i;
+            const float2 o = __ldg(C + off + row_step * a);
+            float2* dst = part + poff + G::BX * G::S * a;
+            const float2 t = cconjmul(o, v[a]);
+            const float2 cur = *dst;
+            *dst = make_float2(cur.x + t.x, cur.y + t.y);
+        }
         sched_fence();
     }
 }

@@ -21,13 +21,61 @@
 
 namespace ptylm {
 
+// Per-kernel argument structs, built from PtyArgs by kernel_launch.  They stay small (the
+// matvec's 88 bytes): larger by-value argument blocks cost the register-bound matvec spills.
+struct FwdArgs {
+    const float2* O;
+    const float2* P;
+    const int2* pos;
+    const float* y;
+    float2* a_cache;
+    float2* out;
+    float* out_real;
+    double* partials;
+    unsigned* counter;
+    double* scal;
+    const float2* tw;
+    float* trp;
+    float2* outP_part;
+    int K, nx;
+    float b;
+    int loss;
+};
+struct MatvecArgs {
+    const float2* O;      // the direction vO
+    const float2* P;
+    const int2* pos;
+    const float2* a_cache;
+    float2* out;
+    const float2* tw;
+    const float2* VP;     // joint: probe part of the direction
+    const float2* Olin;   // joint: object at the linearisation point
+    float2* outP_part;    // joint: per-team probe accumulators
+    int K, nx;
+};
+struct AdjArgs {          // J^T w and J v
+    const float2* O;      // linearisation point
+    const float2* V;      // jvp direction vO
+    const float2* VP;     // jvp joint: probe direction
+    const float2* P;
+    const int2* pos;
+    const float* w;
+    float2* out;
+    float* out_real;
+    float2* scratch;
+    const float2* tw;
+    float2* outP_part;
+    int K, nx;
+    float b;
+};
+
 // ---------------------------------------------------------------------------------------
 // Forward model + error metric (+ cache and gradient when CACHE; intensities only when
 // INTENSITY).
 // ---------------------------------------------------------------------------------------
-template <int LS, bool CACHE, bool INTENSITY = false>
+template <int LS, bool CACHE, bool INTENSITY = false, bool JOINT = false>
 __global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
-k_forward(PtyArgs a) {
+k_forward(FwdArgs a) {
     using G = Geo<LS>;
     TeamCtx<G> c = team_setup<G>(a.tw);
     const float invS = 1.0f / G::S;
@@ -42,6 +90,7 @@ k_forward(PtyArgs a) {
         gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
         if constexpr (CACHE) {
             float2* ak = a.a_cache + (size_t)k * G::M + c.tid;
+            float s2 = 0.0f;  // sum of d2l over this thread's pixels (closed-form diagonal)
             team_fft_roundtrip<G>(v, c.sm, c.tw, c.tid, [&](float2* g, int j) {
 #pragma unroll
                 for (int k2y = 0; k2y < G::BY; ++k2y) {
@@ -51,11 +100,16 @@ k_forward(PtyArgs a) {
                     const PixelTerms t = pixel_terms<true>(a.loss, h, __ldg(yk + e * G::T));
                     sl += t.l;
                     sd += t.dl * t.dl;
+                    s2 += t.d2l;
                     ak[e * G::T] = ps * t.sqrt_d2l_over_zeta;
                     g[k2y] = ps * (t.dl_over_zeta * invS);  // psihat grad l / zeta, inverse 1/S folded in
                 }
             });
+            if (a.trp) a.trp[(size_t)k * G::T + c.tid] = s2;
             scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
+            if constexpr (JOINT)
+                accumulate_probe_adjoint<G>(v, a.outP_part + (size_t)(blockIdx.x * G::TEAMS + c.team) * G::M,
+                                            a.O, a.nx, rc.x, rc.y, c.tid);
         } else {
             team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
 #pragma unroll
@@ -84,9 +138,9 @@ k_forward(PtyArgs a) {
 // chihat = a t (App. A steps 2-4; the closed-form diagonal Hessian of step 3(ii) is folded
 // into a).  out must hold lambda D v (or zero) on entry.
 // ---------------------------------------------------------------------------------------
-template <int LS>
+template <int LS, bool JOINT = false>
 __global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
-k_ggn_matvec(PtyArgs a) {
+k_ggn_matvec(MatvecArgs a) {
     using G = Geo<LS>;
     TeamCtx<G> c = team_setup<G>(a.tw);
     const float invM = 1.0f / G::M;
@@ -94,7 +148,8 @@ k_ggn_matvec(PtyArgs a) {
     for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
         const int2 rc = a.pos[k];
         prefetch_tile_l2(a.a_cache + (size_t)k * G::M, sizeof(float2) * G::M, c.tid);
-        gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
+        if constexpr (JOINT) gather_joint<G>(v, a.O, a.P, a.VP, a.Olin, a.nx, rc.x, rc.y, c.tid);
+        else gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
         const float2* ak = a.a_cache + (size_t)k * G::M + c.tid;
         team_fft_roundtrip<G>(v, c.sm, c.tw, c.tid, [&](float2* g, int j) {
             float2 av[G::BY];
@@ -107,6 +162,9 @@ k_ggn_matvec(PtyArgs a) {
             }
         });
         scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
+        if constexpr (JOINT)
+            accumulate_probe_adjoint<G>(v, a.outP_part + (size_t)(blockIdx.x * G::TEAMS + c.team) * G::M, a.Olin,
+                                        a.nx, rc.x, rc.y, c.tid);
         // No barrier before the next position: its first shared-memory writes go to the
         // slots this same thread read last (team_fft_roundtrip).
     }
@@ -115,9 +173,9 @@ k_ggn_matvec(PtyArgs a) {
 // ---------------------------------------------------------------------------------------
 // J^T w: chihat = psihat w / zeta, recomputing psihat from (O, P).  out += result.
 // ---------------------------------------------------------------------------------------
-template <int LS>
+template <int LS, bool JOINT = false>
 __global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
-k_jtvp(PtyArgs a) {
+k_jtvp(AdjArgs a) {
     using G = Geo<LS>;
     TeamCtx<G> c = team_setup<G>(a.tw);
     const float invS = 1.0f / G::S;
@@ -137,6 +195,9 @@ k_jtvp(PtyArgs a) {
             }
         });
         scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
+        if constexpr (JOINT)
+            accumulate_probe_adjoint<G>(v, a.outP_part + (size_t)(blockIdx.x * G::TEAMS + c.team) * G::M, a.O,
+                                        a.nx, rc.x, rc.y, c.tid);
         // No barrier before the next position: its first shared-memory writes go to the
         // slots this same thread read last (team_fft_roundtrip).
     }
@@ -146,9 +207,9 @@ k_jtvp(PtyArgs a) {
 // J v = Re(conj(psihat) F(P S_k v)) / zeta, written in natural [K][S][S] order.  psihat is
 // recomputed and parked in a per-team global scratch slot while the direction is transformed.
 // ---------------------------------------------------------------------------------------
-template <int LS>
+template <int LS, bool JOINT = false>
 __global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
-k_jvp(PtyArgs a) {
+k_jvp(AdjArgs a) {
     using G = Geo<LS>;
     TeamCtx<G> c = team_setup<G>(a.tw);
     const float invS = 1.0f / G::S;
@@ -161,7 +222,8 @@ k_jvp(PtyArgs a) {
 #pragma unroll
         for (int e = 0; e < 32; ++e) slot[e * G::T] = v[e];
         team_sync<G>();
-        gather_times_probe<G>(v, a.V, a.P, a.nx, rc.x, rc.y, c.tid);
+        if constexpr (JOINT) gather_joint<G>(v, a.V, a.P, a.VP, a.O, a.nx, rc.x, rc.y, c.tid);
+        else gather_times_probe<G>(v, a.V, a.P, a.nx, rc.x, rc.y, c.tid);
         team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
         float* ok = a.out_real + (size_t)k * G::M + freq_ky<G>(c.tid) * G::S;
 #pragma unroll
@@ -208,6 +270,74 @@ cudaError_t permute_measurements(int LS, const float* y, float* y_perm, int K, i
 }
 
 // ---------------------------------------------------------------------------------------
+// Closed-form GGN diagonal, App. B (Eqs. ggn_diag_elem_final, ggn_diag_mat, ggn_joint_diag),
+// in real coordinates: D_O[n] = sum_{k: n in patch k} |P[n - r_k]|^2 tr_k / (2M) and
+// D_P[m] = sum_k |O[r_k + m]|^2 tr_k / (2M), tr_k = sum_m d2l_km.
+// ---------------------------------------------------------------------------------------
+template <int LS>
+__global__ void __launch_bounds__(Geo<LS>::T)
+k_diag_object(const float* __restrict__ trp, const int2* __restrict__ pos, const float2* __restrict__ P, int nx,
+              float* D_O, float* tr) {
+    using G = Geo<LS>;
+    const int k = blockIdx.x, tid = threadIdx.x;
+    double s[1] = {(double)trp[(size_t)k * G::T + tid]};
+    block_sum<1>(s);
+    __shared__ float trk;
+    if (tid == 0) {
+        trk = (float)s[0];
+        tr[k] = trk;
+    }
+    __syncthreads();
+    const float scale = trk / (2.0f * G::M);
+    const int2 rc = pos[k];
+    const int x = tid & (G::S - 1), b = tid >> G::LOG_S;
+#pragma unroll 8
+    for (int a = 0; a < 32; ++a) {
+        const int y = G::BX * a + b;
+        const float2 p = P[y * G::S + x];
+        atomicAdd(D_O + (size_t)(rc.x + y) * nx + rc.y + x, (p.x * p.x + p.y * p.y) * scale);
+    }
+}
+
+template <int LS>
+__global__ void k_diag_probe(const float* __restrict__ tr, const int2* __restrict__ pos, int K,
+                             const float2* __restrict__ O, int nx, float* D_P) {
+    using G = Geo<LS>;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < G::M; m += gridDim.x * blockDim.x) {
+        const int y = m >> G::LOG_S, x = m & (G::S - 1);
+        float acc = 0.0f;
+        for (int k = 0; k < K; ++k) {
+            const int2 rc = pos[k];
+            const float2 o = O[(size_t)(rc.x + y) * nx + rc.y + x];
+            acc += (o.x * o.x + o.y * o.y) * tr[k];
+        }
+        D_P[m] = acc / (2.0f * G::M);
+    }
+}
+
+cudaError_t launch_ggn_diag(int LS, const float* trp, const int2* pos, int K, const float2* O, const float2* P,
+                            int nx, float* D_O, float* D_P, float* tr, cudaStream_t stream) {
+    if (K == 0) return cudaSuccess;
+    switch (LS) {
+        case 5:
+            k_diag_object<5><<<K, Geo<5>::T, 0, stream>>>(trp, pos, P, nx, D_O, tr);
+            if (D_P) k_diag_probe<5><<<(Geo<5>::M + 255) / 256, 256, 0, stream>>>(tr, pos, K, O, nx, D_P);
+            break;
+        case 6:
+            k_diag_object<6><<<K, Geo<6>::T, 0, stream>>>(trp, pos, P, nx, D_O, tr);
+            if (D_P) k_diag_probe<6><<<(Geo<6>::M + 255) / 256, 256, 0, stream>>>(tr, pos, K, O, nx, D_P);
+            break;
+        case 7:
+            k_diag_object<7><<<K, Geo<7>::T, 0, stream>>>(trp, pos, P, nx, D_O, tr);
+            if (D_P) k_diag_probe<7><<<(Geo<7>::M + 255) / 256, 256, 0, stream>>>(tr, pos, K, O, nx, D_P);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
 // Host-side dispatch.
 // ---------------------------------------------------------------------------------------
 int cta_threads(int LS) {
@@ -246,6 +376,10 @@ static const void* kernel_ptr(int kid) {
         case KID_JTVP: return (const void*)k_jtvp<LS>;
         case KID_JVP: return (const void*)k_jvp<LS>;
         case KID_FWD_INTENSITY: return (const void*)k_forward<LS, false, true>;
+        case KID_FWD_CACHE_J: return (const void*)k_forward<LS, true, false, true>;
+        case KID_MATVEC_J: return (const void*)k_ggn_matvec<LS, true>;
+        case KID_JTVP_J: return (const void*)k_jtvp<LS, true>;
+        case KID_JVP_J: return (const void*)k_jvp<LS, true>;
     }
     return nullptr;
 }
@@ -271,8 +405,17 @@ cudaError_t kernel_prepare(int LS, int kid, int* ctas_per_sm) {
 cudaError_t kernel_launch(int LS, int kid, const PtyArgs& a, int grid, cudaStream_t stream) {
     const void* fn = kernel_for(LS, kid);
     if (!fn || grid <= 0) return cudaErrorInvalidValue;
-    PtyArgs copy = a;
-    void* args[] = {&copy};
+    FwdArgs fa{a.O, a.P, a.pos, a.y, a.a_cache, a.out, a.out_real, a.partials, a.counter, a.scal, a.tw,
+               a.trp, a.outP_part, a.K, a.nx, a.b, a.loss};
+    MatvecArgs ma{a.O, a.P, a.pos, a.a_cache, a.out, a.tw, a.VP, a.Olin, a.outP_part, a.K, a.nx};
+    AdjArgs ja{a.O, a.V, a.VP, a.P, a.pos, a.w, a.out, a.out_real, a.scratch, a.tw, a.outP_part, a.K, a.nx, a.b};
+    void* arg = nullptr;
+    switch (kid) {
+        case KID_FWD_LOSS: case KID_FWD_CACHE: case KID_FWD_INTENSITY: case KID_FWD_CACHE_J: arg = &fa; break;
+        case KID_MATVEC: case KID_MATVEC_J: arg = &ma; break;
+        default: arg = &ja; break;
+    }
+    void* args[] = {arg};
     return cudaLaunchKernel(fn, dim3(grid), dim3(cta_threads(LS)), args, cta_smem_bytes(LS), stream);
 }
 

@@ -49,10 +49,13 @@ void ptylm::set_last_error(const char* msg) { g_last_error = msg; }
     } while (0)
 
 // ---------------------------------------------------------------------------------------
-// Vector kernels of the truncated CG and of Algorithm 1.  Products are formed in FP32 and
-// summed per thread over its few grid-stride elements, then reduced in FP64 by
-// grid_reduce (reduce.cuh), whose last CTA also updates the FP64 scalars (alpha, beta,
-// ||p||^2, ...): a CG iteration is the matvec plus two launches, with no host round trip.
+// Vector kernels of the truncated (P)CG and of Algorithms 1 and 2.  Vectors run over the
+// state z (the object, then the probe for joint contexts).  Products are formed in FP32
+// and summed per thread over its few grid-stride elements, then reduced in FP64 by
+// grid_reduce (reduce.cuh), whose last CTA also updates the FP64 scalars (alpha, beta, r.z,
+// r.r): a CG iteration is the matvec plus three launches, with no host round trip.
+// Jacobi preconditioner (Sec. 3.3): z = r / Dg(G + lambda D) = r / ((1 + lambda) D) when
+// D = Dg(G); no preconditioner (z = r) when D is NULL.
 // ---------------------------------------------------------------------------------------
 static constexpr int VEC_THREADS = 256;
 
@@ -60,6 +63,12 @@ __device__ __forceinline__ float rdotf(float2 a, float2 b) { return a.x * b.x + 
 
 #define GRID_STRIDE(i, n) \
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (n); i += (long)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ float2 precondition(float2 r, const float* D, float lambda, long i) {
+    if (!D) return r;
+    const float inv = 1.0f / ((1.0f + lambda) * D[i]);
+    return make_float2(r.x * inv, r.y * inv);
+}
 
 // out = lambda * D * v   (D == NULL: identity).  Initialises the matvec accumulator.
 __global__ void k_damping_init(const float2* __restrict__ v, const float* __restrict__ D, float lambda,
@@ -71,9 +80,10 @@ __global__ void k_damping_init(const float2* __restrict__ v, const float* __rest
     }
 }
 
-// Up to three real-coordinate dot products a_i . b_i into slots [dst, dst + W).
+// Up to three real-coordinate dot products a_i . b_i (the first optionally weighted by
+// w0, i.e. a0^T diag(w0) b0) into slots [dst, dst + W), then `op`.
 template <int W>
-__global__ void k_dots(const float2* __restrict__ a0, const float2* __restrict__ b0,
+__global__ void k_dots(const float2* __restrict__ a0, const float2* __restrict__ b0, const float* __restrict__ w0,
                        const float2* __restrict__ a1, const float2* __restrict__ b1,
                        const float2* __restrict__ a2, const float2* __restrict__ b2, long n,
                        double* part, unsigned* counter, double* sc, int dst, int op) {
@@ -81,7 +91,7 @@ __global__ void k_dots(const float2* __restrict__ a0, const float2* __restrict__
 #pragma unroll
     for (int c = 0; c < W; ++c) f[c] = 0.0f;
     GRID_STRIDE(i, n) {
-        f[0] += rdotf(a0[i], b0[i]);
+        f[0] += (w0 ? w0[i] : 1.0f) * rdotf(a0[i], b0[i]);
         if constexpr (W > 1) f[1] += rdotf(a1[i], b1[i]);
         if constexpr (W > 2) f[2] += rdotf(a2[i], b2[i]);
     }
@@ -91,28 +101,32 @@ __global__ void k_dots(const float2* __restrict__ a0, const float2* __restrict__
     grid_reduce<W>(s, part, counter, sc, dst, op, 1.0);
 }
 
-// CG start: r = -g - q, p = r, q = lambda p; r.r (= p.p) into the slots.
+// CG start: r = -g - q, z = precond(r), p = z, q = lambda D p; r.z and r.r into the slots.
 __global__ void k_cg_start(const float2* __restrict__ g, float2* __restrict__ q, float2* __restrict__ r,
-                           float2* __restrict__ p, float lambda, long n, double* part, unsigned* counter,
-                           double* sc) {
-    float f = 0.0f;
+                           float2* __restrict__ p, const float* __restrict__ D, float lambda, long n, double* part,
+                           unsigned* counter, double* sc) {
+    float f0 = 0.0f, f1 = 0.0f;
     GRID_STRIDE(i, n) {
         const float2 gi = g[i], qi = q[i];
         const float2 ri = make_float2(-gi.x - qi.x, -gi.y - qi.y);
+        const float2 zi = precondition(ri, D, lambda, i);
         r[i] = ri;
-        p[i] = ri;
-        q[i] = make_float2(lambda * ri.x, lambda * ri.y);
-        f += rdotf(ri, ri);
+        p[i] = zi;
+        const float d = lambda * (D ? D[i] : 1.0f);
+        q[i] = make_float2(d * zi.x, d * zi.y);
+        f0 += rdotf(ri, zi);
+        f1 += rdotf(ri, ri);
     }
-    double s[1] = {f};
-    grid_reduce<1>(s, part, counter, sc, 0, OP_START, 1.0);
+    double s[2] = {f0, f1};
+    grid_reduce<2>(s, part, counter, sc, 0, OP_START, 1.0);
 }
 
-// x += alpha p, r -= alpha q; new r.r -> beta (alpha read from the slots).
+// x += alpha p, r -= alpha q; new r.z and r.r -> beta (alpha read from the slots).
 __global__ void k_cg_update(float2* __restrict__ x, float2* __restrict__ r, const float2* __restrict__ p,
-                            const float2* __restrict__ q, long n, double* part, unsigned* counter, double* sc) {
+                            const float2* __restrict__ q, const float* __restrict__ D, float lambda, long n,
+                            double* part, unsigned* counter, double* sc) {
     const float alpha = (float)sc[S_ALPHA];
-    float f = 0.0f;
+    float f0 = 0.0f, f1 = 0.0f;
     GRID_STRIDE(i, n) {
         const float2 pi = p[i], qi = q[i];
         float2 xi = x[i], ri = r[i];
@@ -122,31 +136,99 @@ __global__ void k_cg_update(float2* __restrict__ x, float2* __restrict__ r, cons
         ri.y -= alpha * qi.y;
         x[i] = xi;
         r[i] = ri;
-        f += rdotf(ri, ri);
+        f0 += rdotf(ri, precondition(ri, D, lambda, i));
+        f1 += rdotf(ri, ri);
     }
-    double s[1] = {f};
-    grid_reduce<1>(s, part, counter, sc, 0, OP_BETA, 1.0);
+    double s[2] = {f0, f1};
+    grid_reduce<2>(s, part, counter, sc, 0, OP_BETA, 1.0);
 }
 
-// p = r + beta p;  q = lambda D p (starts the next matvec's accumulator).
+// p = precond(r) + beta p;  q = lambda D p (starts the next matvec's accumulator).
 __global__ void k_cg_direction(const float2* __restrict__ r, float2* __restrict__ p, float2* __restrict__ q,
                                const float* __restrict__ D, float lambda, long n, const double* __restrict__ sc) {
     const float beta = (float)sc[S_BETA];
     GRID_STRIDE(i, n) {
-        const float2 ri = r[i], pi = p[i];
-        const float2 pn = make_float2(ri.x + beta * pi.x, ri.y + beta * pi.y);
+        const float2 zi = precondition(r[i], D, lambda, i), pi = p[i];
+        const float2 pn = make_float2(zi.x + beta * pi.x, zi.y + beta * pi.y);
         p[i] = pn;
         const float d = lambda * (D ? D[i] : 1.0f);
         q[i] = make_float2(d * pn.x, d * pn.y);
     }
 }
 
-// z = x + d
-__global__ void k_add(const float2* __restrict__ x, const float2* __restrict__ d, float2* __restrict__ z, long n) {
+// z = x + alpha d
+__global__ void k_axpy(const float2* __restrict__ x, const float2* __restrict__ d, float alpha,
+                       float2* __restrict__ z, long n) {
     GRID_STRIDE(i, n) {
         const float2 a = x[i], b = d[i];
-        z[i] = make_float2(a.x + b.x, a.y + b.y);
+        z[i] = make_float2(a.x + alpha * b.x, a.y + alpha * b.y);
     }
+}
+
+// Radial projection onto |z_i| <= radius (Eq. constraints): object part [0, N), probe part
+// [N, n) with its own radius (Sec. 4.3: the constraint sets are separable).
+__global__ void k_project(float2* __restrict__ z, long N, long n, float rO, float rP) {
+    GRID_STRIDE(i, n) {
+        const float r = i < N ? rO : rP;
+        const float2 v = z[i];
+        const float a2 = v.x * v.x + v.y * v.y;
+        if (a2 > r * r) {
+            const float s = r * rsqrtf(a2);
+            z[i] = make_float2(v.x * s, v.y * s);
+        }
+    }
+}
+
+// Poisson: sum over measurements of y - y log y (the metric's value where h = y).
+__global__ void k_poisson_fmin(const float* __restrict__ y, long n, double* part, unsigned* counter, double* sc) {
+    float f = 0.0f;
+    GRID_STRIDE(i, n) {
+        const float v = y[i];
+        f += v - (v > 0.0f ? v * logf(v) : 0.0f);
+    }
+    double s[1] = {f};
+    grid_reduce<1>(s, part, counter, sc, S_FMIN, OP_STORE, 1.0);
+}
+
+// Probe block of an adjoint: out[m] (+)= sum over team slots of part[slot][m], slots in order.
+__global__ void k_probe_reduce(const float2* __restrict__ part, int slots, int M, float2* __restrict__ out,
+                               int accumulate) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        float2 acc = accumulate ? out[m] : make_float2(0.0f, 0.0f);
+        for (int s = 0; s < slots; ++s) {
+            const float2 v = part[(size_t)s * M + m];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        out[m] = acc;
+    }
+}
+
+// Per-block maxima of a non-negative array (first pass of the diagonal floor).
+__global__ void k_block_max(const float* __restrict__ D, long n, double* part) {
+    __shared__ float red[VEC_THREADS];
+    float m = 0.0f;
+    GRID_STRIDE(i, n) m = fmaxf(m, D[i]);
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// D = max(D, floor_rel * max D) (the maximum re-derived by every block from the partials).
+__global__ void k_apply_floor(float* __restrict__ D, long n, const double* __restrict__ part, int nparts,
+                              float floor_rel) {
+    __shared__ float fl;
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int b = 0; b < nparts; ++b) m = fmax(m, part[b]);
+        fl = (float)(floor_rel * m);
+    }
+    __syncthreads();
+    GRID_STRIDE(i, n) D[i] = fmaxf(D[i], fl);
 }
 
 // Object-error sums over a mask: <O, O_ref> (re, im), ||O||^2, ||O_ref||^2.
@@ -173,6 +255,7 @@ struct ptylm_ctx {
     ptylm_desc d;
     int LS = 0, S = 0, M = 0;
     long N = 0;
+    long L = 0;                    // length of the state z: N, or N + M for joint contexts
     cudaStream_t stream = nullptr;
     int device = 0, num_sms = 0;
     int grid[KID_COUNT] = {0};
@@ -193,11 +276,17 @@ struct ptylm_ctx {
     double* scal = nullptr;        // device FP64 scalars [S_COUNT]
     double* scal_host = nullptr;   // pinned mirror
     float2* jvp_scratch = nullptr;
+    float2* probe_part = nullptr;  // joint: per-team probe accumulators [probe_slots][M]
+    int probe_slots = 0;
+    float* trp = nullptr;          // per-thread d2l sums of the last linearisation [K][T]
+    float* tr = nullptr;           // per-position d2l sums [K]
     bool has_lin = false;
     double f_lin = 0.0, dl2_lin = 0.0;
 
-    // CG / LM vectors (allocated on first use)
+    // CG / LM vectors over z (allocated on first use)
     float2 *cg_x = nullptr, *cg_r = nullptr, *cg_p = nullptr, *cg_q = nullptr, *trial = nullptr;
+    float2* ls_dir = nullptr;      // Algorithm 2 search direction
+    float* Dg = nullptr;           // scaling D = Dg(G) over z
     // staging for host pointers
     float2 *stage_a = nullptr, *stage_b = nullptr, *stage_P = nullptr;
 
@@ -318,13 +407,16 @@ static ptylm_status read_scalars(ptylm_ctx* c, int first, int count) {
     return PTYLM_OK;
 }
 
-static ptylm_status dots(ptylm_ctx* c, int W, const float2* a0, const float2* b0, const float2* a1,
-                         const float2* b1, const float2* a2, const float2* b2, int dst, int op = OP_STORE) {
+// Dot products over n elements (the first optionally weighted) into slots [dst, dst + W).
+static ptylm_status dots(ptylm_ctx* c, int W, long n, const float2* a0, const float2* b0, const float* w0,
+                         const float2* a1, const float2* b1, const float2* a2, const float2* b2, int dst,
+                         int op = OP_STORE) {
     const int nb = vec_blocks(c);
     unsigned* cnt = c->counters + CNT_VEC;
-    if (W == 1) k_dots<1><<<nb, VEC_THREADS, 0, c->stream>>>(a0, b0, a1, b1, a2, b2, c->N, c->partials, cnt, c->scal, dst, op);
-    else if (W == 2) k_dots<2><<<nb, VEC_THREADS, 0, c->stream>>>(a0, b0, a1, b1, a2, b2, c->N, c->partials, cnt, c->scal, dst, op);
-    else k_dots<3><<<nb, VEC_THREADS, 0, c->stream>>>(a0, b0, a1, b1, a2, b2, c->N, c->partials, cnt, c->scal, dst, op);
+    double* part = c->partials;
+    if (W == 1) k_dots<1><<<nb, VEC_THREADS, 0, c->stream>>>(a0, b0, w0, a1, b1, a2, b2, n, part, cnt, c->scal, dst, op);
+    else if (W == 2) k_dots<2><<<nb, VEC_THREADS, 0, c->stream>>>(a0, b0, w0, a1, b1, a2, b2, n, part, cnt, c->scal, dst, op);
+    else k_dots<3><<<nb, VEC_THREADS, 0, c->stream>>>(a0, b0, w0, a1, b1, a2, b2, n, part, cnt, c->scal, dst, op);
     return vec_launched(c);
 }
 
@@ -340,20 +432,39 @@ static PtyArgs base_args(const ptylm_ctx* c) {
     a.loss = c->d.loss;
     a.partials = c->partials;
     a.scal = c->scal;
+    a.outP_part = c->probe_part;
     return a;
+}
+
+static bool joint(const ptylm_ctx* c) { return c->d.joint != 0; }
+
+// Sum the probe accumulators of `kid`'s teams into out [M] (overwrite or add).
+static ptylm_status probe_reduce(ptylm_ctx* c, int kid, float2* out, bool accumulate) {
+    const int slots = c->grid[kid] * cta_teams(c->LS);
+    k_probe_reduce<<<(c->M + VEC_THREADS - 1) / VEC_THREADS, VEC_THREADS, 0, c->stream>>>(c->probe_part, slots, c->M,
+                                                                                        out, accumulate ? 1 : 0);
+    return vec_launched(c);
+}
+
+static ptylm_status clear_probe_part(ptylm_ctx* c, int kid) {
+    const size_t slots = (size_t)c->grid[kid] * cta_teams(c->LS);
+    CUDA_TRY(cudaMemsetAsync(c->probe_part, 0, sizeof(float2) * slots * c->M, c->stream));
+    return PTYLM_OK;
 }
 
 // ---------------------------------------------------------------------------------------
 // Internal operations on device pointers
 // ---------------------------------------------------------------------------------------
 
-// Forward model + loss; cache=1 also stores a, the linearisation point and grad f.
+// Forward model + loss; cache=1 also stores a, the linearisation point, the per-thread d2l
+// sums and grad f over z (object part by scatter, probe part by team accumulators).
 static ptylm_status op_forward(ptylm_ctx* c, const float2* O, const float2* P, int cache) {
-    const int kid = cache ? KID_FWD_CACHE : KID_FWD_LOSS;
+    const int kid = cache ? (joint(c) ? KID_FWD_CACHE_J : KID_FWD_CACHE) : KID_FWD_LOSS;
     if (cache) {
         if (O != c->O_lin) CUDA_TRY(cudaMemcpyAsync(c->O_lin, O, sizeof(float2) * c->N, cudaMemcpyDeviceToDevice, c->stream));
         if (P != c->P_lin) CUDA_TRY(cudaMemcpyAsync(c->P_lin, P, sizeof(float2) * c->M, cudaMemcpyDeviceToDevice, c->stream));
-        CUDA_TRY(cudaMemsetAsync(c->grad, 0, sizeof(float2) * c->N, c->stream));
+        CUDA_TRY(cudaMemsetAsync(c->grad, 0, sizeof(float2) * c->L, c->stream));
+        if (joint(c)) STATUS_TRY(clear_probe_part(c, kid));
         c->has_lin = false;
     }
     if (c->d.K == 0) {
@@ -365,30 +476,60 @@ static ptylm_status op_forward(ptylm_ctx* c, const float2* O, const float2* P, i
         a.a_cache = c->a_cache;
         a.out = c->grad;
         a.counter = c->counters + CNT_FWD;
+        a.trp = cache ? c->trp : nullptr;
         STATUS_TRY(launch(c, kid, a));
+        if (cache && joint(c)) STATUS_TRY(probe_reduce(c, kid, c->grad + c->N, false));
     }
     if (cache) c->has_lin = true;
     return PTYLM_OK;
 }
 
-// out += G v at the linearisation point (out already holds the damping term).
+// out += G v over z at the linearisation point (out already holds the damping term).
 static ptylm_status op_matvec_accumulate(ptylm_ctx* c, const float2* v, float2* out) {
     if (c->d.K == 0) return PTYLM_OK;
+    const int kid = joint(c) ? KID_MATVEC_J : KID_MATVEC;
+    if (joint(c)) STATUS_TRY(clear_probe_part(c, kid));
     PtyArgs a = base_args(c);
     a.O = v;
     a.P = c->P_lin;
     a.a_cache = c->a_cache;
     a.out = out;
-    STATUS_TRY(launch(c, KID_MATVEC, a));
+    if (joint(c)) {
+        a.VP = v + c->N;
+        a.Olin = c->O_lin;
+    }
+    STATUS_TRY(launch(c, kid, a));
+    if (joint(c)) STATUS_TRY(probe_reduce(c, kid, out + c->N, true));
     return PTYLM_OK;
 }
 
-// out = (G + lambda D) v at the linearisation point (device pointers).
+// out = (G + lambda D) v over z at the linearisation point (device pointers).
 static ptylm_status op_matvec(ptylm_ctx* c, const float2* v, double lambda, const float* D, float2* out) {
     const int nb = vec_blocks(c);
-    k_damping_init<<<nb, VEC_THREADS, 0, c->stream>>>(v, D, (float)lambda, out, c->N);
+    k_damping_init<<<nb, VEC_THREADS, 0, c->stream>>>(v, D, (float)lambda, out, c->L);
     STATUS_TRY(vec_launched(c));
     return op_matvec_accumulate(c, v, out);
+}
+
+// Closed-form Dg(G) over z at the linearisation point, floored at floor_rel * max.
+static ptylm_status op_ggn_diag(ptylm_ctx* c, float* D, double floor_rel) {
+    CUDA_TRY(cudaMemsetAsync(D, 0, sizeof(float) * c->L, c->stream));
+    CUDA_TRY(launch_ggn_diag(c->LS, c->trp, c->pos, c->d.K, c->O_lin, c->P_lin, c->d.nx, D,
+                             joint(c) ? D + c->N : nullptr, c->tr, c->stream));
+    c->launches += joint(c) ? 2 : 1;
+    if (floor_rel > 0.0) {
+        // each block (object, probe) is floored by its own maximum: their scales differ
+        const int nb = vec_blocks(c);
+        for (int blk = 0; blk < (joint(c) ? 2 : 1); ++blk) {
+            float* Db = blk == 0 ? D : D + c->N;
+            const long nblk = blk == 0 ? c->N : c->M;
+            k_block_max<<<nb, VEC_THREADS, 0, c->stream>>>(Db, nblk, c->partials);
+            STATUS_TRY(vec_launched(c));
+            k_apply_floor<<<nb, VEC_THREADS, 0, c->stream>>>(Db, nblk, c->partials, nb, (float)floor_rel);
+            STATUS_TRY(vec_launched(c));
+        }
+    }
+    return PTYLM_OK;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -427,6 +568,16 @@ void ptylm_default_lm_params(ptylm_lm_params* p, int loss) {
     p->max_cg = 100;
     p->fixed_cg = 0;
     p->target_err = 0.0;
+    p->scaled = 0;
+    p->projected = 0;
+    p->radius_O = 1.0;
+    p->radius_P = 1e8;
+    p->gamma = 1e-6;
+    p->tau_s = 1e-8;
+    p->p_s = 2.1;
+    p->sigma = 1e-4;
+    p->max_ls = 30;
+    p->diag_floor = 1e-6;
 }
 
 ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* positions_dev,
@@ -445,7 +596,7 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
     if (d.K < 0) return fail(PTYLM_ERR_ARG, "K must be >= 0");
     if (d.loss != PTYLM_LOSS_GAUSSIAN && d.loss != PTYLM_LOSS_POISSON) return fail(PTYLM_ERR_ARG, "unknown loss %d", d.loss);
     if (!(d.background > 0.0f) || !std::isfinite(d.background)) return fail(PTYLM_ERR_ARG, "background must be finite and > 0");
-    if (d.joint != 0) return fail(PTYLM_ERR_ARG, "joint object+probe contexts are not available in this build");
+    if (d.joint != 0 && d.joint != 1) return fail(PTYLM_ERR_ARG, "joint must be 0 or 1");
     if (d.K > 0 && (!positions_dev || !y_dev)) return fail(PTYLM_ERR_ARG, "positions and y must be non-NULL when K > 0");
     if ((long)d.ny * d.nx > (1L << 31)) return fail(PTYLM_ERR_ARG, "object too large");
 
@@ -468,6 +619,7 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
     c->S = 1 << LS;
     c->M = c->S * c->S;
     c->N = (long)d.ny * d.nx;
+    c->L = c->N + (d.joint ? c->M : 0);
     c->stream = static_cast<cudaStream_t>(stream);
     auto bail = [&](ptylm_status s) {
         ctx_free_all(c);
@@ -489,7 +641,8 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
         const int need = std::max(1, (d.K + teams - 1) / teams);
         c->grid[kid] = std::min(per_sm * c->num_sms, need);
     }
-    c->vec_grid = std::min<long>(c->num_sms * 8L, std::max<long>(1, (c->N + VEC_THREADS - 1) / VEC_THREADS));
+    c->vec_grid = std::min<long>(c->num_sms * 8L, std::max<long>(1, (c->L + VEC_THREADS - 1) / VEC_THREADS));
+    c->probe_slots = d.joint ? std::max({c->grid[KID_FWD_CACHE_J], c->grid[KID_MATVEC_J], c->grid[KID_JTVP_J]}) * teams : 0;
     c->partials_cap = std::max(c->vec_grid, *std::max_element(c->grid, c->grid + KID_COUNT));
 
     ptylm_status s;
@@ -497,7 +650,11 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
     if ((s = ctx_alloc_t(c, &c->tw, c->S, "twiddles")) != PTYLM_OK) return bail(s);
     if ((s = ctx_alloc_t(c, &c->a_cache, (size_t)d.K * c->M, "frequency cache")) != PTYLM_OK) return bail(s);
     if ((s = ctx_alloc_t(c, &c->y_perm, (size_t)d.K * c->M, "measurements")) != PTYLM_OK) return bail(s);
-    if ((s = ctx_alloc_t(c, &c->grad, c->N, "gradient")) != PTYLM_OK) return bail(s);
+    if ((s = ctx_alloc_t(c, &c->grad, c->L, "gradient")) != PTYLM_OK) return bail(s);
+    if ((s = ctx_alloc_t(c, &c->trp, (size_t)std::max(1, d.K) * (c->M / 32), "d2l sums")) != PTYLM_OK) return bail(s);
+    if ((s = ctx_alloc_t(c, &c->tr, std::max(1, d.K), "per-position d2l sums")) != PTYLM_OK) return bail(s);
+    if (d.joint && (s = ctx_alloc_t(c, &c->probe_part, (size_t)c->probe_slots * c->M, "probe accumulators")) != PTYLM_OK)
+        return bail(s);
     if ((s = ctx_alloc_t(c, &c->O_lin, c->N, "object linearisation point")) != PTYLM_OK) return bail(s);
     if ((s = ctx_alloc_t(c, &c->P_lin, c->M, "probe linearisation point")) != PTYLM_OK) return bail(s);
     if ((s = ctx_alloc_t(c, &c->partials, (size_t)c->partials_cap * kMaxReduceWidth, "partials")) != PTYLM_OK) return bail(s);
@@ -613,43 +770,52 @@ ptylm_status forward_loss(ptylm_ctx* c, const ptylm_c64* O, const ptylm_c64* P, 
 ptylm_status gradient(ptylm_ctx* c, ptylm_c64* gO, ptylm_c64* gP) {
     g_last_error.clear();
     if (!c || !gO) return fail(PTYLM_ERR_ARG, "ctx and gO must be non-NULL");
-    if (gP) return fail(PTYLM_ERR_ARG, "probe gradient needs a joint context");
+    if (gP && !joint(c)) return fail(PTYLM_ERR_ARG, "probe gradient needs a joint context");
     if (!c->has_lin) return fail(PTYLM_ERR_STATE, "no linearisation point");
     CUDA_TRY(cudaMemcpyAsync(gO, c->grad, sizeof(float2) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    if (gP) CUDA_TRY(cudaMemcpyAsync(gP, c->grad + c->N, sizeof(float2) * c->M, cudaMemcpyDeviceToDevice, c->stream));
     return PTYLM_OK;
 }
 
 ptylm_status jvp(ptylm_ctx* c, const ptylm_c64* vO, const ptylm_c64* vP, float* out) {
     g_last_error.clear();
     if (!c || !vO || !out) return fail(PTYLM_ERR_ARG, "ctx, vO and out must be non-NULL");
-    if (vP) return fail(PTYLM_ERR_ARG, "probe direction needs a joint context");
+    if (vP && !joint(c)) return fail(PTYLM_ERR_ARG, "probe direction needs a joint context");
     if (!c->has_lin) return fail(PTYLM_ERR_STATE, "no linearisation point");
     if (c->d.K == 0) return PTYLM_OK;
-    if (!c->jvp_scratch)
-        STATUS_TRY(ctx_alloc_t(c, &c->jvp_scratch, (size_t)c->grid[KID_JVP] * cta_teams(c->LS) * c->M, "jvp scratch"));
+    const int kid = vP ? KID_JVP_J : KID_JVP;
+    if (!c->jvp_scratch) {
+        const size_t slots = (size_t)std::max(c->grid[KID_JVP], c->grid[KID_JVP_J]) * cta_teams(c->LS);
+        STATUS_TRY(ctx_alloc_t(c, &c->jvp_scratch, slots * c->M, "jvp scratch"));
+    }
     PtyArgs a = base_args(c);
     a.O = c->O_lin;
     a.V = reinterpret_cast<const float2*>(vO);
+    a.VP = reinterpret_cast<const float2*>(vP);
     a.P = c->P_lin;
     a.out_real = out;
     a.scratch = c->jvp_scratch;
-    STATUS_TRY(launch(c, KID_JVP, a));
+    STATUS_TRY(launch(c, kid, a));
     return PTYLM_OK;
 }
 
 ptylm_status jtvp(ptylm_ctx* c, const float* w, ptylm_c64* outO, ptylm_c64* outP) {
     g_last_error.clear();
     if (!c || !w || !outO) return fail(PTYLM_ERR_ARG, "ctx, w and outO must be non-NULL");
-    if (outP) return fail(PTYLM_ERR_ARG, "probe part needs a joint context");
+    if (outP && !joint(c)) return fail(PTYLM_ERR_ARG, "probe part needs a joint context");
     if (!c->has_lin) return fail(PTYLM_ERR_STATE, "no linearisation point");
     CUDA_TRY(cudaMemsetAsync(outO, 0, sizeof(float2) * c->N, c->stream));
+    if (outP) CUDA_TRY(cudaMemsetAsync(outP, 0, sizeof(float2) * c->M, c->stream));
     if (c->d.K == 0) return PTYLM_OK;
+    const int kid = outP ? KID_JTVP_J : KID_JTVP;
+    if (outP) STATUS_TRY(clear_probe_part(c, kid));
     PtyArgs a = base_args(c);
     a.O = c->O_lin;
     a.P = c->P_lin;
     a.w = w;
     a.out = reinterpret_cast<float2*>(outO);
-    STATUS_TRY(launch(c, KID_JTVP, a));
+    STATUS_TRY(launch(c, kid, a));
+    if (outP) STATUS_TRY(probe_reduce(c, kid, reinterpret_cast<float2*>(outP), false));
     return PTYLM_OK;
 }
 
@@ -657,27 +823,39 @@ ptylm_status ggn_matvec(ptylm_ctx* c, const ptylm_c64* vO, const ptylm_c64* vP, 
                         const float* D, ptylm_c64* outO, ptylm_c64* outP) {
     g_last_error.clear();
     if (!c || !vO || !outO) return fail(PTYLM_ERR_ARG, "ctx, vO and outO must be non-NULL");
-    if (vP || outP) return fail(PTYLM_ERR_ARG, "probe blocks need a joint context");
+    if (joint(c) != (vP != nullptr) || joint(c) != (outP != nullptr))
+        return fail(PTYLM_ERR_ARG, "vP and outP are required in joint contexts and must be NULL otherwise");
     if (!c->has_lin) return fail(PTYLM_ERR_STATE, "no linearisation point");
     if (!std::isfinite(lambda)) return fail(PTYLM_ERR_ARG, "lambda must be finite");
-    const bool host_in = is_host_pointer(vO), host_out = is_host_pointer(outO);
+    const bool host_in = is_host_pointer(vO) || (vP && is_host_pointer(vP));
+    const bool host_out = is_host_pointer(outO) || (outP && is_host_pointer(outP));
+    if (!c->stage_a) STATUS_TRY(ctx_alloc_t(c, &c->stage_a, c->L, "staging (vector)"));
+    if (!c->stage_b) STATUS_TRY(ctx_alloc_t(c, &c->stage_b, c->L, "staging (result)"));
+    // gather z-vectors contiguously (object part, then probe part)
     const float2* v = reinterpret_cast<const float2*>(vO);
-    float2* o = reinterpret_cast<float2*>(outO);
-    if (host_in || host_out) {
-        if (!c->stage_a) STATUS_TRY(ctx_alloc_t(c, &c->stage_a, c->N, "staging (vector)"));
-        if (!c->stage_b) STATUS_TRY(ctx_alloc_t(c, &c->stage_b, c->N, "staging (result)"));
-    }
-    if (host_in) {
-        CUDA_TRY(cudaMemcpyAsync(c->stage_a, vO, sizeof(float2) * c->N, cudaMemcpyHostToDevice, c->stream));
+    if (host_in || joint(c)) {
+        const cudaMemcpyKind k = host_in ? cudaMemcpyDefault : cudaMemcpyDeviceToDevice;
+        CUDA_TRY(cudaMemcpyAsync(c->stage_a, vO, sizeof(float2) * c->N, k, c->stream));
+        if (vP) CUDA_TRY(cudaMemcpyAsync(c->stage_a + c->N, vP, sizeof(float2) * c->M, k, c->stream));
         v = c->stage_a;
     }
-    if (host_out) o = c->stage_b;
+    float2* o = (host_out || joint(c)) ? c->stage_b : reinterpret_cast<float2*>(outO);
     STATUS_TRY(op_matvec(c, v, lambda, D, o));
-    if (host_out) {
-        CUDA_TRY(cudaMemcpyAsync(outO, o, sizeof(float2) * c->N, cudaMemcpyDeviceToHost, c->stream));
-        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (host_out || joint(c)) {
+        const cudaMemcpyKind k = host_out ? cudaMemcpyDefault : cudaMemcpyDeviceToDevice;
+        CUDA_TRY(cudaMemcpyAsync(outO, o, sizeof(float2) * c->N, k, c->stream));
+        if (outP) CUDA_TRY(cudaMemcpyAsync(outP, o + c->N, sizeof(float2) * c->M, k, c->stream));
+        if (host_out) CUDA_TRY(cudaStreamSynchronize(c->stream));
     }
     return PTYLM_OK;
+}
+
+ptylm_status ggn_diag(ptylm_ctx* c, float* D_out, double floor_rel) {
+    g_last_error.clear();
+    if (!c || !D_out) return fail(PTYLM_ERR_ARG, "ctx and D_out must be non-NULL");
+    if (!c->has_lin) return fail(PTYLM_ERR_STATE, "no linearisation point");
+    if (!(floor_rel >= 0.0) || !(floor_rel < 1.0)) return fail(PTYLM_ERR_ARG, "floor_rel must be in [0, 1)");
+    return op_ggn_diag(c, D_out, floor_rel);
 }
 
 ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, const ptylm_lm_params* prm,
@@ -686,29 +864,55 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
     if (!c || !O_inout || !P_inout || !prm) return fail(PTYLM_ERR_ARG, "ctx, O, P and params must be non-NULL");
     if (prm->max_outer < 0 || prm->max_cg < 0 || !(prm->kappa > 1.0) || !(prm->mu0 > 0.0))
         return fail(PTYLM_ERR_ARG, "invalid LM parameters");
+    if (prm->projected && (!(prm->radius_O > 0.0) || !(prm->radius_P > 0.0) || prm->max_ls < 0))
+        return fail(PTYLM_ERR_ARG, "invalid projection parameters");
     if (c->d.K == 0) return fail(PTYLM_ERR_ARG, "lm_solve needs at least one scan position");
-    const long N = c->N;
-    const size_t nbytes = sizeof(float2) * N;
+    const long N = c->N, L = c->L;
+    const size_t zbytes = sizeof(float2) * L;
     if (!c->cg_x) {
-        STATUS_TRY(ctx_alloc_t(c, &c->cg_x, N, "CG x"));
-        STATUS_TRY(ctx_alloc_t(c, &c->cg_r, N, "CG r"));
-        STATUS_TRY(ctx_alloc_t(c, &c->cg_p, N, "CG p"));
-        STATUS_TRY(ctx_alloc_t(c, &c->cg_q, N, "CG q"));
-        STATUS_TRY(ctx_alloc_t(c, &c->trial, N, "trial point"));
+        STATUS_TRY(ctx_alloc_t(c, &c->cg_x, L, "CG x"));
+        STATUS_TRY(ctx_alloc_t(c, &c->cg_r, L, "CG r"));
+        STATUS_TRY(ctx_alloc_t(c, &c->cg_p, L, "CG p"));
+        STATUS_TRY(ctx_alloc_t(c, &c->cg_q, L, "CG q"));
+        STATUS_TRY(ctx_alloc_t(c, &c->trial, L, "trial point"));
     }
-    if (!c->stage_a) STATUS_TRY(ctx_alloc_t(c, &c->stage_a, N, "iterate"));
+    if (prm->projected && !c->ls_dir) STATUS_TRY(ctx_alloc_t(c, &c->ls_dir, L, "line-search direction"));
+    if (prm->scaled && !c->Dg) STATUS_TRY(ctx_alloc_t(c, &c->Dg, L, "scaling"));
+    if (!c->stage_a) STATUS_TRY(ctx_alloc_t(c, &c->stage_a, L, "iterate"));
     if (!c->stage_P) STATUS_TRY(ctx_alloc_t(c, &c->stage_P, c->M, "probe"));
     const bool host_O = is_host_pointer(O_inout), host_P = is_host_pointer(P_inout);
-    // The iterate lives in stage_a throughout (the caller's buffer is read once, written once).
-    CUDA_TRY(cudaMemcpyAsync(c->stage_a, O_inout, nbytes, host_O ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
-    CUDA_TRY(cudaMemcpyAsync(c->stage_P, P_inout, sizeof(float2) * c->M,
-                             host_P ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
-    float2* O = c->stage_a;
-    const float2* P = c->stage_P;
+    const cudaMemcpyKind kin_O = host_O ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind kin_P = host_P ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    // The state z = [O; P] lives in stage_a throughout (the caller's buffers are read once,
+    // written once); object-only contexts keep the fixed probe in stage_P.
+    float2* z = c->stage_a;
+    CUDA_TRY(cudaMemcpyAsync(z, O_inout, sizeof(float2) * N, kin_O, c->stream));
+    if (joint(c)) CUDA_TRY(cudaMemcpyAsync(z + N, P_inout, sizeof(float2) * c->M, kin_P, c->stream));
+    else CUDA_TRY(cudaMemcpyAsync(c->stage_P, P_inout, sizeof(float2) * c->M, kin_P, c->stream));
+    auto probe_of = [&](float2* state) -> const float2* { return joint(c) ? state + N : c->stage_P; };
     float2 *x = c->cg_x, *r = c->cg_r, *p = c->cg_p, *q = c->cg_q, *trial = c->trial;
+    const float* D = prm->scaled ? c->Dg : nullptr;
     const int nb = vec_blocks(c);
     unsigned* cnt = c->counters + CNT_VEC;
-    CUDA_TRY(cudaMemsetAsync(x, 0, nbytes, c->stream));
+    CUDA_TRY(cudaMemsetAsync(x, 0, zbytes, c->stream));
+
+    double f_min = 0.0;  // Algorithm 2 compares f - f_min (the Poisson metric can be negative)
+    if (prm->projected && c->d.loss == PTYLM_LOSS_POISSON) {
+        k_poisson_fmin<<<nb, VEC_THREADS, 0, c->stream>>>(c->y_perm, (long)c->d.K * c->M, c->partials, cnt, c->scal);
+        STATUS_TRY(vec_launched(c));
+        STATUS_TRY(read_scalars(c, S_FMIN, 1));
+        f_min = c->scal_host[S_FMIN];
+    }
+    auto loss_at = [&](float2* state, double* f_out) -> ptylm_status {
+        STATUS_TRY(op_forward(c, state, probe_of(state), 0));
+        STATUS_TRY(read_scalars(c, S_F, 1));
+        *f_out = c->scal_host[S_F];
+        return PTYLM_OK;
+    };
+    auto project = [&](float2* state) -> ptylm_status {
+        k_project<<<nb, VEC_THREADS, 0, c->stream>>>(state, N, L, (float)prm->radius_O, (float)prm->radius_P);
+        return vec_launched(c);
+    };
 
     double mu = prm->mu0;
     int cg_total = 0, matvecs = 0, t = 0;
@@ -716,7 +920,7 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
     ptylm_status status = PTYLM_OK;
     double f_cur = NAN, err = NAN;
     auto object_error = [&](double* e_out) -> ptylm_status {
-        k_err_sums<<<nb, VEC_THREADS, 0, c->stream>>>(O, reinterpret_cast<const float2*>(prm->O_ref), prm->mask, N,
+        k_err_sums<<<nb, VEC_THREADS, 0, c->stream>>>(z, reinterpret_cast<const float2*>(prm->O_ref), prm->mask, N,
                                                       c->partials, cnt, c->scal);
         STATUS_TRY(vec_launched(c));
         STATUS_TRY(read_scalars(c, S_ER, 4));
@@ -727,9 +931,10 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
     };
 
     for (t = 0; t < prm->max_outer; ++t) {
-        // Linearise: f, ||grad_zeta l||^2, cache a, grad f (Algorithm 1, first step of the loop).
-        STATUS_TRY(op_forward(c, O, P, 1));
-        STATUS_TRY(dots(c, 1, c->grad, c->grad, nullptr, nullptr, nullptr, nullptr, S_GG));
+        // Linearise: f, ||grad_zeta l||^2, cache a, grad f, Dg(G) (Algorithm 1, first step).
+        STATUS_TRY(op_forward(c, z, probe_of(z), 1));
+        STATUS_TRY(dots(c, 1, L, c->grad, c->grad, nullptr, nullptr, nullptr, nullptr, nullptr, S_GG));
+        if (D) STATUS_TRY(op_ggn_diag(c, c->Dg, prm->diag_floor));
         STATUS_TRY(read_scalars(c, S_F, S_GG - S_F + 1));
         const double f = c->scal_host[S_F], dl2 = c->scal_host[S_DL2], gg = c->scal_host[S_GG];
         if (!std::isfinite(f) || !std::isfinite(gg)) {
@@ -748,13 +953,14 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
         int cg_this = 0;
         bool stalled = false;
         while (!(rho > prm->rho_min)) {
-            const double lambda = mu * std::pow(std::sqrt(dl2), prm->nu);
+            // lambda = mu ||grad_zeta l||^nu (D = I) or mu (D = Dg(G)), Algorithm 1
+            const double lambda = D ? mu : mu * std::pow(std::sqrt(dl2), prm->nu);
             const float lam32 = (float)lambda;
-            // ---- truncated CG on (G + lambda I) x = -g, warm-started from x ----
-            STATUS_TRY(op_matvec(c, x, lambda, nullptr, q));                      // q = (G + lambda I) x
+            // ---- truncated (P)CG on (G + lambda D) x = -g, warm-started from x ----
+            STATUS_TRY(op_matvec(c, x, lambda, D, q));                            // q = (G + lambda D) x
             ++matvecs;
-            k_cg_start<<<nb, VEC_THREADS, 0, c->stream>>>(c->grad, q, r, p, lam32, N, c->partials, cnt, c->scal);
-            STATUS_TRY(vec_launched(c));                                          // r = p = -g - q, q = lambda p
+            k_cg_start<<<nb, VEC_THREADS, 0, c->stream>>>(c->grad, q, r, p, D, lam32, L, c->partials, cnt, c->scal);
+            STATUS_TRY(vec_launched(c));                                          // r, p = P^-1 r, q = lambda D p
             int it = 0;
             bool converged = false;
             for (;;) {
@@ -767,20 +973,20 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
                 }
                 STATUS_TRY(op_matvec_accumulate(c, p, q));                        // q += G p
                 ++matvecs;
-                STATUS_TRY(dots(c, 1, p, q, nullptr, nullptr, nullptr, nullptr, S_PAP, OP_ALPHA));  // alpha
-                k_cg_update<<<nb, VEC_THREADS, 0, c->stream>>>(x, r, p, q, N, c->partials, cnt, c->scal);
+                STATUS_TRY(dots(c, 1, L, p, q, nullptr, nullptr, nullptr, nullptr, nullptr, S_PAP, OP_ALPHA));
+                k_cg_update<<<nb, VEC_THREADS, 0, c->stream>>>(x, r, p, q, D, lam32, L, c->partials, cnt, c->scal);
                 STATUS_TRY(vec_launched(c));                                      // x, r; beta
-                k_cg_direction<<<nb, VEC_THREADS, 0, c->stream>>>(r, p, q, nullptr, lam32, N, c->scal);
-                STATUS_TRY(vec_launched(c));                                      // p, q = lambda p
+                k_cg_direction<<<nb, VEC_THREADS, 0, c->stream>>>(r, p, q, D, lam32, L, c->scal);
+                STATUS_TRY(vec_launched(c));                                      // p, q = lambda D p
                 ++it;
             }
             cg_this += it;
             if (!converged && prm->fixed_cg <= 0 && it >= prm->max_cg) hit_maxit = true;
             // ---- trial point and gain ratio (Algorithm 1) ----
-            k_add<<<nb, VEC_THREADS, 0, c->stream>>>(O, x, trial, N);
+            k_axpy<<<nb, VEC_THREADS, 0, c->stream>>>(z, x, 1.0f, trial, L);
             STATUS_TRY(vec_launched(c));
-            STATUS_TRY(op_forward(c, trial, P, 0));
-            STATUS_TRY(dots(c, 3, x, x, x, c->grad, x, r, S_DD));
+            STATUS_TRY(op_forward(c, trial, probe_of(trial), 0));
+            STATUS_TRY(dots(c, 3, L, x, x, D, x, c->grad, x, r, S_DD));
             STATUS_TRY(read_scalars(c, S_F, S_DR - S_F + 1));
             const double f_trial = c->scal_host[S_F];
             const double dd = c->scal_host[S_DD], dg = c->scal_host[S_DG], dr = c->scal_host[S_DR];
@@ -791,8 +997,46 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
             else if (rho > 0.25) { /* keep mu */ }
             else mu = prm->kappa * mu;
             if (rho > prm->rho_min) {
-                CUDA_TRY(cudaMemcpyAsync(O, trial, nbytes, cudaMemcpyDeviceToDevice, c->stream));
-                f_cur = f_trial;
+                if (!prm->projected) {
+                    CUDA_TRY(cudaMemcpyAsync(z, trial, zbytes, cudaMemcpyDeviceToDevice, c->stream));
+                    f_cur = f_trial;
+                } else {
+                    // ---- Algorithm 2: projected step, descent test, Armijo backtracking ----
+                    STATUS_TRY(project(trial));
+                    double fp = 0.0;
+                    STATUS_TRY(loss_at(trial, &fp));
+                    if (fp - f_min < prm->gamma * (f - f_min)) {
+                        CUDA_TRY(cudaMemcpyAsync(z, trial, zbytes, cudaMemcpyDeviceToDevice, c->stream));
+                        f_cur = fp;
+                    } else {
+                        float2* sdir = c->ls_dir;
+                        k_axpy<<<nb, VEC_THREADS, 0, c->stream>>>(trial, z, -1.0f, sdir, L);   // s = Pi(z + dz) - z
+                        STATUS_TRY(vec_launched(c));
+                        STATUS_TRY(dots(c, 2, L, c->grad, sdir, nullptr, sdir, sdir, nullptr, nullptr, S_GS));
+                        STATUS_TRY(read_scalars(c, S_GS, 2));
+                        const double gs = c->scal_host[S_GS], ss = c->scal_host[S_SS];
+                        double sn2 = ss;
+                        if (!(gs <= -prm->tau_s * std::pow(std::sqrt(ss), prm->p_s))) {
+                            // not a descent direction: projected gradient step, s = -g
+                            k_axpy<<<nb, VEC_THREADS, 0, c->stream>>>(c->grad, c->grad, -2.0f, sdir, L);
+                            STATUS_TRY(vec_launched(c));
+                            sn2 = gg;
+                        }
+                        double alpha = 1.0;
+                        for (int ls = 0; ls < prm->max_ls; ++ls, alpha *= 0.5) {
+                            k_axpy<<<nb, VEC_THREADS, 0, c->stream>>>(z, sdir, (float)alpha, trial, L);
+                            STATUS_TRY(vec_launched(c));
+                            STATUS_TRY(project(trial));
+                            double fl = 0.0;
+                            STATUS_TRY(loss_at(trial, &fl));
+                            if (fl <= f - prm->sigma * alpha * sn2) {             // Eq. armijo_criterion
+                                CUDA_TRY(cudaMemcpyAsync(z, trial, zbytes, cudaMemcpyDeviceToDevice, c->stream));
+                                f_cur = fl;
+                                break;
+                            }
+                        }
+                    }
+                }
             } else if (mu > prm->mu_max) {
                 stalled = true;
                 break;
@@ -819,7 +1063,11 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
             stats->hist_err[t] = NAN;
         }
     }
-    CUDA_TRY(cudaMemcpyAsync(O_inout, O, nbytes, host_O ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(O_inout, z, sizeof(float2) * N, host_O ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                             c->stream));
+    if (joint(c))
+        CUDA_TRY(cudaMemcpyAsync(P_inout, z + N, sizeof(float2) * c->M,
+                                 host_P ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (stats) {
         stats->n_outer = t;

@@ -17,15 +17,18 @@ enum Slot {
     S_GG = 7,                           // ||grad f||^2
     S_DD = 8, S_DG = 9, S_DR = 10,      // step dots for the predicted reduction
     S_ER = 11, S_EI = 12, S_NO = 13, S_NR = 14,  // object-error sums
+    S_RZ = 15,                          // r.z of the preconditioned CG (= r.r without preconditioner)
+    S_GS = 16, S_SS = 17,               // Algorithm 2: g.s and ||s||^2
+    S_FMIN = 18,                        // Poisson: sum y - y log y
     S_COUNT = 24
 };
 
 // What the last CTA does with the column sums c[] (scaled by `scale`).
 enum FinalOp {
     OP_STORE = 0,   // sc[dst + i] = c[i]
-    OP_ALPHA = 1,   // p.Ap = c[0];  alpha = r.r / p.Ap
-    OP_BETA = 2,    // beta = c[0] / r.r;  r.r = c[0]
-    OP_START = 3    // r.r = c[0]   (CG start)
+    OP_ALPHA = 1,   // p.Ap = c[0];  alpha = r.z / p.Ap
+    OP_BETA = 2,    // beta = c[0] / r.z;  r.z = c[0];  r.r = c[1]
+    OP_START = 3    // r.z = c[0];  r.r = c[1]   (CG start)
 };
 
 // Counters, one per reduction site (kernels on one stream never overlap).
@@ -67,15 +70,17 @@ __device__ __forceinline__ void apply_final_op(const double* c, int W, double* s
             break;
         case OP_ALPHA:
             sc[S_PAP] = c[0];
-            sc[S_ALPHA] = sc[S_RR] / c[0];
+            sc[S_ALPHA] = sc[S_RZ] / c[0];
             break;
         case OP_BETA:
-            sc[S_RRNEW] = c[0];
-            sc[S_BETA] = c[0] / sc[S_RR];
-            sc[S_RR] = c[0];
+            sc[S_RRNEW] = c[1];
+            sc[S_BETA] = c[0] / sc[S_RZ];
+            sc[S_RZ] = c[0];
+            sc[S_RR] = c[1];
             break;
         case OP_START:
-            sc[S_RR] = c[0];
+            sc[S_RZ] = c[0];
+            sc[S_RR] = c[1];
             break;
     }
 }

@@ -54,7 +54,10 @@ class LMParams(ctypes.Structure):
                 ("mu_max", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("max_cg", ctypes.c_int), ("fixed_cg", ctypes.c_int),
                 ("target_err", ctypes.c_double), ("O_ref", ctypes.c_void_p),
-                ("mask", ctypes.c_void_p)]
+                ("mask", ctypes.c_void_p), ("scaled", ctypes.c_int), ("projected", ctypes.c_int),
+                ("radius_O", ctypes.c_double), ("radius_P", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("tau_s", ctypes.c_double), ("p_s", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("max_ls", ctypes.c_int), ("diag_floor", ctypes.c_double)]
 
 
 class LMStats(ctypes.Structure):
@@ -90,6 +93,7 @@ def load_library():
             lib.lm_destroy.argtypes = [vp]
             lib.forward_intensity.argtypes = [vp, vp, vp, vp]
             lib.ptylm_set_measurements.argtypes = [vp, vp]
+            lib.ggn_diag.argtypes = [vp, vp, d]
             lib.ptylm_forward_loss_noalloc.argtypes = [i, i, i, i, i, ctypes.c_float, vp, vp, vp, vp, vp, vp]
             lib.ptylm_profile.argtypes = [vp, i]
             lib.ptylm_profile_read.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
@@ -99,7 +103,7 @@ def load_library():
             lib.ptylm_default_lm_params.argtypes = [ctypes.POINTER(LMParams), i]
             for name in ("lm_init", "forward_loss", "gradient", "jvp", "jtvp", "ggn_matvec",
                          "lm_solve", "lm_destroy", "forward_intensity", "ptylm_set_measurements",
-                         "ptylm_forward_loss_noalloc",
+                         "ptylm_forward_loss_noalloc", "ggn_diag",
                          "ptylm_profile",
                          "ptylm_profile_read"):
                 getattr(lib, name).restype = i
@@ -240,6 +244,11 @@ def ptylm_profile_read(ctx: Context, kernel: int):
     ms, n = ctypes.c_double(), ctypes.c_longlong()
     _check(load_library().ptylm_profile_read(ctx.handle, int(kernel), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def ggn_diag(ctx: Context, D_out, floor_rel: float = 0.0) -> None:
+    """Closed-form Dg(G) over z (object, then probe for joint contexts) into D_out."""
+    _check(load_library().ggn_diag(ctx.handle, _ptr(D_out), ctypes.c_double(floor_rel)))
 
 
 def default_lm_params(loss: int) -> LMParams:

@@ -1,0 +1,189 @@
+"""Joint object+probe (blind) operators, the closed-form GGN diagonal and the scaled /
+projected LM (PLM, PLM-J with Algorithm 2) of the CUDA path against the FP64 oracle.
+
+Tolerances as in test_gpu_parity.py: relative 1e-5 for well-conditioned inputs (Gaussian
+metric, Poisson at its noiseless truth)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_01767_gb300 import synth
+from tests.problems import make_case, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_01767_gb300 import build, ptylm
+    build.build()
+    ptylm.load_library()
+    return ptylm
+
+
+def c64(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.complex64)).cuda()
+
+
+def f32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.complex128 if t.is_complex() else np.float64)
+
+
+def setup(lib, shape, loss=0, seed=40, joint=1, at_truth=False):
+    n, m, K = shape
+    case = make_case(n, m, K=K, loss=loss, peak=1e3 if loss else 0.0, seed=seed, noisy=False)
+    ctx = lib.lm_init(n, n, m, m, torch.from_numpy(case.pos).cuda(), f32(case.y), loss, case.b, joint=joint)
+    if at_truth:
+        O, P = case.O_true, case.P
+    else:
+        O = synth.to_c64(case.O_true + synth.random_complex(case.O_true.shape, seed=seed + 1, scale=0.05))
+        P = synth.to_c64(case.P * 1.05 + synth.random_complex(case.P.shape, seed=seed + 2, scale=0.02))
+    return case, ctx, O, P
+
+
+SHAPES = [(96, 32, 37), (160, 64, 23), (288, 128, 11), (512, 64, 1000)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_joint_gradient(lib, shape):
+    case, ctx, O, P = setup(lib, shape)
+    f, _ = lib.forward_loss(ctx, c64(O), c64(P), cache=1)
+    pb = case.problem()
+    gO = torch.empty((shape[0], shape[0]), dtype=torch.complex64, device="cuda")
+    gP = torch.empty((shape[1], shape[1]), dtype=torch.complex64, device="cuda")
+    lib.gradient(ctx, gO, gP)
+    rO, rP = oracle.gradient(pb, O, P, probe_part=True)
+    assert rel_err(host(gO), rO) <= TOL
+    assert rel_err(host(gP), rP) <= TOL
+    assert abs(f - oracle.loss(pb, O, P)) <= TOL * abs(f)
+
+
+@pytest.mark.parametrize("loss,at_truth", [(0, False), (1, True)])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_joint_ggn_matvec(lib, shape, loss, at_truth):
+    n, m, _ = shape
+    case, ctx, O, P = setup(lib, shape, loss=loss, at_truth=at_truth)
+    lib.forward_loss(ctx, c64(O), c64(P), cache=1)
+    pb = case.problem()
+    L = n * n + m * m
+    v = synth.to_c64(synth.random_complex(L, seed=50))
+    D = synth.to_f32(np.abs(synth.random_real(L, seed=51)) + 0.5)
+    outO = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+    outP = torch.empty((m, m), dtype=torch.complex64, device="cuda")
+    for lam, Dv in ((0.0, None), (0.3, D)):
+        lib.ggn_matvec(ctx, c64(v[:n * n].reshape(n, n)), outO, lam, None if Dv is None else f32(Dv),
+                       vP=c64(v[n * n:].reshape(m, m)), outP=outP)
+        ref = oracle.ggn_matvec_z(pb, O, v, lam=lam, D=Dv, P=P, joint=True)
+        got = np.concatenate([host(outO).ravel(), host(outP).ravel()])
+        assert rel_err(got, ref) <= TOL, lam
+        # the probe block alone, so a small block error cannot hide behind the object block
+        assert rel_err(host(outP).ravel(), ref[n * n:]) <= TOL, lam
+
+
+@pytest.mark.parametrize("shape", SHAPES[:3])
+def test_joint_jvp_and_jtvp(lib, shape):
+    n, m, K = shape
+    case, ctx, O, P = setup(lib, shape)
+    lib.forward_loss(ctx, c64(O), c64(P), cache=1)
+    pb = case.problem()
+    vO = synth.to_c64(synth.random_complex((n, n), seed=60))
+    vP = synth.to_c64(synth.random_complex((m, m), seed=61))
+    out = torch.empty((K, m, m), dtype=torch.float32, device="cuda")
+    lib.jvp(ctx, c64(vO), out, vP=c64(vP))
+    assert rel_err(host(out), oracle.jvp(pb, O, vO, P=P, vP=vP)) <= TOL
+    w = synth.to_f32(synth.random_real((K, m, m), seed=62))
+    outO = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+    outP = torch.empty((m, m), dtype=torch.complex64, device="cuda")
+    lib.jtvp(ctx, f32(w), outO, outP)
+    rO, rP = oracle.jtvp(pb, O, w, P=P, probe_part=True)
+    assert rel_err(host(outO), rO) <= TOL
+    assert rel_err(host(outP), rP) <= TOL
+
+
+@pytest.mark.parametrize("joint", [0, 1])
+@pytest.mark.parametrize("loss", [0, 1])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_ggn_diag(lib, shape, loss, joint):
+    """App. B closed form: GPU (FP32 sums, float atomics) vs oracle (FP64), with the floor."""
+    n, m, _ = shape
+    case, ctx, O, P = setup(lib, shape, loss=loss, joint=joint)
+    if not joint:
+        P = case.P
+    lib.forward_loss(ctx, c64(O), c64(P), cache=1)
+    pb = case.problem()
+    L = n * n + (m * m if joint else 0)
+    for floor in (0.0, 1e-6):
+        D = torch.empty(L, dtype=torch.float32, device="cuda")
+        lib.ggn_diag(ctx, D, floor)
+        rO, rP = oracle.ggn_diag(pb, O, P, floor_rel=floor)
+        ref = np.concatenate([rO.ravel(), rP.ravel()]) if joint else rO.ravel()
+        assert rel_err(host(D), ref) <= TOL, floor
+        if joint:
+            assert rel_err(host(D)[n * n:], rP.ravel()) <= TOL, floor
+
+
+def test_plm_small_workload_matches_oracle(lib):
+    """PLM (D = Dg(G), Jacobi PCG) on the 128^2 noiseless workload: both reach 1e-3 object error."""
+    w = synth.SMALL
+    case = make_case(w.n, w.m, loss=0, seed=0, grid=w.grid, step=w.step, radius=w.radius)
+    ctx = lib.lm_init(w.n, w.n, w.m, w.m, torch.from_numpy(case.pos).cuda(), f32(case.y), 0, case.b)
+    mask = synth.illumination_mask(w.n, case.P, case.pos, 0.1)
+    O0 = synth.flat_object(w.n)
+    _, _, info_ref = oracle.lm_solve2(case.problem(), O0, O_ref=case.O_true, mask=mask, max_outer=60,
+                                      target_err=1e-3, scaled=1)
+    Od = c64(O0)
+    st, info = lib.lm_solve(ctx, Od, c64(case.P), hist_len=60, O_ref=c64(case.O_true),
+                            mask=torch.from_numpy(mask.astype(np.uint8)).cuda(), max_outer=60, target_err=1e-3,
+                            scaled=1)
+    err = oracle.object_error(host(Od), case.O_true, mask)
+    assert err <= 1e-3 and info_ref["err"][-1] <= 1e-3, (err, info, info_ref)
+    assert abs(info["n_outer"] - info_ref["n_outer"]) <= 3, (info["n_outer"], info_ref["n_outer"])
+
+
+def test_plm_joint_projected_blind_matches_oracle(lib):
+    """PLM-J + Algorithm 2 on a small noiseless blind problem (flat object, unphased probe):
+    the GPU and the oracle both reduce the blind-aligned object error twentyfold, keep |O| <= 1,
+    and end within 1e-2 of each other in that error."""
+    n, m = 96, 32
+    O_true = synth.to_c64(synth.object_texture(n, seed=4))
+    P_true = synth.to_c64(synth.probe_disk_defocus(m, 10.0))
+    pos, _ = synth.raster_positions(n, m, 8, 8, 1, seed=5)
+    pb = oracle.Problem((n, n), P_true, pos, None, 0, 1e-8)
+    pb.y = synth.to_f32(oracle.intensity(pb, O_true))
+    mask = synth.illumination_mask(n, P_true, pos, 0.3)
+    P0 = synth.to_c64(synth.probe_disk_defocus(m, 10.0, phased=False))
+    O0 = synth.flat_object(n) * 0.9
+    e0 = oracle.object_error_blind(O0, O_true, mask)
+    O_ref_run, _, _ = oracle.lm_solve2(pb, O0, P0, max_outer=40, scaled=1, joint=1, projected=1)
+    e_oracle = oracle.object_error_blind(O_ref_run, O_true, mask)
+    ctx = lib.lm_init(n, n, m, m, torch.from_numpy(pos).cuda(), f32(pb.y), 0, 1e-8, joint=1)
+    Od, Pd = c64(O0), c64(P0)
+    st, info = lib.lm_solve(ctx, Od, Pd, hist_len=40, max_outer=40, scaled=1, projected=1)
+    e_gpu = oracle.object_error_blind(host(Od), O_true, mask)
+    assert np.abs(host(Od)).max() <= 1.0 + 1e-6
+    assert e_gpu <= 0.05 * e0 and e_oracle <= 0.05 * e0, (e0, e_gpu, e_oracle)
+    assert abs(e_gpu - e_oracle) <= 1e-2, (e_gpu, e_oracle)
+    assert info["f"][-1] < 1e-3 * info["f"][0]
+
+
+def test_joint_argument_errors(lib):
+    case, ctx, O, P = setup(lib, (96, 32, 37), joint=0)
+    lib.forward_loss(ctx, c64(O), c64(case.P), cache=1)
+    g = torch.empty((96, 96), dtype=torch.complex64, device="cuda")
+    with pytest.raises(lib.PtylmError) as e:
+        lib.gradient(ctx, g, torch.empty((32, 32), dtype=torch.complex64, device="cuda"))
+    assert e.value.status == lib.PTYLM_ERR_ARG
+    case, ctxj, O, P = setup(lib, (96, 32, 37), joint=1)
+    lib.forward_loss(ctxj, c64(O), c64(P), cache=1)
+    with pytest.raises(lib.PtylmError) as e:
+        lib.ggn_matvec(ctxj, c64(O), g, 0.1)   # joint contexts need the probe blocks
+    assert e.value.status == lib.PTYLM_ERR_ARG
