@@ -159,6 +159,7 @@ class ClockSampler:
 def workload_config(w, cg_per_step, world):
     _, step_used = synth.raster_positions(w.n, w.m, w.grid, w.step, w.jitter, seed=1)
     return {"workload": w.name, "object": w.n, "probe": w.m, "positions": w.K,
+            "problem": "blind (object + probe), PLM-J with Algorithm 2" if w.joint else "object only, LM",
             "raster_step_used": step_used, "loss": "poisson" if w.loss else "amplitude",
             "peak_photons": w.peak, "cg_iters_per_step": cg_per_step, "parallelism": f"replicas{world}",
             "l2": "inputs larger than L2: 8 K M byte cache streamed per matvec"}
@@ -266,7 +267,7 @@ def setup_workload(ptylm, torch, w, dev, stream):
     pos_np, step_used = synth.raster_positions(w.n, w.m, w.grid, w.step, w.jitter, seed=1)
     pos = torch.from_numpy(pos_np).to(dev)
     y = torch.empty((pos_np.shape[0], w.m, w.m), dtype=torch.float32, device=dev)
-    ctx = ptylm.lm_init(w.n, w.n, w.m, w.m, pos, y, w.loss, 1e-8, stream=stream)
+    ctx = ptylm.lm_init(w.n, w.n, w.m, w.m, pos, y, w.loss, 1e-8, joint=int(w.joint), stream=stream)
     ptylm.forward_intensity(ctx, O_true, P, y)
     torch.cuda.synchronize(dev)
     if w.peak > 0:
@@ -277,6 +278,12 @@ def setup_workload(ptylm, torch, w, dev, stream):
     ptylm.ptylm_set_measurements(ctx, y)
     torch.cuda.synchronize(dev)
     O0 = torch.full((w.n, w.n), complex(float(O_true.abs().mean()), 0.0), dtype=torch.complex64, device=dev)
+    if w.joint:
+        # blind problem: start from the unphased disk with the true probe's integrated intensity
+        P0 = torch.from_numpy(synth.probe_disk_defocus(w.m, w.radius, phased=False).astype(np.complex64)).to(dev)
+        P0 *= math.sqrt(float((P.abs() ** 2).sum()) / float((P0.abs() ** 2).sum()))
+        O0 = torch.full((w.n, w.n), 0.9 + 0.0j, dtype=torch.complex64, device=dev)
+        P = P0
     return ctx, O0, P, y, pos, step_used
 
 
@@ -324,10 +331,16 @@ def main():
     params = ptylm.default_lm_params(w.loss)
     params.max_outer = 1
     params.fixed_cg = args.cg_per_step
+    if w.joint:  # the blind problem needs the scaled, projected variant (PLM-J with Algorithm 2)
+        params.scaled = 1
+        params.projected = 1
+    P_start = P.clone()
 
-    def step(Obuf, Pbuf, Ostart):
+    def step(Obuf, Pbuf, Ostart, Pstart=None):
         # every step is the first LM iteration from the same initial guess: constant work
         Obuf.copy_(Ostart)
+        if w.joint:
+            Pbuf.copy_(P_start if Pstart is None else Pstart)
         st, info = ptylm.lm_solve(ctx, Obuf, Pbuf, params)
         return info["matvecs"]
 
@@ -347,7 +360,7 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize(dev)
     elapsed = ev0.elapsed_time(ev1) / 1e3
-    mv_ms, mv_n = ptylm.ptylm_profile_read(ctx, ptylm.KERNEL_GGN_MATVEC)
+    mv_ms, mv_n = ptylm.ptylm_profile_read(ctx, ptylm.KERNEL_GGN_MATVEC_JOINT if w.joint else ptylm.KERNEL_GGN_MATVEC)
     _, launches = ptylm.ptylm_profile_read(ctx, -1)
     ptylm.ptylm_profile(ctx, False)
     elapsed, total_matvecs = reduce_over_ranks(elapsed, matvecs, dev)
@@ -356,12 +369,13 @@ def main():
     # End to end through the C-ABI with pinned host buffers: H2D of O and P, D2H of O.
     O0_h = O0.cpu().pin_memory()
     O_h = O0_h.clone().pin_memory()
-    P_h = P.cpu().pin_memory()
+    P0_h = P_start.cpu().pin_memory()
+    P_h = P0_h.clone().pin_memory()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     e2e_mv = 0
     for _ in range(args.e2e_steps):
-        e2e_mv += step(O_h, P_h, O0_h)
+        e2e_mv += step(O_h, P_h, O0_h, P0_h)
     e2e_s = time.perf_counter() - t0
     e2e_s, e2e_mv = reduce_over_ranks(e2e_s, e2e_mv, dev)
     N, M, K = w.n * w.n, w.m * w.m, int(pos.shape[0])
@@ -385,7 +399,8 @@ def main():
             "config": workload_config(w, args.cg_per_step, world),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
                          "frac": achieved / peak_fp32, "traffic": recorded_traffic(),
-                         "kernel": "k_ggn_matvec<7>", "avg_launch_us": avg_mv_s * 1e6,
+                         "kernel": f"k_ggn_matvec<{int(math.log2(w.m))}{', joint' if w.joint else ''}>",
+                         "avg_launch_us": avg_mv_s * 1e6,
                          "launches": mv_n, "flops_per_launch": flops,
                          "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
                          "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",

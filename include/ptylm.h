@@ -217,7 +217,11 @@ enum {
     PTYLM_KERNEL_GGN_MATVEC = 2,
     PTYLM_KERNEL_JTVP = 3,
     PTYLM_KERNEL_JVP = 4,
-    PTYLM_KERNEL_FORWARD_INTENSITY = 5
+    PTYLM_KERNEL_FORWARD_INTENSITY = 5,
+    PTYLM_KERNEL_FORWARD_CACHE_JOINT = 6,
+    PTYLM_KERNEL_GGN_MATVEC_JOINT = 7,
+    PTYLM_KERNEL_JTVP_JOINT = 8,
+    PTYLM_KERNEL_JVP_JOINT = 9
 };
 ptylm_status ptylm_profile(ptylm_ctx* ctx, int enable);
 ptylm_status ptylm_profile_read(ptylm_ctx* ctx, int kernel, double* total_ms, long long* launches);

@@ -233,6 +233,10 @@ KERNEL_GGN_MATVEC = 2
 KERNEL_JTVP = 3
 KERNEL_JVP = 4
 KERNEL_FORWARD_INTENSITY = 5
+KERNEL_FORWARD_CACHE_JOINT = 6
+KERNEL_GGN_MATVEC_JOINT = 7
+KERNEL_JTVP_JOINT = 8
+KERNEL_JVP_JOINT = 9
 
 
 def ptylm_profile(ctx: Context, enable: bool) -> None:

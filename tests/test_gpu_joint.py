@@ -2,13 +2,15 @@
 projected LM (PLM, PLM-J with Algorithm 2) of the CUDA path against the FP64 oracle.
 
 Tolerances as in test_gpu_parity.py: relative 1e-5 for well-conditioned inputs (Gaussian
-metric, Poisson at its noiseless truth)."""
+metric, Poisson at its noiseless truth); the Poisson diagonal at a perturbed point, whose
+traces sum 2 y / h over dark pixels, uses max(1e-5, 2 x its FP32 conditioning)."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2103_01767_gb300 import synth
 from tests.problems import make_case, rel_err
+from tests.test_gpu_parity import fp32_conditioning
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -121,14 +123,18 @@ def test_ggn_diag(lib, shape, loss, joint):
     lib.forward_loss(ctx, c64(O), c64(P), cache=1)
     pb = case.problem()
     L = n * n + (m * m if joint else 0)
+    def diag_at(A, floor):
+        rO, rP = oracle.ggn_diag(pb, A, P, floor_rel=floor)
+        return np.concatenate([rO.ravel(), rP.ravel()]) if joint else rO.ravel()
+
     for floor in (0.0, 1e-6):
         D = torch.empty(L, dtype=torch.float32, device="cuda")
         lib.ggn_diag(ctx, D, floor)
-        rO, rP = oracle.ggn_diag(pb, O, P, floor_rel=floor)
-        ref = np.concatenate([rO.ravel(), rP.ravel()]) if joint else rO.ravel()
-        assert rel_err(host(D), ref) <= TOL, floor
+        ref = diag_at(O, floor)
+        tol = TOL if loss == 0 else max(TOL, 2.0 * fp32_conditioning(lambda A: diag_at(A, floor), m, O))
+        assert rel_err(host(D), ref) <= tol, (floor, tol)
         if joint:
-            assert rel_err(host(D)[n * n:], rP.ravel()) <= TOL, floor
+            assert rel_err(host(D)[n * n:], ref[n * n:]) <= tol, (floor, tol)
 
 
 def test_plm_small_workload_matches_oracle(lib):
