@@ -147,12 +147,14 @@ ptylm_status forward_loss(ptylm_ctx* ctx, const ptylm_c64* O, const ptylm_c64* P
  * only available for joint contexts (else PTYLM_ERR_ARG when gP != NULL). */
 ptylm_status gradient(ptylm_ctx* ctx, ptylm_c64* gO, ptylm_c64* gP);
 
-/* Jacobian-vector product at the linearisation point (App. A Eqs. jvp_step_1..3; computed
+/* Jacobian-vector product at the current point (forward_loss(cache=1) or forward_magnitude;
+ * App. A Eqs. jvp_step_1..3; computed
  * in forward mode from App. B Eq. jac_ampl):
  *     out_km = Re( conj(psihat_km) [F (P . S_k vO + vP . S_k O)]_m ) / zeta_km
  *   vO: device [ny][nx]; vP: device [my][mx] (joint contexts only) or NULL (= 0);
  *   out: device float [K][my][mx], natural order.
- * Recomputes psihat from the stored (O, P); does not read the ggn_matvec cache. */
+ * Uses the stored phasor when forward_magnitude kept one, else recomputes psihat from the
+ * stored (O, P); never reads the ggn_matvec cache. */
 ptylm_status jvp(ptylm_ctx* ctx, const ptylm_c64* vO, const ptylm_c64* vP, float* out);
 
 /* Transposed-Jacobian product at the linearisation point (App. A Eq. arbitrary_jtvp_sequence):
@@ -205,6 +207,16 @@ ptylm_status lm_solve(ptylm_ctx* ctx, ptylm_c64* O_inout, ptylm_c64* P_inout,
  * [my][mx]; h_out: device float [K][my][mx] in natural order.  Changes no context state. */
 ptylm_status forward_intensity(ptylm_ctx* ctx, const ptylm_c64* O, const ptylm_c64* P, float* h_out);
 
+/* Magnitudes zeta = (|F diag(P) S_k O|^2 + b)^(1/2) for every position (Sec. 4.1,
+ * Eq. magnitude) into zeta_out (device float [K][my][mx], natural order), and make (O, P)
+ * the point of later jvp / jtvp calls (the loss cache is invalidated: ggn_matvec, gradient
+ * and ggn_diag need forward_loss(cache = 1) again).  store_phasor = 1 also keeps the unit
+ * phasor psihat / zeta (8 K M bytes, allocated once within the workspace budget, else
+ * PTYLM_ERR_NOMEM), so that jvp and jtvp need one 2D FFT per position instead of two;
+ * store_phasor = 0 makes them recompute the exit waves. */
+ptylm_status forward_magnitude(ptylm_ctx* ctx, const ptylm_c64* O, const ptylm_c64* P, float* zeta_out,
+                               int store_phasor);
+
 /* Instrumentation (no counterpart in the paper).  ptylm_profile(ctx, 1) resets the
  * counters and starts timing every launch of the per-position kernels with CUDA events on
  * the context stream; ptylm_profile(ctx, 0) stops.  ptylm_profile_read synchronises the
@@ -221,7 +233,12 @@ enum {
     PTYLM_KERNEL_FORWARD_CACHE_JOINT = 6,
     PTYLM_KERNEL_GGN_MATVEC_JOINT = 7,
     PTYLM_KERNEL_JTVP_JOINT = 8,
-    PTYLM_KERNEL_JVP_JOINT = 9
+    PTYLM_KERNEL_JVP_JOINT = 9,
+    PTYLM_KERNEL_FORWARD_MAGNITUDE = 10,
+    PTYLM_KERNEL_JVP_PHASOR = 11,
+    PTYLM_KERNEL_JVP_PHASOR_JOINT = 12,
+    PTYLM_KERNEL_JTVP_PHASOR = 13,
+    PTYLM_KERNEL_JTVP_PHASOR_JOINT = 14
 };
 ptylm_status ptylm_profile(ptylm_ctx* ctx, int enable);
 ptylm_status ptylm_profile_read(ptylm_ctx* ctx, int kernel, double* total_ms, long long* launches);

@@ -34,7 +34,10 @@ struct PtyArgs {
 enum KernelId {
     KID_FWD_LOSS = 0, KID_FWD_CACHE = 1, KID_MATVEC = 2, KID_JTVP = 3, KID_JVP = 4, KID_FWD_INTENSITY = 5,
     KID_FWD_CACHE_J = 6, KID_MATVEC_J = 7, KID_JTVP_J = 8, KID_JVP_J = 9,
-    KID_COUNT = 10
+    KID_FWD_MAG = 10,                       // zeta (natural order) and optionally u = psihat / zeta
+    KID_JVP_U = 11, KID_JVP_U_J = 12,       // J v from the stored phasor u (one FFT)
+    KID_JTVP_U = 13, KID_JTVP_U_J = 14,     // J^T w from the stored phasor u (one FFT)
+    KID_COUNT = 15
 };
 
 // Closed-form GGN diagonal (App. B, Eqs. ggn_diag_mat and ggn_joint_diag) from the per-thread

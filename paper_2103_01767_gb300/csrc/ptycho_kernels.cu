@@ -73,7 +73,7 @@ struct AdjArgs {          // J^T w and J v
 // Forward model + error metric (+ cache and gradient when CACHE; intensities only when
 // INTENSITY).
 // ---------------------------------------------------------------------------------------
-template <int LS, bool CACHE, bool INTENSITY = false, bool JOINT = false>
+template <int LS, bool CACHE, bool INTENSITY = false, bool JOINT = false, bool MAG = false>
 __global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
 k_forward(FwdArgs a) {
     using G = Geo<LS>;
@@ -85,7 +85,7 @@ k_forward(FwdArgs a) {
     for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
         const int2 rc = a.pos[k];
         const float* yk = a.y + (size_t)k * G::M + c.tid;  // measurements in team-register order
-        if constexpr (!INTENSITY) prefetch_tile_l2(a.y + (size_t)k * G::M, sizeof(float) * G::M, c.tid);
+        if constexpr (!INTENSITY && !MAG) prefetch_tile_l2(a.y + (size_t)k * G::M, sizeof(float) * G::M, c.tid);
         float sl = 0.0f, sd = 0.0f;
         gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
         if constexpr (CACHE) {
@@ -116,7 +116,12 @@ k_forward(FwdArgs a) {
             for (int e = 0; e < 32; ++e) {
                 const float2 ps = v[e] * invS;
                 const float h = ps.x * ps.x + ps.y * ps.y + a.b;
-                if constexpr (INTENSITY) {
+                if constexpr (MAG) {
+                    // zeta in natural order; the unit phasor u = psihat / zeta in team order
+                    const float r = rsqrtf(h);
+                    a.out_real[(size_t)k * G::M + ky * G::S + freq_kx<G>(c.tid, e)] = h * r;
+                    if (a.a_cache) a.a_cache[(size_t)k * G::M + e * G::T + c.tid] = ps * r;
+                } else if constexpr (INTENSITY) {
                     a.out_real[(size_t)k * G::M + ky * G::S + freq_kx<G>(c.tid, e)] = h;
                 } else {
                     const PixelTerms t = pixel_terms<true>(a.loss, h, __ldg(yk + e * G::T));
@@ -130,7 +135,7 @@ k_forward(FwdArgs a) {
         team_sync<G>();
     }
     double sums[2] = {acc_l, acc_d};
-    if constexpr (!INTENSITY) grid_reduce<2>(sums, a.partials, a.counter, a.scal, S_F, OP_STORE, 1.0);
+    if constexpr (!INTENSITY && !MAG) grid_reduce<2>(sums, a.partials, a.counter, a.scal, S_F, OP_STORE, 1.0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -270,6 +275,56 @@ cudaError_t permute_measurements(int LS, const float* y, float* y_perm, int K, i
 }
 
 // ---------------------------------------------------------------------------------------
+// J v and J^T w from a stored unit phasor u = psihat / zeta (team order, a_cache slot):
+//   J v = Re(conj(u) F(P S_k vO + vP S_k O)),   J^T w = S_k^T conj(P) F^H(u w)  (+ probe part)
+// one 2D FFT per position instead of two (psihat is not recomputed).
+// ---------------------------------------------------------------------------------------
+template <int LS, bool JOINT = false>
+__global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
+k_jvp_phasor(AdjArgs a, const float2* __restrict__ u) {
+    using G = Geo<LS>;
+    TeamCtx<G> c = team_setup<G>(a.tw);
+    const float invS = 1.0f / G::S;
+    float2 v[32];
+    for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
+        const int2 rc = a.pos[k];
+        if constexpr (JOINT) gather_joint<G>(v, a.V, a.P, a.VP, a.O, a.nx, rc.x, rc.y, c.tid);
+        else gather_times_probe<G>(v, a.V, a.P, a.nx, rc.x, rc.y, c.tid);
+        team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
+        float* ok = a.out_real + (size_t)k * G::M + freq_ky<G>(c.tid) * G::S;
+        const float2* uk = u + (size_t)k * G::M + c.tid;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            const float2 ue = __ldg(uk + e * G::T);
+            ok[freq_kx<G>(c.tid, e)] = (ue.x * v[e].x + ue.y * v[e].y) * invS;
+        }
+        team_sync<G>();
+    }
+}
+
+template <int LS, bool JOINT = false>
+__global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
+k_jtvp_phasor(AdjArgs a, const float2* __restrict__ u) {
+    using G = Geo<LS>;
+    TeamCtx<G> c = team_setup<G>(a.tw);
+    const float invS = 1.0f / G::S;
+    float2 v[32];
+    for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
+        const int2 rc = a.pos[k];
+        const float* wk = a.w + (size_t)k * G::M + freq_ky<G>(c.tid) * G::S;
+        const float2* uk = u + (size_t)k * G::M + c.tid;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) v[e] = __ldg(uk + e * G::T) * (__ldg(wk + freq_kx<G>(c.tid, e)) * invS);
+        team_sync<G>();  // the previous position's last shared-memory reads are done
+        team_fft_inv<G>(v, c.sm, c.tw, c.tid);
+        scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
+        if constexpr (JOINT)
+            accumulate_probe_adjoint<G>(v, a.outP_part + (size_t)(blockIdx.x * G::TEAMS + c.team) * G::M, a.O,
+                                        a.nx, rc.x, rc.y, c.tid);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // Closed-form GGN diagonal, App. B (Eqs. ggn_diag_elem_final, ggn_diag_mat, ggn_joint_diag),
 // in real coordinates: D_O[n] = sum_{k: n in patch k} |P[n - r_k]|^2 tr_k / (2M) and
 // D_P[m] = sum_k |O[r_k + m]|^2 tr_k / (2M), tr_k = sum_m d2l_km.
@@ -380,6 +435,11 @@ static const void* kernel_ptr(int kid) {
         case KID_MATVEC_J: return (const void*)k_ggn_matvec<LS, true>;
         case KID_JTVP_J: return (const void*)k_jtvp<LS, true>;
         case KID_JVP_J: return (const void*)k_jvp<LS, true>;
+        case KID_FWD_MAG: return (const void*)k_forward<LS, false, false, false, true>;
+        case KID_JVP_U: return (const void*)k_jvp_phasor<LS, false>;
+        case KID_JVP_U_J: return (const void*)k_jvp_phasor<LS, true>;
+        case KID_JTVP_U: return (const void*)k_jtvp_phasor<LS, false>;
+        case KID_JTVP_U_J: return (const void*)k_jtvp_phasor<LS, true>;
     }
     return nullptr;
 }
@@ -409,13 +469,16 @@ cudaError_t kernel_launch(int LS, int kid, const PtyArgs& a, int grid, cudaStrea
                a.trp, a.outP_part, a.K, a.nx, a.b, a.loss};
     MatvecArgs ma{a.O, a.P, a.pos, a.a_cache, a.out, a.tw, a.VP, a.Olin, a.outP_part, a.K, a.nx};
     AdjArgs ja{a.O, a.V, a.VP, a.P, a.pos, a.w, a.out, a.out_real, a.scratch, a.tw, a.outP_part, a.K, a.nx, a.b};
+    const float2* u = a.a_cache;
     void* arg = nullptr;
     switch (kid) {
-        case KID_FWD_LOSS: case KID_FWD_CACHE: case KID_FWD_INTENSITY: case KID_FWD_CACHE_J: arg = &fa; break;
+        case KID_FWD_LOSS: case KID_FWD_CACHE: case KID_FWD_INTENSITY: case KID_FWD_CACHE_J: case KID_FWD_MAG:
+            arg = &fa;
+            break;
         case KID_MATVEC: case KID_MATVEC_J: arg = &ma; break;
         default: arg = &ja; break;
     }
-    void* args[] = {arg};
+    void* args[] = {arg, &u};
     return cudaLaunchKernel(fn, dim3(grid), dim3(cta_threads(LS)), args, cta_smem_bytes(LS), stream);
 }
 

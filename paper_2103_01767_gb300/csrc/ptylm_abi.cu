@@ -280,7 +280,10 @@ struct ptylm_ctx {
     int probe_slots = 0;
     float* trp = nullptr;          // per-thread d2l sums of the last linearisation [K][T]
     float* tr = nullptr;           // per-position d2l sums [K]
-    bool has_lin = false;
+    float2* u_cache = nullptr;     // unit phasor psihat / zeta at the point [K][M] (team order)
+    bool u_valid = false;          // u_cache holds the phasor of the current point
+    bool has_point = false;        // O_lin / P_lin hold a point (jvp, jtvp)
+    bool has_lin = false;          // ... and the loss cache, gradient and d2l sums match it
     double f_lin = 0.0, dl2_lin = 0.0;
 
     // CG / LM vectors over z (allocated on first use)
@@ -466,6 +469,7 @@ static ptylm_status op_forward(ptylm_ctx* c, const float2* O, const float2* P, i
         CUDA_TRY(cudaMemsetAsync(c->grad, 0, sizeof(float2) * c->L, c->stream));
         if (joint(c)) STATUS_TRY(clear_probe_part(c, kid));
         c->has_lin = false;
+        c->u_valid = false;
     }
     if (c->d.K == 0) {
         CUDA_TRY(cudaMemsetAsync(c->scal + S_F, 0, 2 * sizeof(double), c->stream));
@@ -480,7 +484,7 @@ static ptylm_status op_forward(ptylm_ctx* c, const float2* O, const float2* P, i
         STATUS_TRY(launch(c, kid, a));
         if (cache && joint(c)) STATUS_TRY(probe_reduce(c, kid, c->grad + c->N, false));
     }
-    if (cache) c->has_lin = true;
+    if (cache) c->has_lin = c->has_point = true;
     return PTYLM_OK;
 }
 
@@ -695,7 +699,7 @@ ptylm_status ptylm_set_measurements(ptylm_ctx* c, const float* y_dev) {
     g_last_error.clear();
     if (!c) return fail(PTYLM_ERR_ARG, "ctx must be non-NULL");
     if (c->d.K > 0 && !y_dev) return fail(PTYLM_ERR_ARG, "y must be non-NULL when K > 0");
-    c->has_lin = false;
+    c->has_lin = false;  // the loss cache depends on y; the point and the phasor do not
     if (c->d.K == 0) return PTYLM_OK;
     CUDA_TRY(permute_measurements(c->LS, y_dev, c->y_perm, c->d.K, c->d.loss == PTYLM_LOSS_GAUSSIAN, c->vec_grid, c->stream));
     ++c->launches;
@@ -711,6 +715,28 @@ ptylm_status forward_intensity(ptylm_ctx* c, const ptylm_c64* O, const ptylm_c64
     a.P = reinterpret_cast<const float2*>(P);
     a.out_real = h_out;
     STATUS_TRY(launch(c, KID_FWD_INTENSITY, a));
+    return PTYLM_OK;
+}
+
+ptylm_status forward_magnitude(ptylm_ctx* c, const ptylm_c64* O, const ptylm_c64* P, float* zeta_out,
+                               int store_phasor) {
+    g_last_error.clear();
+    if (!c || !O || !P || !zeta_out) return fail(PTYLM_ERR_ARG, "ctx, O, P and zeta_out must be non-NULL");
+    CUDA_TRY(cudaMemcpyAsync(c->O_lin, O, sizeof(float2) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->P_lin, P, sizeof(float2) * c->M, cudaMemcpyDeviceToDevice, c->stream));
+    c->has_lin = false;
+    c->u_valid = false;
+    c->has_point = true;
+    if (store_phasor && !c->u_cache)
+        STATUS_TRY(ctx_alloc_t(c, &c->u_cache, (size_t)std::max(1, c->d.K) * c->M, "phasor cache"));
+    if (c->d.K == 0) return PTYLM_OK;
+    PtyArgs a = base_args(c);
+    a.O = c->O_lin;
+    a.P = c->P_lin;
+    a.out_real = zeta_out;
+    a.a_cache = store_phasor ? c->u_cache : nullptr;
+    STATUS_TRY(launch(c, KID_FWD_MAG, a));
+    c->u_valid = store_phasor != 0;
     return PTYLM_OK;
 }
 
@@ -781,10 +807,10 @@ ptylm_status jvp(ptylm_ctx* c, const ptylm_c64* vO, const ptylm_c64* vP, float* 
     g_last_error.clear();
     if (!c || !vO || !out) return fail(PTYLM_ERR_ARG, "ctx, vO and out must be non-NULL");
     if (vP && !joint(c)) return fail(PTYLM_ERR_ARG, "probe direction needs a joint context");
-    if (!c->has_lin) return fail(PTYLM_ERR_STATE, "no linearisation point");
+    if (!c->has_point) return fail(PTYLM_ERR_STATE, "no linearisation point");
     if (c->d.K == 0) return PTYLM_OK;
-    const int kid = vP ? KID_JVP_J : KID_JVP;
-    if (!c->jvp_scratch) {
+    const int kid = c->u_valid ? (vP ? KID_JVP_U_J : KID_JVP_U) : (vP ? KID_JVP_J : KID_JVP);
+    if (!c->u_valid && !c->jvp_scratch) {
         const size_t slots = (size_t)std::max(c->grid[KID_JVP], c->grid[KID_JVP_J]) * cta_teams(c->LS);
         STATUS_TRY(ctx_alloc_t(c, &c->jvp_scratch, slots * c->M, "jvp scratch"));
     }
@@ -795,6 +821,7 @@ ptylm_status jvp(ptylm_ctx* c, const ptylm_c64* vO, const ptylm_c64* vP, float* 
     a.P = c->P_lin;
     a.out_real = out;
     a.scratch = c->jvp_scratch;
+    a.a_cache = c->u_valid ? c->u_cache : nullptr;
     STATUS_TRY(launch(c, kid, a));
     return PTYLM_OK;
 }
@@ -803,17 +830,18 @@ ptylm_status jtvp(ptylm_ctx* c, const float* w, ptylm_c64* outO, ptylm_c64* outP
     g_last_error.clear();
     if (!c || !w || !outO) return fail(PTYLM_ERR_ARG, "ctx, w and outO must be non-NULL");
     if (outP && !joint(c)) return fail(PTYLM_ERR_ARG, "probe part needs a joint context");
-    if (!c->has_lin) return fail(PTYLM_ERR_STATE, "no linearisation point");
+    if (!c->has_point) return fail(PTYLM_ERR_STATE, "no linearisation point");
     CUDA_TRY(cudaMemsetAsync(outO, 0, sizeof(float2) * c->N, c->stream));
     if (outP) CUDA_TRY(cudaMemsetAsync(outP, 0, sizeof(float2) * c->M, c->stream));
     if (c->d.K == 0) return PTYLM_OK;
-    const int kid = outP ? KID_JTVP_J : KID_JTVP;
+    const int kid = c->u_valid ? (outP ? KID_JTVP_U_J : KID_JTVP_U) : (outP ? KID_JTVP_J : KID_JTVP);
     if (outP) STATUS_TRY(clear_probe_part(c, kid));
     PtyArgs a = base_args(c);
     a.O = c->O_lin;
     a.P = c->P_lin;
     a.w = w;
     a.out = reinterpret_cast<float2*>(outO);
+    a.a_cache = c->u_valid ? c->u_cache : nullptr;
     STATUS_TRY(launch(c, kid, a));
     if (outP) STATUS_TRY(probe_reduce(c, kid, reinterpret_cast<float2*>(outP), false));
     return PTYLM_OK;

@@ -113,11 +113,37 @@ struct RegDFT<2, INV> {
     }
 };
 
+// X = e + w o, Y = e - w o for w = W_32^J (conjugated when INV).  Trivial twiddles cost
+// only the two complex additions.  A general twiddle w = c + i s is applied in the
+// factored form w o = c (o + i (s/c) o) when |c| >= |s| (else s ((c/s) o + i o)), which
+// folds the scaling into the additions: 6 FP32 instructions per butterfly instead of 8.
+template <int J, bool INV>
+__device__ __forceinline__ void twiddle_butterfly(float2 e, float2 o, float2& X, float2& Y) {
+    constexpr int j = J & 31;
+    if constexpr (j == 0 || j == 8 || j == 16 || j == 24) {
+        const float2 t = twmul32<J, INV>(o);
+        X = e + t;
+        Y = e - t;
+    } else {
+        constexpr float c = cos32(j);
+        constexpr float s = INV ? sin32(j) : -sin32(j);
+        if constexpr ((c >= 0 ? c : -c) >= (s >= 0 ? s : -s)) {
+            constexpr float r = s / c;  // w o = c (o.x - r o.y, o.y + r o.x)
+            const float ux = fmaf(-r, o.y, o.x), uy = fmaf(r, o.x, o.y);
+            X = make_float2(fmaf(c, ux, e.x), fmaf(c, uy, e.y));
+            Y = make_float2(fmaf(-c, ux, e.x), fmaf(-c, uy, e.y));
+        } else {
+            constexpr float r = c / s;  // w o = s (r o.x - o.y, o.x + r o.y)
+            const float ux = fmaf(r, o.x, -o.y), uy = fmaf(r, o.y, o.x);
+            X = make_float2(fmaf(s, ux, e.x), fmaf(s, uy, e.y));
+            Y = make_float2(fmaf(-s, ux, e.x), fmaf(-s, uy, e.y));
+        }
+    }
+}
+
 template <int K, int R, bool INV>
 __device__ __forceinline__ void dit_butterfly(float2* v, const float2* e, const float2* o) {
-    float2 t = twmul32<K * (32 / R), INV>(o[K]);
-    v[K] = e[K] + t;
-    v[K + R / 2] = e[K] - t;
+    twiddle_butterfly<K * (32 / R), INV>(e[K], o[K], v[K], v[K + R / 2]);
 }
 
 template <int R, bool INV, int... Ks>

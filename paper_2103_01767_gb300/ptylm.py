@@ -94,6 +94,7 @@ def load_library():
             lib.forward_intensity.argtypes = [vp, vp, vp, vp]
             lib.ptylm_set_measurements.argtypes = [vp, vp]
             lib.ggn_diag.argtypes = [vp, vp, d]
+            lib.forward_magnitude.argtypes = [vp, vp, vp, vp, i]
             lib.ptylm_forward_loss_noalloc.argtypes = [i, i, i, i, i, ctypes.c_float, vp, vp, vp, vp, vp, vp]
             lib.ptylm_profile.argtypes = [vp, i]
             lib.ptylm_profile_read.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
@@ -103,7 +104,7 @@ def load_library():
             lib.ptylm_default_lm_params.argtypes = [ctypes.POINTER(LMParams), i]
             for name in ("lm_init", "forward_loss", "gradient", "jvp", "jtvp", "ggn_matvec",
                          "lm_solve", "lm_destroy", "forward_intensity", "ptylm_set_measurements",
-                         "ptylm_forward_loss_noalloc", "ggn_diag",
+                         "ptylm_forward_loss_noalloc", "ggn_diag", "forward_magnitude",
                          "ptylm_profile",
                          "ptylm_profile_read"):
                 getattr(lib, name).restype = i
@@ -248,6 +249,10 @@ def ptylm_profile_read(ctx: Context, kernel: int):
     ms, n = ctypes.c_double(), ctypes.c_longlong()
     _check(load_library().ptylm_profile_read(ctx.handle, int(kernel), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def forward_magnitude(ctx: Context, O, P, zeta_out, store_phasor: bool = False) -> None:
+    _check(load_library().forward_magnitude(ctx.handle, _ptr(O), _ptr(P), _ptr(zeta_out), int(bool(store_phasor))))
 
 
 def ggn_diag(ctx: Context, D_out, floor_rel: float = 0.0) -> None:
