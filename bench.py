@@ -44,7 +44,7 @@ FP32_LANES_PER_SM = 128
 HBM_FALLBACK_GBS = 6800.0
 PROFILE_FILE = os.path.join(ROOT, "profiles", "ggn_matvec_obj1024_probe128_pos3600.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2103_01767_gb300", "csrc", f)
-                  for f in ("team_fft.cuh", "ptycho_kernels.cu", "kernels.h")]
+                  for f in ("team_fft.cuh", "ptycho_device.cuh", "ptycho_kernels.cu", "kernels.h")]
 
 
 def fft_flops(M):

@@ -94,6 +94,15 @@ typedef struct {
     double sigma;      /* Armijo constant, Eq. armijo_criterion (1e-4)                       */
     int max_ls;        /* Armijo halvings before giving up the move (30)                    */
     double diag_floor; /* Dg(G) is raised to diag_floor * max Dg(G) (1e-6)                  */
+    /* App. E surrogate metric (LM-S / PLM-S): outer iteration t uses the expected intensity
+     * h = |psihat|^2 + b + s_t (Eq. expected_count_surrogate), s_t falling on an evenly
+     * spaced logarithmic grid from surrogate0 at t = 0 to surrogate_end at t = surrogate_T - 1,
+     * and s_t = 0 (the true metric) from t = surrogate_T on.  surrogate_T = 0 turns it off
+     * (default); the paper's runs use surrogate0 = 1, surrogate_T = 100.  Both levels must be
+     * finite and > 0 when surrogate_T > 0. */
+    double surrogate0;
+    double surrogate_end;
+    int surrogate_T;
 } ptylm_lm_params;
 
 /* Per-call results of lm_solve.  hist_* point to host arrays of hist_len entries (or are

@@ -305,7 +305,8 @@ class _LM2Params(ctypes.Structure):
                 ("radius_O", ctypes.c_double), ("radius_P", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("tau_s", ctypes.c_double), ("p_s", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("max_ls", ctypes.c_int), ("diag_floor", ctypes.c_double),
-                ("f_min", ctypes.c_double)]
+                ("f_min", ctypes.c_double), ("surrogate0", ctypes.c_double),
+                ("surrogate_end", ctypes.c_double), ("surrogate_T", ctypes.c_int)]
 
 
 def _z(pb, O, P=None):
@@ -352,6 +353,15 @@ def project(v, radius):
     return v
 
 
+def surrogate_at(t, surrogate0=1.0, surrogate_end=1e-4, surrogate_T=0):
+    """s_t of the App. E surrogate schedule (0 when off or once t >= T)."""
+    p = _LM2Params()
+    p.surrogate0, p.surrogate_end, p.surrogate_T = surrogate0, surrogate_end, int(surrogate_T)
+    lib = _load()
+    lib.orc_surrogate_at.restype = ctypes.c_double
+    return float(lib.orc_surrogate_at(ctypes.byref(p), int(t)))
+
+
 def poisson_f_min(y):
     """sum(y - y log y): the Poisson metric's value at h = y (its minimum over h)."""
     y = np.asarray(y, np.float64)
@@ -359,7 +369,8 @@ def poisson_f_min(y):
 
 
 DEFAULT_LM2 = dict(DEFAULT_LM, scaled=1, joint=0, projected=0, radius_O=1.0, radius_P=1e8, gamma=1e-6,
-                   tau_s=1e-8, p_s=2.1, sigma=1e-4, max_ls=30, diag_floor=1e-6)
+                   tau_s=1e-8, p_s=2.1, sigma=1e-4, max_ls=30, diag_floor=1e-6,
+                   surrogate0=1.0, surrogate_end=1e-4, surrogate_T=0)
 
 
 def lm_solve2(pb: Problem, O0, P0=None, O_ref=None, mask=None, beta=None, **kw):
@@ -373,7 +384,8 @@ def lm_solve2(pb: Problem, O0, P0=None, O_ref=None, mask=None, beta=None, **kw):
     p = _LM2Params(prm["mu0"], prm["mu_min"], prm["kappa"], prm["nu"], prm["rho_min"], beta, prm["mu_max"],
                    int(prm["max_outer"]), int(prm["max_cg"]), prm["target_err"], int(prm["scaled"]),
                    int(prm["joint"]), int(prm["projected"]), prm["radius_O"], prm["radius_P"], prm["gamma"],
-                   prm["tau_s"], prm["p_s"], prm["sigma"], int(prm["max_ls"]), prm["diag_floor"], f_min)
+                   prm["tau_s"], prm["p_s"], prm["sigma"], int(prm["max_ls"]), prm["diag_floor"], f_min,
+                   prm["surrogate0"], prm["surrogate_end"], int(prm["surrogate_T"]))
     O = _c(O0).copy()
     P = (pb.P if P0 is None else _c(P0)).copy()
     L = int(prm["max_outer"])

@@ -731,7 +731,21 @@ typedef struct {
     int max_ls;
     double diag_floor;   /* D >= diag_floor * max D */
     double f_min;        /* subtracted from f in Algorithm 2's tests (Poisson: sum y - y log y) */
+    /* App. E surrogate: h = |psihat|^2 + b + s_t with s_t decreasing on a logarithmic grid
+     * from surrogate0 (t = 0) to surrogate_end (t = T - 1) and s_t = 0 from t = T on;
+     * surrogate_T = 0 turns it off. */
+    double surrogate0, surrogate_end;
+    int surrogate_T;
 } orc_lm2_params;
+
+/* s_t of the App. E schedule (0 when off or when t >= T). */
+double orc_surrogate_at(const orc_lm2_params* prm, int t)
+{
+    if (prm->surrogate_T <= 0 || t >= prm->surrogate_T) return 0.0;
+    if (prm->surrogate_T == 1) return prm->surrogate0;
+    const double u = (double)t / (double)(prm->surrogate_T - 1);
+    return prm->surrogate0 * pow(prm->surrogate_end / prm->surrogate0, u);
+}
 
 /* Algorithm 1 with scaling, the joint state and the Algorithm 2 plug-in.
  * O_inout [N], P_inout [M] (updated when joint).  History as in orc_lm_solve. */
@@ -755,7 +769,10 @@ int orc_lm_solve2(const orc_geom* g, dc* O_inout, dc* P_inout, const int32_t* po
     if (prm->joint) memcpy(z + N, P_inout, sizeof(dc) * M);
     double mu = prm->mu0;
     int cg_total = 0, status = 0, t;
+    orc_geom gt = *g;   /* the geometry with the surrogate background of iteration t */
+    pb.g = &gt;
     for (t = 0; t < prm->max_outer; ++t) {
+        gt.b = g->b + orc_surrogate_at(prm, t);
         double dl2 = 0.0;
         const double f = z_loss(&pb, z, &dl2);
         z_gradient(&pb, z, grad);

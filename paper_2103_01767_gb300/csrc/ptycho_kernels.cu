@@ -69,6 +69,37 @@ struct AdjArgs {          // J^T w and J v
     float b;
 };
 
+// Cache a, team-register order.  For BY >= 2 the two elements (e, e+1) of a thread that
+// share a pass-3 group are adjacent, so one 16-byte access moves both: element e of thread
+// t lives at float2 index (e/2)*2T + 2t + (e%2) of the position's M-element tile.  For
+// BY == 1 (one element per group) the layout is e*T + t.
+template <class G>
+__device__ __forceinline__ void store_cache_group(float2* ak, const float2* av, int j) {
+    const int tid = threadIdx.x % G::T;
+    if constexpr (G::BY >= 2) {
+        float4* a4 = reinterpret_cast<float4*>(ak) + tid;
+#pragma unroll
+        for (int i = 0; i < G::BY / 2; ++i)
+            a4[(j * (G::BY / 2) + i) * G::T] = make_float4(av[2 * i].x, av[2 * i].y, av[2 * i + 1].x, av[2 * i + 1].y);
+    } else {
+        ak[j * G::T + tid] = av[0];
+    }
+}
+template <class G>
+__device__ __forceinline__ void load_cache_group(const float2* ak, float2* av, int j, int tid) {
+    if constexpr (G::BY >= 2) {
+        const float4* a4 = reinterpret_cast<const float4*>(ak) + tid;
+#pragma unroll
+        for (int i = 0; i < G::BY / 2; ++i) {
+            const float4 q = __ldcs(a4 + (j * (G::BY / 2) + i) * G::T);
+            av[2 * i] = make_float2(q.x, q.y);
+            av[2 * i + 1] = make_float2(q.z, q.w);
+        }
+    } else {
+        av[0] = __ldcs(ak + j * G::T + tid);
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // Forward model + error metric (+ cache and gradient when CACHE; intensities only when
 // INTENSITY).
@@ -89,9 +120,10 @@ k_forward(FwdArgs a) {
         float sl = 0.0f, sd = 0.0f;
         gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
         if constexpr (CACHE) {
-            float2* ak = a.a_cache + (size_t)k * G::M + c.tid;
+            float2* ak = a.a_cache + (size_t)k * G::M;
             float s2 = 0.0f;  // sum of d2l over this thread's pixels (closed-form diagonal)
             team_fft_roundtrip<G>(v, c.sm, c.tw, c.tid, [&](float2* g, int j) {
+                float2 av[G::BY];
 #pragma unroll
                 for (int k2y = 0; k2y < G::BY; ++k2y) {
                     const int e = j * G::BY + k2y;
@@ -101,9 +133,10 @@ k_forward(FwdArgs a) {
                     sl += t.l;
                     sd += t.dl * t.dl;
                     s2 += t.d2l;
-                    ak[e * G::T] = ps * t.sqrt_d2l_over_zeta;
+                    av[k2y] = ps * t.sqrt_d2l_over_zeta;
                     g[k2y] = ps * (t.dl_over_zeta * invS);  // psihat grad l / zeta, inverse 1/S folded in
                 }
+                store_cache_group<G>(ak, av, j);
             });
             if (a.trp) a.trp[(size_t)k * G::T + c.tid] = s2;
             scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
@@ -155,11 +188,10 @@ k_ggn_matvec(MatvecArgs a) {
         prefetch_tile_l2(a.a_cache + (size_t)k * G::M, sizeof(float2) * G::M, c.tid);
         if constexpr (JOINT) gather_joint<G>(v, a.O, a.P, a.VP, a.Olin, a.nx, rc.x, rc.y, c.tid);
         else gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
-        const float2* ak = a.a_cache + (size_t)k * G::M + c.tid;
+        const float2* ak = a.a_cache + (size_t)k * G::M;
         team_fft_roundtrip<G>(v, c.sm, c.tw, c.tid, [&](float2* g, int j) {
             float2 av[G::BY];
-#pragma unroll
-            for (int k2y = 0; k2y < G::BY; ++k2y) av[k2y] = __ldcs(ak + (j * G::BY + k2y) * G::T);
+            load_cache_group<G>(ak, av, j, c.tid);
 #pragma unroll
             for (int k2y = 0; k2y < G::BY; ++k2y) {
                 const float t = (av[k2y].x * g[k2y].x + av[k2y].y * g[k2y].y) * invM;

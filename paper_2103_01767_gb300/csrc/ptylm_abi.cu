@@ -285,6 +285,7 @@ struct ptylm_ctx {
     bool has_point = false;        // O_lin / P_lin hold a point (jvp, jtvp)
     bool has_lin = false;          // ... and the loss cache, gradient and d2l sums match it
     double f_lin = 0.0, dl2_lin = 0.0;
+    float b_eff = 0.0f;            // background the kernels use: b, plus s_t inside lm_solve
 
     // CG / LM vectors over z (allocated on first use)
     float2 *cg_x = nullptr, *cg_r = nullptr, *cg_p = nullptr, *cg_q = nullptr, *trial = nullptr;
@@ -431,7 +432,7 @@ static PtyArgs base_args(const ptylm_ctx* c) {
     a.tw = c->tw;
     a.K = c->d.K;
     a.nx = c->d.nx;
-    a.b = c->d.background;
+    a.b = c->b_eff;
     a.loss = c->d.loss;
     a.partials = c->partials;
     a.scal = c->scal;
@@ -582,6 +583,17 @@ void ptylm_default_lm_params(ptylm_lm_params* p, int loss) {
     p->sigma = 1e-4;
     p->max_ls = 30;
     p->diag_floor = 1e-6;
+    p->surrogate0 = 1.0;
+    p->surrogate_end = 1e-4;
+    p->surrogate_T = 0;
+}
+
+// s_t of the App. E schedule: surrogate0 (surrogate_end / surrogate0)^(t / (T - 1)) for
+// t < T, else 0.
+static double surrogate_at(const ptylm_lm_params* p, int t) {
+    if (p->surrogate_T <= 0 || t >= p->surrogate_T) return 0.0;
+    if (p->surrogate_T == 1) return p->surrogate0;
+    return p->surrogate0 * std::pow(p->surrogate_end / p->surrogate0, (double)t / (double)(p->surrogate_T - 1));
 }
 
 ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* positions_dev,
@@ -619,6 +631,7 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
 
     ptylm_ctx* c = new ptylm_ctx();
     c->d = d;
+    c->b_eff = d.background;
     c->LS = LS;
     c->S = 1 << LS;
     c->M = c->S * c->S;
@@ -895,6 +908,20 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
     if (prm->projected && (!(prm->radius_O > 0.0) || !(prm->radius_P > 0.0) || prm->max_ls < 0))
         return fail(PTYLM_ERR_ARG, "invalid projection parameters");
     if (c->d.K == 0) return fail(PTYLM_ERR_ARG, "lm_solve needs at least one scan position");
+    if (prm->surrogate_T < 0 ||
+        (prm->surrogate_T > 0 && (!(prm->surrogate0 > 0.0) || !(prm->surrogate_end > 0.0) ||
+                                  !std::isfinite(prm->surrogate0) || !std::isfinite(prm->surrogate_end))))
+        return fail(PTYLM_ERR_ARG, "invalid surrogate schedule");
+    // Every exit restores the true background; a linearisation taken under s_t > 0 is not
+    // the true metric's, so it is dropped.
+    struct SurrogateGuard {
+        ptylm_ctx* c;
+        bool used = false;
+        ~SurrogateGuard() {
+            c->b_eff = c->d.background;
+            if (used) c->has_lin = c->u_valid = false;
+        }
+    } surrogate_guard{c};
     const long N = c->N, L = c->L;
     const size_t zbytes = sizeof(float2) * L;
     if (!c->cg_x) {
@@ -959,6 +986,9 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
     };
 
     for (t = 0; t < prm->max_outer; ++t) {
+        const double s_t = surrogate_at(prm, t);
+        c->b_eff = (float)(c->d.background + s_t);
+        surrogate_guard.used = s_t > 0.0;
         // Linearise: f, ||grad_zeta l||^2, cache a, grad f, Dg(G) (Algorithm 1, first step).
         STATUS_TRY(op_forward(c, z, probe_of(z), 1));
         STATUS_TRY(dots(c, 1, L, c->grad, c->grad, nullptr, nullptr, nullptr, nullptr, nullptr, S_GG));

@@ -57,7 +57,9 @@ class LMParams(ctypes.Structure):
                 ("mask", ctypes.c_void_p), ("scaled", ctypes.c_int), ("projected", ctypes.c_int),
                 ("radius_O", ctypes.c_double), ("radius_P", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("tau_s", ctypes.c_double), ("p_s", ctypes.c_double),
-                ("sigma", ctypes.c_double), ("max_ls", ctypes.c_int), ("diag_floor", ctypes.c_double)]
+                ("sigma", ctypes.c_double), ("max_ls", ctypes.c_int), ("diag_floor", ctypes.c_double),
+                ("surrogate0", ctypes.c_double), ("surrogate_end", ctypes.c_double),
+                ("surrogate_T", ctypes.c_int)]
 
 
 class LMStats(ctypes.Structure):

@@ -193,3 +193,27 @@ def test_joint_argument_errors(lib):
     with pytest.raises(lib.PtylmError) as e:
         lib.ggn_matvec(ctxj, c64(O), g, 0.1)   # joint contexts need the probe blocks
     assert e.value.status == lib.PTYLM_ERR_ARG
+
+
+def test_plm_surrogate_matches_oracle(lib):
+    """PLM-S (App. E: s_t from 1 down to 1e-2 over T = 4 iterations, then the true Poisson
+    metric) on a small noisy Poisson problem: at every iteration the GPU's f at its
+    linearisation point agrees with the oracle's run to FP32 accuracy while the iterates
+    coincide (the first iterations), and both runs end at the same true-metric value."""
+    n, m = 96, 32
+    case = make_case(n, m, loss=1, peak=1e3, seed=70, grid=8, step=8, jitter=1, radius=10.0, noisy=True)
+    pb = case.problem()
+    O0 = synth.flat_object(n)
+    kw = dict(scaled=1, surrogate0=1.0, surrogate_end=1e-2, surrogate_T=4, max_outer=12)
+    O_ref_run, _, info_ref = oracle.lm_solve2(pb, O0, **kw)
+    ctx = lib.lm_init(n, n, m, m, torch.from_numpy(case.pos).cuda(), f32(case.y), 1, case.b)
+    Od = c64(O0)
+    st, info = lib.lm_solve(ctx, Od, c64(case.P), hist_len=12, **kw)
+    assert info["n_outer"] == info_ref["n_outer"] == 12
+    # t = 0: same point, surrogate background 1 + b
+    assert abs(info["f"][0] - info_ref["f"][0]) <= 1e-5 * abs(info_ref["f"][0])
+    f_gpu, f_orc = oracle.loss(pb, host(Od)), oracle.loss(pb, O_ref_run)
+    f_min = oracle.poisson_f_min(pb.y)
+    assert abs(f_gpu - f_orc) <= 1e-3 * abs(info_ref["f"][0] - f_min), (f_gpu, f_orc)
+    # after T the recorded f is the true metric at the linearisation point
+    assert info["f"][-1] >= f_min

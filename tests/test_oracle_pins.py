@@ -472,3 +472,61 @@ def test_blind_error_metric_invariances():
     Ot = (0.7 - 0.4j) * O * np.exp(1j * (0.3 + 0.05 * yy - 0.02 * xx))
     assert oracle.object_error_blind(Ot, O) < 1e-10
     assert oracle.object_error_blind(O + 0.1 * synth.random_complex(O.shape, seed=8), O) > 0.05
+
+
+# ------------------------------------------------------------------- App. E surrogate metric
+def test_surrogate_schedule_shape():
+    """App. E: s_t starts at s_0, falls monotonically on an evenly spaced logarithmic grid
+    (constant ratio between iterations), and is exactly 0 from t = T on; T = 0 is off."""
+    s0, s_end, T = 1.0, 1e-4, 9
+    s = np.array([oracle.surrogate_at(t, s0, s_end, T) for t in range(T + 3)])
+    assert s[0] == s0 and abs(s[T - 1] - s_end) <= 1e-15
+    assert np.all(np.diff(s[:T]) < 0)
+    ratios = s[1:T] / s[:T - 1]
+    assert np.allclose(ratios, ratios[0], rtol=1e-12, atol=0)
+    assert np.allclose(np.log10(s[:T]), np.linspace(0.0, -4.0, T), atol=1e-12)
+    assert np.all(s[T:] == 0.0)
+    assert oracle.surrogate_at(0, s0, s_end, 0) == 0.0
+    assert oracle.surrogate_at(0, s0, s_end, 1) == s0 and oracle.surrogate_at(1, s0, s_end, 1) == 0.0
+
+
+def small_poisson_problem(seed=30, b=1e-8):
+    n, m = 48, 16
+    O_true = synth.to_c64(synth.object_texture(n, seed=seed))
+    P = synth.to_c64(synth.probe_disk_defocus(m, 5.0))
+    pos, _ = synth.raster_positions(n, m, 6, 6, 1, seed=seed + 1)
+    pb = oracle.Problem((n, n), P, pos, None, oracle.LOSS_POISSON, b)
+    h = oracle.intensity(pb, O_true)
+    P = synth.to_c64(P * np.sqrt(300.0 / h.max()))
+    pb = oracle.Problem((n, n), P, pos, None, oracle.LOSS_POISSON, b)
+    pb.y = synth.poisson_counts(oracle.intensity(pb, O_true), seed=seed + 2)
+    return pb, O_true
+
+
+def test_surrogate_is_a_shifted_background():
+    """Eq. expected_count_surrogate only adds s_t to the background: a constant schedule
+    (s_0 = s_end = s) gives the same iterates as the plain method on b + s."""
+    pb, O_true = small_poisson_problem()
+    s = 0.37
+    O0 = synth.flat_object(pb.nx)
+    Oa, _, ia = oracle.lm_solve2(pb, O0, max_outer=3, scaled=1, surrogate0=s, surrogate_end=s, surrogate_T=50)
+    pb_b = oracle.Problem((pb.ny, pb.nx), pb.P, pb.pos, pb.y, pb.loss, pb.b + s)
+    Ob, _, ib = oracle.lm_solve2(pb_b, O0, max_outer=3, scaled=1)
+    assert np.array_equal(Oa, Ob)
+    assert np.array_equal(ia["f"], ib["f"])
+
+
+def test_surrogate_reverts_to_the_true_metric():
+    """From t = T on the method optimises the Poisson metric itself: the f recorded at
+    iteration T is the true metric at the iterate the first T iterations produced, while the
+    entries before T are the surrogate's (larger background), not the true metric's."""
+    pb, _ = small_poisson_problem()
+    kw = dict(scaled=1, surrogate0=1.0, surrogate_end=1e-2, surrogate_T=3)
+    O0 = synth.flat_object(pb.nx)
+    O3, _, _ = oracle.lm_solve2(pb, O0, max_outer=3, **kw)
+    O5, _, i5 = oracle.lm_solve2(pb, O0, max_outer=5, **kw)
+    assert abs(i5["f"][3] - oracle.loss(pb, O3)) <= 1e-12 * abs(i5["f"][3])
+    # the surrogate iterations really used a larger background: their f differ from the truth
+    O1, _, _ = oracle.lm_solve2(pb, O0, max_outer=1, **kw)
+    assert abs(i5["f"][1] - oracle.loss(pb, O1)) > 1e-6 * abs(i5["f"][1])
+    assert np.isfinite(i5["f"]).all() and i5["f"][4] <= i5["f"][3]
