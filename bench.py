@@ -287,6 +287,108 @@ def setup_workload(ptylm, torch, w, dev, stream):
     return ctx, O0, P, y, pos, step_used
 
 
+# ---------------------------------------------------------------------------------------
+# Comparison and LM time-to-accuracy legs (outside the timed matvec region)
+# ---------------------------------------------------------------------------------------
+def time_cufft_pair(torch, K, M_side, dev, reps=20):
+    """cuFFT (through torch.fft) batched C2C forward + inverse over [K, m, m] complex64: the
+    two transforms one GGN matvec needs, without any of its other work.  Comparison only."""
+    x = torch.randn((K, M_side, M_side), dtype=torch.complex64, device=dev)
+    for _ in range(3):
+        y = torch.fft.ifft2(torch.fft.fft2(x, norm="ortho"), norm="ortho")
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        y = torch.fft.ifft2(torch.fft.fft2(x, norm="ortho"), norm="ortho")
+    e1.record()
+    torch.cuda.synchronize(dev)
+    del x, y
+    return e0.elapsed_time(e1) * 1e3 / reps
+
+
+def small_tta_problem():
+    """The 128^2 / 32^2 noiseless workload (64 positions, amplitude metric) and its truth."""
+    w = synth.SMALL
+    O_true = synth.to_c64(synth.object_texture(w.n, seed=0))
+    P = synth.to_c64(synth.probe_disk_defocus(w.m, w.radius))
+    pos, _ = synth.raster_positions(w.n, w.m, w.grid, w.step, w.jitter, seed=1)
+    mask = synth.illumination_mask(w.n, P, pos, 0.1)
+    return w, O_true, P, pos, mask
+
+
+def oracle_time_to_accuracy(target=1e-3):
+    """The oracle's plain LM (Algorithm 1, FP64) from the flat start to object error <= target
+    on the small noiseless workload, against the ground truth."""
+    import oracle
+    w, O_true, P, pos, mask = small_tta_problem()
+    pb = oracle.Problem((w.n, w.n), P, pos, None, 0, 1e-8)
+    pb.y = synth.to_f32(oracle.intensity(pb, O_true))
+    t0 = time.perf_counter()
+    _, info = oracle.lm_solve(pb, synth.flat_object(w.n), O_ref=O_true, mask=mask, max_outer=100, target_err=target)
+    return {"seconds": time.perf_counter() - t0, "outer": int(info["n_outer"]), "err": float(info["err"][-1]),
+            "threads": oracle.num_threads()}
+
+
+def gpu_time_to_accuracy(ptylm, torch, dev, stream, target=1e-3, reps=5, large_ref_outer=400):
+    """Wall time of lm_solve (plain LM, data resident after lm_init) from the flat start to the
+    first outer iteration with object error <= target, measured on the device each iteration.
+      small: 128^2 / 32^2 noiseless, reference = the ground truth (median of reps runs);
+      large: 1024^2 / 128^2 / 3600 positions, Poisson 1e3, reference = the converged PLM-S
+             reconstruction; plain LM and PLM-S are timed against it."""
+    out = {}
+    w, O_true, P, pos, mask = small_tta_problem()
+    c64 = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.complex64)).to(dev)
+    posd = torch.from_numpy(pos).to(dev)
+    y = torch.empty((pos.shape[0], w.m, w.m), dtype=torch.float32, device=dev)
+    ctx = ptylm.lm_init(w.n, w.n, w.m, w.m, posd, y, 0, 1e-8, stream=stream)
+    Od, Pd, maskd = c64(O_true), c64(P), torch.from_numpy(mask.astype(np.uint8)).to(dev)
+    ptylm.forward_intensity(ctx, Od, Pd, y)
+    ptylm.ptylm_set_measurements(ctx, y)
+    O0 = c64(synth.flat_object(w.n))
+    runs = []
+    for _ in range(reps):
+        O = O0.clone()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        _, info = ptylm.lm_solve(ctx, O, Pd, hist_len=100, O_ref=Od, mask=maskd, max_outer=100, target_err=target)
+        runs.append((time.perf_counter() - t0, info))
+    ptylm.lm_destroy(ctx)
+    secs = sorted(r[0] for r in runs)
+    info = runs[0][1]
+    out["small"] = {"seconds": statistics.median(secs), "outer": int(info["n_outer"]), "cg": int(info["cg_total"]),
+                    "err": float(info["err"][-1]), "reference": "ground truth", "runs": reps}
+
+    wl = synth.LARGE
+    ctx, O0, P, y, posd, _ = setup_workload(ptylm, torch, wl, dev, stream)
+    mask = synth.illumination_mask(wl.n, P.cpu().numpy(), posd.cpu().numpy(), 0.1)
+    maskd = torch.from_numpy(mask.astype(np.uint8)).to(dev)
+    # The noisy data have no exact solution: the reference is the converged reconstruction,
+    # run until the damping runs away (no FP32-resolvable decrease of f is left).
+    variants = {"LM": {}, "PLM-S": {"scaled": 1, "surrogate_T": 20}}
+    O_ref = O0.clone()
+    t0 = time.perf_counter()
+    st, ref_info = ptylm.lm_solve(ctx, O_ref, P, hist_len=large_ref_outer, max_outer=large_ref_outer,
+                                  **variants["PLM-S"])
+    ref_s = time.perf_counter() - t0
+    out["large"] = {"reference": f"PLM-S (s_0 = 1, T = 20) run from the flat start until the damping ran away "
+                                 f"({ref_info['n_outer']} outer iterations, {ref_s:.2f} s, status {st})"}
+    for name, kw in variants.items():
+        O = O0.clone()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        _, info = ptylm.lm_solve(ctx, O, P, hist_len=large_ref_outer, O_ref=O_ref, mask=maskd,
+                                 max_outer=large_ref_outer, target_err=target, **kw)
+        secs = time.perf_counter() - t0
+        err = info["err"][np.isfinite(info["err"])]  # a run that stalls records no error for its last iteration
+        reached = bool(err.size and err[-1] <= target)
+        out["large"][name] = {"seconds": secs if reached else None, "outer": int(info["n_outer"]),
+                              "cg": int(info["cg_total"]), "err": float(err[-1]) if err.size else None,
+                              "err_min": float(err.min()) if err.size else None}
+    ptylm.lm_destroy(ctx)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -297,6 +399,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", default=synth.LARGE.name, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the cuFFT comparison and the LM time-to-accuracy runs")
     args = ap.parse_args()
     w = synth.WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -320,6 +424,9 @@ def main():
         cpu = {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"one FP64 GGN matvec over {n} of {w.K} positions ({secs:.1f} s), "
                          f"scaled by {n}/{w.K}"}
+    oracle_tta = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_extras:
+        oracle_tta = oracle_time_to_accuracy()
 
     from paper_2103_01767_gb300 import build as _build
     _build.build()
@@ -381,6 +488,16 @@ def main():
     N, M, K = w.n * w.n, w.m * w.m, int(pos.shape[0])
 
     clocks = clk.summary()
+    comparison, tta = None, None
+    if rank == 0 and not args.no_extras:
+        cufft_us = time_cufft_pair(torch, K, w.m, dev)
+        comparison = {"cufft_fwd_inv_us": cufft_us, "matvec_us": 1e6 * (mv_ms / 1e3) / max(mv_n, 1),
+                      "note": "cuFFT batched C2C forward + inverse over the same [K, m, m] complex64 "
+                              "(torch.fft, comparison only); the matvec adds gather, probe multiplies, "
+                              "the frequency stage and the overlap scatter-add"}
+        tta = gpu_time_to_accuracy(ptylm, torch, dev, stream)
+        if oracle_tta is not None:
+            tta["small"]["oracle"] = oracle_tta
     avg_mv_s = (mv_ms / 1e3) / max(mv_n, 1)
     flops = matvec_flops(K, M)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
@@ -411,6 +528,8 @@ def main():
                     "d2h_bytes_per_step": 8 * N},
             "clocks": clocks,
             "gpu_launches": int(launches),
+            "comparison": comparison,
+            "time_to_accuracy": tta,
         }
         print(json.dumps(line), flush=True)
     ptylm.lm_destroy(ctx)

@@ -270,7 +270,9 @@ def default_lm_params(loss: int) -> LMParams:
 
 def lm_solve(ctx: Context, O, P, params: LMParams | None = None, hist_len: int = 0,
              O_ref=None, mask=None, **overrides):
-    """Run Algorithm 1 in place on O.  Returns (status, stats dict)."""
+    """Run Algorithm 1 in place on O.  Returns (status, stats dict).  PTYLM_WARN_CG_MAXIT and
+    PTYLM_ERR_STALLED (the damping ran away: no step decreases f any more at FP32 resolution)
+    are returned rather than raised; O, P and the history then hold the last iterate."""
     p = default_lm_params(ctx.desc.loss) if params is None else params
     for k, v in overrides.items():
         setattr(p, k, v)
@@ -284,7 +286,7 @@ def lm_solve(ctx: Context, O, P, params: LMParams | None = None, hist_len: int =
     st = LMStats(0, 0, 0, 0.0, 0.0, L, hf.ctypes.data, hg.ctypes.data, hmu.ctypes.data,
                  hcg.ctypes.data, herr.ctypes.data)
     status = _check(load_library().lm_solve(ctx.handle, _ptr(O), _ptr(P), ctypes.byref(p),
-                                            ctypes.byref(st)), allow=(PTYLM_WARN_CG_MAXIT,))
+                                            ctypes.byref(st)), allow=(PTYLM_WARN_CG_MAXIT, PTYLM_ERR_STALLED))
     n = min(st.n_outer, L)
     return status, dict(n_outer=st.n_outer, cg_total=st.cg_total, matvecs=st.matvecs_total,
                         f_final=st.f_final, err_final=st.err_final, f=hf[:n].copy(),
