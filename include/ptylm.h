@@ -291,6 +291,74 @@ const char* ptylm_last_error(void);
 /* Fill prm with the paper's Algorithm 1 defaults (Sec. 5) for the given loss. */
 void ptylm_default_lm_params(ptylm_lm_params* prm, int loss);
 
+/* ---------------------------------------------------------------------------------------
+ * Batches of independent reconstructions.
+ *
+ * B object-only problems (Sec. 2, Eq. cdp), each with its own object size, probe side
+ * (32, 64 or 128), scan, loss and background, share one batch.  Each per-position operator
+ * (forward model + error metric [+ cache a and gradient], GGN product; App. A) runs over
+ * all problems as ONE persistent kernel launch: 512-thread CTAs take work items (a problem
+ * and a group of its positions) from a device counter, so problems of uneven size balance
+ * across the SMs.  Batch vectors (objects, gradients, directions) are the problems'
+ * objects concatenated in problem order, [ny][nx] row-major each; problem b starts at
+ * element ptylm_batch_offset(batch, b).  All pointers are device pointers.
+ * --------------------------------------------------------------------------------------- */
+typedef struct ptylm_batch ptylm_batch;
+
+/* descs[b]: problem b (joint must be 0; workspace_budget is ignored).  positions_dev[b]:
+ * int32 [K][2]; y_dev[b]: float [K][my][mx] in natural DFT order; probes_dev[b]: [my][mx].
+ * Everything is copied (positions validated on the host: PTYLM_ERR_ARG when outside).
+ * stream: the caller's cudaStream_t (NULL = legacy stream); the batch works on a stream of
+ * its own, ordered after `stream` on entry to every call and before it on exit. */
+ptylm_status ptylm_batch_init(ptylm_batch** batch, int B, const ptylm_desc* descs,
+                              const int32_t* const* positions_dev, const float* const* y_dev,
+                              const ptylm_c64* const* probes_dev, void* stream);
+
+/* First element of problem b in batch vectors; b = B gives the total length; -1 if invalid. */
+long ptylm_batch_offset(const ptylm_batch* batch, int b);
+
+/* f_b and ||grad_zeta l||^2_b at the batch vector O (Eq. error_metric_magnitude per
+ * problem, FP64 sums), into host arrays of B entries (either may be NULL).  cache = 1 also
+ * makes O the linearisation point: cache a and gradient of every problem. */
+ptylm_status ptylm_batch_forward_loss(ptylm_batch* batch, const ptylm_c64* O, double* f_host,
+                                      double* dl_norm2_host, int cache);
+
+/* Copy of the batch gradient at the linearisation point (PTYLM_ERR_STATE without one). */
+ptylm_status ptylm_batch_gradient(ptylm_batch* batch, ptylm_c64* g);
+
+/* out = (G_b + lambda_b I) v_b for every problem (App. A, Eq. ggn_magnitude_appendix_2);
+ * lambda: host array of B values or NULL (= 0). */
+ptylm_status ptylm_batch_ggn_matvec(ptylm_batch* batch, const ptylm_c64* v, ptylm_c64* out,
+                                    const double* lambda);
+
+/* Algorithm 1 with D = I for every problem, in place on the batch vector O_inout.
+ * prm: B parameter sets (scaled and projected must be 0; the App. E surrogate schedule is
+ * honoured; O_ref / mask point to problem b's own reference object and mask).  stats: B
+ * entries or NULL.  All problems advance together: each outer step linearises the problems
+ * whose last step was accepted, runs the truncated CG of all unfinished problems (one CG
+ * iteration of all of them is a captured CUDA graph of four launches; converged problems
+ * are masked out), evaluates every trial point in one launch and accepts or rejects per
+ * problem on the host.  The first call tunes the schedule (ptylm_batch_tune) unless one was
+ * set.  Returns the first non-OK problem status (PTYLM_ERR_STALLED, PTYLM_ERR_NAN) after
+ * finishing the others, else PTYLM_WARN_CG_MAXIT if any CG solve hit max_cg. */
+ptylm_status ptylm_batch_lm_solve(ptylm_batch* batch, ptylm_c64* O_inout, const ptylm_lm_params* prm,
+                                  ptylm_lm_stats* stats);
+
+/* Schedule autotuner: times the batch's GGN product (3 launches after a warm-up) under six
+ * schedules -- work items ordered largest patches first (0..2) or round robin over the
+ * problems (3..5), with 1, 2 or 4 positions per team per item -- and keeps the fastest.
+ * Needs a linearisation point.  choice: index kept; ms: up to n_ms measured times. */
+ptylm_status ptylm_batch_tune(ptylm_batch* batch, int* choice, float* ms, int n_ms);
+
+/* Use schedule `choice` (0..5, as in ptylm_batch_tune) without timing. */
+ptylm_status ptylm_batch_set_schedule(ptylm_batch* batch, int choice);
+
+/* Kernel launches issued by the batch so far (graph replays count their four kernels). */
+ptylm_status ptylm_batch_profile_read(ptylm_batch* batch, long long* launches);
+
+/* Free the batch (NULL is accepted). */
+ptylm_status ptylm_batch_destroy(ptylm_batch* batch);
+
 #ifdef __cplusplus
 }
 #endif

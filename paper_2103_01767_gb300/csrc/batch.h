@@ -1,0 +1,51 @@
+// batch.h -- device-side description of a batch of independent reconstructions and the
+// launchers of the persistent per-position kernels that serve all of them in one launch.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace ptylm {
+
+// One object-only problem of the batch (Sec. 2, Eq. cdp): its scan, measurements, probe,
+// frequency cache and where its object lives inside the concatenated batch vectors.
+struct BatchProblem {
+    const int2* pos;     // [K] (row, column) of each patch
+    const float* y;      // [K][M] measurements in team-register order (sqrt(y) for Gaussian)
+    float2* a_cache;     // [K][M] cache a = psihat (d2l)^(1/2) / zeta of the last linearisation
+    const float2* P;     // [M] probe
+    long z_off;          // first element of this problem's object in the batch vectors
+    int K, nx, LS, loss;
+    float b;             // background b (+ the surrogate s_t inside the batched LM)
+    int pad;
+};
+
+// A work item: positions k0 + team + teams * j (j < per_team) of problem `prob`, where
+// teams = 512 / (S^2 / 32) is the number of thread teams a 512-thread CTA holds for the
+// problem's probe side S (16, 4 and 1 for S = 32, 64, 128).  Every item is the same
+// 16384 * per_team pixels of FFT work.
+struct BatchItem {
+    int prob, k0, per_team, pad;
+};
+
+struct BatchArgs {
+    const BatchProblem* probs;
+    const BatchItem* items;
+    int n_items;
+    unsigned* work;       // next item to take (0 on entry, restored to 0 on exit)
+    unsigned* done;       // CTAs finished (0 on entry, restored to 0 on exit)
+    const float2* tw;     // twiddles W_S^j for S = 32, 64, 128, concatenated (224 entries)
+    const float2* V;      // input batch vector: objects (forward) or directions (matvec)
+    float2* out;          // output batch vector, accumulated into (gradient / GGN product)
+    double* f;            // [B][2]: error metric and ||grad_zeta l||^2 per problem (forward)
+    const int* active;    // [B] or NULL: items of problems with active[b] == 0 are skipped
+};
+
+constexpr int BATCH_THREADS = 512;
+constexpr int BATCH_TW = 32 + 64 + 128;
+
+enum BatchKernel { BK_FWD_LOSS = 0, BK_FWD_CACHE = 1, BK_MATVEC = 2, BK_COUNT = 3 };
+
+// Opt in to the kernels' shared memory and return how many CTAs of each fit on one SM.
+cudaError_t batch_prepare(int* ctas_per_sm);
+cudaError_t batch_launch(int kernel, const BatchArgs& a, int grid, cudaStream_t stream);
+
+}  // namespace ptylm

@@ -1,0 +1,221 @@
+// batch_kernels.cu -- the per-position operators over a batch of independent problems with
+// uneven object sizes, probe sides (32, 64, 128), scans and losses, each operator as ONE
+// persistent launch.
+//
+// Every CTA has 512 threads and 128 KB of exchange buffers, which hold 16 teams for a
+// 32 x 32 probe, 4 teams for 64 x 64 or one team for 128 x 128 (Geo<LS>): a work item is one
+// problem's positions for all teams of the CTA, and every item is the same 16384 pixels
+// of FFT work per position slot.  CTAs take items from a device counter (largest patches
+// first in the default order), branch once per item on the probe side and run the same
+// team code as the single-problem kernels (gather x probe, team 2D FFT, frequency stage,
+// inverse FFT, x conj(probe) and overlap scatter-add; App. A steps 1-4).  Positions beyond
+// a problem's K in its last item run the FFT on zeros (the team barriers are CTA-wide) and
+// touch no memory.  The last CTA to finish restores the counters, so the launch can be
+// replayed inside a CUDA graph.
+#include "batch.h"
+#include "ptycho_device.cuh"
+#include "team_fft.cuh"
+
+namespace ptylm {
+
+__device__ __forceinline__ int batch_tw_offset(int LS) { return LS == 5 ? 0 : (LS == 6 ? 32 : 96); }
+
+// Sum two per-thread doubles over the warp and add them to f[0], f[1].
+__device__ __forceinline__ void warp_add_to(double* f, double x, double y) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(f, x);
+        atomicAdd(f + 1, y);
+    }
+}
+
+// Forward model, error metric and (CACHE) cache a and gradient for one item.
+template <class G, bool CACHE>
+__device__ __forceinline__ void batch_forward_item(const BatchArgs& a, const BatchProblem& p, const BatchItem& it,
+                                                   float2* smem, const float2* tw_all) {
+    constexpr int TEAMS = BATCH_THREADS / G::T;
+    const int team = threadIdx.x / G::T, tid = threadIdx.x % G::T;
+    float2* sm = smem + team * G::M;
+    const float2* tw = tw_all + batch_tw_offset(G::LOG_S);
+    const float invS = 1.0f / G::S;
+    const float2* O = a.V + p.z_off;
+    float2* gout = a.out + p.z_off;
+    double acc_l = 0.0, acc_d = 0.0;
+    float2 v[32];
+    for (int j = 0; j < it.per_team; ++j) {
+        const int k = it.k0 + team + TEAMS * j;
+        const bool valid = k < p.K;
+        const int2 rc = valid ? p.pos[k] : make_int2(0, 0);
+        const float* yk = p.y + (size_t)(valid ? k : 0) * G::M + tid;
+        if (valid) {
+            prefetch_tile_l2(p.y + (size_t)k * G::M, sizeof(float) * G::M, tid);
+            gather_times_probe<G>(v, O, p.P, p.nx, rc.x, rc.y, tid);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = make_float2(0.0f, 0.0f);
+        }
+        float sl = 0.0f, sd = 0.0f;
+        if constexpr (CACHE) {
+            float2* ak = p.a_cache + (size_t)(valid ? k : 0) * G::M;
+            team_fft_roundtrip<G>(v, sm, tw, tid, [&](float2* g, int jj) {
+                float2 av[G::BY];
+#pragma unroll
+                for (int k2y = 0; k2y < G::BY; ++k2y) {
+                    const int e = jj * G::BY + k2y;
+                    const float2 ps = g[k2y] * invS;
+                    const float h = ps.x * ps.x + ps.y * ps.y + p.b;   // Eq. expected_count
+                    const PixelTerms t = pixel_terms<true>(p.loss, h, valid ? __ldg(yk + e * G::T) : 0.0f);
+                    sl += t.l;
+                    sd += t.dl * t.dl;
+                    av[k2y] = ps * t.sqrt_d2l_over_zeta;
+                    g[k2y] = ps * (t.dl_over_zeta * invS);
+                }
+                if (valid) store_cache_group<G>(ak, av, jj);
+            });
+            if (valid) scatter_times_conj_probe<G>(v, gout, p.P, p.nx, rc.x, rc.y, tid);
+        } else {
+            team_fft_fwd<G>(v, sm, tw, tid);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const float2 ps = v[e] * invS;
+                const float h = ps.x * ps.x + ps.y * ps.y + p.b;
+                const PixelTerms t = pixel_terms<true>(p.loss, h, valid ? __ldg(yk + e * G::T) : 0.0f);
+                sl += t.l;
+                sd += t.dl * t.dl;
+            }
+        }
+        if (valid) {
+            acc_l += (double)sl;
+            acc_d += (double)sd;
+        }
+        team_sync<G>();
+    }
+    warp_add_to(a.f + 2 * it.prob, acc_l, acc_d);
+}
+
+// out += J^T (Hess l . J v) for one item (App. A steps 2-4 with the cache a).
+template <class G>
+__device__ __forceinline__ void batch_matvec_item(const BatchArgs& a, const BatchProblem& p, const BatchItem& it,
+                                                  float2* smem, const float2* tw_all) {
+    constexpr int TEAMS = BATCH_THREADS / G::T;
+    const int team = threadIdx.x / G::T, tid = threadIdx.x % G::T;
+    float2* sm = smem + team * G::M;
+    const float2* tw = tw_all + batch_tw_offset(G::LOG_S);
+    const float invM = 1.0f / G::M;
+    const float2* V = a.V + p.z_off;
+    float2* out = a.out + p.z_off;
+    float2 v[32];
+    for (int j = 0; j < it.per_team; ++j) {
+        const int k = it.k0 + team + TEAMS * j;
+        const bool valid = k < p.K;
+        const int2 rc = valid ? p.pos[k] : make_int2(0, 0);
+        const float2* ak = p.a_cache + (size_t)(valid ? k : 0) * G::M;
+        if (valid) {
+            prefetch_tile_l2(ak, sizeof(float2) * G::M, tid);
+            gather_times_probe<G>(v, V, p.P, p.nx, rc.x, rc.y, tid);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = make_float2(0.0f, 0.0f);
+        }
+        team_fft_roundtrip<G>(v, sm, tw, tid, [&](float2* g, int jj) {
+            float2 av[G::BY];
+            if (valid) {
+                load_cache_group<G>(ak, av, jj, tid);
+            } else {
+#pragma unroll
+                for (int k2y = 0; k2y < G::BY; ++k2y) av[k2y] = make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int k2y = 0; k2y < G::BY; ++k2y) {
+                const float t = (av[k2y].x * g[k2y].x + av[k2y].y * g[k2y].y) * invM;
+                g[k2y] = av[k2y] * t;
+            }
+        });
+        if (valid) scatter_times_conj_probe<G>(v, out, p.P, p.nx, rc.x, rc.y, tid);
+        team_sync<G>();
+    }
+}
+
+// The persistent scheduler: take items until none are left, then let the last CTA reset
+// the counters.
+template <int KIND>
+__global__ void __launch_bounds__(BATCH_THREADS, 1) k_batch(BatchArgs a) {
+    extern __shared__ float4 dyn_smem_f4[];
+    float2* tw = reinterpret_cast<float2*>(dyn_smem_f4);
+    float2* smem = tw + BATCH_TW;
+    __shared__ int s_item;
+    for (int i = threadIdx.x; i < BATCH_TW; i += blockDim.x) tw[i] = a.tw[i];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(a.work, 1u);
+        __syncthreads();  // also orders the twiddle stores before the first item
+        const int idx = s_item;
+        __syncthreads();
+        if (idx >= a.n_items) break;
+        const BatchItem it = a.items[idx];
+        if (a.active && !a.active[it.prob]) continue;
+        const BatchProblem p = a.probs[it.prob];
+        switch (p.LS) {
+            case 5:
+                if constexpr (KIND == BK_MATVEC) batch_matvec_item<Geo<5>>(a, p, it, smem, tw);
+                else batch_forward_item<Geo<5>, KIND == BK_FWD_CACHE>(a, p, it, smem, tw);
+                break;
+            case 6:
+                if constexpr (KIND == BK_MATVEC) batch_matvec_item<Geo<6>>(a, p, it, smem, tw);
+                else batch_forward_item<Geo<6>, KIND == BK_FWD_CACHE>(a, p, it, smem, tw);
+                break;
+            default:
+                if constexpr (KIND == BK_MATVEC) batch_matvec_item<Geo<7>>(a, p, it, smem, tw);
+                else batch_forward_item<Geo<7>, KIND == BK_FWD_CACHE>(a, p, it, smem, tw);
+                break;
+        }
+        __syncthreads();  // the next item may lay its teams out differently in shared memory
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.done, 1u) == gridDim.x - 1) {
+            atomicExch(a.work, 0u);
+            atomicExch(a.done, 0u);
+            __threadfence();
+        }
+    }
+}
+
+static size_t batch_smem_bytes() { return sizeof(float2) * (BATCH_TW + 16384); }
+
+static const void* batch_kernel_ptr(int kernel) {
+    switch (kernel) {
+        case BK_FWD_LOSS: return (const void*)k_batch<BK_FWD_LOSS>;
+        case BK_FWD_CACHE: return (const void*)k_batch<BK_FWD_CACHE>;
+        case BK_MATVEC: return (const void*)k_batch<BK_MATVEC>;
+    }
+    return nullptr;
+}
+
+cudaError_t batch_prepare(int* ctas_per_sm) {
+    int best = 1 << 30;
+    for (int k = 0; k < BK_COUNT; ++k) {
+        const void* fn = batch_kernel_ptr(k);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes());
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, BATCH_THREADS, batch_smem_bytes());
+        if (e != cudaSuccess) return e;
+        best = n < best ? n : best;
+    }
+    *ctas_per_sm = best;
+    return cudaSuccess;
+}
+
+cudaError_t batch_launch(int kernel, const BatchArgs& a, int grid, cudaStream_t stream) {
+    const void* fn = batch_kernel_ptr(kernel);
+    if (!fn || grid <= 0) return cudaErrorInvalidValue;
+    BatchArgs arg = a;
+    void* args[] = {&arg};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(BATCH_THREADS), args, batch_smem_bytes(), stream);
+}
+
+}  // namespace ptylm

@@ -26,6 +26,37 @@ __device__ __forceinline__ void prefetch_tile_l2(const void* tile, unsigned byte
     if (off < bytes) prefetch_l2(reinterpret_cast<const char*>(tile) + off, min(kChunk, bytes - off));
 }
 
+// Cache a, team-register order.  For BY >= 2 the two elements (e, e+1) of a thread that
+// share a pass-3 group are adjacent, so one 16-byte access moves both: element e of thread
+// t lives at float2 index (e/2)*2T + 2t + (e%2) of the position's M-element tile.  For
+// BY == 1 (one element per group) the layout is e*T + t.
+template <class G>
+__device__ __forceinline__ void store_cache_group(float2* ak, const float2* av, int j) {
+    const int tid = threadIdx.x % G::T;
+    if constexpr (G::BY >= 2) {
+        float4* a4 = reinterpret_cast<float4*>(ak) + tid;
+#pragma unroll
+        for (int i = 0; i < G::BY / 2; ++i)
+            a4[(j * (G::BY / 2) + i) * G::T] = make_float4(av[2 * i].x, av[2 * i].y, av[2 * i + 1].x, av[2 * i + 1].y);
+    } else {
+        ak[j * G::T + tid] = av[0];
+    }
+}
+template <class G>
+__device__ __forceinline__ void load_cache_group(const float2* ak, float2* av, int j, int tid) {
+    if constexpr (G::BY >= 2) {
+        const float4* a4 = reinterpret_cast<const float4*>(ak) + tid;
+#pragma unroll
+        for (int i = 0; i < G::BY / 2; ++i) {
+            const float4 q = __ldcs(a4 + (j * (G::BY / 2) + i) * G::T);
+            av[2 * i] = make_float2(q.x, q.y);
+            av[2 * i + 1] = make_float2(q.z, q.w);
+        }
+    } else {
+        av[0] = __ldcs(ak + j * G::T + tid);
+    }
+}
+
 // Per-pixel error-metric terms of Sec. 4.1 Eq. ell_magnitude, from h = |psihat|^2 + b and
 // the stored measurement term ym (sqrt(y) for the Gaussian metric, y for Poisson):
 //   Gaussian  l = (zeta - sqrt y)^2 / 2,   dl = zeta - sqrt y,     d2l = 1

@@ -69,37 +69,6 @@ struct AdjArgs {          // J^T w and J v
     float b;
 };
 
-// Cache a, team-register order.  For BY >= 2 the two elements (e, e+1) of a thread that
-// share a pass-3 group are adjacent, so one 16-byte access moves both: element e of thread
-// t lives at float2 index (e/2)*2T + 2t + (e%2) of the position's M-element tile.  For
-// BY == 1 (one element per group) the layout is e*T + t.
-template <class G>
-__device__ __forceinline__ void store_cache_group(float2* ak, const float2* av, int j) {
-    const int tid = threadIdx.x % G::T;
-    if constexpr (G::BY >= 2) {
-        float4* a4 = reinterpret_cast<float4*>(ak) + tid;
-#pragma unroll
-        for (int i = 0; i < G::BY / 2; ++i)
-            a4[(j * (G::BY / 2) + i) * G::T] = make_float4(av[2 * i].x, av[2 * i].y, av[2 * i + 1].x, av[2 * i + 1].y);
-    } else {
-        ak[j * G::T + tid] = av[0];
-    }
-}
-template <class G>
-__device__ __forceinline__ void load_cache_group(const float2* ak, float2* av, int j, int tid) {
-    if constexpr (G::BY >= 2) {
-        const float4* a4 = reinterpret_cast<const float4*>(ak) + tid;
-#pragma unroll
-        for (int i = 0; i < G::BY / 2; ++i) {
-            const float4 q = __ldcs(a4 + (j * (G::BY / 2) + i) * G::T);
-            av[2 * i] = make_float2(q.x, q.y);
-            av[2 * i + 1] = make_float2(q.z, q.w);
-        }
-    } else {
-        av[0] = __ldcs(ak + j * G::T + tid);
-    }
-}
-
 // ---------------------------------------------------------------------------------------
 // Forward model + error metric (+ cache and gradient when CACHE; intensities only when
 // INTENSITY).

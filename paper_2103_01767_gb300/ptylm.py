@@ -104,6 +104,22 @@ def load_library():
             lib.ptylm_strerror.restype = ctypes.c_char_p
             lib.ptylm_last_error.restype = ctypes.c_char_p
             lib.ptylm_default_lm_params.argtypes = [ctypes.POINTER(LMParams), i]
+            P = ctypes.POINTER
+            lib.ptylm_batch_init.argtypes = [P(vp), i, P(Desc), P(vp), P(vp), P(vp), vp]
+            lib.ptylm_batch_offset.argtypes = [vp, i]
+            lib.ptylm_batch_offset.restype = ctypes.c_long
+            lib.ptylm_batch_forward_loss.argtypes = [vp, vp, P(d), P(d), i]
+            lib.ptylm_batch_gradient.argtypes = [vp, vp]
+            lib.ptylm_batch_ggn_matvec.argtypes = [vp, vp, vp, P(d)]
+            lib.ptylm_batch_lm_solve.argtypes = [vp, vp, P(LMParams), P(LMStats)]
+            lib.ptylm_batch_tune.argtypes = [vp, P(i), P(ctypes.c_float), i]
+            lib.ptylm_batch_set_schedule.argtypes = [vp, i]
+            lib.ptylm_batch_profile_read.argtypes = [vp, P(ctypes.c_longlong)]
+            lib.ptylm_batch_destroy.argtypes = [vp]
+            for name in ("ptylm_batch_init", "ptylm_batch_forward_loss", "ptylm_batch_gradient",
+                         "ptylm_batch_ggn_matvec", "ptylm_batch_lm_solve", "ptylm_batch_tune",
+                         "ptylm_batch_set_schedule", "ptylm_batch_profile_read", "ptylm_batch_destroy"):
+                getattr(lib, name).restype = i
             for name in ("lm_init", "forward_loss", "gradient", "jvp", "jtvp", "ggn_matvec",
                          "lm_solve", "lm_destroy", "forward_intensity", "ptylm_set_measurements",
                          "ptylm_forward_loss_noalloc", "ggn_diag", "forward_magnitude",
@@ -292,3 +308,144 @@ def lm_solve(ctx: Context, O, P, params: LMParams | None = None, hist_len: int =
                         f_final=st.f_final, err_final=st.err_final, f=hf[:n].copy(),
                         gnorm=hg[:n].copy(), mu=hmu[:n].copy(), cg=hcg[:n].copy(),
                         err=herr[:n].copy())
+
+
+# ---------------------------------------------------------------------------------------
+# Batches of independent reconstructions
+# ---------------------------------------------------------------------------------------
+N_SCHEDULES = 6
+
+
+class Batch:
+    """Owns one C batch (ptylm_batch_init ... ptylm_batch_destroy)."""
+
+    def __init__(self, handle, descs, offsets):
+        self.handle = handle
+        self.descs = descs
+        self.offsets = offsets          # [B + 1] element offsets of the problems
+        self.B = len(descs)
+
+    @property
+    def total(self):
+        return self.offsets[-1]
+
+    def views(self, vec):
+        """Per-problem [ny, nx] views of a flat batch vector (torch tensor)."""
+        return [vec[self.offsets[b]:self.offsets[b + 1]].view(d.ny, d.nx) for b, d in enumerate(self.descs)]
+
+    def close(self):
+        if self.handle:
+            _check(load_library().ptylm_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_init(problems, stream=None) -> Batch:
+    """problems: list of dicts with ny, nx, m, positions (device int32 [K, 2]), y (device
+    float32 [K, m, m]), probe (device complex64 [m, m]), loss, background."""
+    lib = load_library()
+    B = len(problems)
+    descs = (Desc * B)()
+    pos = (ctypes.c_void_p * B)()
+    ys = (ctypes.c_void_p * B)()
+    probes = (ctypes.c_void_p * B)()
+    for b, pr in enumerate(problems):
+        K = int(pr["positions"].shape[0])
+        descs[b] = Desc(int(pr["ny"]), int(pr["nx"]), int(pr["m"]), int(pr["m"]), K, int(pr.get("loss", 0)),
+                        float(pr.get("background", 1e-8)), 0, 0)
+        pos[b] = _ptr(pr["positions"])
+        ys[b] = _ptr(pr["y"])
+        probes[b] = _ptr(pr["probe"])
+    h = ctypes.c_void_p()
+    _check(lib.ptylm_batch_init(ctypes.byref(h), B, descs, pos, ys, probes, _stream_ptr(stream)))
+    offsets = [int(lib.ptylm_batch_offset(h, b)) for b in range(B + 1)]
+    return Batch(h, [descs[b] for b in range(B)], offsets)
+
+
+def batch_forward_loss(batch: Batch, O, cache: int = 0):
+    """Returns (f[B], ||grad_zeta l||^2[B]) as numpy arrays."""
+    f = np.zeros(batch.B)
+    n2 = np.zeros(batch.B)
+    _check(load_library().ptylm_batch_forward_loss(
+        batch.handle, _ptr(O), f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        n2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(cache)))
+    return f, n2
+
+
+def batch_gradient(batch: Batch, g) -> None:
+    _check(load_library().ptylm_batch_gradient(batch.handle, _ptr(g)))
+
+
+def batch_ggn_matvec(batch: Batch, v, out, lam=None) -> None:
+    lp = None
+    if lam is not None:
+        lam = np.ascontiguousarray(np.broadcast_to(np.asarray(lam, np.float64), (batch.B,)))
+        lp = lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _check(load_library().ptylm_batch_ggn_matvec(batch.handle, _ptr(v), _ptr(out), lp))
+
+
+def batch_tune(batch: Batch):
+    """Returns (chosen schedule, measured ms per schedule)."""
+    choice = ctypes.c_int(-1)
+    ms = (ctypes.c_float * N_SCHEDULES)()
+    _check(load_library().ptylm_batch_tune(batch.handle, ctypes.byref(choice), ms, N_SCHEDULES))
+    return choice.value, list(ms)
+
+
+def batch_set_schedule(batch: Batch, choice: int) -> None:
+    _check(load_library().ptylm_batch_set_schedule(batch.handle, int(choice)))
+
+
+def batch_launches(batch: Batch) -> int:
+    n = ctypes.c_longlong()
+    _check(load_library().ptylm_batch_profile_read(batch.handle, ctypes.byref(n)))
+    return n.value
+
+
+def batch_lm_solve(batch: Batch, O, params=None, hist_len: int = 0, O_refs=None, masks=None, **overrides):
+    """Algorithm 1 on every problem, in place on the flat batch vector O.  params: one
+    LMParams (copied per problem, loss-specific defaults otherwise) or a list of B.  Returns
+    (status, [stats dict per problem]); PTYLM_ERR_STALLED and PTYLM_WARN_CG_MAXIT are
+    returned, not raised."""
+    lib = load_library()
+    B = batch.B
+    prm = (LMParams * B)()
+    for b in range(B):
+        if params is None:
+            p = default_lm_params(batch.descs[b].loss)
+        elif isinstance(params, (list, tuple)):
+            p = params[b]
+        else:
+            p = params
+        ctypes.memmove(ctypes.byref(prm[b]), ctypes.byref(p), ctypes.sizeof(LMParams))
+        for k, v in overrides.items():
+            setattr(prm[b], k, v)
+        if O_refs is not None and O_refs[b] is not None:
+            prm[b].O_ref = _ptr(O_refs[b])
+        if masks is not None and masks[b] is not None:
+            prm[b].mask = _ptr(masks[b])
+    L = int(hist_len)
+    hists = []
+    stats = (LMStats * B)()
+    for b in range(B):
+        hf, hg, hmu, herr = (np.full(max(L, 1), math.nan) for _ in range(4))
+        hcg = np.zeros(max(L, 1), np.int32)
+        hists.append((hf, hg, hmu, hcg, herr))
+        stats[b] = LMStats(0, 0, 0, 0.0, 0.0, L, hf.ctypes.data, hg.ctypes.data, hmu.ctypes.data,
+                           hcg.ctypes.data, herr.ctypes.data)
+    status = _check(lib.ptylm_batch_lm_solve(batch.handle, _ptr(O), prm, stats),
+                    allow=(PTYLM_WARN_CG_MAXIT, PTYLM_ERR_STALLED))
+    out = []
+    for b in range(B):
+        st = stats[b]
+        n = min(st.n_outer, L)
+        hf, hg, hmu, hcg, herr = hists[b]
+        out.append(dict(n_outer=st.n_outer, cg_total=st.cg_total, matvecs=st.matvecs_total, f_final=st.f_final,
+                        err_final=st.err_final, f=hf[:n].copy(), gnorm=hg[:n].copy(), mu=hmu[:n].copy(),
+                        cg=hcg[:n].copy(), err=herr[:n].copy()))
+    return status, out

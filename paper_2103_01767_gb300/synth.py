@@ -146,3 +146,46 @@ def illumination_mask(n: int, probe: np.ndarray, positions: np.ndarray, frac: fl
     for r, c in positions:
         acc[r:r + m0, c:c + m1] += p2
     return acc >= frac * acc.max()
+
+
+# ---------------------------------------------------------------------------------------
+# Batches of independent reconstructions of uneven sizes
+# ---------------------------------------------------------------------------------------
+@dataclass(frozen=True)
+class BatchMember:
+    n: int          # object side
+    m: int          # probe side (32, 64 or 128)
+    K: int          # scan positions
+    loss: int       # 0 Gaussian (noiseless data), 1 Poisson (counts at `peak`)
+    peak: float
+    seed: int
+
+    @property
+    def radius(self):
+        return 0.3125 * self.m
+
+
+def batch_members(B: int = 64, seed: int = 7, n_range=(128, 512), K_range=(64, 1024)):
+    """B problems drawn uniformly: probe side from {32, 64, 128}, object side from
+    [max(n_lo, 2 m), n_hi] (so N >= 2 x probe), K from K_range, loss Gaussian or Poisson
+    (peak 1e3 photons)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(B):
+        m = int(rng.choice([32, 64, 128]))
+        n = int(rng.integers(max(n_range[0], 2 * m), n_range[1] + 1))
+        K = int(rng.integers(K_range[0], K_range[1] + 1))
+        loss = int(rng.integers(0, 2))
+        out.append(BatchMember(n, m, K, loss, 1e3 if loss else 0.0, 1000 * seed + b))
+    return out
+
+
+def batch_positions(mem: BatchMember, jitter: int = 2):
+    """The first K points of a ceil(sqrt K)^2 jittered raster with step m / 4 (reduced to
+    fit the object)."""
+    g = int(math.ceil(math.sqrt(mem.K)))
+    pos, _ = raster_positions(mem.n, mem.m, g, max(1, mem.m // 4), jitter, seed=mem.seed + 1)
+    return np.ascontiguousarray(pos[:mem.K])
+
+
+BATCH64 = "batch64_obj128-512_probe32-128_pos64-1024_mixed"

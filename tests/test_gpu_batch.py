@@ -1,0 +1,190 @@
+"""Batches of independent reconstructions (one persistent launch per operator, CG under a
+captured CUDA graph, schedule autotuner) against the FP64 oracle problem by problem.
+
+Tolerances as in test_gpu_parity.py: relative 1e-5 for the Gaussian metric, the FP32
+conditioning bound for the Poisson metric away from the truth."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_01767_gb300 import synth
+from tests.problems import make_case, rel_err
+from tests.test_gpu_parity import fp32_conditioning
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+# (object side, probe side, K, loss, noisy): uneven sizes, all three probe sides, ragged
+# position counts (last work items partly empty), both losses
+MEMBERS = [(96, 32, 37, 0, False), (160, 64, 23, 1, False), (288, 128, 11, 0, False), (128, 32, 100, 1, True),
+           (256, 64, 50, 0, False), (256, 128, 5, 1, True)]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_01767_gb300 import build, ptylm
+    build.build()
+    ptylm.load_library()
+    return ptylm
+
+
+def c64(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.complex64)).cuda()
+
+
+def f32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.complex128)
+
+
+@pytest.fixture(scope="module")
+def batch(lib):
+    cases = []
+    for i, (n, m, K, loss, noisy) in enumerate(MEMBERS):
+        case = make_case(n, m, K=K, loss=loss, peak=1e3 if loss else 0.0, seed=80 + i, noisy=noisy)
+        case.noisy = noisy
+        cases.append(case)
+    probs = [dict(ny=c.n, nx=c.n, m=c.m, positions=torch.from_numpy(c.pos).cuda(), y=f32(c.y), probe=c64(c.P),
+                  loss=c.loss, background=c.b) for c in cases]
+    bt = lib.batch_init(probs)
+    points = [synth.to_c64(c.O_true + synth.random_complex(c.O_true.shape, seed=90 + i, scale=0.05))
+              for i, c in enumerate(cases)]
+    O = torch.cat([c64(p).reshape(-1) for p in points])
+    return bt, cases, points, O
+
+
+def tol_for(case, fn, *arrays):
+    """1e-5 for the Gaussian metric; Poisson data away from the truth (every point here is
+    perturbed) use max(1e-5, 2 x the FP32 conditioning), as in test_gpu_parity.py."""
+    if case.loss == 0:
+        return TOL
+    return max(TOL, 2.0 * fp32_conditioning(fn, case.m, *arrays))
+
+
+def test_offsets_concatenate_the_objects(lib, batch):
+    bt, cases, _, _ = batch
+    assert bt.offsets[0] == 0
+    assert all(bt.offsets[i + 1] - bt.offsets[i] == c.n * c.n for i, c in enumerate(cases))
+
+
+def test_batch_forward_loss_and_gradient(lib, batch):
+    bt, cases, points, O = batch
+    f, dl2 = lib.batch_forward_loss(bt, O, cache=1)
+    g = torch.empty_like(O)
+    lib.batch_gradient(bt, g)
+    gv = bt.views(g)
+    for b, (c, X) in enumerate(zip(cases, points)):
+        pb = c.problem()
+        f_ref, dl2_ref = oracle.loss(pb, X, return_dl_norm2=True)
+        assert abs(f[b] - f_ref) <= tol_for(c, lambda A: oracle.loss(pb, A), X) * abs(f_ref), b
+        assert abs(dl2[b] - dl2_ref) <= tol_for(c, lambda A: oracle.loss(pb, A, return_dl_norm2=True)[1], X) * dl2_ref, b
+        g_ref = oracle.gradient(pb, X)
+        assert rel_err(host(gv[b]), g_ref) <= tol_for(c, lambda A: oracle.gradient(pb, A), X), b
+
+
+def test_batch_loss_without_cache_matches(lib, batch):
+    bt, cases, points, O = batch
+    f1, _ = lib.batch_forward_loss(bt, O, cache=1)
+    f0, _ = lib.batch_forward_loss(bt, O, cache=0)
+    assert np.allclose(f0, f1, rtol=1e-6, atol=0)
+
+
+def test_batch_ggn_matvec(lib, batch):
+    bt, cases, points, O = batch
+    lib.batch_forward_loss(bt, O, cache=1)
+    vs = [synth.to_c64(synth.random_complex((c.n, c.n), seed=100 + i)) for i, c in enumerate(cases)]
+    v = torch.cat([c64(x).reshape(-1) for x in vs])
+    out = torch.empty_like(v)
+    lam = np.array([0.0, 0.3, 0.0, 1.7, 0.01, 0.5])
+    lib.batch_ggn_matvec(bt, v, out, lam)
+    ov = bt.views(out)
+    for b, (c, X) in enumerate(zip(cases, points)):
+        pb = c.problem()
+        ref = oracle.ggn_matvec(pb, X, vs[b], lam=lam[b])
+        tol = tol_for(c, lambda A, B: oracle.ggn_matvec(pb, A, B, lam=lam[b]), X, vs[b])
+        assert rel_err(host(ov[b]), ref) <= tol, (b, tol)
+
+
+def test_every_schedule_gives_the_same_product(lib, batch):
+    bt, cases, points, O = batch
+    lib.batch_forward_loss(bt, O, cache=1)
+    v = torch.cat([c64(synth.random_complex((c.n, c.n), seed=110 + i)).reshape(-1) for i, c in enumerate(cases)])
+    choice, ms = lib.batch_tune(bt)
+    assert 0 <= choice < lib.N_SCHEDULES and all(t > 0 for t in ms) and ms[choice] == min(ms)
+    outs = []
+    for s in range(lib.N_SCHEDULES):
+        lib.batch_set_schedule(bt, s)
+        out = torch.empty_like(v)
+        lib.batch_ggn_matvec(bt, v, out, 0.2)
+        outs.append(host(out))
+    for s in range(1, lib.N_SCHEDULES):
+        assert rel_err(outs[s], outs[0]) <= 2 * TOL, s
+
+
+def test_batch_lm_reaches_accuracy_like_single_problem_lm(lib):
+    """Noiseless amplitude problems of three probe sides: the batched LM reaches 1e-3 object
+    error on each, in a number of outer iterations within 3 of the single-problem lm_solve
+    (and of the oracle's run for the smallest)."""
+    specs = [(128, 32, 8, 8), (192, 64, 6, 16), (256, 128, 4, 32)]
+    cases, probs, O0, refs, masks = [], [], [], [], []
+    for i, (n, m, grid, step) in enumerate(specs):
+        c = make_case(n, m, loss=0, seed=120 + i, grid=grid, step=step, radius=0.3125 * m)
+        cases.append(c)
+        probs.append(dict(ny=n, nx=n, m=m, positions=torch.from_numpy(c.pos).cuda(), y=f32(c.y), probe=c64(c.P),
+                          loss=0, background=c.b))
+        O0.append(synth.flat_object(n))
+        refs.append(c64(c.O_true))
+        masks.append(torch.from_numpy(synth.illumination_mask(n, c.P, c.pos, 0.1).astype(np.uint8)).cuda())
+    bt = lib.batch_init(probs)
+    O = torch.cat([c64(o).reshape(-1) for o in O0])
+    st, infos = lib.batch_lm_solve(bt, O, hist_len=80, O_refs=refs, masks=masks, max_outer=80, target_err=1e-3)
+    ov = bt.views(O)
+    for b, c in enumerate(cases):
+        mask = synth.illumination_mask(c.n, c.P, c.pos, 0.1)
+        assert oracle.object_error(host(ov[b]), c.O_true, mask) <= 1e-3, b
+        ctx = lib.lm_init(c.n, c.n, c.m, c.m, torch.from_numpy(c.pos).cuda(), f32(c.y), 0, c.b)
+        Od = c64(O0[b])
+        _, single = lib.lm_solve(ctx, Od, c64(c.P), hist_len=80, O_ref=refs[b], mask=masks[b], max_outer=80,
+                                 target_err=1e-3)
+        assert abs(infos[b]["n_outer"] - single["n_outer"]) <= 3, (b, infos[b]["n_outer"], single["n_outer"])
+        assert infos[b]["err"][-1] <= 1e-3
+    _, info_ref = oracle.lm_solve(cases[0].problem(), O0[0], O_ref=cases[0].O_true,
+                                  mask=synth.illumination_mask(128, cases[0].P, cases[0].pos, 0.1), max_outer=80,
+                                  target_err=1e-3)
+    assert abs(infos[0]["n_outer"] - info_ref["n_outer"]) <= 3
+    assert lib.batch_launches(bt) > 0
+
+
+def test_batch_lm_fixed_cg_counts(lib, batch):
+    """fixed_cg runs exactly that many CG iterations per solve on every problem."""
+    bt, cases, points, O = batch
+    X = O.clone()
+    st, infos = lib.batch_lm_solve(bt, X, hist_len=4, max_outer=2, fixed_cg=5)
+    for info in infos:
+        assert info["n_outer"] >= 1
+        assert info["cg_total"] % 5 == 0 and info["cg_total"] >= 5
+        assert np.all(info["cg"] % 5 == 0)
+
+
+def test_batch_argument_errors(lib):
+    c = make_case(96, 32, K=10, loss=0, seed=1)
+    good = dict(ny=96, nx=96, m=32, positions=torch.from_numpy(c.pos).cuda(), y=f32(c.y), probe=c64(c.P), loss=0)
+    bad = dict(good)
+    pos = c.pos.copy()
+    pos[3] = (90, 0)   # 90 + 32 > 96
+    bad["positions"] = torch.from_numpy(pos).cuda()
+    with pytest.raises(lib.PtylmError) as e:
+        lib.batch_init([good, bad])
+    assert e.value.status == lib.PTYLM_ERR_ARG
+    bt = lib.batch_init([good])
+    v = torch.zeros(96 * 96, dtype=torch.complex64, device="cuda")
+    with pytest.raises(lib.PtylmError) as e:
+        lib.batch_ggn_matvec(bt, v, torch.empty_like(v))
+    assert e.value.status == lib.PTYLM_ERR_STATE
