@@ -389,6 +389,139 @@ def gpu_time_to_accuracy(ptylm, torch, dev, stream, target=1e-3, reps=5, large_r
     return out
 
 
+# ---------------------------------------------------------------------------------------
+# Batch of 64 independent reconstructions (one persistent launch per operator)
+# ---------------------------------------------------------------------------------------
+BATCH_METRIC = "batched GGN matvecs/s (64 uneven reconstructions)"
+BATCH_UNIT = "problem-matvec/s"
+
+
+def setup_batch(ptylm, torch, dev, members):
+    """Simulate every member's data with the single-problem forward model on the GPU."""
+    probs, O0 = [], []
+    for mem in members:
+        O_true = torch.from_numpy(synth.object_texture(mem.n, seed=mem.seed).astype(np.complex64)).to(dev)
+        P = torch.from_numpy(synth.probe_disk_defocus(mem.m, mem.radius).astype(np.complex64)).to(dev)
+        pos = torch.from_numpy(synth.batch_positions(mem)).to(dev)
+        y = torch.empty((mem.K, mem.m, mem.m), dtype=torch.float32, device=dev)
+        ctx = ptylm.lm_init(mem.n, mem.n, mem.m, mem.m, pos, y, mem.loss, 1e-8)
+        ptylm.forward_intensity(ctx, O_true, P, y)
+        torch.cuda.synchronize(dev)
+        if mem.peak > 0:
+            P *= math.sqrt(mem.peak / float(y.max()))
+            ptylm.forward_intensity(ctx, O_true, P, y)
+            y.copy_(torch.from_numpy(synth.poisson_counts(y.cpu().numpy(), seed=mem.seed + 2).astype(np.float32)))
+        ptylm.lm_destroy(ctx)
+        probs.append(dict(ny=mem.n, nx=mem.n, m=mem.m, positions=pos, y=y, probe=P, loss=mem.loss, background=1e-8))
+        O0.append(torch.full((mem.n * mem.n,), complex(float(O_true.abs().mean()), 0.0), dtype=torch.complex64,
+                             device=dev))
+    return probs, torch.cat(O0)
+
+
+def run_batch(args):
+    import torch
+    from paper_2103_01767_gb300 import build as _build
+    _build.build()
+    from paper_2103_01767_gb300 import ptylm
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    members = synth.batch_members()
+    probs, O0 = setup_batch(ptylm, torch, dev, members)
+    bt = ptylm.batch_init(probs, stream=torch.cuda.current_stream(dev))
+    ptylm.batch_forward_loss(bt, O0, cache=1)
+    choice, tune_ms = ptylm.batch_tune(bt)
+    v = torch.randn(bt.total, dtype=torch.complex64, device=dev)
+    out = torch.empty_like(v)
+    lam = np.full(bt.B, 1e-3)
+    for _ in range(args.warmup):
+        ptylm.batch_ggn_matvec(bt, v, out, lam)
+    torch.cuda.synchronize(dev)
+    n0 = ptylm.batch_launches(bt)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            ptylm.batch_ggn_matvec(bt, v, out, lam)
+        ev1.record()
+        torch.cuda.synchronize(dev)
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = ptylm.batch_launches(bt) - n0
+    value = bt.B * args.steps / elapsed
+    flops = sum(matvec_flops(m.K, m.m * m.m) for m in members)
+    bytes_ = sum(matvec_bytes(m.K, m.m * m.m, m.n * m.n) for m in members)
+    clocks = clk.summary()
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_fp32 = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    t_step = elapsed / args.steps
+    # e2e: the direction from pinned host memory, the product back to it, every step
+    v_h = v.cpu().pin_memory()
+    o_h = torch.empty_like(v_h).pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.e2e_steps)):
+        v.copy_(v_h, non_blocking=True)
+        ptylm.batch_ggn_matvec(bt, v, out, lam)
+        o_h.copy_(out, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / max(1, args.e2e_steps)
+    # comparison: the same 64 products through 64 single-problem contexts, one after another
+    ctxs = []
+    for pr, mem in zip(probs, members):
+        ctx = ptylm.lm_init(mem.n, mem.n, mem.m, mem.m, pr["positions"], pr["y"], mem.loss, 1e-8)
+        ctxs.append(ctx)
+    views = bt.views(O0)
+    vv, ov = bt.views(v), bt.views(out)
+    for c, o, pr in zip(ctxs, views, probs):
+        ptylm.forward_loss(c, o, pr["probe"], cache=1)
+    for c, a, b in zip(ctxs, vv, ov):
+        ptylm.ggn_matvec(c, a, b, 1e-3)
+    torch.cuda.synchronize(dev)
+    ev0.record()
+    reps = 5
+    for _ in range(reps):
+        for c, a, b in zip(ctxs, vv, ov):
+            ptylm.ggn_matvec(c, a, b, 1e-3)
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    seq_s = ev0.elapsed_time(ev1) / 1e3 / reps
+    for c in ctxs:
+        ptylm.lm_destroy(c)
+    # one LM step of all problems (Algorithm 1, 10 CG iterations each, CG under the graph)
+    Ob = O0.clone()
+    ptylm.batch_lm_solve(bt, Ob, max_outer=1, fixed_cg=10)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    Ob.copy_(O0)
+    _, infos = ptylm.batch_lm_solve(bt, Ob, max_outer=1, fixed_cg=10)
+    lm_step_s = time.perf_counter() - t0
+    line = {
+        "metric": BATCH_METRIC, "value": value, "unit": BATCH_UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": synth.BATCH64, "problems": bt.B, "positions": int(sum(m.K for m in members)),
+                   "objects": [min(m.n for m in members), max(m.n for m in members)],
+                   "probes": sorted({m.m for m in members}), "losses": {"gaussian": sum(m.loss == 0 for m in members),
+                                                                         "poisson": sum(m.loss == 1 for m in members)},
+                   "step": "one batched GGN product (damping + one persistent launch) over all problems",
+                   "parallelism": "replicas1", "l2": "inputs larger than L2: 2.5 GB of caches streamed per step"},
+        "roofline": {"bound": "alu", "achieved": flops / t_step / 1e12, "peak": peak_fp32, "unit": "TFLOP/s",
+                     "frac": flops / t_step / 1e12 / peak_fp32, "traffic": None, "kernel": "k_batch<matvec>",
+                     "flops_per_launch": flops, "hbm_bytes_per_launch": bytes_},
+        "cpu_baseline": None,
+        "e2e": {"value": bt.B / e2e_s, "unit": BATCH_UNIT, "h2d_bytes_per_step": 8 * bt.total,
+                "d2h_bytes_per_step": 8 * bt.total},
+        "clocks": clocks, "gpu_launches": int(launches),
+        "schedule": {"chosen": choice, "tune_ms": tune_ms},
+        "comparison": {"sequential_single_contexts_ms": 1e3 * seq_s, "batched_ms": 1e3 * t_step,
+                       "speedup": seq_s / t_step},
+        "lm_step_ms": 1e3 * lm_step_s,
+    }
+    print(json.dumps(line), flush=True)
+    bt.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,11 +530,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cg-per-step", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", default=synth.LARGE.name, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default=synth.LARGE.name, choices=sorted(synth.WORKLOADS) + [synth.BATCH64])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the cuFFT comparison and the LM time-to-accuracy runs")
     args = ap.parse_args()
+    if args.workload == synth.BATCH64:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle has no batched form; "
+                              "run the single-problem workloads"}), flush=True)
+            return 0
+        return run_batch(args)
     w = synth.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
