@@ -359,6 +359,62 @@ ptylm_status ptylm_batch_profile_read(ptylm_batch* batch, long long* launches);
 /* Free the batch (NULL is accepted). */
 ptylm_status ptylm_batch_destroy(ptylm_batch* batch);
 
+/* ---------------------------------------------------------------------------------------
+ * Learned initialisation (not part of the paper): a data-driven initial object for
+ * Algorithm 1 from the measured magnitudes, for 128 x 128 patterns.
+ *
+ * Per pattern k the physics input is e_k = F^-1(sqrt(y_k) u) conj(P) / (|P|^2 + 1e-3 max|P|^2)
+ * with u = F(P) / max(|F(P)|, 1e-3 max|F(P)|) (the far-field magnitudes with the probe's own
+ * far-field phase, propagated back through the forward model of Sec. 2 and divided by the
+ * probe), two channels (Re, Im) of [128][128] float.  A 6-layer convolutional encoder-decoder refines it into the object
+ * patch: three 3 x 3 stride-2 convolutions 2 -> C1 -> C2 -> C3 (ReLU), then three x2
+ * nearest upsamplings each followed by a 3 x 3 convolution C3 -> C2 -> C1 (ReLU) -> 2
+ * (linear).  Weights are bfloat16 copies of FP32 master weights; activations and all sums
+ * are FP32.  The patch estimates are averaged into the object with weights |P|^2 over
+ * their overlaps (1 where no probe reaches).  Parameter layout (flat float array):
+ * W1 b1 W2 b2 ... W6 b6, W_l as [c_out][c_in][3][3].  Arrays are device arrays unless named
+ * *_host; images are [N][2][128][128] float.
+ * --------------------------------------------------------------------------------------- */
+typedef struct ptylm_net ptylm_net;
+
+/* m must be 128; widths = {C1, C2, C3}, positive multiples of 16; max_batch: patterns per
+ * forward / training batch; seed: He-normal initial weights, zero biases. */
+ptylm_status ptylm_net_create(ptylm_net** net, int m, const int* widths, int max_batch, uint64_t seed,
+                              void* stream);
+/* Number of floats in the flat parameter array (-1 for NULL). */
+long ptylm_net_num_params(const ptylm_net* net);
+/* Load / read the FP32 master parameters (host arrays); grads_host receives the gradients
+ * of the last ptylm_net_loss_grad or training step (either pointer may be NULL). */
+ptylm_status ptylm_net_set_params(ptylm_net* net, const float* params_host);
+ptylm_status ptylm_net_get_params(ptylm_net* net, float* params_host, float* grads_host);
+/* out = network(X) for N <= max_batch images. */
+ptylm_status ptylm_net_forward(ptylm_net* net, const float* X, int N, float* out);
+/* Loss L = sum mask (out - T)^2 / (2 N sum mask) (mask [128][128] broadcast over channels
+ * and batch) and its gradients (kept in the network, read with ptylm_net_get_params). */
+ptylm_status ptylm_net_loss_grad(ptylm_net* net, const float* X, const float* T, const float* mask, int N,
+                                 double* loss_host);
+/* Training pairs from a pool of objects [n_obj][side][side] (complex64): samples int32
+ * [N][3] = (object, row, column); X = physics input of the noiseless pattern of P times the
+ * object patch, T = the patch (Re, Im).  PTYLM_ERR_ARG for samples outside their object. */
+ptylm_status ptylm_net_pairs(ptylm_net* net, const ptylm_c64* pool, int side, const int32_t* samples, int N,
+                             const ptylm_c64* P, float* X, float* T);
+/* `steps` Adam steps (beta 0.9 / 0.999, learning rate lr falling linearly to lr/10) on
+ * batches of fresh pairs drawn uniformly from the pool by a splitmix64 stream seeded with
+ * `seed`; loss per step into loss_hist_host (steps entries, may be NULL).  The loss mask is
+ * the probe's support. */
+ptylm_status ptylm_net_train(ptylm_net* net, const ptylm_c64* pool, int n_obj, int side, const ptylm_c64* P,
+                             int steps, int batch, double lr, uint64_t seed, double* loss_hist_host);
+/* Physics inputs of the context's measurements at positions idx[0..count) (int32 device
+ * array) into X [count][2][128][128]. */
+ptylm_status ptylm_learned_inputs(ptylm_ctx* ctx, ptylm_net* net, const ptylm_c64* P, const int32_t* idx,
+                                  int count, float* X);
+/* Initial object O0 [ny][nx] of the context: physics inputs of positions idx[0..count),
+ * network, |P|^2-weighted overlap average (chunks of max_batch patterns). */
+ptylm_status ptylm_learned_init(ptylm_ctx* ctx, ptylm_net* net, const ptylm_c64* P, const int32_t* idx, int count,
+                                ptylm_c64* O0);
+/* Free the network (NULL is accepted). */
+ptylm_status ptylm_net_destroy(ptylm_net* net);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,10 +6,11 @@ TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``: only ``tests/`` and the 
 ``bench.py`` use it, and it shares no code with the CUDA path.  Plain numpy in float64.
 
 Pipeline, per diffraction pattern y_k (M = m x m pixels, orthonormal DFT F):
-  1. physics input  e_k = F^-1( sqrt(y_k) . F(P) / |F(P)| ) . conj(P) / (|P|^2 + eps max|P|^2)
-     (the far-field magnitudes combined with the probe's own far-field phase, propagated
-     back and divided by the probe: a rough object estimate inside the illuminated disk),
-     as two channels (Re, Im);
+  1. physics input  e_k = F^-1( sqrt(y_k) . u ) . conj(P) / (|P|^2 + eps max|P|^2) with
+     u = F(P) / max(|F(P)|, 1e-3 max|F(P)|) (the far-field magnitudes combined with the
+     probe's own far-field phase, propagated back and divided by the probe: a rough object
+     estimate inside the illuminated disk; u fades where F(P) nearly vanishes, whose phase
+     single precision cannot resolve), as two channels (Re, Im);
   2. a 6-layer convolutional encoder-decoder maps it to the object patch (Re, Im);
   3. the patch estimates are averaged into one object with weights |P|^2 over the
      overlaps; pixels no probe covers keep 1.
@@ -23,6 +24,8 @@ Loss: mean over the probe support (|P| > 0) and both channels of (out - target)^
 from __future__ import annotations
 
 import numpy as np
+
+U_FLOOR = 1e-3   # F(P) / max(|F(P)|, U_FLOOR max|F(P)|): the phasor fades where F(P) nearly vanishes
 
 # (c_in, c_out, stride, upsample, relu) per layer, from the widths (C1, C2, C3)
 def layer_specs(widths=(32, 64, 128)):
@@ -117,7 +120,7 @@ def net_loss_and_grads(params, x, target, mask, widths=(32, 64, 128)):
 def physics_input(y, P, eps=1e-3):
     """e_k of step 1 for y [K, m, m] (natural DFT order) and probe P [m, m]: [K, 2, m, m]."""
     FP = np.fft.fft2(P, norm="ortho")
-    u = FP / np.maximum(np.abs(FP), 1e-30)
+    u = FP / np.maximum(np.abs(FP), U_FLOOR * np.abs(FP).max())
     e = np.fft.ifft2(np.sqrt(np.maximum(y, 0.0)) * u[None], norm="ortho")
     d = np.abs(P) ** 2 + eps * np.max(np.abs(P) ** 2)
     e = e * (np.conj(P) / d)[None]

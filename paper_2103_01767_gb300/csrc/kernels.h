@@ -62,6 +62,17 @@ cudaError_t permute_measurements(int LS, const float* y, float* y_perm, int K, i
 // Record the thread-local message that ptylm_last_error() returns (shared by all entry points).
 void set_last_error(const char* msg);
 
+// Read-only view of a single-problem context for the learned initialisation: measurements
+// in team-register order (sqrt(y) for the Gaussian metric), positions, twiddles, sizes.
+struct CtxView {
+    const float* y_team;
+    const int2* pos;
+    const float2* tw;
+    int K, ny, nx, m, loss, num_sms;
+    cudaStream_t stream;
+};
+bool ctx_view(const struct ptylm_ctx* c, CtxView* v);
+
 // Launch kernel `kid` for patch side 2^LS on `grid` CTAs.
 cudaError_t kernel_launch(int LS, int kid, const PtyArgs& a, int grid, cudaStream_t stream);
 

@@ -330,6 +330,21 @@ static ptylm_status take_event(ptylm_ctx* c, cudaEvent_t* e) {
     return PTYLM_OK;
 }
 
+bool ptylm::ctx_view(const ptylm_ctx* c, CtxView* v) {
+    if (!c || !v) return false;
+    v->y_team = c->y_perm;
+    v->pos = c->pos;
+    v->tw = c->tw;
+    v->K = c->d.K;
+    v->ny = c->d.ny;
+    v->nx = c->d.nx;
+    v->m = c->S;
+    v->loss = c->d.loss;
+    v->num_sms = c->num_sms;
+    v->stream = c->stream;
+    return true;
+}
+
 // Launch a per-position kernel, timing it with events when profiling is on.
 static ptylm_status launch(ptylm_ctx* c, int kid, const PtyArgs& a) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -116,6 +116,23 @@ def load_library():
             lib.ptylm_batch_set_schedule.argtypes = [vp, i]
             lib.ptylm_batch_profile_read.argtypes = [vp, P(ctypes.c_longlong)]
             lib.ptylm_batch_destroy.argtypes = [vp]
+            u64 = ctypes.c_uint64
+            lib.ptylm_net_create.argtypes = [P(vp), i, P(i), i, u64, vp]
+            lib.ptylm_net_num_params.argtypes = [vp]
+            lib.ptylm_net_num_params.restype = ctypes.c_long
+            lib.ptylm_net_set_params.argtypes = [vp, vp]
+            lib.ptylm_net_get_params.argtypes = [vp, vp, vp]
+            lib.ptylm_net_forward.argtypes = [vp, vp, i, vp]
+            lib.ptylm_net_loss_grad.argtypes = [vp, vp, vp, vp, i, P(d)]
+            lib.ptylm_net_pairs.argtypes = [vp, vp, i, vp, i, vp, vp, vp]
+            lib.ptylm_net_train.argtypes = [vp, vp, i, i, vp, i, i, d, u64, vp]
+            lib.ptylm_learned_inputs.argtypes = [vp, vp, vp, vp, i, vp]
+            lib.ptylm_learned_init.argtypes = [vp, vp, vp, vp, i, vp]
+            lib.ptylm_net_destroy.argtypes = [vp]
+            for name in ("ptylm_net_create", "ptylm_net_set_params", "ptylm_net_get_params", "ptylm_net_forward",
+                         "ptylm_net_loss_grad", "ptylm_net_pairs", "ptylm_net_train", "ptylm_learned_inputs",
+                         "ptylm_learned_init", "ptylm_net_destroy"):
+                getattr(lib, name).restype = i
             for name in ("ptylm_batch_init", "ptylm_batch_forward_loss", "ptylm_batch_gradient",
                          "ptylm_batch_ggn_matvec", "ptylm_batch_lm_solve", "ptylm_batch_tune",
                          "ptylm_batch_set_schedule", "ptylm_batch_profile_read", "ptylm_batch_destroy"):
@@ -449,3 +466,85 @@ def batch_lm_solve(batch: Batch, O, params=None, hist_len: int = 0, O_refs=None,
                         err_final=st.err_final, f=hf[:n].copy(), gnorm=hg[:n].copy(), mu=hmu[:n].copy(),
                         cg=hcg[:n].copy(), err=herr[:n].copy()))
     return status, out
+
+
+# ---------------------------------------------------------------------------------------
+# Learned initialisation (128 x 128 patterns)
+# ---------------------------------------------------------------------------------------
+class Net:
+    """Owns one C network (ptylm_net_create ... ptylm_net_destroy)."""
+
+    def __init__(self, handle, widths, max_batch):
+        self.handle = handle
+        self.widths = tuple(widths)
+        self.max_batch = max_batch
+
+    @property
+    def num_params(self):
+        return int(load_library().ptylm_net_num_params(self.handle))
+
+    def close(self):
+        if self.handle:
+            _check(load_library().ptylm_net_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def net_create(widths=(32, 64, 128), max_batch=64, seed=0, m=128, stream=None) -> Net:
+    w = (ctypes.c_int * 3)(*[int(x) for x in widths])
+    h = ctypes.c_void_p()
+    _check(load_library().ptylm_net_create(ctypes.byref(h), int(m), w, int(max_batch), int(seed), _stream_ptr(stream)))
+    return Net(h, widths, max_batch)
+
+
+def net_set_params(net: Net, params) -> None:
+    p = np.ascontiguousarray(params, np.float32)
+    if p.size != net.num_params:
+        raise ValueError(f"expected {net.num_params} parameters, got {p.size}")
+    _check(load_library().ptylm_net_set_params(net.handle, p.ctypes.data))
+
+
+def net_get_params(net: Net):
+    """(params, grads of the last loss_grad / training step) as float32 numpy arrays."""
+    p = np.empty(net.num_params, np.float32)
+    g = np.empty(net.num_params, np.float32)
+    _check(load_library().ptylm_net_get_params(net.handle, p.ctypes.data, g.ctypes.data))
+    return p, g
+
+
+def net_forward(net: Net, X, out, N=None) -> None:
+    N = int(X.shape[0]) if N is None else int(N)
+    _check(load_library().ptylm_net_forward(net.handle, _ptr(X), N, _ptr(out)))
+
+
+def net_loss_grad(net: Net, X, T, mask, N=None) -> float:
+    N = int(X.shape[0]) if N is None else int(N)
+    loss = ctypes.c_double()
+    _check(load_library().ptylm_net_loss_grad(net.handle, _ptr(X), _ptr(T), _ptr(mask), N, ctypes.byref(loss)))
+    return loss.value
+
+
+def net_pairs(net: Net, pool, side, samples, P, X, T) -> None:
+    _check(load_library().ptylm_net_pairs(net.handle, _ptr(pool), int(side), _ptr(samples), int(samples.shape[0]),
+                                          _ptr(P), _ptr(X), _ptr(T)))
+
+
+def net_train(net: Net, pool, n_obj, side, P, steps, batch, lr=1e-3, seed=0):
+    """Returns the per-step loss history (numpy)."""
+    hist = np.zeros(max(1, int(steps)))
+    _check(load_library().ptylm_net_train(net.handle, _ptr(pool), int(n_obj), int(side), _ptr(P), int(steps),
+                                          int(batch), float(lr), int(seed), hist.ctypes.data))
+    return hist[:int(steps)]
+
+
+def learned_inputs(ctx: Context, net: Net, P, idx, X) -> None:
+    _check(load_library().ptylm_learned_inputs(ctx.handle, net.handle, _ptr(P), _ptr(idx), int(idx.shape[0]), _ptr(X)))
+
+
+def learned_init(ctx: Context, net: Net, P, idx, O0) -> None:
+    _check(load_library().ptylm_learned_init(ctx.handle, net.handle, _ptr(P), _ptr(idx), int(idx.shape[0]), _ptr(O0)))

@@ -1,0 +1,144 @@
+"""Learned initialisation on the GPU against its FP64 oracle (oracle/learned.py): physics
+input, training pairs, network forward and gradients (bfloat16 weights on both sides, FP32
+arithmetic on the GPU), the stitched initial object, and training that lowers the loss.
+
+Tolerances: 1e-5 relative for the FFT-based inputs (the FP32 bound of the forward model);
+1e-4 for network outputs and gradients, whose FP32 sums run over up to 1152 products per
+output and 2 x 128^2 x 9 products per weight gradient."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import learned as L
+from paper_2103_01767_gb300 import synth
+from tests.problems import make_case, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+M = 128
+WIDTHS = (16, 32, 48)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_01767_gb300 import build, ptylm
+    build.build()
+    ptylm.load_library()
+    return ptylm
+
+
+def c64(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.complex64)).cuda()
+
+
+def f32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def probe():
+    return synth.to_c64(synth.probe_disk_defocus(M, 40.0))
+
+
+def flat_params(params):
+    return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in params]).astype(np.float32)
+
+
+def bf16_params(params):
+    return [(L.to_bf16(W), np.asarray(b, np.float32).astype(np.float64)) for W, b in params]
+
+
+def test_training_pairs_match_the_oracle(lib):
+    pool = np.stack([synth.to_c64(synth.object_texture(160, seed=s)) for s in (1, 2)])
+    P = probe()
+    samples = np.array([[0, 5, 7], [1, 20, 31], [0, 32, 0], [1, 0, 32]], np.int32)
+    net = lib.net_create(WIDTHS, max_batch=4)
+    X = torch.empty((4, 2, M, M), dtype=torch.float32, device="cuda")
+    T = torch.empty_like(X)
+    lib.net_pairs(net, c64(pool), 160, torch.from_numpy(samples).cuda(), c64(P), X, T)
+    for i, (o, r, c) in enumerate(samples):
+        patch = pool[o, r:r + M, c:c + M].astype(np.complex128)
+        y = np.abs(np.fft.fft2(P * patch, norm="ortho")) ** 2
+        ref = L.physics_input(y[None], P)[0]
+        assert rel_err(X[i].cpu().numpy(), ref) <= 1e-5, i
+        assert np.array_equal(T[i, 0].cpu().numpy(), patch.real.astype(np.float32))
+        assert np.array_equal(T[i, 1].cpu().numpy(), patch.imag.astype(np.float32))
+    bad = torch.from_numpy(np.array([[0, 40, 0]], np.int32)).cuda()   # 40 + 128 > 160
+    with pytest.raises(lib.PtylmError):
+        lib.net_pairs(net, c64(pool), 160, bad, c64(P), X, T)
+
+
+@pytest.mark.parametrize("loss", [0, 1])
+def test_physics_inputs_from_a_context(lib, loss):
+    case = make_case(288, M, K=9, loss=loss, peak=1e3 if loss else 0.0, seed=60 + loss, noisy=False)
+    ctx = lib.lm_init(288, 288, M, M, torch.from_numpy(case.pos).cuda(), f32(case.y), loss, case.b)
+    net = lib.net_create(WIDTHS, max_batch=4)
+    idx = np.array([0, 4, 8], np.int32)
+    X = torch.empty((3, 2, M, M), dtype=torch.float32, device="cuda")
+    lib.learned_inputs(ctx, net, c64(case.P), torch.from_numpy(idx).cuda(), X)
+    ref = L.physics_input(case.y[idx], case.P)
+    assert rel_err(X.cpu().numpy(), ref) <= 1e-5
+
+
+def test_network_forward_and_gradients_match_the_oracle(lib):
+    params = L.init_params(WIDTHS, seed=3)
+    # non-zero biases so they take part in the comparison
+    params = [(W, 0.05 * np.random.default_rng(10 + l).standard_normal(b.shape)) for l, (W, b) in enumerate(params)]
+    net = lib.net_create(WIDTHS, max_batch=2, seed=1)
+    lib.net_set_params(net, flat_params(params))
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((2, 2, M, M)).astype(np.float32)
+    T = rng.standard_normal((2, 2, M, M)).astype(np.float32)
+    mask = (np.abs(probe()) > 0).astype(np.float32)
+    out = torch.empty((2, 2, M, M), dtype=torch.float32, device="cuda")
+    lib.net_forward(net, f32(X), out)
+    pb = bf16_params(params)
+    acts = L.net_forward(pb, X.astype(np.float64), WIDTHS)
+    assert rel_err(out.cpu().numpy(), acts[-1]) <= 1e-4
+    loss = lib.net_loss_grad(net, f32(X), f32(T), f32(mask))
+    loss_ref, grads_ref = L.net_loss_and_grads(pb, X.astype(np.float64), T.astype(np.float64), mask.astype(np.float64),
+                                               WIDTHS)
+    assert abs(loss - loss_ref) <= 1e-5 * loss_ref
+    _, g = lib.net_get_params(net)
+    off = 0
+    for l, (dW, db) in enumerate(grads_ref):
+        gw = g[off:off + dW.size].reshape(dW.shape)
+        off += dW.size
+        gb = g[off:off + db.size]
+        off += db.size
+        assert rel_err(gw, dW) <= 1e-4, l
+        assert rel_err(gb, db) <= 1e-4, l
+
+
+def test_stitched_initial_object_matches_the_oracle(lib):
+    case = make_case(256, M, K=12, loss=0, seed=70, noisy=False)
+    ctx = lib.lm_init(256, 256, M, M, torch.from_numpy(case.pos).cuda(), f32(case.y), 0, case.b)
+    params = L.init_params(WIDTHS, seed=5)
+    net = lib.net_create(WIDTHS, max_batch=5, seed=2)   # 12 positions -> chunks of 5, 5, 2
+    lib.net_set_params(net, flat_params(params))
+    idx = np.arange(12, dtype=np.int32)
+    O0 = torch.empty((256, 256), dtype=torch.complex64, device="cuda")
+    lib.learned_init(ctx, net, c64(case.P), torch.from_numpy(idx).cuda(), O0)
+    e = L.physics_input(case.y, case.P)
+    acts = L.net_forward(bf16_params(params), e, WIDTHS)
+    patches = acts[-1][:, 0] + 1j * acts[-1][:, 1]
+    ref = L.stitch(patches, case.pos, case.P, (256, 256))
+    assert rel_err(O0.cpu().numpy(), ref) <= 1e-4
+
+
+def test_training_lowers_the_loss(lib):
+    pool = np.stack([synth.to_c64(synth.object_texture(256, seed=s)) for s in range(4)])
+    net = lib.net_create(WIDTHS, max_batch=16, seed=7)
+    hist = lib.net_train(net, c64(pool), 4, 256, c64(probe()), steps=300, batch=16, lr=2e-3, seed=11)
+    assert np.all(np.isfinite(hist))
+    assert hist[-30:].mean() < 0.5 * hist[:10].mean(), (hist[:10].mean(), hist[-30:].mean())
+
+
+def test_learned_argument_errors(lib):
+    with pytest.raises(lib.PtylmError) as e:
+        lib.net_create((16, 24, 32))
+    assert e.value.status == lib.PTYLM_ERR_ARG
+    with pytest.raises(lib.PtylmError):
+        lib.net_create(WIDTHS, m=64)
