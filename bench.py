@@ -389,6 +389,79 @@ def gpu_time_to_accuracy(ptylm, torch, dev, stream, target=1e-3, reps=5, large_r
     return out
 
 
+def learned_vs_plain(ptylm, torch, dev, target=1e-3, pairs=200_000, batch=64, reps=3):
+    """Learned initialisation against the flat start (plain LM, Algorithm 1, D = I) on a
+    held-out 1024^2 object / 3600 positions / 128^2 probe with noiseless amplitude data:
+    train the 6-layer network on `pairs` forward-model pairs cut from 8 other random objects,
+    then time, from the data resident on the device, (a) LM from the flat start and (b) the
+    stitched network estimate from every 4th raster row and column (225 patterns) followed
+    by LM, each to object error <= target against the ground truth (median of reps)."""
+    n, m, R = 1024, 128, 40.0
+    c64 = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.complex64)).to(dev)
+    P = c64(synth.probe_disk_defocus(m, R))
+    pool = c64(np.stack([synth.object_texture(n, seed=100 + s) for s in range(8)]))
+    widths = (32, 64, 128)
+    net = ptylm.net_create(widths, max_batch=batch, seed=1)
+    steps = pairs // batch
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    hist = ptylm.net_train(net, pool, 8, n, P, steps=steps, batch=batch, lr=2e-3, seed=5)
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    del pool
+    O_true = c64(synth.object_texture(n, seed=0))
+    pos_np, _ = synth.raster_positions(n, m, 60, 16, 2, seed=1)
+    pos = torch.from_numpy(pos_np).to(dev)
+    y = torch.empty((pos_np.shape[0], m, m), dtype=torch.float32, device=dev)
+    ctx = ptylm.lm_init(n, n, m, m, pos, y, 0, 1e-8)
+    ptylm.forward_intensity(ctx, O_true, P, y)
+    ptylm.ptylm_set_measurements(ctx, y)
+    mask = torch.from_numpy(synth.illumination_mask(n, P.cpu().numpy(), pos_np, 0.1).astype(np.uint8)).to(dev)
+    idx = torch.from_numpy(np.array([i * 60 + j for i in range(0, 60, 4) for j in range(0, 60, 4)], np.int32)).to(dev)
+    flat = torch.full((n, n), complex(float(O_true.abs().mean()), 0.0), dtype=torch.complex64, device=dev)
+    O0 = torch.empty_like(flat)
+
+    def run(start_learned):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        if start_learned:
+            ptylm.learned_init(ctx, net, P, idx, O0)
+            O = O0.clone()
+        else:
+            O = flat.clone()
+        t_init = time.perf_counter() - t0
+        _, info = ptylm.lm_solve(ctx, O, P, hist_len=200, O_ref=O_true, mask=mask, max_outer=200, target_err=target)
+        return time.perf_counter() - t0, t_init, info
+
+    out = {"network": {"widths": list(widths), "params": net.num_params, "pairs": steps * batch,
+                       "train_s": train_s, "loss_first": float(hist[:20].mean()), "loss_last": float(hist[-50:].mean())},
+           "workload": "held-out 1024^2 object, 3600 positions, 128^2 probe, noiseless amplitude data, "
+                       "reference = ground truth"}
+    for name, learned in (("plain", False), ("learned", True)):
+        runs = [run(learned) for _ in range(reps + 1)][1:]   # first run warms the path
+        secs = sorted(r[0] for r in runs)
+        info = runs[0][2]
+        err = info["err"][np.isfinite(info["err"])]
+        out[name] = {"seconds": statistics.median(secs), "init_ms": 1e3 * statistics.median(r[1] for r in runs),
+                     "outer": int(info["n_outer"]), "cg": int(info["cg_total"]),
+                     "reached": bool(err.size and err[-1] <= target)}
+    ptylm.learned_init(ctx, net, P, idx, O0)
+    out["learned"]["start_err"] = _object_error(O0, O_true, mask)
+    out["plain"]["start_err"] = _object_error(flat, O_true, mask)
+    out["speedup"] = out["plain"]["seconds"] / out["learned"]["seconds"]
+    ptylm.lm_destroy(ctx)
+    net.close()
+    return out
+
+
+def _object_error(O, O_ref, mask):
+    """Phase-aligned relative error over the mask (host arithmetic on the copies; reporting only)."""
+    a = O.cpu().numpy().astype(np.complex128)[mask.cpu().numpy().astype(bool)]
+    b = O_ref.cpu().numpy().astype(np.complex128)[mask.cpu().numpy().astype(bool)]
+    c = np.vdot(a, b)
+    return float(np.linalg.norm(a * (c / abs(c)) - b) / np.linalg.norm(b))
+
+
 # ---------------------------------------------------------------------------------------
 # Batch of 64 independent reconstructions (one persistent launch per operator)
 # ---------------------------------------------------------------------------------------
@@ -637,6 +710,7 @@ def main():
         tta = gpu_time_to_accuracy(ptylm, torch, dev, stream)
         if oracle_tta is not None:
             tta["small"]["oracle"] = oracle_tta
+        tta["learned_vs_plain"] = learned_vs_plain(ptylm, torch, dev)
     avg_mv_s = (mv_ms / 1e3) / max(mv_n, 1)
     flops = matvec_flops(K, M)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
