@@ -158,6 +158,37 @@ __device__ __forceinline__ void scatter_times_conj_probe(const float2* v, float2
     }
 }
 
+// Scatter of one position fused with the gather of the next, which share the probe values
+// (the same thread layout): per chunk of 8 rows one probe load serves
+//   out[r0 + y][c0 + x] += conj(P[y][x]) v[a]        (this position, Eq. jac_ampl adjoint)
+//   v[a] = P[y][x] A[r1 + y][c1 + x]                  (next position, Eq. exit_wave)
+// and the next position's object loads are in flight while the reductions issue, so the
+// two memory phases cost one round trip per chunk instead of two.
+template <class G>
+__device__ __forceinline__ void scatter_then_gather(float2* v, float2* out, const float2* __restrict__ A,
+                                                    const float2* __restrict__ P, int nx, int r0, int c0,
+                                                    int r1, int c1, int tid) {
+    const int x = tid & (G::S - 1), b = tid >> G::LOG_S;
+    float2* dst = out + (size_t)(r0 + b) * nx + c0 + x;
+    const float2* src = A + (size_t)(r1 + b) * nx + c1 + x;
+    const float2* pr = P + b * G::S + x;
+    const size_t row_step = (size_t)G::BX * nx;
+#pragma unroll
+    for (int a0 = 0; a0 < 32; a0 += 8) {
+        float2 pv[8], av[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            pv[i] = pr[G::BX * G::S * (a0 + i)];
+            av[i] = __ldg(src + row_step * (a0 + i));
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) red_add_c64(dst + row_step * (a0 + i), cmulc(v[a0 + i], pv[i]));
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[a0 + i] = cmul(pv[i], av[i]);
+        sched_fence();
+    }
+}
+
 // Joint gather (Eq. jac_ampl with both blocks): v[a] = P[y][x] A[r0+y][c0+x] + B[y][x] C[r0+y][c0+x],
 // i.e. P . S_k dO + dP . S_k O for the direction (A, B) = (dO, dP) at the object C.
 template <class G>

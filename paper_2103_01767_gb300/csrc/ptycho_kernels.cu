@@ -81,13 +81,24 @@ k_forward(FwdArgs a) {
     const float invS = 1.0f / G::S;
     double acc_l = 0.0, acc_d = 0.0;
     const int ky = freq_ky<G>(c.tid);
+    const int stride = gridDim.x * G::TEAMS;
+    // 128^2 object-only linearisations fuse each position's gradient scatter with the next
+    // position's gather (one probe load serves both), as the GGN product does.
+    constexpr bool FUSED = CACHE && LS == 7 && !JOINT && !INTENSITY && !MAG;
     float2 v[32];
-    for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
+    int k = blockIdx.x * G::TEAMS + c.team;
+    if constexpr (FUSED) {
+        if (k < a.K) {
+            const int2 rc = a.pos[k];
+            gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
+        }
+    }
+    for (; k < a.K; k += stride) {
         const int2 rc = a.pos[k];
         const float* yk = a.y + (size_t)k * G::M + c.tid;  // measurements in team-register order
         if constexpr (!INTENSITY && !MAG) prefetch_tile_l2(a.y + (size_t)k * G::M, sizeof(float) * G::M, c.tid);
         float sl = 0.0f, sd = 0.0f;
-        gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
+        if constexpr (!FUSED) gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
         if constexpr (CACHE) {
             float2* ak = a.a_cache + (size_t)k * G::M;
             float s2 = 0.0f;  // sum of d2l over this thread's pixels (closed-form diagonal)
@@ -108,7 +119,17 @@ k_forward(FwdArgs a) {
                 store_cache_group<G>(ak, av, j);
             });
             if (a.trp) a.trp[(size_t)k * G::T + c.tid] = s2;
-            scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
+            if constexpr (FUSED) {
+                const int kn = k + stride;
+                if (kn < a.K) {
+                    const int2 rn = a.pos[kn];
+                    scatter_then_gather<G>(v, a.out, a.O, a.P, a.nx, rc.x, rc.y, rn.x, rn.y, c.tid);
+                } else {
+                    scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
+                }
+            } else {
+                scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
+            }
             if constexpr (JOINT)
                 accumulate_probe_adjoint<G>(v, a.outP_part + (size_t)(blockIdx.x * G::TEAMS + c.team) * G::M,
                                             a.O, a.nx, rc.x, rc.y, c.tid);
@@ -151,13 +172,27 @@ k_ggn_matvec(MatvecArgs a) {
     using G = Geo<LS>;
     TeamCtx<G> c = team_setup<G>(a.tw);
     const float invM = 1.0f / G::M;
+    const int stride = gridDim.x * G::TEAMS;
+    // 128^2 object-only products fuse each position's scatter with the next one's gather
+    // (one probe load serves both); elsewhere the registers this keeps live across the
+    // loop would spill.
+    constexpr bool FUSED = LS == 7 && !JOINT;
     float2 v[32];
-    for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
+    int k = blockIdx.x * G::TEAMS + c.team;
+    if constexpr (FUSED) {
+        if (k < a.K) {
+            const int2 rc = a.pos[k];
+            gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
+        }
+    }
+    for (; k < a.K; k += stride) {
         const int2 rc = a.pos[k];
-        prefetch_tile_l2(a.a_cache + (size_t)k * G::M, sizeof(float2) * G::M, c.tid);
-        if constexpr (JOINT) gather_joint<G>(v, a.O, a.P, a.VP, a.Olin, a.nx, rc.x, rc.y, c.tid);
-        else gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
         const float2* ak = a.a_cache + (size_t)k * G::M;
+        prefetch_tile_l2(ak, sizeof(float2) * G::M, c.tid);
+        if constexpr (!FUSED) {
+            if constexpr (JOINT) gather_joint<G>(v, a.O, a.P, a.VP, a.Olin, a.nx, rc.x, rc.y, c.tid);
+            else gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
+        }
         team_fft_roundtrip<G>(v, c.sm, c.tw, c.tid, [&](float2* g, int j) {
             float2 av[G::BY];
             load_cache_group<G>(ak, av, j, c.tid);
@@ -167,10 +202,20 @@ k_ggn_matvec(MatvecArgs a) {
                 g[k2y] = av[k2y] * t;
             }
         });
-        scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
-        if constexpr (JOINT)
-            accumulate_probe_adjoint<G>(v, a.outP_part + (size_t)(blockIdx.x * G::TEAMS + c.team) * G::M, a.Olin,
-                                        a.nx, rc.x, rc.y, c.tid);
+        if constexpr (FUSED) {
+            const int kn = k + stride;
+            if (kn < a.K) {
+                const int2 rn = a.pos[kn];
+                scatter_then_gather<G>(v, a.out, a.O, a.P, a.nx, rc.x, rc.y, rn.x, rn.y, c.tid);
+            } else {
+                scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
+            }
+        } else {
+            scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
+            if constexpr (JOINT)
+                accumulate_probe_adjoint<G>(v, a.outP_part + (size_t)(blockIdx.x * G::TEAMS + c.team) * G::M, a.Olin,
+                                            a.nx, rc.x, rc.y, c.tid);
+        }
         // No barrier before the next position: its first shared-memory writes go to the
         // slots this same thread read last (team_fft_roundtrip).
     }
