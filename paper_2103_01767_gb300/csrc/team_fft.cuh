@@ -213,7 +213,7 @@ template <class G>
 __device__ __forceinline__ void pass1_fwd(float2* v, const float2* tw, int t1) {
     RegDFT<32, false>::run(v);
     if constexpr (G::BX > 1) {
-        const int bx = t1 >> G::LOG_S;
+        const int bx = (t1 >> G::LOG_S) & (G::BX - 1);
 #pragma unroll
         for (int k0 = 0; k0 < 32; k0 += 8) {
             float2 w[8];
@@ -248,7 +248,7 @@ __device__ __forceinline__ void ex1_load_to_p1(const float2* sm, float2* v, int 
 // pass-2 register layout: v[ay*BX + bx] (before pass 2) / v[k1y*BX + k2x] (after)
 template <class G>
 __device__ __forceinline__ void ex1_load_to_p2(const float2* sm, float2* v, int t2) {
-    const int k1x = t2 & 31, by = t2 >> 5;
+    const int k1x = t2 & 31, by = (t2 >> 5) & (G::BY - 1);  // t2 < T = 32 BY: the mask states the range
 #pragma unroll
     for (int ay = 0; ay < G::AY; ++ay)
 #pragma unroll
@@ -259,7 +259,7 @@ __device__ __forceinline__ void ex1_load_to_p2(const float2* sm, float2* v, int 
 }
 template <class G>
 __device__ __forceinline__ void ex1_store_from_p2(float2* sm, const float2* v, int t2) {
-    const int k1x = t2 & 31, by = t2 >> 5;
+    const int k1x = t2 & 31, by = (t2 >> 5) & (G::BY - 1);  // t2 < T = 32 BY: the mask states the range
 #pragma unroll
     for (int ay = 0; ay < G::AY; ++ay)
 #pragma unroll
@@ -277,7 +277,7 @@ __device__ __forceinline__ void pass2_fwd(float2* v, const float2* tw, int t2) {
 #pragma unroll
     for (int k2x = 0; k2x < G::BX; ++k2x) dft_strided<G::AY, G::BX, false>(v, k2x);
     if constexpr (G::BY > 1) {
-        const int by = t2 >> 5;
+        const int by = (t2 >> 5) & (G::BY - 1);  // t2 < T = 32 BY: the mask states the range
 #pragma unroll
         for (int k1y = 1; k1y < G::AY; ++k1y) {
             const float2 w = tw[by * k1y];
@@ -291,7 +291,7 @@ template <class G>
 __device__ __forceinline__ void pass2_inv(float2* v, const float2* tw, int t2) {
     const int k1x = t2 & 31;
     if constexpr (G::BY > 1) {
-        const int by = t2 >> 5;
+        const int by = (t2 >> 5) & (G::BY - 1);  // t2 < T = 32 BY: the mask states the range
 #pragma unroll
         for (int k1y = 1; k1y < G::AY; ++k1y) {
             const float2 w = tw[by * k1y];
@@ -320,7 +320,7 @@ __device__ __forceinline__ int ex2_slot(int k2x, int k1y, int by, int k1x) {
 }
 template <class G>
 __device__ __forceinline__ void ex2_store_from_p2(float2* sm, const float2* v, int t2) {
-    const int k1x = t2 & 31, by = t2 >> 5;
+    const int k1x = t2 & 31, by = (t2 >> 5) & (G::BY - 1);  // t2 < T = 32 BY: the mask states the range
 #pragma unroll
     for (int k1y = 0; k1y < G::AY; ++k1y)
 #pragma unroll
@@ -329,7 +329,7 @@ __device__ __forceinline__ void ex2_store_from_p2(float2* sm, const float2* v, i
 }
 template <class G>
 __device__ __forceinline__ void ex2_load_to_p2(const float2* sm, float2* v, int t2) {
-    const int k1x = t2 & 31, by = t2 >> 5;
+    const int k1x = t2 & 31, by = (t2 >> 5) & (G::BY - 1);  // t2 < T = 32 BY: the mask states the range
 #pragma unroll
     for (int k1y = 0; k1y < G::AY; ++k1y)
 #pragma unroll
@@ -434,7 +434,7 @@ __device__ __forceinline__ void team_fft_roundtrip(float2* v, float2* sm, const 
         team_sync<G>();  // all ex1 reads done before ex2 overwrites
         ex2_store_from_p2<G>(sm, v, tid);
         team_sync<G>();
-        const int k1x = tid & 31, k2x = (tid & (G::S - 1)) >> 5, k1y0 = tid >> G::LOG_S;
+        const int k1x = tid & 31, k2x = (tid & (G::S - 1)) >> 5, k1y0 = (tid >> G::LOG_S) & (G::BX - 1);
 #pragma unroll 1
         for (int j = 0; j < G::G3; ++j) {
             float2 g[G::BY];
