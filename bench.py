@@ -680,6 +680,14 @@ def main():
         torch.cuda.synchronize(dev)
     elapsed = ev0.elapsed_time(ev1) / 1e3
     mv_ms, mv_n = ptylm.ptylm_profile_read(ctx, ptylm.KERNEL_GGN_MATVEC_JOINT if w.joint else ptylm.KERNEL_GGN_MATVEC)
+    per_kernel = {}
+    for name, kid in (("forward_cache", ptylm.KERNEL_FORWARD_CACHE_JOINT if w.joint else ptylm.KERNEL_FORWARD_CACHE),
+                      ("forward_loss", ptylm.KERNEL_FORWARD_LOSS),
+                      ("ggn_matvec", ptylm.KERNEL_GGN_MATVEC_JOINT if w.joint else ptylm.KERNEL_GGN_MATVEC)):
+        ms_k, n_k = ptylm.ptylm_profile_read(ctx, kid)
+        if n_k:
+            per_kernel[name] = {"avg_us": 1e3 * ms_k / n_k, "launches": int(n_k),
+                                "share_of_step": ms_k / (1e3 * elapsed) if elapsed > 0 else None}
     _, launches = ptylm.ptylm_profile_read(ctx, -1)
     ptylm.ptylm_profile(ctx, False)
     elapsed, total_matvecs = reduce_over_ranks(elapsed, matvecs, dev)
@@ -741,6 +749,7 @@ def main():
                     "d2h_bytes_per_step": 8 * N},
             "clocks": clocks,
             "gpu_launches": int(launches),
+            "kernels": per_kernel,
             "comparison": comparison,
             "time_to_accuracy": tta,
         }
