@@ -223,6 +223,40 @@ def time_oracle_matvec(w, budget_s=15.0):
     return (n / w.K) / dt, dt, n, oracle.num_threads()
 
 
+def oracle_op_table(budget_s=1.0):
+    """The oracle's forward_loss, J^T w and GGN product at the three single-problem
+    workloads, each on a position sample sized for about budget_s seconds and scaled to the
+    full K, on all host threads; the GGN product also on one thread."""
+    import oracle
+    oracle.build()
+    threads = oracle.num_threads()
+    table = {"threads": threads}
+    for w in (synth.SMALL, synth.MEDIUM, synth.LARGE):
+        pb, O, v = oracle_sample_problem(w, 4)
+        t0 = time.perf_counter()
+        oracle.ggn_matvec(pb, O, v, lam=1e-3)
+        per = (time.perf_counter() - t0) / 4
+        n = int(min(w.K, max(4, budget_s / max(per, 1e-6))))
+        pb, O, v = oracle_sample_problem(w, n)
+        wts = synth.random_real((n, w.m, w.m), seed=4)
+        row = {"positions_timed": n}
+        for name, fn in (("forward_loss_s", lambda: oracle.loss(pb, O)),
+                         ("jtvp_s", lambda: oracle.jtvp(pb, O, wts)),
+                         ("ggn_matvec_s", lambda: oracle.ggn_matvec(pb, O, v, lam=1e-3))):
+            t0 = time.perf_counter()
+            fn()
+            row[name] = (time.perf_counter() - t0) * w.K / n
+        n1 = max(2, n // threads)
+        pb1, O1, v1 = oracle_sample_problem(w, n1)
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        oracle.ggn_matvec(pb1, O1, v1, lam=1e-3)
+        row["ggn_matvec_1thread_s"] = (time.perf_counter() - t0) * w.K / n1
+        oracle.set_threads(threads)
+        table[w.name] = row
+    return table
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -639,6 +673,7 @@ def main():
     oracle_tta = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_extras:
         oracle_tta = oracle_time_to_accuracy()
+        cpu["ops_full_K"] = oracle_op_table()
 
     from paper_2103_01767_gb300 import build as _build
     _build.build()
