@@ -673,7 +673,9 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
         const int need = std::max(1, (d.K + teams - 1) / teams);
         c->grid[kid] = std::min(per_sm * c->num_sms, need);
     }
-    c->vec_grid = std::min<long>(c->num_sms * 8L, std::max<long>(1, (c->L + VEC_THREADS - 1) / VEC_THREADS));
+    // 4 CTAs per SM: enough loads in flight for the vector streams, and few enough partial
+    // sums that the last CTA of each FP64 reduction finishes quickly
+    c->vec_grid = std::min<long>(c->num_sms * 4L, std::max<long>(1, (c->L + VEC_THREADS - 1) / VEC_THREADS));
     c->probe_slots = d.joint ? std::max({c->grid[KID_FWD_CACHE_J], c->grid[KID_MATVEC_J], c->grid[KID_JTVP_J]}) * teams : 0;
     c->partials_cap = std::max(c->vec_grid, *std::max_element(c->grid, c->grid + KID_COUNT));
 
