@@ -4,6 +4,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "team_fft.cuh"
 
 namespace ptylm {
@@ -56,6 +58,18 @@ __device__ __forceinline__ void load_cache_group(const float2* ak, float2* av, i
         av[0] = __ldcs(ak + j * G::T + tid);
     }
 }
+
+// Asynchronous copy of `bytes` (a multiple of 16, both ends 16-byte aligned) from global to
+// shared memory by the team's threads in 16-byte pieces; the caller waits with
+// cp_async_wait_all() and a team barrier before any thread reads the copy.
+__device__ __forceinline__ void cp_async_tile(void* dst_smem, const void* src, unsigned bytes, int tid, int nthreads) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst_smem));
+    const char* s = reinterpret_cast<const char*>(src);
+    for (unsigned off = 16u * tid; off < bytes; off += 16u * nthreads)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + off), "l"(s + off) : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Per-pixel error-metric terms of Sec. 4.1 Eq. ell_magnitude, from h = |psihat|^2 + b and
 // the stored measurement term ym (sqrt(y) for the Gaussian metric, y for Poisson):

@@ -73,6 +73,10 @@ struct AdjArgs {          // J^T w and J v
 // Forward model + error metric (+ cache and gradient when CACHE; intensities only when
 // INTENSITY).
 // ---------------------------------------------------------------------------------------
+// Whether k_forward stages the measurements in shared memory (it then needs 4 M more bytes).
+template <int LS, bool CACHE, bool INTENSITY, bool JOINT, bool MAG>
+__host__ __device__ constexpr bool forward_stages_y() { return LS == 7 && !INTENSITY && !JOINT && !MAG; }
+
 template <int LS, bool CACHE, bool INTENSITY = false, bool JOINT = false, bool MAG = false>
 __global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
 k_forward(FwdArgs a) {
@@ -85,6 +89,11 @@ k_forward(FwdArgs a) {
     // 128^2 object-only linearisations fuse each position's gradient scatter with the next
     // position's gather (one probe load serves both), as the GGN product does.
     constexpr bool FUSED = CACHE && LS == 7 && !JOINT && !INTENSITY && !MAG;
+    // 128^2 object-only error-metric evaluations (with or without the cache) stage each
+    // position's measurements (64 KB) in shared memory with asynchronous copies issued
+    // before the FFT, instead of waiting on 32 dependent loads per thread after it.
+    constexpr bool STAGE_Y = forward_stages_y<LS, CACHE, INTENSITY, JOINT, MAG>();
+    float* sy = reinterpret_cast<float*>(c.sm + G::M);
     float2 v[32];
     int k = blockIdx.x * G::TEAMS + c.team;
     if constexpr (FUSED) {
@@ -96,28 +105,35 @@ k_forward(FwdArgs a) {
     for (; k < a.K; k += stride) {
         const int2 rc = a.pos[k];
         const float* yk = a.y + (size_t)k * G::M + c.tid;  // measurements in team-register order
-        if constexpr (!INTENSITY && !MAG) prefetch_tile_l2(a.y + (size_t)k * G::M, sizeof(float) * G::M, c.tid);
+        if constexpr (STAGE_Y) cp_async_tile(sy, a.y + (size_t)k * G::M, sizeof(float) * G::M, c.tid, G::T);
+        else if constexpr (!INTENSITY && !MAG) prefetch_tile_l2(a.y + (size_t)k * G::M, sizeof(float) * G::M, c.tid);
         float sl = 0.0f, sd = 0.0f;
         if constexpr (!FUSED) gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
         if constexpr (CACHE) {
             float2* ak = a.a_cache + (size_t)k * G::M;
             float s2 = 0.0f;  // sum of d2l over this thread's pixels (closed-form diagonal)
-            team_fft_roundtrip<G>(v, c.sm, c.tw, c.tid, [&](float2* g, int j) {
-                float2 av[G::BY];
+            team_fft_roundtrip<G>(
+                v, c.sm, c.tw, c.tid,
+                [&](float2* g, int j) {
+                    float2 av[G::BY];
 #pragma unroll
-                for (int k2y = 0; k2y < G::BY; ++k2y) {
-                    const int e = j * G::BY + k2y;
-                    const float2 ps = g[k2y] * invS;                    // orthonormal psihat
-                    const float h = ps.x * ps.x + ps.y * ps.y + a.b;    // Eq. expected_count
-                    const PixelTerms t = pixel_terms<true>(a.loss, h, __ldg(yk + e * G::T));
-                    sl += t.l;
-                    sd += t.dl * t.dl;
-                    s2 += t.d2l;
-                    av[k2y] = ps * t.sqrt_d2l_over_zeta;
-                    g[k2y] = ps * (t.dl_over_zeta * invS);  // psihat grad l / zeta, inverse 1/S folded in
-                }
-                store_cache_group<G>(ak, av, j);
-            });
+                    for (int k2y = 0; k2y < G::BY; ++k2y) {
+                        const int e = j * G::BY + k2y;
+                        const float2 ps = g[k2y] * invS;                    // orthonormal psihat
+                        const float h = ps.x * ps.x + ps.y * ps.y + a.b;    // Eq. expected_count
+                        const float ym = STAGE_Y ? sy[e * G::T + c.tid] : __ldg(yk + e * G::T);
+                        const PixelTerms t = pixel_terms<true>(a.loss, h, ym);
+                        sl += t.l;
+                        sd += t.dl * t.dl;
+                        s2 += t.d2l;
+                        av[k2y] = ps * t.sqrt_d2l_over_zeta;
+                        g[k2y] = ps * (t.dl_over_zeta * invS);  // psihat grad l / zeta, inverse 1/S folded in
+                    }
+                    store_cache_group<G>(ak, av, j);
+                },
+                [&] {
+                    if constexpr (STAGE_Y) cp_async_wait_all();   // the pass-3 barrier follows
+                });
             if (a.trp) a.trp[(size_t)k * G::T + c.tid] = s2;
             if constexpr (FUSED) {
                 const int kn = k + stride;
@@ -135,6 +151,10 @@ k_forward(FwdArgs a) {
                                             a.O, a.nx, rc.x, rc.y, c.tid);
         } else {
             team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
+            if constexpr (STAGE_Y) {
+                cp_async_wait_all();
+                __syncthreads();
+            }
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
                 const float2 ps = v[e] * invS;
@@ -147,7 +167,8 @@ k_forward(FwdArgs a) {
                 } else if constexpr (INTENSITY) {
                     a.out_real[(size_t)k * G::M + ky * G::S + freq_kx<G>(c.tid, e)] = h;
                 } else {
-                    const PixelTerms t = pixel_terms<true>(a.loss, h, __ldg(yk + e * G::T));
+                    const float ym = STAGE_Y ? sy[e * G::T + c.tid] : __ldg(yk + e * G::T);
+                    const PixelTerms t = pixel_terms<true>(a.loss, h, ym);
                     sl += t.l;
                     sd += t.dl * t.dl;
                 }
@@ -499,10 +520,18 @@ static const void* kernel_for(int LS, int kid) {
     return nullptr;
 }
 
+// Dynamic shared memory of kernel `kid`: the team buffers, plus the staged measurements of
+// the 128^2 error-metric kernel.
+static size_t kernel_smem_bytes(int LS, int kid) {
+    const bool stage = LS == 7 && ((kid == KID_FWD_LOSS && forward_stages_y<7, false, false, false, false>()) ||
+                                   (kid == KID_FWD_CACHE && forward_stages_y<7, true, false, false, false>()));
+    return cta_smem_bytes(LS) + (stage ? sizeof(float) * Geo<7>::M : 0);
+}
+
 cudaError_t kernel_prepare(int LS, int kid, int* ctas_per_sm) {
     const void* fn = kernel_for(LS, kid);
     if (!fn) return cudaErrorInvalidValue;
-    const size_t smem = cta_smem_bytes(LS);
+    const size_t smem = kernel_smem_bytes(LS, kid);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, cta_threads(LS), smem);
@@ -525,7 +554,7 @@ cudaError_t kernel_launch(int LS, int kid, const PtyArgs& a, int grid, cudaStrea
         default: arg = &ja; break;
     }
     void* args[] = {arg, &u};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(cta_threads(LS)), args, cta_smem_bytes(LS), stream);
+    return cudaLaunchKernel(fn, dim3(grid), dim3(cta_threads(LS)), args, kernel_smem_bytes(LS, kid), stream);
 }
 
 }  // namespace ptylm

@@ -425,6 +425,16 @@ __device__ __forceinline__ void team_fft_inv(float2* v, float2* sm, const float2
 template <class G, class Stage>
 __device__ __forceinline__ void team_fft_roundtrip(float2* v, float2* sm, const float2* tw, int tid,
                                                    Stage&& stage) {
+    team_fft_roundtrip<G>(v, sm, tw, tid, stage, [] {});
+}
+
+// As above, with `before_pass3()` run by every thread just before the barrier that precedes
+// pass 3 when BY > 1 (so data the spectral stage reads from shared memory, written
+// asynchronously, can be waited for there); when BY == 1 it runs before the first stage
+// call with no barrier after it.
+template <class G, class Stage, class Pre>
+__device__ __forceinline__ void team_fft_roundtrip(float2* v, float2* sm, const float2* tw, int tid,
+                                                   Stage&& stage, Pre&& before_pass3) {
     pass1_fwd<G>(v, tw, tid);
     ex1_store_from_p1<G>(sm, v, tid);
     team_sync<G>();
@@ -433,6 +443,7 @@ __device__ __forceinline__ void team_fft_roundtrip(float2* v, float2* sm, const 
     if constexpr (G::BY > 1) {
         team_sync<G>();  // all ex1 reads done before ex2 overwrites
         ex2_store_from_p2<G>(sm, v, tid);
+        before_pass3();
         team_sync<G>();
         const int k1x = tid & 31, k2x = (tid & (G::S - 1)) >> 5, k1y0 = (tid >> G::LOG_S) & (G::BX - 1);
 #pragma unroll 1
@@ -452,6 +463,7 @@ __device__ __forceinline__ void team_fft_roundtrip(float2* v, float2* sm, const 
         team_sync<G>();  // all ex2 reads done before ex1 overwrites
     } else {
         // BY == 1: the pass-2 registers already hold the spectrum, one value per group.
+        before_pass3();
 #pragma unroll
         for (int j = 0; j < G::G3; ++j) stage(v + j, j);
     }
