@@ -279,6 +279,12 @@ struct ptylm_ctx {
     float2* probe_part = nullptr;  // joint: per-team probe accumulators [probe_slots][M]
     int probe_slots = 0;
     float* trp = nullptr;          // per-thread d2l sums of the last linearisation [K][T]
+    // Look-ahead linearisation (object-only lm_solve): the trial point's forward pass also
+    // fills this second set; when the step is accepted the sets swap, so the next outer
+    // iteration starts without a forward pass of its own.
+    float2 *a_cache_b = nullptr, *grad_b = nullptr, *O_lin_b = nullptr;
+    float* trp_b = nullptr;
+    bool lookahead_failed = false; // the second set did not fit the workspace budget
     float* tr = nullptr;           // per-position d2l sums [K]
     float2* u_cache = nullptr;     // unit phasor psihat / zeta at the point [K][M] (team order)
     bool u_valid = false;          // u_cache holds the phasor of the current point
@@ -502,6 +508,48 @@ static ptylm_status op_forward(ptylm_ctx* c, const float2* O, const float2* P, i
     }
     if (cache) c->has_lin = c->has_point = true;
     return PTYLM_OK;
+}
+
+// Forward pass with cache and gradient at `O` (object-only contexts; the probe is the one of
+// the current linearisation) into the look-ahead set; the error metric and ||grad l||^2
+// land in the scalar slots as for any forward pass.
+static ptylm_status op_forward_lookahead(ptylm_ctx* c, const float2* O) {
+    CUDA_TRY(cudaMemcpyAsync(c->O_lin_b, O, sizeof(float2) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->grad_b, 0, sizeof(float2) * c->L, c->stream));
+    PtyArgs a = base_args(c);
+    a.O = c->O_lin_b;
+    a.P = c->P_lin;
+    a.a_cache = c->a_cache_b;
+    a.out = c->grad_b;
+    a.counter = c->counters + CNT_FWD;
+    a.trp = c->trp_b;
+    return launch(c, KID_FWD_CACHE, a);
+}
+
+// Allocate the look-ahead set once; false (and no error) when the workspace budget or the
+// device has no room for it, in which case the context never asks again.
+static bool lookahead_set(ptylm_ctx* c) {
+    if (c->trp_b) return true;
+    if (c->lookahead_failed) return false;
+    if (ctx_alloc_t(c, &c->a_cache_b, (size_t)c->d.K * c->M, "look-ahead cache") != PTYLM_OK ||
+        ctx_alloc_t(c, &c->grad_b, c->L, "look-ahead gradient") != PTYLM_OK ||
+        ctx_alloc_t(c, &c->O_lin_b, c->N, "look-ahead point") != PTYLM_OK ||
+        ctx_alloc_t(c, &c->trp_b, (size_t)c->d.K * (c->M / 32), "look-ahead d2l sums") != PTYLM_OK) {
+        c->lookahead_failed = true;   // a partial set stays allocated until the context is freed
+        g_last_error.clear();
+        return false;
+    }
+    return true;
+}
+
+// Make the look-ahead set the linearisation.
+static void swap_lookahead(ptylm_ctx* c) {
+    std::swap(c->a_cache, c->a_cache_b);
+    std::swap(c->grad, c->grad_b);
+    std::swap(c->O_lin, c->O_lin_b);
+    std::swap(c->trp, c->trp_b);
+    c->has_lin = c->has_point = true;
+    c->u_valid = false;
 }
 
 // out += G v over z at the linearisation point (out already holds the damping term).
@@ -950,6 +998,9 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
     }
     if (prm->projected && !c->ls_dir) STATUS_TRY(ctx_alloc_t(c, &c->ls_dir, L, "line-search direction"));
     if (prm->scaled && !c->Dg) STATUS_TRY(ctx_alloc_t(c, &c->Dg, L, "scaling"));
+    // The look-ahead set (a second cache, gradient, point and d2l sums) is optional: when the
+    // workspace budget has no room for it every outer iteration runs its own forward pass.
+    const bool lookahead = !joint(c) && c->d.K > 0 && !prm->projected && lookahead_set(c);
     if (!c->stage_a) STATUS_TRY(ctx_alloc_t(c, &c->stage_a, L, "iterate"));
     if (!c->stage_P) STATUS_TRY(ctx_alloc_t(c, &c->stage_P, c->M, "probe"));
     const bool host_O = is_host_pointer(O_inout), host_P = is_host_pointer(P_inout);
@@ -1002,12 +1053,14 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
         return PTYLM_OK;
     };
 
+    bool ahead = false;   // the linearisation at z came with the accepted trial point
     for (t = 0; t < prm->max_outer; ++t) {
         const double s_t = surrogate_at(prm, t);
         c->b_eff = (float)(c->d.background + s_t);
         surrogate_guard.used = s_t > 0.0;
         // Linearise: f, ||grad_zeta l||^2, cache a, grad f, Dg(G) (Algorithm 1, first step).
-        STATUS_TRY(op_forward(c, z, probe_of(z), 1));
+        if (!ahead) STATUS_TRY(op_forward(c, z, probe_of(z), 1));
+        ahead = false;
         STATUS_TRY(dots(c, 1, L, c->grad, c->grad, nullptr, nullptr, nullptr, nullptr, nullptr, S_GG));
         if (D) STATUS_TRY(op_ggn_diag(c, c->Dg, prm->diag_floor));
         STATUS_TRY(read_scalars(c, S_F, S_GG - S_F + 1));
@@ -1060,7 +1113,12 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
             // ---- trial point and gain ratio (Algorithm 1) ----
             k_axpy<<<nb, VEC_THREADS, 0, c->stream>>>(z, x, 1.0f, trial, L);
             STATUS_TRY(vec_launched(c));
-            STATUS_TRY(op_forward(c, trial, probe_of(trial), 0));
+            // the trial's forward pass doubles as the next linearisation when the next outer
+            // iteration exists and uses the same background
+            const bool ahead_here = lookahead && t + 1 < prm->max_outer &&
+                                    surrogate_at(prm, t + 1) == s_t;
+            if (ahead_here) STATUS_TRY(op_forward_lookahead(c, trial));
+            else STATUS_TRY(op_forward(c, trial, probe_of(trial), 0));
             STATUS_TRY(dots(c, 3, L, x, x, D, x, c->grad, x, r, S_DD));
             STATUS_TRY(read_scalars(c, S_F, S_DR - S_F + 1));
             const double f_trial = c->scal_host[S_F];
@@ -1075,6 +1133,10 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
                 if (!prm->projected) {
                     CUDA_TRY(cudaMemcpyAsync(z, trial, zbytes, cudaMemcpyDeviceToDevice, c->stream));
                     f_cur = f_trial;
+                    if (ahead_here) {
+                        swap_lookahead(c);
+                        ahead = true;
+                    }
                 } else {
                     // ---- Algorithm 2: projected step, descent test, Armijo backtracking ----
                     STATUS_TRY(project(trial));
