@@ -718,7 +718,8 @@ def main():
     per_kernel = {}
     for name, kid in (("forward_cache", ptylm.KERNEL_FORWARD_CACHE_JOINT if w.joint else ptylm.KERNEL_FORWARD_CACHE),
                       ("forward_loss", ptylm.KERNEL_FORWARD_LOSS),
-                      ("ggn_matvec", ptylm.KERNEL_GGN_MATVEC_JOINT if w.joint else ptylm.KERNEL_GGN_MATVEC)):
+                      ("ggn_matvec", ptylm.KERNEL_GGN_MATVEC_JOINT if w.joint else ptylm.KERNEL_GGN_MATVEC),
+                      ("cg_iteration", ptylm.KERNEL_CG_ITERATION)):
         ms_k, n_k = ptylm.ptylm_profile_read(ctx, kid)
         if n_k:
             per_kernel[name] = {"avg_us": 1e3 * ms_k / n_k, "launches": int(n_k),

@@ -103,6 +103,12 @@ typedef struct {
     double surrogate0;
     double surrogate_end;
     int surrogate_T;
+    /* 0 (default): each CG iteration after its GGN product is one cooperative launch with
+     * two grid-wide FP64 reductions inside it (when the device supports cooperative
+     * launches); 1: three launches (p.q; x, r and r.z; p and q).  Both give the same
+     * results bit for bit.  A bounded grid-wide wait that gives up ends lm_solve with
+     * PTYLM_ERR_TIMEOUT. */
+    int separate_cg_kernels;
 } ptylm_lm_params;
 
 /* Per-call results of lm_solve.  hist_* point to host arrays of hist_len entries (or are
@@ -235,7 +241,9 @@ ptylm_status forward_magnitude(ptylm_ctx* ctx, const ptylm_c64* O, const ptylm_c
  * the context stream; ptylm_profile(ctx, 0) stops.  ptylm_profile_read synchronises the
  * stream and returns, for kernel id `kernel` (PTYLM_KERNEL_*), the summed device time in
  * milliseconds and the number of timed launches; kernel = -1 returns 0 ms and the number
- * of launches of all the library's kernels (vector kernels included) since the reset. */
+ * of launches of all the library's kernels (vector kernels included) since the reset.
+ * PTYLM_KERNEL_CG_ITERATION times, per CG iteration of lm_solve, the vector work after the
+ * GGN product (one cooperative launch, or three launches with separate_cg_kernels). */
 enum {
     PTYLM_KERNEL_FORWARD_LOSS = 0,
     PTYLM_KERNEL_FORWARD_CACHE = 1,
@@ -251,7 +259,8 @@ enum {
     PTYLM_KERNEL_JVP_PHASOR = 11,
     PTYLM_KERNEL_JVP_PHASOR_JOINT = 12,
     PTYLM_KERNEL_JTVP_PHASOR = 13,
-    PTYLM_KERNEL_JTVP_PHASOR_JOINT = 14
+    PTYLM_KERNEL_JTVP_PHASOR_JOINT = 14,
+    PTYLM_KERNEL_CG_ITERATION = 15
 };
 ptylm_status ptylm_profile(ptylm_ctx* ctx, int enable);
 ptylm_status ptylm_profile_read(ptylm_ctx* ctx, int kernel, double* total_ms, long long* launches);

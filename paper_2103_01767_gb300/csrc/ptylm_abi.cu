@@ -13,6 +13,7 @@
 
 #include "../../include/ptylm.h"
 #include "kernels.h"
+#include "cg_iteration.cuh"
 #include "reduce.cuh"
 
 using namespace ptylm;
@@ -53,22 +54,16 @@ void ptylm::set_last_error(const char* msg) { g_last_error = msg; }
 // state z (the object, then the probe for joint contexts).  Products are formed in FP32
 // and summed per thread over its few grid-stride elements, then reduced in FP64 by
 // grid_reduce (reduce.cuh), whose last CTA also updates the FP64 scalars (alpha, beta, r.z,
-// r.r): a CG iteration is the matvec plus three launches, with no host round trip.
+// r.r): a CG iteration is the matvec plus three launches, with no host round trip (or the
+// matvec plus one cooperative launch, k_cg_iteration in cg_iteration.cuh).
 // Jacobi preconditioner (Sec. 3.3): z = r / Dg(G + lambda D) = r / ((1 + lambda) D) when
-// D = Dg(G); no preconditioner (z = r) when D is NULL.
+// D = Dg(G); no preconditioner (z = r) when D is NULL (rdotf and precondition live in
+// cg_iteration.cuh, shared with the single-launch iteration).
 // ---------------------------------------------------------------------------------------
 static constexpr int VEC_THREADS = 256;
 
-__device__ __forceinline__ float rdotf(float2 a, float2 b) { return a.x * b.x + a.y * b.y; }
-
 #define GRID_STRIDE(i, n) \
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (n); i += (long)gridDim.x * blockDim.x)
-
-__device__ __forceinline__ float2 precondition(float2 r, const float* D, float lambda, long i) {
-    if (!D) return r;
-    const float inv = 1.0f / ((1.0f + lambda) * D[i]);
-    return make_float2(r.x * inv, r.y * inv);
-}
 
 // out = lambda * D * v   (D == NULL: identity).  Initialises the matvec accumulator.
 __global__ void k_damping_init(const float2* __restrict__ v, const float* __restrict__ D, float lambda,
@@ -251,6 +246,10 @@ __global__ void k_err_sums(const float2* __restrict__ O, const float2* __restric
 // ---------------------------------------------------------------------------------------
 // Context
 // ---------------------------------------------------------------------------------------
+// Timed sections: the per-position kernels (KernelId), then the CG iteration's vector work.
+static constexpr int PROF_CG = KID_COUNT, PROF_COUNT = KID_COUNT + 1;
+static_assert(PROF_CG == PTYLM_KERNEL_CG_ITERATION, "profile ids follow the kernel ids");
+
 struct ptylm_ctx {
     ptylm_desc d;
     int LS = 0, S = 0, M = 0;
@@ -260,6 +259,7 @@ struct ptylm_ctx {
     int device = 0, num_sms = 0;
     int grid[KID_COUNT] = {0};
     int vec_grid = 0;
+    int coop_grid = 0;             // grid of the single-launch CG iteration (0: three launches)
     size_t allocated = 0;
     std::vector<void*> allocations;
 
@@ -306,8 +306,8 @@ struct ptylm_ctx {
     struct Rec { int kid; cudaEvent_t a, b; };
     std::vector<cudaEvent_t> ev_free;
     std::vector<Rec> recs;
-    double prof_ms[KID_COUNT] = {0};
-    long long prof_n[KID_COUNT] = {0};
+    double prof_ms[PROF_COUNT] = {0};
+    long long prof_n[PROF_COUNT] = {0};
 };
 
 // Accumulate the elapsed time of every recorded launch (synchronises the stream).
@@ -351,22 +351,30 @@ bool ptylm::ctx_view(const ptylm_ctx* c, CtxView* v) {
     return true;
 }
 
+// Events around a timed section when profiling is on (no-ops otherwise).
+static ptylm_status prof_begin(ptylm_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1) {
+    if (!c->prof_on) return PTYLM_OK;
+    if (c->recs.size() >= 2048) STATUS_TRY(prof_flush(c));
+    STATUS_TRY(take_event(c, e0));
+    STATUS_TRY(take_event(c, e1));
+    CUDA_TRY(cudaEventRecord(*e0, c->stream));
+    return PTYLM_OK;
+}
+
+static ptylm_status prof_end(ptylm_ctx* c, int id, cudaEvent_t e0, cudaEvent_t e1) {
+    if (!c->prof_on) return PTYLM_OK;
+    CUDA_TRY(cudaEventRecord(e1, c->stream));
+    c->recs.push_back({id, e0, e1});
+    return PTYLM_OK;
+}
+
 // Launch a per-position kernel, timing it with events when profiling is on.
 static ptylm_status launch(ptylm_ctx* c, int kid, const PtyArgs& a) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (c->prof_on) {
-        if (c->recs.size() >= 2048) STATUS_TRY(prof_flush(c));
-        STATUS_TRY(take_event(c, &e0));
-        STATUS_TRY(take_event(c, &e1));
-        CUDA_TRY(cudaEventRecord(e0, c->stream));
-    }
+    STATUS_TRY(prof_begin(c, &e0, &e1));
     CUDA_TRY(kernel_launch(c->LS, kid, a, c->grid[kid], c->stream));
     ++c->launches;
-    if (c->prof_on) {
-        CUDA_TRY(cudaEventRecord(e1, c->stream));
-        c->recs.push_back({kid, e0, e1});
-    }
-    return PTYLM_OK;
+    return prof_end(c, kid, e0, e1);
 }
 
 // Count a vector-kernel launch and check it was accepted.
@@ -510,6 +518,32 @@ static ptylm_status op_forward(ptylm_ctx* c, const float2* O, const float2* P, i
     return PTYLM_OK;
 }
 
+// One CG iteration after q = (G + lambda D) p: alpha, x, r, beta, p and q = lambda D p
+// (the next product's damping term), as one cooperative launch or as three launches.
+static ptylm_status cg_iteration(ptylm_ctx* c, float2* x, float2* r, float2* p, float2* q, const float* D,
+                                 float lambda, bool separate) {
+    long n = c->L;
+    double* part = c->partials;
+    double* sc = c->scal;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    STATUS_TRY(prof_begin(c, &e0, &e1));
+    if (!separate && c->coop_grid > 0) {
+        unsigned* cnt = c->counters + CNT_COOP;
+        void* args[] = {&x, &r, &p, &q, &D, &lambda, &n, &part, &cnt, &sc};
+        CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_cg_iteration, dim3(c->coop_grid), dim3(VEC_THREADS), args, 0,
+                                             c->stream));
+        ++c->launches;
+    } else {
+        STATUS_TRY(dots(c, 1, n, p, q, nullptr, nullptr, nullptr, nullptr, nullptr, S_PAP, OP_ALPHA));
+        const int nb = vec_blocks(c);
+        k_cg_update<<<nb, VEC_THREADS, 0, c->stream>>>(x, r, p, q, D, lambda, n, part, c->counters + CNT_VEC, sc);
+        STATUS_TRY(vec_launched(c));                                      // x, r; beta
+        k_cg_direction<<<nb, VEC_THREADS, 0, c->stream>>>(r, p, q, D, lambda, n, sc);
+        STATUS_TRY(vec_launched(c));                                      // p, q = lambda D p
+    }
+    return prof_end(c, PROF_CG, e0, e1);
+}
+
 // Forward pass with cache and gradient at `O` (object-only contexts; the probe is the one of
 // the current linearisation) into the look-ahead set; the error metric and ||grad l||^2
 // land in the scalar slots as for any forward pass.
@@ -649,6 +683,7 @@ void ptylm_default_lm_params(ptylm_lm_params* p, int loss) {
     p->surrogate0 = 1.0;
     p->surrogate_end = 1e-4;
     p->surrogate_T = 0;
+    p->separate_cg_kernels = 0;
 }
 
 // s_t of the App. E schedule: surrogate0 (surrogate_end / surrogate0)^(t / (T - 1)) for
@@ -726,6 +761,19 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
     c->vec_grid = std::min<long>(c->num_sms * 4L, std::max<long>(1, (c->L + VEC_THREADS - 1) / VEC_THREADS));
     c->probe_slots = d.joint ? std::max({c->grid[KID_FWD_CACHE_J], c->grid[KID_MATVEC_J], c->grid[KID_JTVP_J]}) * teams : 0;
     c->partials_cap = std::max(c->vec_grid, *std::max_element(c->grid, c->grid + KID_COUNT));
+    // Single-launch CG iteration: the vector grid (all of it co-resident at 48 registers a
+    // thread, so both forms give each thread the same elements and sum them in the same
+    // order), capped at what is co-resident; 0 (three launches per iteration) when the
+    // device cannot launch it cooperatively.
+    {
+        int coop = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device) == cudaSuccess && coop &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_cg_iteration, VEC_THREADS, 0) ==
+                cudaSuccess)
+            c->coop_grid = (int)std::min<long>(c->vec_grid, (long)per_sm * c->num_sms);
+        cudaGetLastError();
+        c->partials_cap = std::max(c->partials_cap, c->coop_grid);   // rounds 1 and 2 use 3 x grid doubles
+    }
 
     ptylm_status s;
     if ((s = ctx_alloc_t(c, &c->pos, std::max(1, d.K), "positions")) != PTYLM_OK) return bail(s);
@@ -822,7 +870,7 @@ ptylm_status ptylm_profile(ptylm_ctx* c, int enable) {
     if (!c) return fail(PTYLM_ERR_ARG, "ctx must be non-NULL");
     if (enable) {
         STATUS_TRY(prof_flush(c));
-        for (int k = 0; k < KID_COUNT; ++k) {
+        for (int k = 0; k < PROF_COUNT; ++k) {
             c->prof_ms[k] = 0.0;
             c->prof_n[k] = 0;
         }
@@ -834,7 +882,7 @@ ptylm_status ptylm_profile(ptylm_ctx* c, int enable) {
 
 ptylm_status ptylm_profile_read(ptylm_ctx* c, int kernel, double* total_ms, long long* launches) {
     if (!c) return fail(PTYLM_ERR_ARG, "ctx must be non-NULL");
-    if (kernel < -1 || kernel >= KID_COUNT) return fail(PTYLM_ERR_ARG, "unknown kernel id %d", kernel);
+    if (kernel < -1 || kernel >= PROF_COUNT) return fail(PTYLM_ERR_ARG, "unknown kernel id %d", kernel);
     STATUS_TRY(prof_flush(c));
     if (kernel == -1) {
         if (total_ms) *total_ms = 0.0;
@@ -1009,6 +1057,7 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
     // The state z = [O; P] lives in stage_a throughout (the caller's buffers are read once,
     // written once); object-only contexts keep the fixed probe in stage_P.
     float2* z = c->stage_a;
+    CUDA_TRY(cudaMemsetAsync(c->scal + S_CG_TIMEOUT, 0, sizeof(double), c->stream));
     CUDA_TRY(cudaMemcpyAsync(z, O_inout, sizeof(float2) * N, kin_O, c->stream));
     if (joint(c)) CUDA_TRY(cudaMemcpyAsync(z + N, P_inout, sizeof(float2) * c->M, kin_P, c->stream));
     else CUDA_TRY(cudaMemcpyAsync(c->stage_P, P_inout, sizeof(float2) * c->M, kin_P, c->stream));
@@ -1079,7 +1128,7 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
         }
         double rho = 0.0;
         int cg_this = 0;
-        bool stalled = false;
+        bool stalled = false, timed_out = false;
         while (!(rho > prm->rho_min)) {
             // lambda = mu ||grad_zeta l||^nu (D = I) or mu (D = Dg(G)), Algorithm 1
             const double lambda = D ? mu : mu * std::pow(std::sqrt(dl2), prm->nu);
@@ -1101,11 +1150,7 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
                 }
                 STATUS_TRY(op_matvec_accumulate(c, p, q));                        // q += G p
                 ++matvecs;
-                STATUS_TRY(dots(c, 1, L, p, q, nullptr, nullptr, nullptr, nullptr, nullptr, S_PAP, OP_ALPHA));
-                k_cg_update<<<nb, VEC_THREADS, 0, c->stream>>>(x, r, p, q, D, lam32, L, c->partials, cnt, c->scal);
-                STATUS_TRY(vec_launched(c));                                      // x, r; beta
-                k_cg_direction<<<nb, VEC_THREADS, 0, c->stream>>>(r, p, q, D, lam32, L, c->scal);
-                STATUS_TRY(vec_launched(c));                                      // p, q = lambda D p
+                STATUS_TRY(cg_iteration(c, x, r, p, q, D, lam32, prm->separate_cg_kernels != 0));
                 ++it;
             }
             cg_this += it;
@@ -1120,7 +1165,11 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
             if (ahead_here) STATUS_TRY(op_forward_lookahead(c, trial));
             else STATUS_TRY(op_forward(c, trial, probe_of(trial), 0));
             STATUS_TRY(dots(c, 3, L, x, x, D, x, c->grad, x, r, S_DD));
-            STATUS_TRY(read_scalars(c, S_F, S_DR - S_F + 1));
+            STATUS_TRY(read_scalars(c, S_F, S_CG_TIMEOUT - S_F + 1));
+            if (c->scal_host[S_CG_TIMEOUT] != 0.0) {
+                timed_out = true;
+                break;
+            }
             const double f_trial = c->scal_host[S_F];
             const double dd = c->scal_host[S_DD], dg = c->scal_host[S_DG], dr = c->scal_host[S_DR];
             const double dfa = f - f_trial;
@@ -1183,6 +1232,10 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
         if (stats && stats->hist_len > t) {
             if (stats->hist_mu) stats->hist_mu[t] = mu;
             if (stats->hist_cg) stats->hist_cg[t] = cg_this;
+        }
+        if (timed_out) {
+            status = fail(PTYLM_ERR_TIMEOUT, "a grid-wide wait of the CG iteration gave up at outer iteration %d", t);
+            break;
         }
         if (stalled) {
             status = fail(PTYLM_ERR_STALLED, "mu exceeded %g at outer iteration %d", prm->mu_max, t);

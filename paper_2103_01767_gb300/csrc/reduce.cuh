@@ -20,6 +20,7 @@ enum Slot {
     S_RZ = 15,                          // r.z of the preconditioned CG (= r.r without preconditioner)
     S_GS = 16, S_SS = 17,               // Algorithm 2: g.s and ||s||^2
     S_FMIN = 18,                        // Poisson: sum y - y log y
+    S_CG_TIMEOUT = 19,                  // set when a wait of the single-launch CG iteration gave up
     S_COUNT = 24
 };
 
@@ -32,7 +33,10 @@ enum FinalOp {
 };
 
 // Counters, one per reduction site (kernels on one stream never overlap).
-enum Counter { CNT_FWD = 0, CNT_VEC = 1, CNT_COUNT = 4 };
+// From CNT_COOP: arrivals and exits of the single-launch CG iteration, and 32 words (one
+// 128-byte line) further its released round (cg_iteration.cuh).
+enum Counter { CNT_FWD = 0, CNT_VEC = 1, CNT_COOP = 32, CNT_COUNT = 96 };
+constexpr int kCoopRelease = 32;
 
 constexpr int kMaxReduceWidth = 4;
 

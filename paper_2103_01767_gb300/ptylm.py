@@ -59,7 +59,7 @@ class LMParams(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("tau_s", ctypes.c_double), ("p_s", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("max_ls", ctypes.c_int), ("diag_floor", ctypes.c_double),
                 ("surrogate0", ctypes.c_double), ("surrogate_end", ctypes.c_double),
-                ("surrogate_T", ctypes.c_int)]
+                ("surrogate_T", ctypes.c_int), ("separate_cg_kernels", ctypes.c_int)]
 
 
 class LMStats(ctypes.Structure):
@@ -273,6 +273,7 @@ KERNEL_FORWARD_CACHE_JOINT = 6
 KERNEL_GGN_MATVEC_JOINT = 7
 KERNEL_JTVP_JOINT = 8
 KERNEL_JVP_JOINT = 9
+KERNEL_CG_ITERATION = 15   # the vector work of one CG iteration of lm_solve
 
 
 def ptylm_profile(ctx: Context, enable: bool) -> None:
