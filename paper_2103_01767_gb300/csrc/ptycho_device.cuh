@@ -107,6 +107,62 @@ __device__ __forceinline__ PixelTerms pixel_terms(int loss, float h, float ym) {
     return t;
 }
 
+// The same terms for the single-problem error-metric kernels, taken straight from the
+// unnormalised FFT output q (psihat = q / S, h = |q|^2 / M + b) with every constant factor
+// of the per-thread sums applied once per position (LossSums::finish) instead of per pixel:
+//   Gaussian  s0 = sum d^2, d = zeta - sqrt y       (l = s0 / 2, dl^2 = s0, d2l = 1 each)
+//   Poisson   s0 = sum h,  s1 = sum y log2 h        (l = s0 - s1 ln 2)
+//             s2 = sum ((h - y) r)^2                (dl^2 = 4 s2)
+//             s3 = sum (h + y) r^2                  (d2l = 2 s3)
+// With CACHE the cache factor a = psihat sqrt(d2l) / zeta = q ca and the gradient's
+// frequency term (psihat / zeta) dl / S = q cg are returned as the real scales ca, cg.
+// y log2 h needs no guard for y = 0: h >= b > 0.
+struct LossSums {
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    // this thread's sums of l, dl^2 and d2l over its `pixels` pixels
+    template <int LOSS>
+    __device__ __forceinline__ void finish(int pixels, float& l, float& dl2, float& d2l) const {
+        if constexpr (LOSS == 0) {
+            l = 0.5f * s0;
+            dl2 = s0;
+            d2l = (float)pixels;
+        } else {
+            l = fmaf(-0.69314718055994531f, s1, s0);
+            dl2 = 4.0f * s2;
+            d2l = 2.0f * s3;
+        }
+    }
+};
+
+template <int LOSS, bool CACHE>
+__device__ __forceinline__ void loss_pixel(float2 q, float ym, float b, float invS, LossSums& acc, float& ca,
+                                           float& cg) {
+    const float invM = invS * invS;
+    const float h = fmaf(invM, fmaf(q.x, q.x, q.y * q.y), b);
+    const float r = rsqrtf(h);
+    if constexpr (LOSS == 0) {
+        const float d = fmaf(h, r, -ym);  // zeta - sqrt y
+        acc.s0 = fmaf(d, d, acc.s0);
+        if constexpr (CACHE) {
+            ca = invS * r;         // sqrt(d2l) / zeta / S
+            cg = (d * r) * invM;   // dl / zeta / S^2
+        }
+    } else {
+        const float hy = h - ym;
+        acc.s0 += h;
+        acc.s1 = fmaf(ym, __log2f(h), acc.s1);
+        const float u = hy * r;
+        acc.s2 = fmaf(u, u, acc.s2);
+        if constexpr (CACHE) {
+            const float hp = h + ym;
+            const float r2 = r * r;
+            acc.s3 = fmaf(hp, r2, acc.s3);
+            ca = (invS * 1.41421356237309505f) * (hp * rsqrtf(hp)) * r2;  // sqrt(2 (h + y)) / h / S
+            cg = (hy * r2) * (2.0f * invM);                                 // 2 (h - y) / h / S^2
+        }
+    }
+}
+
 // Common prologue: twiddles into shared memory, team and thread indices.
 template <class G>
 struct TeamCtx {

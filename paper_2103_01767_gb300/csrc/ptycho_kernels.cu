@@ -14,6 +14,8 @@
 //   KID_MATVEC     J^T( Hess l . J v )  with the cache a     (App. A steps 2-4)
 //   KID_JTVP       J^T w                                     (App. A Eq. arbitrary_jtvp_sequence)
 //   KID_JVP        J v                                       (App. B Eq. jac_ampl, forward mode)
+#include <type_traits>
+
 #include "kernels.h"
 #include "ptycho_device.cuh"
 #include "reduce.cuh"
@@ -108,32 +110,38 @@ k_forward(FwdArgs a) {
         if constexpr (STAGE_Y) cp_async_tile(sy, a.y + (size_t)k * G::M, sizeof(float) * G::M, c.tid, G::T);
         else if constexpr (!INTENSITY && !MAG) prefetch_tile_l2(a.y + (size_t)k * G::M, sizeof(float) * G::M, c.tid);
         float sl = 0.0f, sd = 0.0f;
+        LossSums ls;  // this thread's error-metric sums at position k (loss_pixel)
         if constexpr (!FUSED) gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
         if constexpr (CACHE) {
             float2* ak = a.a_cache + (size_t)k * G::M;
-            float s2 = 0.0f;  // sum of d2l over this thread's pixels (closed-form diagonal)
+            // psihat = g / S (Eq. expected_count: h = |psihat|^2 + b); the cache gets
+            // psihat sqrt(d2l) / zeta, g becomes psihat dl / zeta with the inverse's 1/S folded in
+            auto group = [&](auto loss_c, float2* g, int j) {
+                constexpr int LOSS = decltype(loss_c)::value;
+                float2 av[G::BY];
+#pragma unroll
+                for (int k2y = 0; k2y < G::BY; ++k2y) {
+                    const int e = j * G::BY + k2y;
+                    const float ym = STAGE_Y ? sy[e * G::T + c.tid] : __ldg(yk + e * G::T);
+                    float ca, cg;
+                    loss_pixel<LOSS, true>(g[k2y], ym, a.b, invS, ls, ca, cg);
+                    av[k2y] = g[k2y] * ca;
+                    g[k2y] = g[k2y] * cg;
+                }
+                store_cache_group<G>(ak, av, j);
+            };
             team_fft_roundtrip<G>(
                 v, c.sm, c.tw, c.tid,
                 [&](float2* g, int j) {
-                    float2 av[G::BY];
-#pragma unroll
-                    for (int k2y = 0; k2y < G::BY; ++k2y) {
-                        const int e = j * G::BY + k2y;
-                        const float2 ps = g[k2y] * invS;                    // orthonormal psihat
-                        const float h = ps.x * ps.x + ps.y * ps.y + a.b;    // Eq. expected_count
-                        const float ym = STAGE_Y ? sy[e * G::T + c.tid] : __ldg(yk + e * G::T);
-                        const PixelTerms t = pixel_terms<true>(a.loss, h, ym);
-                        sl += t.l;
-                        sd += t.dl * t.dl;
-                        s2 += t.d2l;
-                        av[k2y] = ps * t.sqrt_d2l_over_zeta;
-                        g[k2y] = ps * (t.dl_over_zeta * invS);  // psihat grad l / zeta, inverse 1/S folded in
-                    }
-                    store_cache_group<G>(ak, av, j);
+                    if (a.loss == 0) group(std::integral_constant<int, 0>{}, g, j);
+                    else group(std::integral_constant<int, 1>{}, g, j);
                 },
                 [&] {
                     if constexpr (STAGE_Y) cp_async_wait_all();   // the pass-3 barrier follows
                 });
+            float s2;  // sum of d2l over this thread's pixels (closed-form diagonal)
+            if (a.loss == 0) ls.finish<0>(32, sl, sd, s2);
+            else ls.finish<1>(32, sl, sd, s2);
             if (a.trp) a.trp[(size_t)k * G::T + c.tid] = s2;
             if constexpr (FUSED) {
                 const int kn = k + stride;
@@ -155,23 +163,34 @@ k_forward(FwdArgs a) {
                 cp_async_wait_all();
                 __syncthreads();
             }
+            if constexpr (MAG || INTENSITY) {
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-                const float2 ps = v[e] * invS;
-                const float h = ps.x * ps.x + ps.y * ps.y + a.b;
-                if constexpr (MAG) {
-                    // zeta in natural order; the unit phasor u = psihat / zeta in team order
-                    const float r = rsqrtf(h);
-                    a.out_real[(size_t)k * G::M + ky * G::S + freq_kx<G>(c.tid, e)] = h * r;
-                    if (a.a_cache) a.a_cache[(size_t)k * G::M + e * G::T + c.tid] = ps * r;
-                } else if constexpr (INTENSITY) {
-                    a.out_real[(size_t)k * G::M + ky * G::S + freq_kx<G>(c.tid, e)] = h;
-                } else {
-                    const float ym = STAGE_Y ? sy[e * G::T + c.tid] : __ldg(yk + e * G::T);
-                    const PixelTerms t = pixel_terms<true>(a.loss, h, ym);
-                    sl += t.l;
-                    sd += t.dl * t.dl;
+                for (int e = 0; e < 32; ++e) {
+                    const float2 ps = v[e] * invS;
+                    const float h = ps.x * ps.x + ps.y * ps.y + a.b;
+                    if constexpr (MAG) {
+                        // zeta in natural order; the unit phasor u = psihat / zeta in team order
+                        const float r = rsqrtf(h);
+                        a.out_real[(size_t)k * G::M + ky * G::S + freq_kx<G>(c.tid, e)] = h * r;
+                        if (a.a_cache) a.a_cache[(size_t)k * G::M + e * G::T + c.tid] = ps * r;
+                    } else {
+                        a.out_real[(size_t)k * G::M + ky * G::S + freq_kx<G>(c.tid, e)] = h;
+                    }
                 }
+            } else {
+                auto pixels = [&](auto loss_c) {
+                    constexpr int LOSS = decltype(loss_c)::value;
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        float ca, cg;
+                        loss_pixel<LOSS, false>(v[e], STAGE_Y ? sy[e * G::T + c.tid] : __ldg(yk + e * G::T), a.b,
+                                                invS, ls, ca, cg);
+                    }
+                    float s2;
+                    ls.finish<LOSS>(32, sl, sd, s2);
+                };
+                if (a.loss == 0) pixels(std::integral_constant<int, 0>{});
+                else pixels(std::integral_constant<int, 1>{});
             }
         }
         acc_l += (double)sl;
