@@ -12,6 +12,8 @@
 // a problem's K in its last item run the FFT on zeros (the team barriers are CTA-wide) and
 // touch no memory.  The last CTA to finish restores the counters, so the launch can be
 // replayed inside a CUDA graph.
+#include <type_traits>
+
 #include "batch.h"
 #include "ptycho_device.cuh"
 #include "team_fft.cuh"
@@ -58,36 +60,43 @@ __device__ __forceinline__ void batch_forward_item(const BatchArgs& a, const Bat
 #pragma unroll
             for (int e = 0; e < 32; ++e) v[e] = make_float2(0.0f, 0.0f);
         }
-        float sl = 0.0f, sd = 0.0f;
+        float sl = 0.0f, sd = 0.0f, s2;
+        LossSums ls;  // loss_pixel: h = |g / S|^2 + b (Eq. expected_count), constant factors at the end
         if constexpr (CACHE) {
             float2* ak = p.a_cache + (size_t)(valid ? k : 0) * G::M;
-            team_fft_roundtrip<G>(v, sm, tw, tid, [&](float2* g, int jj) {
+            auto group = [&](auto loss_c, float2* g, int jj) {
+                constexpr int LOSS = decltype(loss_c)::value;
                 float2 av[G::BY];
 #pragma unroll
                 for (int k2y = 0; k2y < G::BY; ++k2y) {
                     const int e = jj * G::BY + k2y;
-                    const float2 ps = g[k2y] * invS;
-                    const float h = ps.x * ps.x + ps.y * ps.y + p.b;   // Eq. expected_count
-                    const PixelTerms t = pixel_terms<true>(p.loss, h, valid ? __ldg(yk + e * G::T) : 0.0f);
-                    sl += t.l;
-                    sd += t.dl * t.dl;
-                    av[k2y] = ps * t.sqrt_d2l_over_zeta;
-                    g[k2y] = ps * (t.dl_over_zeta * invS);
+                    float ca, cg;
+                    loss_pixel<LOSS, true>(g[k2y], valid ? __ldg(yk + e * G::T) : 0.0f, p.b, invS, ls, ca, cg);
+                    av[k2y] = g[k2y] * ca;
+                    g[k2y] = g[k2y] * cg;
                 }
                 if (valid) store_cache_group<G>(ak, av, jj);
+            };
+            team_fft_roundtrip<G>(v, sm, tw, tid, [&](float2* g, int jj) {
+                if (p.loss == 0) group(std::integral_constant<int, 0>{}, g, jj);
+                else group(std::integral_constant<int, 1>{}, g, jj);
             });
             if (valid) scatter_times_conj_probe<G>(v, gout, p.P, p.nx, rc.x, rc.y, tid);
         } else {
             team_fft_fwd<G>(v, sm, tw, tid);
+            auto pixels = [&](auto loss_c) {
+                constexpr int LOSS = decltype(loss_c)::value;
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-                const float2 ps = v[e] * invS;
-                const float h = ps.x * ps.x + ps.y * ps.y + p.b;
-                const PixelTerms t = pixel_terms<true>(p.loss, h, valid ? __ldg(yk + e * G::T) : 0.0f);
-                sl += t.l;
-                sd += t.dl * t.dl;
-            }
+                for (int e = 0; e < 32; ++e) {
+                    float ca, cg;
+                    loss_pixel<LOSS, false>(v[e], valid ? __ldg(yk + e * G::T) : 0.0f, p.b, invS, ls, ca, cg);
+                }
+            };
+            if (p.loss == 0) pixels(std::integral_constant<int, 0>{});
+            else pixels(std::integral_constant<int, 1>{});
         }
+        if (p.loss == 0) ls.finish<0>(32, sl, sd, s2);
+        else ls.finish<1>(32, sl, sd, s2);
         if (valid) {
             acc_l += (double)sl;
             acc_d += (double)sd;
