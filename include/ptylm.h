@@ -211,8 +211,10 @@ ptylm_status ggn_matvec(ptylm_ctx* ctx, const ptylm_c64* vO, const ptylm_c64* vP
  * FP32; dot products, lambda, mu, the gain ratio and f are FP64 on the device.  Object-only
  * unprojected solves evaluate each trial point with the cached forward pass, so that an
  * accepted trial is already the next linearisation; this needs a second loss cache, gradient
- * and point (8 K M + 16 ny nx + K M / 8 bytes), taken once within the workspace budget and
- * skipped (one forward pass per outer iteration instead) when it does not fit.
+ * and point (8 K M + 16 ny nx + K M / 8 bytes), taken once, after every buffer the solve
+ * needs, when it fits the workspace budget whole with room left for the PLM scaling and the
+ * Algorithm 2 direction (12 ny nx bytes, unless already taken); otherwise none of it is
+ * taken and every outer iteration runs its own forward pass.
  *   O_inout: host or device [ny][nx]; initial guess in, final iterate out.
  *   P_inout: host or device [my][mx] probe: read only for object-only contexts, updated
  *   in place for joint contexts.

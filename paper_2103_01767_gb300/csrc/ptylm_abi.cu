@@ -560,11 +560,20 @@ static ptylm_status op_forward_lookahead(ptylm_ctx* c, const float2* O) {
     return launch(c, KID_FWD_CACHE, a);
 }
 
-// Allocate the look-ahead set once; false (and no error) when the workspace budget or the
-// device has no room for it, in which case the context never asks again.
+// Allocate the look-ahead set once, after everything lm_solve needs; false (and no error)
+// when the workspace budget has no room for the whole set (then nothing of it is taken) or
+// the device runs out midway, in which case the context never asks again.
 static bool lookahead_set(ptylm_ctx* c) {
     if (c->trp_b) return true;
     if (c->lookahead_failed) return false;
+    const size_t need = sizeof(float2) * ((size_t)c->d.K * c->M + c->L + c->N) +
+                        sizeof(float) * (size_t)c->d.K * (c->M / 32);
+    // room is kept for the buffers a later PLM or projected solve would still take
+    const size_t reserve = (c->Dg ? 0 : sizeof(float) * c->L) + (c->ls_dir ? 0 : sizeof(float2) * c->L);
+    if (c->d.workspace_budget && c->allocated + need + reserve > c->d.workspace_budget) {
+        c->lookahead_failed = true;
+        return false;
+    }
     if (ctx_alloc_t(c, &c->a_cache_b, (size_t)c->d.K * c->M, "look-ahead cache") != PTYLM_OK ||
         ctx_alloc_t(c, &c->grad_b, c->L, "look-ahead gradient") != PTYLM_OK ||
         ctx_alloc_t(c, &c->O_lin_b, c->N, "look-ahead point") != PTYLM_OK ||
@@ -1046,11 +1055,11 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
     }
     if (prm->projected && !c->ls_dir) STATUS_TRY(ctx_alloc_t(c, &c->ls_dir, L, "line-search direction"));
     if (prm->scaled && !c->Dg) STATUS_TRY(ctx_alloc_t(c, &c->Dg, L, "scaling"));
+    if (!c->stage_a) STATUS_TRY(ctx_alloc_t(c, &c->stage_a, L, "iterate"));
+    if (!c->stage_P) STATUS_TRY(ctx_alloc_t(c, &c->stage_P, c->M, "probe"));
     // The look-ahead set (a second cache, gradient, point and d2l sums) is optional: when the
     // workspace budget has no room for it every outer iteration runs its own forward pass.
     const bool lookahead = !joint(c) && c->d.K > 0 && !prm->projected && lookahead_set(c);
-    if (!c->stage_a) STATUS_TRY(ctx_alloc_t(c, &c->stage_a, L, "iterate"));
-    if (!c->stage_P) STATUS_TRY(ctx_alloc_t(c, &c->stage_P, c->M, "probe"));
     const bool host_O = is_host_pointer(O_inout), host_P = is_host_pointer(P_inout);
     const cudaMemcpyKind kin_O = host_O ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     const cudaMemcpyKind kin_P = host_P ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;

@@ -81,3 +81,49 @@ def test_single_launch_cg_on_overlapping_scan(lib):
     assert a["st"] == b["st"] == 0
     assert a["info"]["f"][0] == b["info"]["f"][0]                   # deterministic error metric
     assert rel_err(a["info"]["f"], b["info"]["f"]) <= 1e-5
+
+
+def lm_ctx(lib, case, budget=0):
+    n, m = case.n, case.m
+    return lib.lm_init(n, n, m, m, torch.from_numpy(case.pos).cuda(),
+                       torch.from_numpy(np.ascontiguousarray(case.y, np.float32)).cuda(), case.loss, case.b,
+                       workspace_budget=budget)
+
+
+def test_lookahead_linearisation_and_its_fallback(lib):
+    """Object-only lm_solve evaluates each trial point with the cached forward pass into a
+    second cache set and starts the next outer iteration from it when the step is accepted.
+    Under a workspace budget with no room for that set it runs the loss-only trial pass and
+    its own linearisation instead; both runs give the same iterates (tiled scan: every
+    scatter is deterministic), and the forward-launch counts show which path ran."""
+    n, m = 96, 32
+    case = make_case(n, m, loss=0, seed=11, grid=n // m, step=m, radius=0.3 * m)
+    # smallest budget under which lm_solve runs at all (binary search over whole contexts)
+    lo, hi = 1 << 16, 1 << 26
+    while hi - lo > 4096:
+        mid = (lo + hi) // 2
+        try:
+            ctx = lm_ctx(lib, case, mid)
+            lib.lm_solve(ctx, c64(synth.flat_object(n)), c64(case.P), max_outer=1, fixed_cg=1)
+            hi = mid
+        except lib.PtylmError as e:
+            assert e.status == lib.PTYLM_ERR_NOMEM
+            lo = mid
+    K, M, N = len(case.pos), m * m, n * n
+    lookahead_bytes = 8 * K * M + 16 * N + K * M // 8 + 12 * N   # the set, plus room kept for PLM / projection
+    runs = {}
+    for name, budget in (("tight", hi + lookahead_bytes - 4096), ("unlimited", 0)):
+        ctx = lm_ctx(lib, case, budget)
+        O = c64(synth.flat_object(n))
+        lib.ptylm_profile(ctx, 1)
+        st, info = lib.lm_solve(ctx, O, c64(case.P), hist_len=8, max_outer=5, fixed_cg=8)
+        n_cache = lib.ptylm_profile_read(ctx, lib.KERNEL_FORWARD_CACHE)[1]
+        n_loss = lib.ptylm_profile_read(ctx, lib.KERNEL_FORWARD_LOSS)[1]
+        lib.ptylm_profile(ctx, 0)
+        assert st == 0 and info["n_outer"] == 5
+        runs[name] = (info, O.cpu().numpy(), n_cache, n_loss, info["cg_total"] // 8)
+    (i_t, O_t, c_t, l_t, trials_t), (i_u, O_u, c_u, l_u, trials_u) = runs["tight"], runs["unlimited"]
+    assert (c_t, l_t) == (5, trials_t)                # a linearisation per iteration, loss-only trials
+    assert c_u + l_u == 1 + trials_u and l_u < l_t    # trials double as the next linearisation
+    assert rel_err(i_u["f"], i_t["f"]) <= 1e-6
+    assert rel_err(O_u, O_t) <= 1e-5
