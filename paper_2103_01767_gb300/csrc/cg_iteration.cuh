@@ -14,6 +14,11 @@
 // the round, which then updates the scalar slots exactly as OP_ALPHA / OP_BETA do and
 // releases the round.
 //
+// With tol >= 0 the CTA that finishes the second reduction also counts the iteration
+// (S_CG_ITERS) and sets S_CG_DONE once ||r|| <= tol; a launch that finds S_CG_DONE set
+// returns at once, as does the GGN product given the same flag, so the host can queue
+// several iterations between two reads of the scalars.
+//
 // Waits: the launch is cooperative (every CTA resident), and each wait is additionally
 // bounded; a wait that gives up sets S_CG_TIMEOUT and carries on, so no launch can hang.
 // The last CTA to leave resets the counters (arrivals cnt[0], exits cnt[1], released round
@@ -60,7 +65,8 @@ __device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v
 // arrival is an acquire-release add (it publishes the CTA's partial and, for the last CTA,
 // makes every partial visible); the release is a release store read by acquire loads.
 template <int W>
-__device__ void coop_reduce_round(double (&s)[W], double* part, unsigned* cnt, double* sc, int op, unsigned round) {
+__device__ void coop_reduce_round(double (&s)[W], double* part, unsigned* cnt, double* sc, int op, unsigned round,
+                                  double tol = -1.0) {
     __shared__ bool is_last;
     block_sum<W>(s);
     if (threadIdx.x == 0) {
@@ -80,6 +86,10 @@ __device__ void coop_reduce_round(double (&s)[W], double* part, unsigned* cnt, d
         block_sum<W>(t);
         if (threadIdx.x == 0) {
             apply_final_op(t, W, sc, 0, op);
+            if (tol >= 0.0) {  // the CG stopping test ||r|| <= tol, taken on the device
+                sc[S_CG_ITERS] += 1.0;
+                sc[S_CG_DONE] = sqrt(sc[S_RR]) <= tol ? 1.0 : 0.0;
+            }
             st_release_gpu(cnt + kCoopRelease, round);
         }
     } else if (threadIdx.x == 0) {
@@ -101,8 +111,9 @@ constexpr int kCgUnroll = 2;
 __global__ void __launch_bounds__(256) k_cg_iteration(float2* __restrict__ x, float2* __restrict__ r,
                                                       float2* __restrict__ p, float2* __restrict__ q,
                                                       const float* __restrict__ D, float lambda, long n,
-                                                      double* part, unsigned* cnt, double* sc) {
+                                                      double* part, unsigned* cnt, double* sc, double tol) {
     constexpr int U = kCgUnroll;
+    if (tol >= 0.0 && __ldcg(sc + S_CG_DONE) != 0.0) return;  // converged earlier: every CTA sees the same flag
     const long stride = (long)gridDim.x * blockDim.x;
     const long i0 = blockIdx.x * (long)blockDim.x + threadIdx.x;
 
@@ -159,7 +170,7 @@ __global__ void __launch_bounds__(256) k_cg_iteration(float2* __restrict__ x, fl
         }
     }
     double s2[2] = {f0, f1};
-    coop_reduce_round<2>(s2, part + gridDim.x, cnt, sc, OP_BETA, 2u);
+    coop_reduce_round<2>(s2, part + gridDim.x, cnt, sc, OP_BETA, 2u, tol);
     const float beta = (float)__ldcg(sc + S_BETA);
 
     // p = z + beta p, q = lambda D p

@@ -29,6 +29,7 @@ struct PtyArgs {
     const float2* Olin;    // joint: object at the linearisation point (matvec)
     float2* outP_part;     // joint: per-team probe accumulators [grid * TEAMS][M]
     float* trp;            // optional: per-thread sums of d2l [K][T] (forward + cache)
+    const double* skip;    // matvec: return at once when *skip != 0 (a CG solve that has converged)
 };
 
 enum KernelId {

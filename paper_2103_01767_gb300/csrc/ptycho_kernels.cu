@@ -54,6 +54,7 @@ struct MatvecArgs {
     const float2* Olin;   // joint: object at the linearisation point
     float2* outP_part;    // joint: per-team probe accumulators
     int K, nx;
+    const double* skip;   // return at once when *skip != 0 (NULL: never)
 };
 struct AdjArgs {          // J^T w and J v
     const float2* O;      // linearisation point
@@ -210,6 +211,7 @@ template <int LS, bool JOINT = false>
 __global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
 k_ggn_matvec(MatvecArgs a) {
     using G = Geo<LS>;
+    if (a.skip && __ldcg(a.skip) != 0.0) return;  // every CTA reads the same value
     TeamCtx<G> c = team_setup<G>(a.tw);
     const float invM = 1.0f / G::M;
     const int stride = gridDim.x * G::TEAMS;
@@ -561,7 +563,7 @@ cudaError_t kernel_launch(int LS, int kid, const PtyArgs& a, int grid, cudaStrea
     if (!fn || grid <= 0) return cudaErrorInvalidValue;
     FwdArgs fa{a.O, a.P, a.pos, a.y, a.a_cache, a.out, a.out_real, a.partials, a.counter, a.scal, a.tw,
                a.trp, a.outP_part, a.K, a.nx, a.b, a.loss};
-    MatvecArgs ma{a.O, a.P, a.pos, a.a_cache, a.out, a.tw, a.VP, a.Olin, a.outP_part, a.K, a.nx};
+    MatvecArgs ma{a.O, a.P, a.pos, a.a_cache, a.out, a.tw, a.VP, a.Olin, a.outP_part, a.K, a.nx, a.skip};
     AdjArgs ja{a.O, a.V, a.VP, a.P, a.pos, a.w, a.out, a.out_real, a.scratch, a.tw, a.outP_part, a.K, a.nx, a.b};
     const float2* u = a.a_cache;
     void* arg = nullptr;

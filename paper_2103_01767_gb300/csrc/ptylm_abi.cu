@@ -260,6 +260,7 @@ struct ptylm_ctx {
     int grid[KID_COUNT] = {0};
     int vec_grid = 0;
     int coop_grid = 0;             // grid of the single-launch CG iteration (0: three launches)
+    int cg_chunk = 1;              // CG iterations the last solve took (the next solve queues as many at once)
     size_t allocated = 0;
     std::vector<void*> allocations;
 
@@ -519,9 +520,11 @@ static ptylm_status op_forward(ptylm_ctx* c, const float2* O, const float2* P, i
 }
 
 // One CG iteration after q = (G + lambda D) p: alpha, x, r, beta, p and q = lambda D p
-// (the next product's damping term), as one cooperative launch or as three launches.
+// (the next product's damping term), as one cooperative launch or as three launches.  With
+// tol >= 0 (cooperative form only) the device applies the stopping test ||r|| <= tol itself
+// (S_CG_DONE, S_CG_ITERS) and the iteration is a no-op once it has passed.
 static ptylm_status cg_iteration(ptylm_ctx* c, float2* x, float2* r, float2* p, float2* q, const float* D,
-                                 float lambda, bool separate) {
+                                 float lambda, bool separate, double tol = -1.0) {
     long n = c->L;
     double* part = c->partials;
     double* sc = c->scal;
@@ -529,7 +532,7 @@ static ptylm_status cg_iteration(ptylm_ctx* c, float2* x, float2* r, float2* p, 
     STATUS_TRY(prof_begin(c, &e0, &e1));
     if (!separate && c->coop_grid > 0) {
         unsigned* cnt = c->counters + CNT_COOP;
-        void* args[] = {&x, &r, &p, &q, &D, &lambda, &n, &part, &cnt, &sc};
+        void* args[] = {&x, &r, &p, &q, &D, &lambda, &n, &part, &cnt, &sc, &tol};
         CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_cg_iteration, dim3(c->coop_grid), dim3(VEC_THREADS), args, 0,
                                              c->stream));
         ++c->launches;
@@ -596,11 +599,13 @@ static void swap_lookahead(ptylm_ctx* c) {
 }
 
 // out += G v over z at the linearisation point (out already holds the damping term).
-static ptylm_status op_matvec_accumulate(ptylm_ctx* c, const float2* v, float2* out) {
+// With `skip`, the product is not formed (and out keeps its value) once *skip != 0.
+static ptylm_status op_matvec_accumulate(ptylm_ctx* c, const float2* v, float2* out, const double* skip = nullptr) {
     if (c->d.K == 0) return PTYLM_OK;
     const int kid = joint(c) ? KID_MATVEC_J : KID_MATVEC;
     if (joint(c)) STATUS_TRY(clear_probe_part(c, kid));
     PtyArgs a = base_args(c);
+    a.skip = skip;
     a.O = v;
     a.P = c->P_lin;
     a.a_cache = c->a_cache;
@@ -1149,18 +1154,47 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
             STATUS_TRY(vec_launched(c));                                          // r, p = P^-1 r, q = lambda D p
             int it = 0;
             bool converged = false;
-            for (;;) {
-                if (prm->fixed_cg > 0) {
-                    if (it >= prm->fixed_cg) break;
-                } else {
-                    STATUS_TRY(read_scalars(c, S_RR, 1));
-                    if (std::sqrt(c->scal_host[S_RR]) <= tol) { converged = true; break; }
-                    if (it >= prm->max_cg) break;
+            const bool separate = prm->separate_cg_kernels != 0;
+            if (prm->fixed_cg <= 0 && !separate && c->coop_grid > 0) {
+                // The stopping test (Eq. lma_termination_magnitude) runs on the device after each
+                // iteration; the host queues as many iterations as the last solve took (then a
+                // quarter of that at a time) and reads the count and the flag once per batch.
+                STATUS_TRY(read_scalars(c, S_RR, 1));
+                converged = std::sqrt(c->scal_host[S_RR]) <= tol;
+                if (!converged && prm->max_cg > 0) {
+                    CUDA_TRY(cudaMemsetAsync(c->scal + S_CG_DONE, 0, 2 * sizeof(double), c->stream));
+                    const int first = std::max(1, c->cg_chunk);
+                    int queued = 0, batch = first;
+                    for (;;) {
+                        const int nq = std::min(batch, prm->max_cg - queued);
+                        for (int i = 0; i < nq; ++i) {
+                            STATUS_TRY(op_matvec_accumulate(c, p, q, c->scal + S_CG_DONE));   // q += G p
+                            STATUS_TRY(cg_iteration(c, x, r, p, q, D, lam32, false, tol));
+                        }
+                        queued += nq;
+                        STATUS_TRY(read_scalars(c, S_CG_DONE, 2));
+                        it = (int)c->scal_host[S_CG_ITERS];
+                        converged = c->scal_host[S_CG_DONE] != 0.0;
+                        if (converged || queued >= prm->max_cg) break;
+                        batch = std::max(1, first / 4);
+                    }
+                    c->cg_chunk = it;
                 }
-                STATUS_TRY(op_matvec_accumulate(c, p, q));                        // q += G p
-                ++matvecs;
-                STATUS_TRY(cg_iteration(c, x, r, p, q, D, lam32, prm->separate_cg_kernels != 0));
-                ++it;
+                matvecs += it;
+            } else {
+                for (;;) {
+                    if (prm->fixed_cg > 0) {
+                        if (it >= prm->fixed_cg) break;
+                    } else {
+                        STATUS_TRY(read_scalars(c, S_RR, 1));
+                        if (std::sqrt(c->scal_host[S_RR]) <= tol) { converged = true; break; }
+                        if (it >= prm->max_cg) break;
+                    }
+                    STATUS_TRY(op_matvec_accumulate(c, p, q));                        // q += G p
+                    ++matvecs;
+                    STATUS_TRY(cg_iteration(c, x, r, p, q, D, lam32, separate));
+                    ++it;
+                }
             }
             cg_this += it;
             if (!converged && prm->fixed_cg <= 0 && it >= prm->max_cg) hit_maxit = true;

@@ -21,6 +21,7 @@ enum Slot {
     S_GS = 16, S_SS = 17,               // Algorithm 2: g.s and ||s||^2
     S_FMIN = 18,                        // Poisson: sum y - y log y
     S_CG_TIMEOUT = 19,                  // set when a wait of the single-launch CG iteration gave up
+    S_CG_DONE = 20, S_CG_ITERS = 21,    // device-side CG stopping: converged flag, iterations run
     S_COUNT = 24
 };
 
