@@ -116,6 +116,15 @@ __global__ void k_cg_start(const float2* __restrict__ g, float2* __restrict__ q,
     grid_reduce<2>(s, part, counter, sc, 0, OP_START, 1.0);
 }
 
+// The stopping test before the first CG iteration, taken on the device: S_CG_DONE =
+// (||r0|| <= tol), S_CG_ITERS = 0 (one thread).
+__global__ void k_cg_check(double* sc, double tol) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        sc[S_CG_DONE] = sqrt(sc[S_RR]) <= tol ? 1.0 : 0.0;
+        sc[S_CG_ITERS] = 0.0;
+    }
+}
+
 // x += alpha p, r -= alpha q; new r.z and r.r -> beta (alpha read from the slots).
 __global__ void k_cg_update(float2* __restrict__ x, float2* __restrict__ r, const float2* __restrict__ p,
                             const float2* __restrict__ q, const float* __restrict__ D, float lambda, long n,
@@ -1156,13 +1165,15 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
             bool converged = false;
             const bool separate = prm->separate_cg_kernels != 0;
             if (prm->fixed_cg <= 0 && !separate && c->coop_grid > 0) {
-                // The stopping test (Eq. lma_termination_magnitude) runs on the device after each
-                // iteration; the host queues as many iterations as the last solve took (then a
-                // quarter of that at a time) and reads the count and the flag once per batch.
-                STATUS_TRY(read_scalars(c, S_RR, 1));
-                converged = std::sqrt(c->scal_host[S_RR]) <= tol;
-                if (!converged && prm->max_cg > 0) {
-                    CUDA_TRY(cudaMemsetAsync(c->scal + S_CG_DONE, 0, 2 * sizeof(double), c->stream));
+                // The stopping test (Eq. lma_termination_magnitude) runs on the device before and
+                // after each iteration; the host queues as many iterations as the last solve took
+                // (then a quarter of that at a time) and reads the count and the flag once per batch.
+                if (prm->max_cg == 0) {
+                    STATUS_TRY(read_scalars(c, S_RR, 1));
+                    converged = std::sqrt(c->scal_host[S_RR]) <= tol;
+                } else {
+                    k_cg_check<<<1, 32, 0, c->stream>>>(c->scal, tol);
+                    STATUS_TRY(vec_launched(c));
                     const int first = std::max(1, c->cg_chunk);
                     int queued = 0, batch = first;
                     for (;;) {
