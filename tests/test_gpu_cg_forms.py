@@ -133,3 +133,18 @@ def test_lookahead_linearisation_and_its_fallback(lib):
     assert c_u + l_u == 1 + trials_u and l_u < l_t    # trials double as the next linearisation
     assert rel_err(i_u["f"], i_t["f"]) <= 1e-6
     assert rel_err(O_u, O_t) <= 1e-5
+
+
+def test_device_cg_stopping_at_the_iteration_limit(lib):
+    """Adaptive CG capped by max_cg: the device-side stopping (single-launch form) and the
+    host-side test (three-launch form) both stop every solve at the cap, report
+    PTYLM_WARN_CG_MAXIT and return the same iterate (tiled scan: deterministic scatters)."""
+    n, m = 96, 32
+    case = make_case(n, m, loss=1, seed=5, grid=n // m, step=m, radius=0.3 * m, peak=1e4)
+    a, b = both_forms(lib, case, 0, max_outer=3, max_cg=2)
+    assert a["st"] == b["st"] == lib.PTYLM_WARN_CG_MAXIT
+    cg = list(a["info"]["cg"])
+    assert cg == list(b["info"]["cg"]) and all(c > 0 and c % 2 == 0 for c in cg)   # every solve stops at 2
+    assert a["info"]["matvecs"] == b["info"]["matvecs"]
+    assert np.array_equal(a["info"]["f"], b["info"]["f"])
+    assert np.array_equal(a["O"], b["O"])
