@@ -265,6 +265,11 @@ enum {
     PTYLM_KERNEL_CG_ITERATION = 15
 };
 ptylm_status ptylm_profile(ptylm_ctx* ctx, int enable);
+/* As ptylm_profile(ctx, 1), but times only the sections whose bit is set in mask (bit k:
+ * kernel id k, PTYLM_KERNEL_*); the launch count still covers every kernel.  Each timed
+ * section adds a pair of event records to the stream, so timing one kernel costs the others
+ * nothing.  mask = 0 stops. */
+ptylm_status ptylm_profile_select(ptylm_ctx* ctx, unsigned mask);
 ptylm_status ptylm_profile_read(ptylm_ctx* ctx, int kernel, double* total_ms, long long* launches);
 
 /* Allocation-free error metric (the paper has no counterpart: this serves callers that

@@ -312,7 +312,7 @@ struct ptylm_ctx {
 
     // instrumentation
     long long launches = 0;
-    bool prof_on = false;
+    unsigned prof_mask = 0;        // bit k: time the launches of section k (kernel id, or PROF_CG)
     struct Rec { int kid; cudaEvent_t a, b; };
     std::vector<cudaEvent_t> ev_free;
     std::vector<Rec> recs;
@@ -361,9 +361,11 @@ bool ptylm::ctx_view(const ptylm_ctx* c, CtxView* v) {
     return true;
 }
 
-// Events around a timed section when profiling is on (no-ops otherwise).
-static ptylm_status prof_begin(ptylm_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1) {
-    if (!c->prof_on) return PTYLM_OK;
+// Events around a timed section when profiling covers it (no-ops otherwise).
+static bool prof_wants(const ptylm_ctx* c, int id) { return (c->prof_mask >> id) & 1u; }
+
+static ptylm_status prof_begin(ptylm_ctx* c, int id, cudaEvent_t* e0, cudaEvent_t* e1) {
+    if (!prof_wants(c, id)) return PTYLM_OK;
     if (c->recs.size() >= 2048) STATUS_TRY(prof_flush(c));
     STATUS_TRY(take_event(c, e0));
     STATUS_TRY(take_event(c, e1));
@@ -372,7 +374,7 @@ static ptylm_status prof_begin(ptylm_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1) {
 }
 
 static ptylm_status prof_end(ptylm_ctx* c, int id, cudaEvent_t e0, cudaEvent_t e1) {
-    if (!c->prof_on) return PTYLM_OK;
+    if (!prof_wants(c, id)) return PTYLM_OK;
     CUDA_TRY(cudaEventRecord(e1, c->stream));
     c->recs.push_back({id, e0, e1});
     return PTYLM_OK;
@@ -381,7 +383,7 @@ static ptylm_status prof_end(ptylm_ctx* c, int id, cudaEvent_t e0, cudaEvent_t e
 // Launch a per-position kernel, timing it with events when profiling is on.
 static ptylm_status launch(ptylm_ctx* c, int kid, const PtyArgs& a) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    STATUS_TRY(prof_begin(c, &e0, &e1));
+    STATUS_TRY(prof_begin(c, kid, &e0, &e1));
     CUDA_TRY(kernel_launch(c->LS, kid, a, c->grid[kid], c->stream));
     ++c->launches;
     return prof_end(c, kid, e0, e1);
@@ -538,7 +540,7 @@ static ptylm_status cg_iteration(ptylm_ctx* c, float2* x, float2* r, float2* p, 
     double* part = c->partials;
     double* sc = c->scal;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    STATUS_TRY(prof_begin(c, &e0, &e1));
+    STATUS_TRY(prof_begin(c, PROF_CG, &e0, &e1));
     if (!separate && c->coop_grid > 0) {
         unsigned* cnt = c->counters + CNT_COOP;
         void* args[] = {&x, &r, &p, &q, &D, &lambda, &n, &part, &cnt, &sc, &tol};
@@ -889,9 +891,9 @@ ptylm_status forward_magnitude(ptylm_ctx* c, const ptylm_c64* O, const ptylm_c64
     return PTYLM_OK;
 }
 
-ptylm_status ptylm_profile(ptylm_ctx* c, int enable) {
+ptylm_status ptylm_profile_select(ptylm_ctx* c, unsigned mask) {
     if (!c) return fail(PTYLM_ERR_ARG, "ctx must be non-NULL");
-    if (enable) {
+    if (mask) {
         STATUS_TRY(prof_flush(c));
         for (int k = 0; k < PROF_COUNT; ++k) {
             c->prof_ms[k] = 0.0;
@@ -899,9 +901,11 @@ ptylm_status ptylm_profile(ptylm_ctx* c, int enable) {
         }
         c->launches = 0;
     }
-    c->prof_on = enable != 0;
+    c->prof_mask = mask & ((1u << PROF_COUNT) - 1u);
     return PTYLM_OK;
 }
+
+ptylm_status ptylm_profile(ptylm_ctx* c, int enable) { return ptylm_profile_select(c, enable ? ~0u : 0u); }
 
 ptylm_status ptylm_profile_read(ptylm_ctx* c, int kernel, double* total_ms, long long* launches) {
     if (!c) return fail(PTYLM_ERR_ARG, "ctx must be non-NULL");

@@ -99,6 +99,7 @@ def load_library():
             lib.forward_magnitude.argtypes = [vp, vp, vp, vp, i]
             lib.ptylm_forward_loss_noalloc.argtypes = [i, i, i, i, i, ctypes.c_float, vp, vp, vp, vp, vp, vp]
             lib.ptylm_profile.argtypes = [vp, i]
+            lib.ptylm_profile_select.argtypes = [vp, ctypes.c_uint]
             lib.ptylm_profile_read.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
             lib.ptylm_strerror.argtypes = [i]
             lib.ptylm_strerror.restype = ctypes.c_char_p
@@ -140,7 +141,7 @@ def load_library():
             for name in ("lm_init", "forward_loss", "gradient", "jvp", "jtvp", "ggn_matvec",
                          "lm_solve", "lm_destroy", "forward_intensity", "ptylm_set_measurements",
                          "ptylm_forward_loss_noalloc", "ggn_diag", "forward_magnitude",
-                         "ptylm_profile",
+                         "ptylm_profile", "ptylm_profile_select",
                          "ptylm_profile_read"):
                 getattr(lib, name).restype = i
             _lib = lib
@@ -278,6 +279,14 @@ KERNEL_CG_ITERATION = 15   # the vector work of one CG iteration of lm_solve
 
 def ptylm_profile(ctx: Context, enable: bool) -> None:
     _check(load_library().ptylm_profile(ctx.handle, int(bool(enable))))
+
+
+def ptylm_profile_select(ctx: Context, kernels) -> None:
+    """Time only the launches of the given kernel ids (empty: stop)."""
+    mask = 0
+    for k in kernels:
+        mask |= 1 << int(k)
+    _check(load_library().ptylm_profile_select(ctx.handle, mask))
 
 
 def ptylm_profile_read(ctx: Context, kernel: int):

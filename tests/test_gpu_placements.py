@@ -103,3 +103,22 @@ def test_matvec_launches_are_profiled(lib):
     ms, n = lib.ptylm_profile_read(ctx, lib.KERNEL_GGN_MATVEC)
     lib.ptylm_profile(ctx, 0)
     assert n == 3 and ms > 0.0
+
+
+def test_profile_select_times_only_the_chosen_kernel(lib):
+    ny, nx = 260, 266
+    pb, ctx, O_np = setup(lib, ny, nx, 10, seed=5)
+    O, P = c64(O_np), c64(pb.P)
+    v = c64(synth.random_complex((ny, nx), seed=10))
+    out = torch.empty_like(v)
+    lib.ptylm_profile_select(ctx, [lib.KERNEL_GGN_MATVEC])
+    for _ in range(2):
+        lib.forward_loss(ctx, O, P, cache=1)
+        lib.ggn_matvec(ctx, v, out, 0.0)
+    mv = lib.ptylm_profile_read(ctx, lib.KERNEL_GGN_MATVEC)
+    fc = lib.ptylm_profile_read(ctx, lib.KERNEL_FORWARD_CACHE)
+    _, launches = lib.ptylm_profile_read(ctx, -1)
+    lib.ptylm_profile_select(ctx, [])
+    assert mv[1] == 2 and mv[0] > 0.0
+    assert fc == (0.0, 0)                 # not timed
+    assert launches >= 4                  # but every launch is counted
