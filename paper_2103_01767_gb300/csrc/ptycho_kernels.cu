@@ -108,11 +108,12 @@ k_forward(FwdArgs a) {
     for (; k < a.K; k += stride) {
         const int2 rc = a.pos[k];
         const float* yk = a.y + (size_t)k * G::M + c.tid;  // measurements in team-register order
+        // the gather's loads go first: the measurement copies are only waited for after the FFT
+        if constexpr (!FUSED) gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
         if constexpr (STAGE_Y) cp_async_tile(sy, a.y + (size_t)k * G::M, sizeof(float) * G::M, c.tid, G::T);
         else if constexpr (!INTENSITY && !MAG) prefetch_tile_l2(a.y + (size_t)k * G::M, sizeof(float) * G::M, c.tid);
         float sl = 0.0f, sd = 0.0f;
         LossSums ls;  // this thread's error-metric sums at position k (loss_pixel)
-        if constexpr (!FUSED) gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
         if constexpr (CACHE) {
             float2* ak = a.a_cache + (size_t)k * G::M;
             // psihat = g / S (Eq. expected_count: h = |psihat|^2 + b); the cache gets
