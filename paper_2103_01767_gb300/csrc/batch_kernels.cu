@@ -54,8 +54,8 @@ __device__ __forceinline__ void batch_forward_item(const BatchArgs& a, const Bat
         const int2 rc = valid ? p.pos[k] : make_int2(0, 0);
         const float* yk = p.y + (size_t)(valid ? k : 0) * G::M + tid;
         if (valid) {
+            gather_times_probe<G>(v, O, p.P, p.nx, rc.x, rc.y, tid);   // its loads first, then the prefetch
             prefetch_tile_l2(p.y + (size_t)k * G::M, sizeof(float) * G::M, tid);
-            gather_times_probe<G>(v, O, p.P, p.nx, rc.x, rc.y, tid);
         } else {
 #pragma unroll
             for (int e = 0; e < 32; ++e) v[e] = make_float2(0.0f, 0.0f);
@@ -124,8 +124,8 @@ __device__ __forceinline__ void batch_matvec_item(const BatchArgs& a, const Batc
         const int2 rc = valid ? p.pos[k] : make_int2(0, 0);
         const float2* ak = p.a_cache + (size_t)(valid ? k : 0) * G::M;
         if (valid) {
+            gather_times_probe<G>(v, V, p.P, p.nx, rc.x, rc.y, tid);   // its loads first, then the prefetch
             prefetch_tile_l2(ak, sizeof(float2) * G::M, tid);
-            gather_times_probe<G>(v, V, p.P, p.nx, rc.x, rc.y, tid);
         } else {
 #pragma unroll
             for (int e = 0; e < 32; ++e) v[e] = make_float2(0.0f, 0.0f);
