@@ -277,7 +277,7 @@ def lm_solve(pb: Problem, O0, O_ref=None, mask=None, beta=None, **kw):
                   prm["mu_max"], int(prm["max_outer"]), int(prm["max_cg"]), prm["target_err"])
     O = _c(O0).copy()
     L = int(prm["max_outer"])
-    hf, hg, hmu, herr = (np.full(L, np.nan) for _ in range(4))
+    hf, hg, hmu, herr, hrho = (np.full(L, np.nan) for _ in range(5))
     hcg = np.zeros(L, np.int32)
     n_outer, cg_total = ctypes.c_int(0), ctypes.c_int(0)
     Oref = None if O_ref is None else _c(O_ref)
@@ -286,10 +286,10 @@ def lm_solve(pb: Problem, O0, O_ref=None, mask=None, beta=None, **kw):
     st = _load().orc_lm_solve(ctypes.byref(g), _p(O), _p(pb.P), _p(pb.pos), _p(pb.y),
                               ctypes.byref(p), _p(Oref), _p(m), ctypes.byref(n_outer),
                               ctypes.byref(cg_total), _p(hf), _p(hg), _p(hmu), _p(hcg),
-                              _p(herr), L)
+                              _p(herr), _p(hrho), L)
     n = n_outer.value
     return O, dict(status=st, n_outer=n, cg_total=cg_total.value, f=hf[:n], gnorm=hg[:n],
-                   mu=hmu[:n], cg=hcg[:n], err=herr[:n])
+                   mu=hmu[:n], cg=hcg[:n], err=herr[:n], rho=hrho[:n])
 
 
 # ---------------------------------------------------------------------------------------

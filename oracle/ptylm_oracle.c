@@ -33,7 +33,10 @@
  *
  * Parity pins: each function is checked in the CPU test-suite against invariants that
  * hold independently of this code (adjoint identity, finite differences, Parseval,
- * direct DFT, dense brute force on tiny sizes, zero loss/gradient at a noiseless truth).
+ * direct DFT, dense brute force on tiny sizes, zero loss/gradient at a noiseless truth);
+ * Algorithm 1 against a dense restatement step for step (error metric, gain ratio, mu,
+ * iterate) with its CG run to convergence.  Parity unpinned: the CG forcing term eta and
+ * the warm start, which only matter for truncated CG.
  */
 #include <complex.h>
 #include <math.h>
@@ -510,7 +513,7 @@ int orc_lm_solve(const orc_geom* g, dc* O, const dc* P, const int32_t* pos, cons
                  const orc_lm_params* prm, const dc* O_ref, const unsigned char* mask,
                  int* n_outer_out, int* cg_total_out,
                  double* hist_f, double* hist_gnorm, double* hist_mu, int* hist_cg,
-                 double* hist_err, int hist_len)
+                 double* hist_err, double* hist_rho, int hist_len)
 {
     const long N = (long)g->ny * g->nx;
     dc* grad = (dc*)malloc(sizeof(dc) * N);
@@ -558,6 +561,7 @@ int orc_lm_solve(const orc_geom* g, dc* O, const dc* P, const int32_t* pos, cons
         cg_total += cg_this;
         if (hist_mu && t < hist_len) hist_mu[t] = mu;
         if (hist_cg && t < hist_len) hist_cg[t] = cg_this;
+        if (hist_rho && t < hist_len) hist_rho[t] = rho;   /* gain ratio of the step that ended it */
         if (status) { ++t; break; }
         if (O_ref) {
             double e = orc_object_error(N, O, O_ref, mask);

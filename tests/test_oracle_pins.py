@@ -530,3 +530,62 @@ def test_surrogate_reverts_to_the_true_metric():
     O1, _, _ = oracle.lm_solve2(pb, O0, max_outer=1, **kw)
     assert abs(i5["f"][1] - oracle.loss(pb, O1)) > 1e-6 * abs(i5["f"][1])
     assert np.isfinite(i5["f"]).all() and i5["f"][4] <= i5["f"][3]
+
+
+# ----------------------------------------------------------------------- Algorithm 1, densely
+def dense_lm(pb, O0, mu0, n_outer, kappa=4.0, nu=1.0, rho_min=1e-4, mu_min=1e-8):
+    """Algorithm 1 (D = I) on a tiny problem with every linear-algebra step done densely:
+    J by central differences of the forward model, g = J^T dl and G = J^T diag(d2l) J from
+    the pinned metric derivatives, the step by a direct solve of (G + lambda I) d = -g, the
+    predicted reduction from its definition -(g.d + d.G.d / 2), lambda = mu ||dl||^nu.
+    Returns the iterate, the error metric at each linearisation, mu after each outer
+    iteration, the gain ratio of the step that ended it, and the smallest distance of a
+    gain ratio to the mu thresholds 1/4 and 3/4."""
+    O, mu = O0.copy(), mu0
+    hist_f, hist_mu, hist_rho, margin = [], [], [], np.inf
+    for _ in range(n_outer):
+        J = dense_jacobian(pb, O)
+        l, dl, d2l = oracle.ell_terms(pb.loss, zeta_of(pb, O).ravel(), pb.y.ravel())
+        f = float(l.sum())
+        g = J.T @ dl
+        G = J.T @ (d2l[:, None] * J)
+        hist_f.append(f)
+        while True:
+            lam = mu * np.linalg.norm(dl) ** nu
+            d = np.linalg.solve(G + lam * np.eye(G.shape[0]), -g)
+            O_try = O + from_real(d, O.shape)
+            pred = -(g @ d + 0.5 * d @ (G @ d))
+            rho = (f - oracle.loss(pb, O_try)) / pred if pred > 0 else -1.0
+            margin = min(margin, abs(rho - 0.25), abs(rho - 0.75))
+            if rho > 0.75:
+                mu = max(mu / kappa, mu_min)
+            elif rho <= 0.25:
+                mu = kappa * mu
+            if rho > rho_min:
+                O = O_try
+                break
+        hist_mu.append(mu)
+        hist_rho.append(rho)
+    return O, np.array(hist_f), np.array(hist_mu), np.array(hist_rho), margin
+
+
+@pytest.mark.parametrize("loss,mu0", [(0, 1e-2), (1, 1e-1)])
+def test_lm_trajectory_equals_dense_algorithm(loss, mu0):
+    """The oracle's matrix-free Algorithm 1 (truncated CG run to a 1e-10 relative residual,
+    the predicted reduction from the CG residual, lambda from ||grad_zeta l||) follows the
+    dense restatement step for step: same error metric at every linearisation, same gain
+    ratio (the predicted reduction from its definition against the oracle's residual form),
+    same mu after every outer iteration (no gain ratio within 1e-3 of a mu threshold), same
+    iterate."""
+    pb, O_true = tiny_problem(loss, noiseless=False)
+    O0 = O_true + synth.random_complex(O_true.shape, seed=70 + loss, scale=0.08)
+    n_outer = 5
+    O_d, f_d, mu_d, rho_d, margin = dense_lm(pb, O0, mu0, n_outer)
+    assert margin > 1e-3
+    O_o, info = oracle.lm_solve(pb, O0, beta=1e-10, mu0=mu0, max_outer=n_outer, max_cg=1000)
+    assert info["n_outer"] == n_outer
+    np.testing.assert_allclose(info["f"], f_d, rtol=1e-6)
+    np.testing.assert_array_equal(info["mu"], mu_d)
+    np.testing.assert_allclose(info["rho"], rho_d, rtol=1e-4)
+    assert np.linalg.norm(O_o - O_d) <= 1e-5 * np.linalg.norm(O_d)
+    assert f_d[-1] < f_d[0]
