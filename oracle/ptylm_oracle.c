@@ -35,8 +35,8 @@
  * hold independently of this code (adjoint identity, finite differences, Parseval,
  * direct DFT, dense brute force on tiny sizes, zero loss/gradient at a noiseless truth);
  * Algorithm 1 against a dense restatement step for step (error metric, gain ratio, mu,
- * iterate) with its CG run to convergence.  Parity unpinned: the CG forcing term eta and
- * the warm start, which only matter for truncated CG.
+ * iterate) with its CG run to convergence; truncated CG against the forcing bound with
+ * the dense G, and the forcing term eta of Algorithm 1 through its CG iteration counts.
  */
 #include <complex.h>
 #include <math.h>

@@ -305,6 +305,49 @@ def test_cg_matches_dense_solve():
     np.testing.assert_allclose(to_real(r), -to_real(g) - A @ to_real(x), atol=1e-8)
 
 
+@pytest.mark.parametrize("eta", [0.5, 0.1, 0.02])
+def test_truncated_cg_stops_at_the_first_iterate_meeting_the_forcing_bound(eta):
+    """Eq. lma_termination_magnitude: CG stops as soon as ||(G + lambda I) x + g|| <= eta ||g||,
+    checked with the dense G: the returned iterate meets the bound, the one before it does
+    not, and a warm start from the converged solution stops at once."""
+    pb, O_true = tiny_problem(1, noiseless=False)
+    O = O_true + synth.random_complex(O_true.shape, seed=91, scale=0.05)
+    g = oracle.gradient(pb, O)
+    lam = 0.05
+    J = dense_jacobian(pb, O)
+    _, _, d2l = oracle.ell_terms(pb.loss, zeta_of(pb, O).ravel(), pb.y.ravel())
+    A = J.T @ (d2l[:, None] * J) + lam * np.eye(2 * O.size)
+    bound = eta * np.linalg.norm(to_real(g))
+    residual = lambda x: np.linalg.norm(A @ to_real(x) + to_real(g))
+    x, _, it, conv = oracle.cg(pb, O, g, lam, eta=eta, max_iter=400)
+    assert conv and it >= 1
+    assert residual(x) <= bound * (1 + 1e-9)
+    x_prev, _, it_prev, conv_prev = oracle.cg(pb, O, g, lam, eta=eta, max_iter=it - 1)
+    assert it_prev == it - 1 and not conv_prev and residual(x_prev) > bound
+    _, _, it_warm, conv_warm = oracle.cg(pb, O, g, lam, eta=eta, max_iter=400, x0=x)
+    assert conv_warm and it_warm == 0
+
+
+@pytest.mark.parametrize("beta,scale,noiseless,root_branch",
+                         [(0.9, 0.05, False, False), (0.9, 0.002, True, True), (1e-3, 0.05, False, False)])
+def test_lm_forcing_term_is_min_of_beta_and_root_gradient_norm(beta, scale, noiseless, root_branch):
+    """Reading C4: the first outer iteration of Algorithm 1 runs exactly as many CG
+    iterations as a cold-started truncated CG with eta = min(beta, ||grad f||^(1/2)) and
+    lambda = mu0 ||grad_zeta l|| (the truncated CG itself is pinned above)."""
+    pb, O_true = tiny_problem(1, noiseless=noiseless)
+    O0 = O_true + synth.random_complex(O_true.shape, seed=92, scale=scale)
+    mu0 = 1e-2
+    _, info = oracle.lm_solve(pb, O0, beta=beta, mu0=mu0, max_outer=1, max_cg=400)
+    g = oracle.gradient(pb, O0)
+    gnorm = np.linalg.norm(to_real(g))
+    _, dl, _ = oracle.ell_terms(pb.loss, zeta_of(pb, O0).ravel(), pb.y.ravel())
+    eta = min(beta, math.sqrt(gnorm))
+    _, _, it, conv = oracle.cg(pb, O0, g, mu0 * np.linalg.norm(dl), eta=eta, max_iter=400)
+    assert conv and info["mu"][0] <= mu0          # the first step was accepted (one CG solve)
+    assert info["cg"][0] == it
+    assert (math.sqrt(gnorm) < beta) == root_branch   # both branches of the minimum are exercised
+
+
 def test_object_error_phase_invariance():
     O = synth.object_texture(32, seed=1)
     assert oracle.object_error(O * np.exp(1.3j), O) < 1e-14
