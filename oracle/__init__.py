@@ -389,7 +389,7 @@ def lm_solve2(pb: Problem, O0, P0=None, O_ref=None, mask=None, beta=None, **kw):
     O = _c(O0).copy()
     P = (pb.P if P0 is None else _c(P0)).copy()
     L = int(prm["max_outer"])
-    hf, hg, hmu, herr = (np.full(L, np.nan) for _ in range(4))
+    hf, hg, hmu, herr, hrho = (np.full(L, np.nan) for _ in range(5))
     hcg = np.zeros(L, np.int32)
     n_outer, cg_total = ctypes.c_int(0), ctypes.c_int(0)
     Oref = None if O_ref is None else _c(O_ref)
@@ -399,10 +399,10 @@ def lm_solve2(pb: Problem, O0, P0=None, O_ref=None, mask=None, beta=None, **kw):
     lib.orc_lm_solve2.restype = ctypes.c_int
     st = lib.orc_lm_solve2(ctypes.byref(g), _p(O), _p(P), _p(pb.pos), _p(pb.y), ctypes.byref(p), _p(Oref),
                            _p(m), ctypes.byref(n_outer), ctypes.byref(cg_total), _p(hf), _p(hg), _p(hmu),
-                           _p(hcg), _p(herr), L)
+                           _p(hcg), _p(herr), _p(hrho), L)
     n = n_outer.value
     return O, P, dict(status=st, n_outer=n, cg_total=cg_total.value, f=hf[:n], gnorm=hg[:n], mu=hmu[:n],
-                      cg=hcg[:n], err=herr[:n])
+                      cg=hcg[:n], err=herr[:n], rho=hrho[:n])
 
 
 def object_error_blind(O, O_ref, mask=None, ramp_iterations=3):

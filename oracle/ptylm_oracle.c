@@ -756,7 +756,7 @@ double orc_surrogate_at(const orc_lm2_params* prm, int t)
 int orc_lm_solve2(const orc_geom* g, dc* O_inout, dc* P_inout, const int32_t* pos, const double* y,
                   const orc_lm2_params* prm, const dc* O_ref, const unsigned char* mask,
                   int* n_outer_out, int* cg_total_out, double* hist_f, double* hist_gnorm, double* hist_mu,
-                  int* hist_cg, double* hist_err, int hist_len)
+                  int* hist_cg, double* hist_err, double* hist_rho, int hist_len)
 {
     orc_problem pb = {g, pos, y, prm->joint, P_inout};
     const long N = (long)g->ny * g->nx;
@@ -835,6 +835,7 @@ int orc_lm_solve2(const orc_geom* g, dc* O_inout, dc* P_inout, const int32_t* po
         cg_total += cg_this;
         if (hist_mu && t < hist_len) hist_mu[t] = mu;
         if (hist_cg && t < hist_len) hist_cg[t] = cg_this;
+        if (hist_rho && t < hist_len) hist_rho[t] = rho;   /* gain ratio of the step that ended it */
         if (status) { ++t; break; }
         if (O_ref) {
             double e = orc_object_error(N, z, O_ref, mask);

@@ -612,6 +612,56 @@ def dense_lm(pb, O0, mu0, n_outer, kappa=4.0, nu=1.0, rho_min=1e-4, mu_min=1e-8)
     return O, np.array(hist_f), np.array(hist_mu), np.array(hist_rho), margin
 
 
+def dense_plm(pb, O0, mu0, n_outer, floor=1e-6, kappa=4.0, rho_min=1e-4, mu_min=1e-8):
+    """PLM (Sec. 3.3): Algorithm 1 with D = Dg(G) (the closed form, pinned against the dense
+    diagonal above) and lambda = mu, every step solved densely; returns as dense_lm."""
+    O, mu = O0.copy(), mu0
+    hist_f, hist_mu, hist_rho, margin = [], [], [], np.inf
+    for _ in range(n_outer):
+        J = dense_jacobian(pb, O)
+        l, dl, d2l = oracle.ell_terms(pb.loss, zeta_of(pb, O).ravel(), pb.y.ravel())
+        f = float(l.sum())
+        g = J.T @ dl
+        G = J.T @ (d2l[:, None] * J)
+        D_O, _ = oracle.ggn_diag(pb, O, floor_rel=floor)
+        D = np.concatenate([D_O.ravel(), D_O.ravel()])   # the same scale on Re and Im
+        hist_f.append(f)
+        while True:
+            d = np.linalg.solve(G + mu * np.diag(D), -g)
+            O_try = O + from_real(d, O.shape)
+            pred = -(g @ d + 0.5 * d @ (G @ d))
+            rho = (f - oracle.loss(pb, O_try)) / pred if pred > 0 else -1.0
+            margin = min(margin, abs(rho - 0.25), abs(rho - 0.75))
+            if rho > 0.75:
+                mu = max(mu / kappa, mu_min)
+            elif rho <= 0.25:
+                mu = kappa * mu
+            if rho > rho_min:
+                O = O_try
+                break
+        hist_mu.append(mu)
+        hist_rho.append(rho)
+    return O, np.array(hist_f), np.array(hist_mu), np.array(hist_rho), margin
+
+
+@pytest.mark.parametrize("loss,mu0", [(0, 1e-1), (1, 1.0)])
+def test_plm_trajectory_equals_dense_algorithm(loss, mu0):
+    """The oracle's PLM (Jacobi PCG run to a 1e-10 relative residual, D = Dg(G) floored at
+    1e-6 of its maximum, lambda = mu) follows the dense restatement step for step."""
+    pb, O_true = tiny_problem(loss, noiseless=False)
+    O0 = O_true + synth.random_complex(O_true.shape, seed=80 + loss, scale=0.08)
+    n_outer = 5
+    O_d, f_d, mu_d, rho_d, margin = dense_plm(pb, O0, mu0, n_outer)
+    assert margin > 1e-3
+    O_o, _, info = oracle.lm_solve2(pb, O0, beta=1e-10, mu0=mu0, max_outer=n_outer, max_cg=1000, scaled=1)
+    assert info["n_outer"] == n_outer
+    np.testing.assert_allclose(info["f"], f_d, rtol=1e-6)
+    np.testing.assert_array_equal(info["mu"], mu_d)
+    np.testing.assert_allclose(info["rho"], rho_d, rtol=1e-4)
+    assert np.linalg.norm(O_o - O_d) <= 1e-5 * np.linalg.norm(O_d)
+    assert f_d[-1] < f_d[0]
+
+
 @pytest.mark.parametrize("loss,mu0", [(0, 1e-2), (1, 1e-1)])
 def test_lm_trajectory_equals_dense_algorithm(loss, mu0):
     """The oracle's matrix-free Algorithm 1 (truncated CG run to a 1e-10 relative residual,
