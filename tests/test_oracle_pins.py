@@ -682,3 +682,53 @@ def test_lm_trajectory_equals_dense_algorithm(loss, mu0):
     np.testing.assert_allclose(info["rho"], rho_d, rtol=1e-4)
     assert np.linalg.norm(O_o - O_d) <= 1e-5 * np.linalg.norm(O_d)
     assert f_d[-1] < f_d[0]
+
+
+@pytest.mark.parametrize("loss,mu0", [(0, 1e-1), (1, 1.0)])
+def test_joint_plm_trajectory_equals_dense_algorithm(loss, mu0):
+    """PLM on the joint state z = (O, P) (BPR, Sec. 3.3 with the joint diagonal): the oracle
+    (Jacobi PCG to a 1e-10 relative residual) follows a dense restatement -- joint J by
+    central differences, D = Dg(G) from the pinned joint closed form (each block floored at
+    1e-6 of its maximum), direct solves of (G + mu D) d = -g -- step for step."""
+    pb, O_true = tiny_problem(loss, noiseless=False, b=1e-12)
+    O0 = O_true + synth.random_complex(O_true.shape, seed=110 + loss, scale=0.06)
+    P0 = pb.P * (1.0 + synth.random_complex(pb.P.shape, seed=120 + loss, scale=0.05))
+    N, M = O0.size, P0.size
+    O, P, mu = O0.copy(), P0.copy(), mu0
+    f_d, mu_d, rho_d, margin = [], [], [], np.inf
+    for _ in range(4):
+        J = dense_jacobian_joint(pb, O, P)
+        l, dl, d2l = oracle.ell_terms(pb.loss, zeta_of(pb, O, P).ravel(), pb.y.ravel())
+        f = float(l.sum())
+        g = J.T @ dl
+        G = J.T @ (d2l[:, None] * J)
+        D_O, D_P = oracle.ggn_diag(pb, O, P=P, floor_rel=1e-6)
+        Dz = np.concatenate([D_O.ravel(), D_P.ravel()])
+        D = np.concatenate([Dz, Dz])                     # Re O, Re P, Im O, Im P
+        f_d.append(f)
+        while True:
+            d = np.linalg.solve(G + mu * np.diag(D), -g)
+            dz = d[:N + M] + 1j * d[N + M:]
+            O_try, P_try = O + dz[:N].reshape(O.shape), P + dz[N:].reshape(P.shape)
+            pred = -(g @ d + 0.5 * d @ (G @ d))
+            rho = (f - oracle.loss(pb, O_try, P_try)) / pred if pred > 0 else -1.0
+            margin = min(margin, abs(rho - 0.25), abs(rho - 0.75))
+            if rho > 0.75:
+                mu = max(mu / 4.0, 1e-8)
+            elif rho <= 0.25:
+                mu = 4.0 * mu
+            if rho > 1e-4:
+                O, P = O_try, P_try
+                break
+        mu_d.append(mu)
+        rho_d.append(rho)
+    assert margin > 1e-3
+    O_o, P_o, info = oracle.lm_solve2(pb, O0, P0, beta=1e-10, mu0=mu0, max_outer=4, max_cg=4000,
+                                      scaled=1, joint=1)
+    assert info["n_outer"] == 4
+    np.testing.assert_allclose(info["f"], f_d, rtol=1e-6)
+    np.testing.assert_array_equal(info["mu"], mu_d)
+    np.testing.assert_allclose(info["rho"], rho_d, rtol=1e-4)
+    assert np.linalg.norm(O_o - O) <= 1e-5 * np.linalg.norm(O)
+    assert np.linalg.norm(P_o - P) <= 1e-5 * np.linalg.norm(P)
+    assert f_d[-1] < f_d[0]
