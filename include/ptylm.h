@@ -208,7 +208,10 @@ ptylm_status ggn_matvec(ptylm_ctx* ctx, const ptylm_c64* vO, const ptylm_c64* vP
  * (Sec. 4.3) with the radial constraints of Eq. constraints.  The inner truncated (P)CG is
  * stopped by Eqs. lma_termination_magnitude / lma_termination_eta with
  * eta = min(beta, ||grad f||^(1/2)) and warm-started from the previous step.  CG vectors are
- * FP32; dot products, lambda, mu, the gain ratio and f are FP64 on the device.  Object-only
+ * FP32; dot products, lambda, mu, the gain ratio and f are FP64 on the device.  With the
+ * single-launch CG iteration (separate_cg_kernels = 0) the stopping test runs on the device
+ * and the host queues iterations in batches (as many as the previous solve took), reading
+ * the scalars once per batch; iterations queued past the stop return at once.  Object-only
  * unprojected solves evaluate each trial point with the cached forward pass, so that an
  * accepted trial is already the next linearisation; this needs a second loss cache, gradient
  * and point (8 K M + 16 ny nx + K M / 8 bytes), taken once, after every buffer the solve
