@@ -35,3 +35,22 @@ def test_strerror_without_gpu():
     build.build()
     assert ptylm.ptylm_strerror(0) == "success"
     assert "argument" in ptylm.ptylm_strerror(1)
+
+
+def test_calls_fail_cleanly_without_a_gpu():
+    """Without a usable GPU the library reports errors instead of crashing: argument
+    errors are found on the host first, CUDA failures come back as PTYLM_ERR_CUDA."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("checks the path taken when no GPU is present")
+    from paper_2103_01767_gb300 import build, ptylm
+    build.build()
+    pos = torch.zeros((4, 2), dtype=torch.int32)
+    y = torch.zeros((4, 32, 32), dtype=torch.float32)
+    with pytest.raises(ptylm.PtylmError) as e:
+        ptylm.lm_init(64, 64, 30, 30, pos, y)
+    assert e.value.status == ptylm.PTYLM_ERR_ARG
+    with pytest.raises(ptylm.PtylmError) as e:
+        ptylm.lm_init(64, 64, 32, 32, pos, y)
+    assert e.value.status == ptylm.PTYLM_ERR_CUDA and "CUDA" in str(e.value)
