@@ -732,3 +732,84 @@ def test_joint_plm_trajectory_equals_dense_algorithm(loss, mu0):
     assert np.linalg.norm(O_o - O) <= 1e-5 * np.linalg.norm(O)
     assert np.linalg.norm(P_o - P) <= 1e-5 * np.linalg.norm(P)
     assert f_d[-1] < f_d[0]
+
+
+def radial_projection(v, radius):
+    a = np.abs(v)
+    return np.where(a > radius, v * (radius / np.maximum(a, 1e-300)), v)
+
+
+@pytest.mark.parametrize("loss,sigma", [(0, 0.3), (1, 1.5)])
+def test_projected_joint_plm_trajectory_equals_dense_algorithm(loss, sigma):
+    """Algorithm 2 on top of joint PLM (Sec. 4.3, reading C9): after an accepted step the
+    iterate is projected onto |O| <= 1, kept if f(Pi) - f_min < gamma (f - f_min), else an
+    Armijo search along s = Pi(z + d) - z (or -g when s is no descent direction) with
+    projection at every trial; gain ratio and mu use the unprojected step.  The oracle matches
+    a dense restatement step for step (the object's amplitudes reach 1, so the projection and
+    the line search are both exercised; a strict sufficient-decrease constant sigma makes the
+    search halve its step)."""
+    gamma, tau_s, p_s, max_ls, rO, rP = 1e-6, 1e-8, 2.1, 30, 1.0, 1e8
+    pb, O_true = tiny_problem(loss, noiseless=False, b=1e-12)
+    y = pb.y.ravel()
+    f_min = float(np.sum(y - np.where(y > 0, y * np.log(np.where(y > 0, y, 1.0)), 0.0))) if loss else 0.0
+    O0 = O_true + synth.random_complex(O_true.shape, seed=130 + loss, scale=0.06)
+    P0 = pb.P * (1.0 + synth.random_complex(pb.P.shape, seed=140 + loss, scale=0.05))
+    N, M = O0.size, P0.size
+    proj = lambda z: np.concatenate([radial_projection(z[:N], rO), radial_projection(z[N:], rP)])
+    fz = lambda z: oracle.loss(pb, z[:N].reshape(O0.shape), z[N:].reshape(P0.shape))
+    z, mu = np.concatenate([O0.ravel(), P0.ravel()]), 1.0
+    f_d, mu_d, rho_d, margin, searched, projected, halved = [], [], [], np.inf, 0, 0, 0
+    for _ in range(4):
+        O, P = z[:N].reshape(O0.shape), z[N:].reshape(P0.shape)
+        J = dense_jacobian_joint(pb, O, P)
+        l, dl, d2l = oracle.ell_terms(pb.loss, zeta_of(pb, O, P).ravel(), y)
+        f = float(l.sum())
+        g = J.T @ dl
+        G = J.T @ (d2l[:, None] * J)
+        D_O, D_P = oracle.ggn_diag(pb, O, P=P, floor_rel=1e-6)
+        Dz = np.concatenate([D_O.ravel(), D_P.ravel()])
+        D = np.concatenate([Dz, Dz])
+        g_c = g[:N + M] + 1j * g[N + M:]
+        f_d.append(f)
+        while True:
+            d = np.linalg.solve(G + mu * np.diag(D), -g)
+            trial = z + d[:N + M] + 1j * d[N + M:]
+            pred = -(g @ d + 0.5 * d @ (G @ d))
+            rho = (f - fz(trial)) / pred if pred > 0 else -1.0
+            margin = min(margin, abs(rho - 0.25), abs(rho - 0.75))
+            if rho > 0.75:
+                mu = max(mu / 4.0, 1e-8)
+            elif rho <= 0.25:
+                mu = 4.0 * mu
+            if rho > 1e-4:
+                tp = proj(trial)
+                projected += int(np.any(np.abs(trial[:N]) > rO))
+                if fz(tp) - f_min < gamma * (f - f_min):
+                    z = tp
+                else:
+                    searched += 1
+                    s = tp - z
+                    ss = float(np.sum(np.abs(s) ** 2))
+                    if not (float(np.sum((g_c.conj() * s).real)) <= -tau_s * ss ** (p_s / 2)):
+                        s = -g_c
+                    sn2 = float(np.sum(np.abs(s) ** 2))
+                    alpha = 1.0
+                    for _ls in range(max_ls):
+                        t_ = proj(z + alpha * s)
+                        if fz(t_) <= f - sigma * alpha * sn2:
+                            z = t_
+                            break
+                        alpha *= 0.5
+                        halved += 1
+                break
+        mu_d.append(mu)
+        rho_d.append(rho)
+    assert margin > 1e-3 and projected > 0 and searched > 0 and halved > 0
+    O_o, P_o, info = oracle.lm_solve2(pb, O0, P0, beta=1e-10, mu0=1.0, max_outer=4, max_cg=4000,
+                                      scaled=1, joint=1, projected=1, sigma=sigma)
+    assert info["n_outer"] == 4
+    np.testing.assert_allclose(info["f"], f_d, rtol=1e-6)
+    np.testing.assert_array_equal(info["mu"], mu_d)
+    np.testing.assert_allclose(info["rho"], rho_d, rtol=1e-4)
+    assert np.linalg.norm(O_o.ravel() - z[:N]) <= 1e-5 * np.linalg.norm(z[:N])
+    assert np.linalg.norm(P_o.ravel() - z[N:]) <= 1e-5 * np.linalg.norm(z[N:])
