@@ -1,0 +1,33 @@
+"""Host-side arithmetic of bench.py (no GPU): the roofline's algorithmic work per GGN
+product, the metric labels, and the traffic record that ties a profile summary to the
+kernel sources it was captured from."""
+import math
+
+import bench
+from paper_2103_01767_gb300 import synth
+
+
+def test_algorithmic_work_per_product_at_the_headline_size():
+    K, M, N = 3600, 128 * 128, 1024 * 1024
+    # two M-point 2D FFTs per position at 5 M log2 M flops, plus 24 flops per pixel
+    assert bench.matvec_flops(K, M) == K * (2 * 5 * M * 14 + 24 * M) == 9_673_113_600
+    # the cache (8 K M), v and out read-modify-written (3 x 8 N), the probe (8 M)
+    assert bench.matvec_bytes(K, M, N) == 8 * K * M + 24 * N + 8 * M == 497_156_096
+    assert math.isclose(bench.fft_flops(M), 5 * M * math.log2(M))
+
+
+def test_metric_labels_follow_the_workload():
+    assert bench.metric_for(synth.LARGE) == bench.METRIC
+    assert bench.metric_for(synth.SMALL) == "GGN matvecs/s (128^2 obj, 64 pos, 32^2 probe)"
+
+
+def test_recorded_traffic_is_tied_to_the_kernel_sources():
+    """The profile summary's traffic line carries the hash of the kernel sources it was
+    captured from; the bench reports the traffic only while they are unchanged (else null)."""
+    with open(bench.PROFILE_FILE) as fh:
+        text = fh.read()
+    line = [l for l in text.splitlines() if l.startswith("traffic_bytes_per_launch:")][-1]
+    _, value, _, h = line.split()
+    assert bench.recorded_traffic() == (float(value) if h == bench.kernel_hash() else None)
+    # within 1 % of the algorithmic bytes: no re-reads
+    assert abs(float(value) - bench.matvec_bytes(3600, 128 * 128, 1024 * 1024)) < 0.01 * float(value)
