@@ -329,6 +329,45 @@ def setup_workload(ptylm, torch, w, dev, stream):
     return ctx, O0, P, y, pos, step_used
 
 
+def measure_fp32_peak(ptylm, dev, stream, launches=10, iters=50000):
+    """The library's FFMA loop (ptylm_fp32_peak): every SM's FP32 pipes busy with independent
+    FMA chains, 10 timed launches of ~50 ms, median; clocks sampled while it runs."""
+    with ClockSampler(dev.index) as clk:
+        tflops, ms = ptylm.ptylm_fp32_peak(launches=launches, iters=iters, stream=stream)
+    return {"tflops": tflops, "ms_per_launch": ms, "launches": launches, "clocks": clk.summary(),
+            "kernel": "k_ffma_loop (2048 threads per SM, 8 independent FMA chains per thread)"}
+
+
+def matvec_protocol(ptylm, torch, ctx, N, dev, stream, trials=10, min_trial_s=0.2, warmup=10):
+    """The GGN product alone, back to back: `warmup` products, then `trials` trials of as many
+    products as fill `min_trial_s` each (CUDA events on the context stream around each
+    trial), clocks sampled throughout.  The context must hold a linearisation point."""
+    v = torch.randn((N,), dtype=torch.complex64, device=dev)
+    out = torch.empty_like(v)
+    for _ in range(warmup):
+        ptylm.ggn_matvec(ctx, v, out, 1e-3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(warmup):
+        ptylm.ggn_matvec(ctx, v, out, 1e-3)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    per = e0.elapsed_time(e1) / 1e3 / warmup
+    n = max(10, int(math.ceil(min_trial_s / max(per, 1e-6))))
+    times = []
+    with ClockSampler(dev.index) as clk:
+        for _ in range(trials):
+            e0.record(stream)
+            for _ in range(n):
+                ptylm.ggn_matvec(ctx, v, out, 1e-3)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            times.append(e0.elapsed_time(e1) / 1e3 / n)
+    med = statistics.median(times)
+    return {"trials": trials, "products_per_trial": n, "median_us": 1e6 * med, "min_us": 1e6 * min(times),
+            "max_us": 1e6 * max(times), "timed_s": sum(times) * n, "clocks": clk.summary()}
+
+
 # ---------------------------------------------------------------------------------------
 # Comparison and LM time-to-accuracy legs (outside the timed matvec region)
 # ---------------------------------------------------------------------------------------
@@ -372,12 +411,13 @@ def oracle_time_to_accuracy(target=1e-3):
             "threads": oracle.num_threads()}
 
 
-def gpu_time_to_accuracy(ptylm, torch, dev, stream, target=1e-3, reps=5, large_ref_outer=400):
+def gpu_time_to_accuracy(ptylm, torch, dev, stream, target=1e-3, reps=5, large_ref_outer=200):
     """Wall time of lm_solve (plain LM, data resident after lm_init) from the flat start to the
     first outer iteration with object error <= target, measured on the device each iteration.
       small: 128^2 / 32^2 noiseless, reference = the ground truth (median of reps runs);
-      large: 1024^2 / 128^2 / 3600 positions, Poisson 1e3, reference = the converged PLM-S
-             reconstruction; plain LM and PLM-S are timed against it."""
+      large: 1024^2 / 128^2 / 3600 positions, Poisson 1e3, reference = the converged plain-LM
+             reconstruction (reading C15); plain LM, PLM and PLM-S are timed against it.
+    Returns the results and the large workload's reference (its context stays open)."""
     out = {}
     w, O_true, P, pos, mask = small_tta_problem()
     c64 = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.complex64)).to(dev)
@@ -401,37 +441,49 @@ def gpu_time_to_accuracy(ptylm, torch, dev, stream, target=1e-3, reps=5, large_r
     out["small"] = {"seconds": statistics.median(secs), "outer": int(info["n_outer"]), "cg": int(info["cg_total"]),
                     "err": float(info["err"][-1]), "reference": "ground truth", "runs": reps}
 
+    ref = large_poisson_reference(ptylm, torch, dev, stream, large_ref_outer)
+    out["large"] = {"reference": ref["description"]}
+    variants = {"LM": {}, "PLM": {"scaled": 1}, "PLM-S": {"scaled": 1, "surrogate_T": 20}}
+    for name, kw in variants.items():
+        out["large"][name] = timed_solve(ptylm, torch, dev, ref, ref["O0"].clone(), target, large_ref_outer, **kw)
+    return out, ref
+
+
+def large_poisson_reference(ptylm, torch, dev, stream, max_outer=200):
+    """The 1024^2 / 128^2 / 3600-position Poisson 1e3 workload and its reference object:
+    the converged plain-LM reconstruction (Algorithm 1, D = I) from the flat start, run for
+    max_outer outer iterations or until the damping runs away (reading C15)."""
     wl = synth.LARGE
     ctx, O0, P, y, posd, _ = setup_workload(ptylm, torch, wl, dev, stream)
     mask = synth.illumination_mask(wl.n, P.cpu().numpy(), posd.cpu().numpy(), 0.1)
     maskd = torch.from_numpy(mask.astype(np.uint8)).to(dev)
-    # The noisy data have no exact solution: the reference is the converged reconstruction,
-    # run until the damping runs away (no FP32-resolvable decrease of f is left).
-    variants = {"LM": {}, "PLM-S": {"scaled": 1, "surrogate_T": 20}}
     O_ref = O0.clone()
+    torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    st, ref_info = ptylm.lm_solve(ctx, O_ref, P, hist_len=large_ref_outer, max_outer=large_ref_outer,
-                                  **variants["PLM-S"])
+    st, info = ptylm.lm_solve(ctx, O_ref, P, hist_len=max_outer, max_outer=max_outer)
     ref_s = time.perf_counter() - t0
-    out["large"] = {"reference": f"PLM-S (s_0 = 1, T = 20) run from the flat start until the damping ran away "
-                                 f"({ref_info['n_outer']} outer iterations, {ref_s:.2f} s, status {st})"}
-    for name, kw in variants.items():
-        O = O0.clone()
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        _, info = ptylm.lm_solve(ctx, O, P, hist_len=large_ref_outer, O_ref=O_ref, mask=maskd,
-                                 max_outer=large_ref_outer, target_err=target, **kw)
-        secs = time.perf_counter() - t0
-        err = info["err"][np.isfinite(info["err"])]  # a run that stalls records no error for its last iteration
-        reached = bool(err.size and err[-1] <= target)
-        out["large"][name] = {"seconds": secs if reached else None, "outer": int(info["n_outer"]),
-                              "cg": int(info["cg_total"]), "err": float(err[-1]) if err.size else None,
-                              "err_min": float(err.min()) if err.size else None}
-    ptylm.lm_destroy(ctx)
-    return out
+    g = info["gnorm"][np.isfinite(info["gnorm"])]
+    desc = (f"plain LM (Algorithm 1, D = I) from the flat start, {info['n_outer']} outer iterations "
+            f"({'the damping ran away' if st == ptylm.PTYLM_ERR_STALLED else 'iteration limit'}), {ref_s:.2f} s; "
+            f"||grad f|| {g[0]:.3e} -> {g[-1]:.3e} (min {g.min():.3e})" if g.size else "plain LM from the flat start")
+    return {"ctx": ctx, "O0": O0, "P": P, "pos": posd, "O_ref": O_ref, "mask": maskd, "description": desc,
+            "outer": int(info["n_outer"])}
 
 
-def learned_vs_plain(ptylm, torch, dev, target=1e-3, pairs=200_000, batch=64, reps=3):
+def timed_solve(ptylm, torch, dev, ref, O, target, max_outer, prefix_s=0.0, **kw):
+    """lm_solve from O (data resident) until object error <= target against ref["O_ref"]."""
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    _, info = ptylm.lm_solve(ref["ctx"], O, ref["P"], hist_len=max_outer, O_ref=ref["O_ref"], mask=ref["mask"],
+                             max_outer=max_outer, target_err=target, **kw)
+    secs = time.perf_counter() - t0 + prefix_s
+    err = info["err"][np.isfinite(info["err"])]  # a run that stalls records no error for its last iteration
+    reached = bool(err.size and err[-1] <= target)
+    return {"seconds": secs if reached else None, "outer": int(info["n_outer"]), "cg": int(info["cg_total"]),
+            "err": float(err[-1]) if err.size else None, "err_min": float(err.min()) if err.size else None}
+
+
+def learned_vs_plain(ptylm, torch, dev, target=1e-3, pairs=200_000, batch=64, reps=3, poisson_ref=None):
     """Learned initialisation against the flat start (plain LM, Algorithm 1, D = I) on a
     held-out 1024^2 object / 3600 positions / 128^2 probe with noiseless amplitude data:
     train the 6-layer network on `pairs` forward-model pairs cut from 8 other random objects,
@@ -492,6 +544,36 @@ def learned_vs_plain(ptylm, torch, dev, target=1e-3, pairs=200_000, batch=64, re
     out["plain"]["start_err"] = _object_error(flat, O_true, mask)
     out["speedup"] = out["plain"]["seconds"] / out["learned"]["seconds"]
     ptylm.lm_destroy(ctx)
+    if poisson_ref is not None:
+        # the Poisson 1e3 data of the headline workload (same object, scan and probe shape),
+        # against its converged plain-LM reconstruction: plain LM from the flat start vs LM
+        # from the stitched network estimate (inference and stitching inside the time)
+        ref = poisson_ref
+        Pp = ref["P"]
+        Ol = torch.empty_like(ref["O0"])
+        res = {"workload": "1024^2 / 3600 positions / 128^2 probe, Poisson 1e3 photons peak; reference = "
+                           + ref["description"]}
+        for name in ("plain", "learned"):
+            runs = []
+            for _ in range(reps):
+                if name == "learned":
+                    torch.cuda.synchronize(dev)
+                    t0 = time.perf_counter()
+                    ptylm.learned_init(ref["ctx"], net, Pp, idx, Ol)
+                    torch.cuda.synchronize(dev)
+                    runs.append(timed_solve(ptylm, torch, dev, ref, Ol.clone(), target, 200,
+                                            prefix_s=time.perf_counter() - t0))
+                else:
+                    runs.append(timed_solve(ptylm, torch, dev, ref, ref["O0"].clone(), target, 200))
+            ok = [r["seconds"] for r in runs if r["seconds"] is not None]
+            res[name] = dict(runs[0], seconds=statistics.median(ok) if len(ok) == len(runs) else None,
+                             runs=len(runs))
+        ptylm.learned_init(ref["ctx"], net, Pp, idx, Ol)
+        res["learned"]["start_err"] = _object_error(Ol, ref["O_ref"], ref["mask"])
+        res["plain"]["start_err"] = _object_error(ref["O0"], ref["O_ref"], ref["mask"])
+        if res["plain"]["seconds"] and res["learned"]["seconds"]:
+            res["speedup"] = res["plain"]["seconds"] / res["learned"]["seconds"]
+        out["poisson"] = res
     net.close()
     return out
 
@@ -565,9 +647,8 @@ def run_batch(args):
     flops = sum(matvec_flops(m.K, m.m * m.m) for m in members)
     bytes_ = sum(matvec_bytes(m.K, m.m * m.m, m.n * m.n) for m in members)
     clocks = clk.summary()
-    sm_max = clocks.get("sm_max_mhz") or 2070.0
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_fp32 = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fp32 = measure_fp32_peak(ptylm, dev, torch.cuda.current_stream(dev))
+    peak_fp32 = fp32["tflops"]
     t_step = elapsed / args.steps
     # e2e: the direction from pinned host memory, the product back to it, every step
     v_h = v.cpu().pin_memory()
@@ -622,6 +703,8 @@ def run_batch(args):
                    "parallelism": "replicas1", "l2": "inputs larger than L2: 2.5 GB of caches streamed per step"},
         "roofline": {"bound": "alu", "achieved": flops / t_step / 1e12, "peak": peak_fp32, "unit": "TFLOP/s",
                      "frac": flops / t_step / 1e12 / peak_fp32, "traffic": None, "kernel": "k_batch<matvec>",
+                     "peak_kind": "measured in this run: FFMA loop (ptylm_fp32_peak), median of 10 launches",
+                     "peak_measured": fp32,
                      "flops_per_launch": flops, "hbm_bytes_per_launch": bytes_},
         "cpu_baseline": None,
         "e2e": {"value": bt.B / e2e_s, "unit": BATCH_UNIT, "h2d_bytes_per_step": 8 * bt.total,
@@ -714,16 +797,23 @@ def main():
     # inside the timed region only the GGN product's launches carry event pairs (roofline)
     mv_kid = ptylm.KERNEL_GGN_MATVEC_JOINT if w.joint else ptylm.KERNEL_GGN_MATVEC
     ptylm.ptylm_profile_select(ctx, [mv_kid])
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    matvecs = 0
+    # the K timed steps run as (up to) 10 equal trials, each bracketed by its own events
+    n_trials = max(1, min(10, args.steps))
+    bounds = [round(i * args.steps / n_trials) for i in range(n_trials + 1)]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(n_trials + 1)]
+    matvecs, trial_mv = 0, []
     with ClockSampler(local) as clk:
         torch.cuda.synchronize(dev)
-        ev0.record(stream)
-        for _ in range(args.steps):
-            matvecs += step(O, P, O0)
-        ev1.record(stream)
+        evs[0].record(stream)
+        for i in range(n_trials):
+            mv0 = matvecs
+            for _ in range(bounds[i + 1] - bounds[i]):
+                matvecs += step(O, P, O0)
+            evs[i + 1].record(stream)
+            trial_mv.append(matvecs - mv0)
         torch.cuda.synchronize(dev)
-    elapsed = ev0.elapsed_time(ev1) / 1e3
+    elapsed = evs[0].elapsed_time(evs[-1]) / 1e3
+    trial_values = [mv / (evs[i].elapsed_time(evs[i + 1]) / 1e3) for i, mv in enumerate(trial_mv)]
     mv_ms, mv_n = ptylm.ptylm_profile_read(ctx, mv_kid)
     _, launches = ptylm.ptylm_profile_read(ctx, -1)
     ptylm.ptylm_profile(ctx, False)
@@ -752,6 +842,10 @@ def main():
     ptylm.ptylm_profile(ctx, False)
     elapsed, total_matvecs = reduce_over_ranks(elapsed, matvecs, dev)
     value = total_matvecs / elapsed
+    # outside the timed region: the FP32 peak of this GPU and the GGN product's own protocol
+    # (10 trials of back-to-back products, >= 2 s), at the linearisation the last step left
+    fp32 = measure_fp32_peak(ptylm, dev, stream)
+    protocol = None if w.joint else matvec_protocol(ptylm, torch, ctx, w.n * w.n, dev, stream)
 
     # End to end through the C-ABI with pinned host buffers: H2D of O and P, D2H of O.
     O0_h = O0.cpu().pin_memory()
@@ -775,15 +869,18 @@ def main():
                       "note": "cuFFT batched C2C forward + inverse over the same [K, m, m] complex64 "
                               "(torch.fft, comparison only); the matvec adds gather, probe multiplies, "
                               "the frequency stage and the overlap scatter-add"}
-        tta = gpu_time_to_accuracy(ptylm, torch, dev, stream)
+        tta, large_ref = gpu_time_to_accuracy(ptylm, torch, dev, stream)
         if oracle_tta is not None:
             tta["small"]["oracle"] = oracle_tta
-        tta["learned_vs_plain"] = learned_vs_plain(ptylm, torch, dev)
+        tta["learned_vs_plain"] = learned_vs_plain(ptylm, torch, dev, poisson_ref=large_ref)
+        ptylm.lm_destroy(large_ref["ctx"])
+        del large_ref
     avg_mv_s = (mv_ms / 1e3) / max(mv_n, 1)
     flops = matvec_flops(K, M)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_fp32 = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    peak_derived = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    peak_fp32 = fp32["tflops"]
     achieved = flops / avg_mv_s / 1e12
     hbm_peak, hbm_kind = measured_peaks()
     hbm_achieved = matvec_bytes(K, M, N) / avg_mv_s / 1e9
@@ -800,7 +897,11 @@ def main():
                          "kernel": f"k_ggn_matvec<{int(math.log2(w.m))}{', joint' if w.joint else ''}>",
                          "avg_launch_us": avg_mv_s * 1e6,
                          "launches": mv_n, "flops_per_launch": flops,
-                         "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                         "peak_kind": "measured in this run: FFMA loop (ptylm_fp32_peak), median of 10 launches",
+                         "peak_measured": fp32,
+                         "peak_derived": peak_derived,
+                         "frac_of_derived": achieved / peak_derived,
+                         "peak_basis_derived": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
                          "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                                  "frac": hbm_achieved / hbm_peak, "peak_kind": hbm_kind,
                                  "bytes_per_launch": matvec_bytes(K, M, N)}},
@@ -809,6 +910,9 @@ def main():
                     "d2h_bytes_per_step": 8 * N},
             "clocks": clocks,
             "gpu_launches": int(launches),
+            "trials": {"n": n_trials, "steps_per_trial": [bounds[i + 1] - bounds[i] for i in range(n_trials)],
+                       "values": trial_values, "median": statistics.median(trial_values)},
+            "matvec_protocol": protocol,
             "kernels": per_kernel,
             "comparison": comparison,
             "time_to_accuracy": tta,

@@ -109,6 +109,12 @@ typedef struct {
      * results bit for bit.  A bounded grid-wide wait that gives up ends lm_solve with
      * PTYLM_ERR_TIMEOUT. */
     int separate_cg_kernels;
+    /* Polls of each bounded grid-wide wait of the single-launch CG iteration before it gives
+     * up: 0 (default) about a second (2^24 polls of >= 32 ns); > 0 that many.  A small value
+     * exists for fault-injection tests: the waits then run out, every CTA still finishes its
+     * in-bounds work and exits, and lm_solve returns PTYLM_ERR_TIMEOUT with the context
+     * usable for the next call. */
+    int wait_polls;
 } ptylm_lm_params;
 
 /* Per-call results of lm_solve.  hist_* point to host arrays of hist_len entries (or are
@@ -179,6 +185,15 @@ ptylm_status jvp(ptylm_ctx* ctx, const ptylm_c64* vO, const ptylm_c64* vP, float
  *   (joint contexts only) or NULL. */
 ptylm_status jtvp(ptylm_ctx* ctx, const float* w, ptylm_c64* outO, ptylm_c64* outP);
 
+/* Closed-form diagonal of the GGN in real coordinates at the linearisation point (App. B,
+ * Eqs. ggn_diag_elem_final, ggn_diag_mat, ggn_joint_diag; the paper's h ~ |psihat|^2
+ * approximation):  D_O[n] = sum_{k: n in patch k} |P[n - r_k]|^2 tr_k / (2M),
+ *                  D_P[m] = sum_k |O[r_k + m]|^2 tr_k / (2M),   tr_k = sum_m d2l_km.
+ *   D_out: device float [ny*nx] or, for joint contexts, [ny*nx + my*mx].
+ *   floor_rel: entries of each block below floor_rel * (that block's max) are raised to
+ *   it (0 disables). */
+ptylm_status ggn_diag(ptylm_ctx* ctx, float* D_out, double floor_rel);
+
 /* Damped GGN-vector product, the hot path (App. A steps 2-4, Eq. ggn_magnitude_appendix_2):
  *     outO = J^T( Hess_zeta l . J vO ) + lambda D vO
  * One fused kernel per call: patch gather x P, 2D FFT, frequency stage with the cached a
@@ -189,15 +204,6 @@ ptylm_status jtvp(ptylm_ctx* ctx, const float* w, ptylm_c64* outO, ptylm_c64* ou
  *   D: device float diagonal scaling over z -- [ny*nx] (object only) or [ny*nx + my*mx]
  *   (object then probe) -- or NULL for the identity.
  * Needs a linearisation point (PTYLM_ERR_STATE otherwise). */
-
-/* Closed-form diagonal of the GGN in real coordinates at the linearisation point (App. B,
- * Eqs. ggn_diag_elem_final, ggn_diag_mat, ggn_joint_diag; the paper's h ~ |psihat|^2
- * approximation):  D_O[n] = sum_{k: n in patch k} |P[n - r_k]|^2 tr_k / (2M),
- *                  D_P[m] = sum_k |O[r_k + m]|^2 tr_k / (2M),   tr_k = sum_m d2l_km.
- *   D_out: device float [ny*nx] or, for joint contexts, [ny*nx + my*mx].
- *   floor_rel: entries of each block below floor_rel * (that block's max) are raised to
- *   it (0 disables). */
-ptylm_status ggn_diag(ptylm_ctx* ctx, float* D_out, double floor_rel);
 ptylm_status ggn_matvec(ptylm_ctx* ctx, const ptylm_c64* vO, const ptylm_c64* vP, double lambda,
                         const float* D, ptylm_c64* outO, ptylm_c64* outP);
 
@@ -275,32 +281,45 @@ ptylm_status ptylm_profile(ptylm_ctx* ctx, int enable);
 ptylm_status ptylm_profile_select(ptylm_ctx* ctx, unsigned mask);
 ptylm_status ptylm_profile_read(ptylm_ctx* ctx, int kernel, double* total_ms, long long* launches);
 
-/* Allocation-free error metric (the paper has no counterpart: this serves callers that
- * cannot allocate device memory -- code that issues work while its stream is being
- * captured into a CUDA graph, where cudaMalloc is not allowed; steady-state loops that
- * forbid allocation after start-up; hosts whose device memory is owned by another
- * allocator).  Computes the same f = sum_k sum_m l(zeta_km, y_km) and ||grad_zeta l||^2 as
- * forward_loss(cache = 0), without a context and without allocating: the caller passes
- * all inputs and the output, and the only scratch (twiddle tables, FP64 partial sums, a
- * counter, an error flag) is a file-scope device array of PTYLM_NOALLOC_SCRATCH_BYTES that
- * every GPU loading the library holds until the process exits.
+/* Allocation-free error metric (the paper has no counterpart).  It serves callers that must
+ * not allocate device memory: serving or real-time loops that reserve all their memory at
+ * start-up, because cudaMalloc and cudaFree can synchronise the device and take unbounded
+ * time; plug-ins inside a host framework whose memory pool already holds nearly all of the
+ * device memory, so a cudaMalloc of their own would fail; and code whose every device byte
+ * must be accounted to another allocator.  It computes the same f = sum_k sum_m
+ * l(zeta_km, y_km) (Eq. ell_magnitude) and ||grad_zeta l||^2 as forward_loss(cache = 0),
+ * without a context and without allocating: the caller passes all inputs and the output,
+ * and the only scratch (twiddle tables, FP64 partial sums, a counter, an error flag) is a
+ * file-scope device array of PTYLM_NOALLOC_SCRATCH_BYTES that every GPU loading the
+ * library holds until the process exits.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.
  *   ny, nx: object size; m: probe side (32, 64 or 128; larger sizes are rejected with
  *   PTYLM_ERR_ARG); K >= 0; loss, background: as in ptylm_desc.
  *   O [ny][nx], P [m][m], positions int32 [K][2] (8-byte aligned), y float [K][m][m] in
  *   natural order: device pointers.  out_dev: device double[2] <- (f, ||grad_zeta l||^2).
- *   stream: cudaStream_t.
+ *   stream: cudaStream_t (NULL = legacy default stream).
  * At most PTYLM_NOALLOC_MAX_CTAS CTAs run (fewer positions in flight, same result).
- * The first call on a device sets up that device's scratch (symbol address, twiddle
- * upload): make it before any stream capture.  Every call shares the scratch, which keeps
- * the last call's contents; the counter and flag are cleared at the start of each call.
- * Calls whose work overlaps on the GPU (other streams, other threads) race and give wrong
- * results.  The call synchronises `stream` to read the error flag: positions outside the
- * object return PTYLM_ERR_ARG. */
+ * The first call on a device, with that device current, looks up the scratch's device
+ * address and uploads the twiddle tables there (a synchronous copy).  Every call shares
+ * the scratch, which keeps the last call's contents; the counter and the flag are cleared
+ * at the start of each call.  Calls whose work overlaps on the GPU (other streams, other
+ * threads) race and give wrong results.  Before returning, the call waits for its work on
+ * `stream` to finish and reads the error flag: positions outside the object return
+ * PTYLM_ERR_ARG. */
 #define PTYLM_NOALLOC_MAX_CTAS 2048
 #define PTYLM_NOALLOC_SCRATCH_BYTES 35328
 ptylm_status ptylm_forward_loss_noalloc(int ny, int nx, int m, int K, int loss, float background,
                                         const ptylm_c64* O, const ptylm_c64* P, const int32_t* positions,
                                         const float* y, double* out_dev, void* stream);
+
+/* Measured FP32 peak of the current device (instrumentation; the paper has no counterpart):
+ * `launches` timed launches (after one untimed one) of an FFMA loop that keeps every SM's
+ * FP32 pipes busy -- 2048 threads per SM, 8 independent FMA chains per thread, 128 * iters
+ * FMAs per thread -- each timed with CUDA events on `stream` (cudaStream_t, NULL = legacy
+ * stream).  tflops_host: host double <- 2 x FMAs / median launch time, in TFLOP/s; ms_host:
+ * host double <- the median launch time in ms (may be NULL).  The call synchronises
+ * `stream`.  PTYLM_ERR_ARG for launches < 1, iters < 1 or tflops_host == NULL. */
+ptylm_status ptylm_fp32_peak(int launches, int iters, double* tflops_host, double* ms_host, void* stream);
 
 /* Free the context and everything it allocated (NULL is accepted). */
 ptylm_status lm_destroy(ptylm_ctx* ctx);

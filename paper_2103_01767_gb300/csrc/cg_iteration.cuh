@@ -40,7 +40,7 @@ __device__ __forceinline__ float2 precondition(float2 r, const float* D, float l
     return make_float2(r.x * inv, r.y * inv);
 }
 
-constexpr unsigned kCoopSpinLimit = 1u << 24;   // x >= 32 ns sleep: about a second
+constexpr unsigned kCoopSpinLimit = 1u << 24;   // x >= 32 ns sleep: about a second (the default limit)
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     unsigned v;
@@ -66,7 +66,7 @@ __device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v
 // makes every partial visible); the release is a release store read by acquire loads.
 template <int W>
 __device__ void coop_reduce_round(double (&s)[W], double* part, unsigned* cnt, double* sc, int op, unsigned round,
-                                  double tol = -1.0) {
+                                  unsigned spin_limit, double tol = -1.0) {
     __shared__ bool is_last;
     block_sum<W>(s);
     if (threadIdx.x == 0) {
@@ -95,7 +95,7 @@ __device__ void coop_reduce_round(double (&s)[W], double* part, unsigned* cnt, d
     } else if (threadIdx.x == 0) {
         unsigned spins = 0;
         while (ld_acquire_gpu(cnt + kCoopRelease) < round) {
-            if (++spins > kCoopSpinLimit) {
+            if (++spins > spin_limit) {
                 *(volatile double*)(sc + S_CG_TIMEOUT) = 1.0;
                 break;
             }
@@ -111,7 +111,8 @@ constexpr int kCgUnroll = 2;
 __global__ void __launch_bounds__(256) k_cg_iteration(float2* __restrict__ x, float2* __restrict__ r,
                                                       float2* __restrict__ p, float2* __restrict__ q,
                                                       const float* __restrict__ D, float lambda, long n,
-                                                      double* part, unsigned* cnt, double* sc, double tol) {
+                                                      double* part, unsigned* cnt, double* sc, double tol,
+                                                      unsigned spin_limit) {
     constexpr int U = kCgUnroll;
     if (tol >= 0.0 && __ldcg(sc + S_CG_DONE) != 0.0) return;  // converged earlier: every CTA sees the same flag
     const long stride = (long)gridDim.x * blockDim.x;
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(256) k_cg_iteration(float2* __restrict__ x, fl
             if (base + k * stride < n) f += rdotf(pv[k], qv[k]);
     }
     double s1[1] = {f};
-    coop_reduce_round<1>(s1, part, cnt, sc, OP_ALPHA, 1u);
+    coop_reduce_round<1>(s1, part, cnt, sc, OP_ALPHA, 1u, spin_limit);
     const float alpha = (float)__ldcg(sc + S_ALPHA);
 
     // x += alpha p, r -= alpha q; r.z and r.r -> beta
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(256) k_cg_iteration(float2* __restrict__ x, fl
         }
     }
     double s2[2] = {f0, f1};
-    coop_reduce_round<2>(s2, part + gridDim.x, cnt, sc, OP_BETA, 2u, tol);
+    coop_reduce_round<2>(s2, part + gridDim.x, cnt, sc, OP_BETA, 2u, spin_limit, tol);
     const float beta = (float)__ldcg(sc + S_BETA);
 
     // p = z + beta p, q = lambda D p

@@ -56,9 +56,11 @@ size_t cta_smem_bytes(int LS);
 cudaError_t kernel_prepare(int LS, int kid, int* ctas_per_sm);
 
 // Copy measurements from natural [K][S][S] order into the kernels' team-register order
-// (square roots when take_sqrt: the Gaussian metric only uses sqrt(y)).
+// (square roots when take_sqrt: the Gaussian metric only uses sqrt(y)).  When `bad` is not
+// NULL, *bad |= 1 if any entry is negative, infinite or NaN (the caller zeroes it first);
+// y_perm == NULL only checks.
 cudaError_t permute_measurements(int LS, const float* y, float* y_perm, int K, int take_sqrt, int blocks,
-                                 cudaStream_t stream);
+                                 cudaStream_t stream, unsigned* bad);
 
 // Record the thread-local message that ptylm_last_error() returns (shared by all entry points).
 void set_last_error(const char* msg);

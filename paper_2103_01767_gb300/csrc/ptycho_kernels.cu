@@ -339,25 +339,28 @@ k_jvp(AdjArgs a) {
 // ---------------------------------------------------------------------------------------
 template <int LS>
 __global__ void k_permute_measurements(const float* __restrict__ y, float* __restrict__ y_perm, long total,
-                                       int take_sqrt) {
+                                       int take_sqrt, unsigned* bad) {
     using G = Geo<LS>;
+    bool ok = true;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
         const long k = i / G::M;
         const int r = (int)(i - k * G::M);
         const int e = r / G::T, t = r % G::T;
         const float v = y[k * G::M + freq_ky<G>(t) * G::S + freq_kx<G>(t, e)];
-        y_perm[i] = take_sqrt ? sqrtf(v) : v;
+        ok = ok && (v >= 0.0f) && (v <= 3.402823466e38f);   // counts are finite and >= 0 (NaN fails both)
+        if (y_perm) y_perm[i] = take_sqrt ? sqrtf(v) : v;
     }
+    if (bad && !ok) atomicOr(bad, 1u);
 }
 
 cudaError_t permute_measurements(int LS, const float* y, float* y_perm, int K, int take_sqrt, int blocks,
-                                 cudaStream_t stream) {
+                                 cudaStream_t stream, unsigned* bad) {
     const long total = (long)K << (2 * LS);
     if (total == 0) return cudaSuccess;
     switch (LS) {
-        case 5: k_permute_measurements<5><<<blocks, 256, 0, stream>>>(y, y_perm, total, take_sqrt); break;
-        case 6: k_permute_measurements<6><<<blocks, 256, 0, stream>>>(y, y_perm, total, take_sqrt); break;
-        case 7: k_permute_measurements<7><<<blocks, 256, 0, stream>>>(y, y_perm, total, take_sqrt); break;
+        case 5: k_permute_measurements<5><<<blocks, 256, 0, stream>>>(y, y_perm, total, take_sqrt, bad); break;
+        case 6: k_permute_measurements<6><<<blocks, 256, 0, stream>>>(y, y_perm, total, take_sqrt, bad); break;
+        case 7: k_permute_measurements<7><<<blocks, 256, 0, stream>>>(y, y_perm, total, take_sqrt, bad); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -261,6 +261,7 @@ static_assert(PROF_CG == PTYLM_KERNEL_CG_ITERATION, "profile ids follow the kern
 
 struct ptylm_ctx {
     ptylm_desc d;
+    unsigned cg_spin_limit = kCoopSpinLimit;  // polls per bounded wait of the CG iteration
     int LS = 0, S = 0, M = 0;
     long N = 0;
     long L = 0;                    // length of the state z: N, or N + M for joint contexts
@@ -543,7 +544,8 @@ static ptylm_status cg_iteration(ptylm_ctx* c, float2* x, float2* r, float2* p, 
     STATUS_TRY(prof_begin(c, PROF_CG, &e0, &e1));
     if (!separate && c->coop_grid > 0) {
         unsigned* cnt = c->counters + CNT_COOP;
-        void* args[] = {&x, &r, &p, &q, &D, &lambda, &n, &part, &cnt, &sc, &tol};
+        unsigned spin = c->cg_spin_limit;
+        void* args[] = {&x, &r, &p, &q, &D, &lambda, &n, &part, &cnt, &sc, &tol, &spin};
         CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_cg_iteration, dim3(c->coop_grid), dim3(VEC_THREADS), args, 0,
                                              c->stream));
         ++c->launches;
@@ -709,6 +711,7 @@ void ptylm_default_lm_params(ptylm_lm_params* p, int loss) {
     p->surrogate_end = 1e-4;
     p->surrogate_T = 0;
     p->separate_cg_kernels = 0;
+    p->wait_polls = 0;
 }
 
 // s_t of the App. E schedule: surrogate0 (surrogate_end / surrogate0)^(t / (T - 1)) for
@@ -838,11 +841,36 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
         return bail(fail(PTYLM_ERR_CUDA, "uploading context tables: %s", cudaGetErrorString(e)));
     }
     if (d.K > 0) {
-        cudaError_t e = permute_measurements(LS, y_dev, c->y_perm, d.K, d.loss == PTYLM_LOSS_GAUSSIAN, c->vec_grid, c->stream);
+        cudaError_t e = permute_measurements(LS, y_dev, c->y_perm, d.K, d.loss == PTYLM_LOSS_GAUSSIAN, c->vec_grid,
+                                             c->stream, c->counters + CNT_YBAD);
+        unsigned bad = 0;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&c->scal_host[0], c->counters + CNT_YBAD, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return bail(fail(PTYLM_ERR_CUDA, "copying measurements: %s", cudaGetErrorString(e)));
+        memcpy(&bad, &c->scal_host[0], sizeof bad);
+        if (bad) return bail(fail(PTYLM_ERR_ARG, "measurements y must be finite and >= 0"));
+        if (cudaMemsetAsync(c->counters + CNT_YBAD, 0, sizeof(unsigned), c->stream) != cudaSuccess)
+            return bail(fail(PTYLM_ERR_CUDA, "clearing the measurement flag"));
     }
     *out = c;
+    return PTYLM_OK;
+}
+
+// Whether y (natural order, K M entries) is finite and >= 0: one read-only pass on the
+// context stream, then a wait for the flag.
+static ptylm_status check_measurements(ptylm_ctx* c, const float* y_dev) {
+    CUDA_TRY(cudaMemsetAsync(c->counters + CNT_YBAD, 0, sizeof(unsigned), c->stream));
+    CUDA_TRY(permute_measurements(c->LS, y_dev, nullptr, c->d.K, 0, c->vec_grid, c->stream, c->counters + CNT_YBAD));
+    ++c->launches;
+    unsigned bad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&c->scal_host[0], c->counters + CNT_YBAD, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                             c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    memcpy(&bad, &c->scal_host[0], sizeof bad);
+    CUDA_TRY(cudaMemsetAsync(c->counters + CNT_YBAD, 0, sizeof(unsigned), c->stream));
+    if (bad) return fail(PTYLM_ERR_ARG, "measurements y must be finite and >= 0");
     return PTYLM_OK;
 }
 
@@ -850,9 +878,14 @@ ptylm_status ptylm_set_measurements(ptylm_ctx* c, const float* y_dev) {
     g_last_error.clear();
     if (!c) return fail(PTYLM_ERR_ARG, "ctx must be non-NULL");
     if (c->d.K > 0 && !y_dev) return fail(PTYLM_ERR_ARG, "y must be non-NULL when K > 0");
+    if (c->d.K == 0) {
+        c->has_lin = false;
+        return PTYLM_OK;
+    }
+    STATUS_TRY(check_measurements(c, y_dev));  // rejected data leave the context as it was
     c->has_lin = false;  // the loss cache depends on y; the point and the phasor do not
-    if (c->d.K == 0) return PTYLM_OK;
-    CUDA_TRY(permute_measurements(c->LS, y_dev, c->y_perm, c->d.K, c->d.loss == PTYLM_LOSS_GAUSSIAN, c->vec_grid, c->stream));
+    CUDA_TRY(permute_measurements(c->LS, y_dev, c->y_perm, c->d.K, c->d.loss == PTYLM_LOSS_GAUSSIAN, c->vec_grid,
+                                  c->stream, nullptr));
     ++c->launches;
     return PTYLM_OK;
 }
@@ -1043,8 +1076,9 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
                       ptylm_lm_stats* stats) {
     g_last_error.clear();
     if (!c || !O_inout || !P_inout || !prm) return fail(PTYLM_ERR_ARG, "ctx, O, P and params must be non-NULL");
-    if (prm->max_outer < 0 || prm->max_cg < 0 || !(prm->kappa > 1.0) || !(prm->mu0 > 0.0))
+    if (prm->max_outer < 0 || prm->max_cg < 0 || !(prm->kappa > 1.0) || !(prm->mu0 > 0.0) || prm->wait_polls < 0)
         return fail(PTYLM_ERR_ARG, "invalid LM parameters");
+    c->cg_spin_limit = prm->wait_polls > 0 ? (unsigned)prm->wait_polls : kCoopSpinLimit;
     if (prm->projected && (!(prm->radius_O > 0.0) || !(prm->radius_P > 0.0) || prm->max_ls < 0))
         return fail(PTYLM_ERR_ARG, "invalid projection parameters");
     if (c->d.K == 0) return fail(PTYLM_ERR_ARG, "lm_solve needs at least one scan position");

@@ -283,7 +283,7 @@ struct ptylm_batch {
     BatchProblem* probs = nullptr;
     BatchItem* items = nullptr;
     int n_items = 0, items_cap = 0;
-    unsigned* counters = nullptr;        // [0] work, [1] done, [2] dot counter
+    unsigned* counters = nullptr;        // [0] work, [1] done, [2] dot counter, [3] bad-measurement flag
     float2* tw = nullptr;
     double* f = nullptr;                 // [B][2]
     int* lm_active = nullptr;            // [B] problems still running their LM
@@ -624,7 +624,12 @@ ptylm_status ptylm_batch_init(ptylm_batch** out, int B, const ptylm_desc* descs,
         return bail(bfail(PTYLM_ERR_NOMEM, "pinned host buffers"));
     }
 
-    // per-problem data: positions (validated on the host), measurements, probe, cache
+    // per-problem data: positions (validated on the host), measurements (validated on the
+    // device: counters[3] is set by any negative or non-finite entry), probe, cache
+    if (cudaMemsetAsync(bt->counters, 0, sizeof(unsigned) * 4, bt->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(bfail(PTYLM_ERR_CUDA, "clearing batch counters"));
+    }
     bt->hprobs.resize(B);
     for (int b = 0; b < B; ++b) {
         const ptylm_desc& d = descs[b];
@@ -661,7 +666,7 @@ ptylm_status ptylm_batch_init(ptylm_batch** out, int B, const ptylm_desc* descs,
         if (d.K > 0) {
             cudaError_t e = permute_measurements(LS, y_dev[b], y, d.K, d.loss == PTYLM_LOSS_GAUSSIAN,
                                                  std::min(bt->num_sms * 8, std::max(1, (int)((long)d.K * M / 256))),
-                                                 bt->stream);
+                                                 bt->stream, bt->counters + 3);
             if (e != cudaSuccess) return bail(bfail(PTYLM_ERR_CUDA, "problem %d: measurements: %s", b, cudaGetErrorString(e)));
         }
         p.pos = pos;
@@ -679,16 +684,19 @@ ptylm_status ptylm_batch_init(ptylm_batch** out, int B, const ptylm_desc* descs,
     if (cudaMemcpyAsync(bt->tw, htw.data(), sizeof(float2) * BATCH_TW, cudaMemcpyHostToDevice, bt->stream) != cudaSuccess ||
         cudaMemcpyAsync(bt->chunks, hch.data(), sizeof(Chunk) * hch.size(), cudaMemcpyHostToDevice, bt->stream) != cudaSuccess ||
         cudaMemcpyAsync(bt->chunk_first, hfirst.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice, bt->stream) != cudaSuccess ||
-        cudaMemsetAsync(bt->counters, 0, sizeof(unsigned) * 4, bt->stream) != cudaSuccess ||
+        cudaMemsetAsync(bt->counters, 0, sizeof(unsigned) * 3, bt->stream) != cudaSuccess ||
         cudaMemsetAsync(bt->scal, 0, sizeof(double) * S_COUNT * B, bt->stream) != cudaSuccess) {
         cudaGetLastError();
         return bail(bfail(PTYLM_ERR_CUDA, "uploading batch tables"));
     }
     if ((s = upload_probs(bt)) != PTYLM_OK || (s = upload_items(bt, 0, 1)) != PTYLM_OK) return bail(s);
-    if (cudaStreamSynchronize(bt->stream) != cudaSuccess) {
+    if (cudaMemcpyAsync(bt->h_int, bt->counters + 3, sizeof(unsigned), cudaMemcpyDeviceToHost, bt->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(bt->stream) != cudaSuccess) {
         cudaGetLastError();
         return bail(bfail(PTYLM_ERR_CUDA, "batch initialisation"));
     }
+    if (bt->h_int[0] != 0) return bail(bfail(PTYLM_ERR_ARG, "measurements y must be finite and >= 0"));
     *out = bt;
     return PTYLM_OK;
 }

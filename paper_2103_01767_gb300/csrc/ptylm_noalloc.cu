@@ -1,13 +1,15 @@
 // ptylm_noalloc.cu -- ptylm_forward_loss_noalloc: the error metric f and ||grad_zeta l||^2
 // at (O, P) without a context and without allocating device memory.
 //
-// Some callers cannot allocate: a stream being captured into a CUDA graph (cudaMalloc is
-// not capturable), steady-state loops that forbid allocation after start-up, or hosts whose
-// device memory belongs to another allocator.  This entry point takes inputs and outputs
-// from the caller and keeps its only scratch -- twiddle tables, one FP64 partial pair per
-// CTA, the reduction counter, an error flag and two result slots -- in the file-scope
-// device array g_noalloc_scratch below, which every GPU that loads the library holds until
-// the process exits.  All calls share it: calls whose work overlaps on the GPU race.
+// Some callers must not allocate device memory: serving or real-time loops that reserve
+// all their memory at start-up (cudaMalloc and cudaFree can synchronise the device and take
+// unbounded time), plug-ins inside a host framework whose memory pool already holds nearly
+// all of the device memory, and code whose device bytes must all be accounted to another
+// allocator.  This entry point takes inputs and outputs from the caller and keeps its only
+// scratch -- twiddle tables, one FP64 partial pair per CTA, the reduction counter, an error
+// flag and two result slots -- in the file-scope device array g_noalloc_scratch below,
+// which every GPU that loads the library holds until the process exits.  All calls share
+// it: calls whose work overlaps on the GPU race.
 #include <cuda_runtime.h>
 
 #include <algorithm>

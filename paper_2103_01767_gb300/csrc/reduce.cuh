@@ -36,7 +36,8 @@ enum FinalOp {
 // Counters, one per reduction site (kernels on one stream never overlap).
 // From CNT_COOP: arrivals and exits of the single-launch CG iteration, and 32 words (one
 // 128-byte line) further its released round (cg_iteration.cuh).
-enum Counter { CNT_FWD = 0, CNT_VEC = 1, CNT_COOP = 32, CNT_COUNT = 96 };
+// CNT_YBAD: flag set by the measurement copy when an entry of y is negative or not finite.
+enum Counter { CNT_FWD = 0, CNT_VEC = 1, CNT_YBAD = 2, CNT_COOP = 32, CNT_COUNT = 96 };
 constexpr int kCoopRelease = 32;
 
 constexpr int kMaxReduceWidth = 4;

@@ -59,7 +59,8 @@ class LMParams(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("tau_s", ctypes.c_double), ("p_s", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("max_ls", ctypes.c_int), ("diag_floor", ctypes.c_double),
                 ("surrogate0", ctypes.c_double), ("surrogate_end", ctypes.c_double),
-                ("surrogate_T", ctypes.c_int), ("separate_cg_kernels", ctypes.c_int)]
+                ("surrogate_T", ctypes.c_int), ("separate_cg_kernels", ctypes.c_int),
+                ("wait_polls", ctypes.c_int)]
 
 
 class LMStats(ctypes.Structure):
@@ -99,6 +100,7 @@ def load_library():
             lib.forward_magnitude.argtypes = [vp, vp, vp, vp, i]
             lib.ptylm_forward_loss_noalloc.argtypes = [i, i, i, i, i, ctypes.c_float, vp, vp, vp, vp, vp, vp]
             lib.ptylm_profile.argtypes = [vp, i]
+            lib.ptylm_fp32_peak.argtypes = [i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]
             lib.ptylm_profile_select.argtypes = [vp, ctypes.c_uint]
             lib.ptylm_profile_read.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
             lib.ptylm_strerror.argtypes = [i]
@@ -251,13 +253,62 @@ def ptylm_set_measurements(ctx: Context, y) -> None:
     _check(load_library().ptylm_set_measurements(ctx.handle, _ptr(y)))
 
 
+def _require_tensor(x, name, dtype, numel=None, min_numel=None, shape=None):
+    """Check one argument of the context-free entry point, which has no context holding
+    sizes or types: a contiguous torch tensor of `dtype` with the given element count or
+    shape (device placement is checked afterwards)."""
+    import torch
+    if not isinstance(x, torch.Tensor):
+        raise ValueError(f"{name} must be a torch tensor on the GPU, got {type(x).__name__}")
+    if x.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(x.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(x.shape)}")
+    if numel is not None and x.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {x.numel()}")
+    if min_numel is not None and x.numel() < min_numel:
+        raise ValueError(f"{name} must have at least {min_numel} elements, got {x.numel()}")
+
+
 def ptylm_forward_loss_noalloc(ny, nx, m, positions, y, O, P, out, loss=LOSS_GAUSSIAN,
                                background=1e-8, stream=None) -> None:
-    """Context-free, allocation-free (f, ||grad_zeta l||^2) into device double[2] `out`."""
-    K = 0 if positions is None else int(positions.shape[0])
-    _check(load_library().ptylm_forward_loss_noalloc(int(ny), int(nx), int(m), K, int(loss), float(background),
+    """Context-free, allocation-free (f, ||grad_zeta l||^2) into device double[2] `out`.
+
+    The library trusts every pointer it is given, so the types, sizes and device of the
+    arguments are checked here first (ValueError): O complex64 [ny, nx], P complex64
+    [m, m], positions int32 [K, 2], y float32 with K*m*m elements, out float64 with at least
+    two elements, all CUDA tensors on the current device."""
+    import torch
+    ny, nx, m = int(ny), int(nx), int(m)
+    _require_tensor(positions, "positions", torch.int32)
+    if positions.dim() != 2 or positions.shape[1] != 2:
+        raise ValueError(f"positions must have shape [K, 2], got {tuple(positions.shape)}")
+    K = int(positions.shape[0])
+    _require_tensor(O, "O", torch.complex64, numel=ny * nx)
+    _require_tensor(P, "P", torch.complex64, numel=m * m)
+    _require_tensor(y, "y", torch.float32, numel=K * m * m)
+    _require_tensor(out, "out", torch.float64, min_numel=2)
+    args = {"O": O, "P": P, "positions": positions, "y": y, "out": out}
+    for name, t in args.items():
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor (host memory is not accepted here)")
+    dev = torch.cuda.current_device()
+    for name, t in args.items():
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+    _check(load_library().ptylm_forward_loss_noalloc(ny, nx, m, K, int(loss), float(background),
                                                      _ptr(O), _ptr(P), _ptr(positions), _ptr(y), _ptr(out),
                                                      _stream_ptr(stream)))
+
+
+def ptylm_fp32_peak(launches=5, iters=40000, stream=None):
+    """(TFLOP/s, ms) of the median timed launch of the library's FFMA loop on the current device."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().ptylm_fp32_peak(int(launches), int(iters), ctypes.byref(tf), ctypes.byref(ms),
+                                          _stream_ptr(stream)))
+    return tf.value, ms.value
 
 
 def forward_intensity(ctx: Context, O, P, h_out) -> None:

@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -54,3 +56,40 @@ def test_calls_fail_cleanly_without_a_gpu():
     with pytest.raises(ptylm.PtylmError) as e:
         ptylm.lm_init(64, 64, 32, 32, pos, y)
     assert e.value.status == ptylm.PTYLM_ERR_CUDA and "CUDA" in str(e.value)
+
+
+def test_noalloc_wrapper_rejects_bad_arguments_before_the_library():
+    """The context-free entry point has no context holding sizes or types, so the binding
+    checks dtypes, sizes and device placement itself and raises ValueError before any
+    pointer reaches the library."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    from paper_2103_01767_gb300 import ptylm
+    n, m, K = 64, 32, 3
+    good = dict(positions=torch.zeros((K, 2), dtype=torch.int32),
+                y=torch.zeros((K, m, m), dtype=torch.float32),
+                O=torch.zeros((n, n), dtype=torch.complex64),
+                P=torch.zeros((m, m), dtype=torch.complex64),
+                out=torch.zeros(2, dtype=torch.float64))
+    bad_cases = [
+        ("positions", torch.zeros((K, 2), dtype=torch.int64)),            # int64 read as int2
+        ("positions", torch.zeros((K, 3), dtype=torch.int32)),
+        ("O", torch.zeros((n, n), dtype=torch.complex128)),
+        ("O", torch.zeros((n, n - 1), dtype=torch.complex64)),
+        ("P", torch.zeros((m, m), dtype=torch.float32)),
+        ("y", torch.zeros((K, m, m), dtype=torch.float64)),
+        ("y", torch.zeros((K - 1, m, m), dtype=torch.float32)),
+        ("out", torch.zeros(2, dtype=torch.float32)),                      # 16-byte store into 8 bytes
+        ("out", torch.zeros(1, dtype=torch.float64)),
+        ("O", torch.zeros((n, 2 * n), dtype=torch.complex64)[:, ::2]),     # not contiguous
+        ("O", np.zeros((n, n), np.complex64)),                             # host numpy array
+    ]
+    for name, bad in bad_cases:
+        args = dict(good)
+        args[name] = bad
+        with pytest.raises(ValueError):
+            ptylm.ptylm_forward_loss_noalloc(n, n, m, args["positions"], args["y"], args["O"], args["P"],
+                                             args["out"])
+    # well-typed host tensors are rejected too: the kernels would read host pointers
+    with pytest.raises(ValueError, match="CUDA"):
+        ptylm.ptylm_forward_loss_noalloc(n, n, m, good["positions"], good["y"], good["O"], good["P"], good["out"])

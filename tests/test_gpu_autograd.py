@@ -5,6 +5,7 @@ import pytest
 
 import oracle
 from paper_2103_01767_gb300 import synth
+from tests import parity
 from tests.problems import make_case, rel_err
 
 torch = pytest.importorskip("torch")
@@ -41,10 +42,12 @@ def test_magnitude_forward_backward_and_jvp(ag, shape, budget):
     O = case.O_true  # the truth: well-conditioned phases
     Od = c64(O, grad=True)
     zeta = ag.far_field_magnitude(Od, c64(case.P), problem)
-    assert rel_err(host(zeta), np.sqrt(oracle.intensity(pb, O))) <= TOL
+    parity.check("zeta (autograd forward)", host(zeta), np.sqrt(oracle.intensity(pb, O)), TOL)
+    parity.check("zeta (autograd forward)", host(zeta), np.sqrt(oracle.intensity(pb, O)), TOL, norm="max")
     w = synth.to_f32(synth.random_real((K, m, m), seed=71))
     (zeta * torch.from_numpy(w.astype(np.float32)).cuda()).sum().backward()
-    assert rel_err(host(Od.grad), oracle.jtvp(pb, O, w)) <= TOL
+    parity.check("J^T w (autograd backward)", host(Od.grad), oracle.jtvp(pb, O, w), TOL)
+    parity.check("J^T w (autograd backward)", host(Od.grad), oracle.jtvp(pb, O, w), TOL, norm="max")
     # forward mode
     import torch.autograd.forward_ad as fwAD
     v = synth.to_c64(synth.random_complex((n, n), seed=72))
@@ -52,7 +55,8 @@ def test_magnitude_forward_backward_and_jvp(ag, shape, budget):
         dual = fwAD.make_dual(c64(O), c64(v))
         out = ag.far_field_magnitude(dual, c64(case.P), problem)
         tangent = fwAD.unpack_dual(out).tangent
-    assert rel_err(host(tangent), oracle.jvp(pb, O, v)) <= TOL
+    parity.check("J v (autograd forward mode)", host(tangent), oracle.jvp(pb, O, v), TOL)
+    parity.check("J v (autograd forward mode)", host(tangent), oracle.jvp(pb, O, v), TOL, norm="max")
 
 
 def test_joint_probe_gradient(ag):
@@ -64,8 +68,10 @@ def test_joint_probe_gradient(ag):
     w = synth.to_f32(synth.random_real((K, m, m), seed=74))
     (ag.far_field_magnitude(Od, Pd, problem) * torch.from_numpy(w.astype(np.float32)).cuda()).sum().backward()
     rO, rP = oracle.jtvp(pb, case.O_true, w, probe_part=True)
-    assert rel_err(host(Od.grad), rO) <= TOL
-    assert rel_err(host(Pd.grad), rP) <= TOL
+    parity.check("joint J^T w object (autograd)", host(Od.grad), rO, TOL)
+    parity.check("joint J^T w object (autograd)", host(Od.grad), rO, TOL, norm="max")
+    parity.check("joint J^T w probe (autograd)", host(Pd.grad), rP, TOL)
+    parity.check("joint J^T w probe (autograd)", host(Pd.grad), rP, TOL, norm="max")
 
 
 def test_finite_differences(ag):
@@ -111,4 +117,5 @@ def test_torch_loss_gradient_matches_library_gradient(ag):
     ptylm.forward_loss(ctx, c64(O0), c64(case.P), cache=1)
     g = torch.empty((n, n), dtype=torch.complex64, device="cuda")
     ptylm.gradient(ctx, g)
-    assert rel_err(host(O.grad), host(g)) <= TOL
+    parity.check("grad f via torch-written metric", host(O.grad), host(g), TOL)
+    parity.check("grad f via torch-written metric", host(O.grad), host(g), TOL, norm="max")

@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 from paper_2103_01767_gb300 import synth
+from tests import parity
 from tests.problems import make_case, rel_err
 from tests.test_gpu_parity import fp32_conditioning
 
@@ -64,8 +65,10 @@ def test_joint_gradient(lib, shape):
     gP = torch.empty((shape[1], shape[1]), dtype=torch.complex64, device="cuda")
     lib.gradient(ctx, gO, gP)
     rO, rP = oracle.gradient(pb, O, P, probe_part=True)
-    assert rel_err(host(gO), rO) <= TOL
-    assert rel_err(host(gP), rP) <= TOL
+    parity.check("joint grad f, object block", host(gO), rO, TOL)
+    parity.check("joint grad f, object block", host(gO), rO, TOL, norm="max")
+    parity.check("joint grad f, probe block", host(gP), rP, TOL)
+    parity.check("joint grad f, probe block", host(gP), rP, TOL, norm="max")
     assert abs(f - oracle.loss(pb, O, P)) <= TOL * abs(f)
 
 
@@ -86,9 +89,11 @@ def test_joint_ggn_matvec(lib, shape, loss, at_truth):
                        vP=c64(v[n * n:].reshape(m, m)), outP=outP)
         ref = oracle.ggn_matvec_z(pb, O, v, lam=lam, D=Dv, P=P, joint=True)
         got = np.concatenate([host(outO).ravel(), host(outP).ravel()])
-        assert rel_err(got, ref) <= TOL, lam
+        parity.check(f"joint (G + {lam} D) v, whole z", got, ref, TOL)
+        parity.check(f"joint (G + {lam} D) v, whole z", got, ref, TOL, norm="max")
         # the probe block alone, so a small block error cannot hide behind the object block
-        assert rel_err(host(outP).ravel(), ref[n * n:]) <= TOL, lam
+        parity.check(f"joint (G + {lam} D) v, probe block", host(outP).ravel(), ref[n * n:], TOL)
+        parity.check(f"joint (G + {lam} D) v, probe block", host(outP).ravel(), ref[n * n:], TOL, norm="max")
 
 
 @pytest.mark.parametrize("shape", SHAPES[:3])
@@ -101,14 +106,17 @@ def test_joint_jvp_and_jtvp(lib, shape):
     vP = synth.to_c64(synth.random_complex((m, m), seed=61))
     out = torch.empty((K, m, m), dtype=torch.float32, device="cuda")
     lib.jvp(ctx, c64(vO), out, vP=c64(vP))
-    assert rel_err(host(out), oracle.jvp(pb, O, vO, P=P, vP=vP)) <= TOL
+    parity.check("joint J v", host(out), oracle.jvp(pb, O, vO, P=P, vP=vP), TOL)
+    parity.check("joint J v", host(out), oracle.jvp(pb, O, vO, P=P, vP=vP), TOL, norm="max")
     w = synth.to_f32(synth.random_real((K, m, m), seed=62))
     outO = torch.empty((n, n), dtype=torch.complex64, device="cuda")
     outP = torch.empty((m, m), dtype=torch.complex64, device="cuda")
     lib.jtvp(ctx, f32(w), outO, outP)
     rO, rP = oracle.jtvp(pb, O, w, P=P, probe_part=True)
-    assert rel_err(host(outO), rO) <= TOL
-    assert rel_err(host(outP), rP) <= TOL
+    parity.check("joint J^T w, object block", host(outO), rO, TOL)
+    parity.check("joint J^T w, object block", host(outO), rO, TOL, norm="max")
+    parity.check("joint J^T w, probe block", host(outP), rP, TOL)
+    parity.check("joint J^T w, probe block", host(outP), rP, TOL, norm="max")
 
 
 @pytest.mark.parametrize("joint", [0, 1])
@@ -132,9 +140,10 @@ def test_ggn_diag(lib, shape, loss, joint):
         lib.ggn_diag(ctx, D, floor)
         ref = diag_at(O, floor)
         tol = TOL if loss == 0 else max(TOL, 2.0 * fp32_conditioning(lambda A: diag_at(A, floor), m, O))
-        assert rel_err(host(D), ref) <= tol, (floor, tol)
+        basis = "1e-5" if loss == 0 else "2 x FP32 conditioning"
+        parity.check(f"Dg(G) (floor {floor})", host(D), ref, tol, basis=basis)
         if joint:
-            assert rel_err(host(D)[n * n:], ref[n * n:]) <= tol, (floor, tol)
+            parity.check(f"Dg(G) probe block (floor {floor})", host(D)[n * n:], ref[n * n:], tol, basis=basis)
 
 
 def test_plm_small_workload_matches_oracle(lib):

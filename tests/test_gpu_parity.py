@@ -1,17 +1,29 @@
 """CUDA path (through the C-ABI) against the FP64 oracle on identical seeded inputs.
 
-Tolerance: relative 1e-5 (2-norm) on f, ||grad_zeta l||^2, grad f, J v, J^T w and
-(G + lambda I) v, the FP32 bound of the hot path; the FP64 oracle's own error is ~1e-13.
-Derived exception for ill-conditioned inputs: for the Poisson metric, pixels where the
-model is much darker than the data (zeta^2 << y) carry weights 2y/zeta^2 and 2y/zeta that
-amplify the FFT's absolute rounding error into relative errors above 1e-5 for ANY
-single-precision evaluation (the paper computes in single precision throughout, Sec. 5).
-A single-precision FFT's rounding error has RMS about u sqrt(log2 M) times the RMS of the
-transform (u = 2^-24); an equivalent perturbation of the FFT inputs by that relative amount
-gives the quantity's FP32 conditioning, measured with the FP64 oracle itself
-(fp32_conditioning).  Those cases use tol = max(1e-5, 2 x conditioning).  Well-conditioned
-inputs -- the Gaussian metric, Poisson data at their noiseless truth (d2l = 4 everywhere) --
-are held to 1e-5 without widening."""
+Every comparison is recorded with the error it reached (tests/parity.py).
+
+Tolerance: relative 1e-5 on f, ||grad_zeta l||^2, grad f, J v, J^T w and (G + lambda I) v,
+the FP32 bound of the hot path (the FP64 oracle's own error is ~1e-13), both as a 2-norm
+over the whole vector and element-wise (max |gpu - oracle| / max |oracle|), for
+well-conditioned inputs: the Gaussian metric and Poisson data at their noiseless truth
+(d2l = 4 everywhere).
+
+Poisson inputs away from the truth: pixels where the model is much darker than the data
+(zeta^2 << y) carry weights 2y/zeta^2 and 2y/zeta that amplify the FFT's absolute rounding
+error into relative errors above 1e-5 for ANY single-precision evaluation (the paper
+computes in single precision throughout, Sec. 5).  For those quantities three checks run:
+  1. the derived bound: a single-precision FFT's rounding error has RMS about u sqrt(log2 M)
+     times the RMS of the transform (u = 2^-24); perturbing the FFT inputs by that relative
+     amount gives the quantity's FP32 conditioning, measured with the FP64 oracle itself
+     (fp32_conditioning); tol = max(1e-5, 2 x conditioning);
+  2. the arithmetic, not the kernel: an independent FP32 evaluation (tests/fp32_eval.py,
+     scipy complex64 FFTs in two axis orders, no code shared with the CUDA path) misses the
+     oracle too, and the CUDA path's error is at most twice the worse of the two;
+  3. the same problem with the measurements of the 1 % of detector pixels with the largest
+     curvature weight d2l replaced by the model's expected counts there (d2l = 4 at those
+     pixels, every weight at most the 99th percentile): here the FP32 argument does not
+     apply and the CUDA path is held to 1e-5, 2-norm and element-wise.
+"""
 import numpy as np
 import pytest
 
@@ -19,6 +31,8 @@ import oracle
 from paper_2103_01767_gb300 import synth
 import math
 
+from tests import parity
+from tests.fp32_eval import Fp32Model, evaluations
 from tests.problems import make_case, rel_err
 
 torch = pytest.importorskip("torch")
@@ -115,6 +129,57 @@ def kind_case(n, m, K, kind, seed, at_truth=False):
     return case
 
 
+def fp32_model(case, y=None):
+    return Fp32Model((case.n, case.n), case.P, case.pos, case.y if y is None else y, case.loss, case.b)
+
+
+def moderate_weight_measurements(case, O, q=99.0):
+    """y with the entries of the detector pixels whose Poisson curvature weight
+    d2l = 2 + 2y/zeta^2 (at O, FP64 oracle) lies above the q-th percentile replaced by the
+    expected counts h there, rounded to FP32 (d2l = 4 at those pixels)."""
+    h = oracle.intensity(case.problem(), O)
+    d2l = 2.0 + 2.0 * case.y / h
+    cut = np.percentile(d2l, q)
+    return synth.to_f32(np.where(d2l > cut, h, case.y))
+
+
+def compare(name, gpu, ref, case, cond_fn, cond_arrays, fp32_fn=None):
+    """The checks of the module docstring for one quantity: 1e-5 (2-norm and element-wise)
+    for well-conditioned inputs; else the derived bound and the independent FP32 evaluation."""
+    if case.loss == 0 or case.at_truth:
+        parity.check(name, gpu, ref)
+        if np.ndim(ref):
+            parity.check(name, gpu, ref, norm="max")
+        return
+    tol = max(TOL, 2.0 * fp32_conditioning(cond_fn, case.m, *cond_arrays))
+    parity.check(name, gpu, ref, tol, basis="2 x FP32 conditioning")
+    if fp32_fn is not None:
+        parity.check_against_fp32(name, gpu, ref, fp32_fn())
+
+
+def check_moderate_weights(lib, case, O, v, w=None):
+    """Check 3 of the module docstring: f, ||grad_zeta l||^2, grad f, (G + lambda I) v (and
+    J^T w) at 1e-5 on the moderate-weight variant of a Poisson problem."""
+    y_mod = moderate_weight_measurements(case, O)
+    pb = oracle.Problem((case.n, case.n), case.P, case.pos, y_mod, case.loss, case.b)
+    ctx = lib.lm_init(case.n, case.n, case.m, case.m, dev_i32(case.pos), dev_f32(y_mod), case.loss, case.b)
+    f, dl2 = lib.forward_loss(ctx, dev_c64(O), dev_c64(case.P), cache=1)
+    f_ref, dl2_ref = oracle.loss(pb, O, return_dl_norm2=True)
+    parity.check("f (moderate weights)", f, f_ref)
+    parity.check("||dl||^2 (moderate weights)", dl2, dl2_ref)
+    g = torch.empty((case.n, case.n), dtype=torch.complex64, device="cuda")
+    lib.gradient(ctx, g)
+    g_ref = oracle.gradient(pb, O)
+    parity.check("grad f (moderate weights)", host(g), g_ref)
+    parity.check("grad f (moderate weights)", host(g), g_ref, norm="max")
+    out = torch.empty_like(g)
+    lib.ggn_matvec(ctx, dev_c64(v), out, 0.37)
+    ref = oracle.ggn_matvec(pb, O, v, lam=0.37)
+    parity.check("(G + lam I) v (moderate weights)", host(out), ref)
+    parity.check("(G + lam I) v (moderate weights)", host(out), ref, norm="max")
+    lib.lm_destroy(ctx)
+
+
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("shape", SHAPES)
 def test_forward_loss_and_gradient(lib, shape, kind):
@@ -125,23 +190,27 @@ def test_forward_loss_and_gradient(lib, shape, kind):
     Od = dev_c64(O)
     f, dl2 = lib.forward_loss(g.ctx, Od, g.P, cache=1)
     pb = case.problem()
+    mdl = fp32_model(case)
     f_ref, dl2_ref = oracle.loss(pb, O, return_dl_norm2=True)
-    assert scalar_rel(f, f_ref) <= tol_for(case, lambda A: oracle.loss(pb, A), O), (f, f_ref)
-    tol_d = tol_for(case, lambda A: oracle.loss(pb, A, return_dl_norm2=True)[1], O)
-    assert scalar_rel(dl2, dl2_ref) <= tol_d, (dl2, dl2_ref, tol_d)
+    compare("f", f, f_ref, case, lambda A: oracle.loss(pb, A), (O,),
+            lambda: [mdl.loss_value(O, order=o)[0] for o in (0, 1)])
+    compare("||dl||^2", dl2, dl2_ref, case, lambda A: oracle.loss(pb, A, return_dl_norm2=True)[1], (O,),
+            lambda: [mdl.loss_value(O, order=o)[1] for o in (0, 1)])
     gd = torch.empty_like(Od)
     lib.gradient(g.ctx, gd)
     g_ref = oracle.gradient(pb, O)
-    tol_g = tol_for(case, lambda A: oracle.gradient(pb, A), O)
-    assert rel_err(host(gd), g_ref) <= tol_g
+    g_gpu = host(gd)
+    compare("grad f", g_gpu, g_ref, case, lambda A: oracle.gradient(pb, A), (O,),
+            lambda: evaluations(mdl, "gradient", O))
     # loss-only evaluation at another point leaves the linearisation intact
     O2 = g.point(seed=6)
     f2, dl2_2 = lib.forward_loss(g.ctx, dev_c64(O2), g.P, cache=0)
     f2_ref, dl2_2_ref = oracle.loss(pb, O2, return_dl_norm2=True)
-    assert scalar_rel(f2, f2_ref) <= tol_for(case, lambda A: oracle.loss(pb, A), O2)
-    assert scalar_rel(dl2_2, dl2_2_ref) <= tol_for(case, lambda A: oracle.loss(pb, A, return_dl_norm2=True)[1], O2)
+    compare("f (cache=0)", f2, f2_ref, case, lambda A: oracle.loss(pb, A), (O2,))
+    compare("||dl||^2 (cache=0)", dl2_2, dl2_2_ref, case, lambda A: oracle.loss(pb, A, return_dl_norm2=True)[1],
+            (O2,), lambda: [mdl.loss_value(O2, order=o)[1] for o in (0, 1)])
     lib.gradient(g.ctx, gd)
-    assert rel_err(host(gd), g_ref) <= tol_g
+    assert rel_err(host(gd), g_gpu) <= 1e-6   # the same linearisation as before the cache=0 call
 
 
 @pytest.mark.parametrize("kind", KINDS + [(1, False, "truth")])
@@ -157,11 +226,15 @@ def test_ggn_matvec(lib, shape, kind):
     vd = dev_c64(v)
     out = torch.empty_like(vd)
     pb = case.problem()
+    mdl = fp32_model(case)
     for lam in (0.0, 0.37):
         lib.ggn_matvec(g.ctx, vd, out, lam)
         ref = oracle.ggn_matvec(pb, O, v, lam=lam)
-        tol = tol_for(case, lambda A, B: oracle.ggn_matvec(pb, A, B, lam=lam), O, v)
-        assert rel_err(host(out), ref) <= tol, (lam, tol)
+        compare(f"(G + {lam} I) v", host(out), ref, case,
+                lambda A, B: oracle.ggn_matvec(pb, A, B, lam=lam), (O, v),
+                lambda: evaluations(mdl, "ggn_matvec", O, v, lam=lam))
+    if case.loss == 1 and not at_truth:
+        check_moderate_weights(lib, case, O, v)
 
 
 @pytest.mark.parametrize("at_truth", [False, True])
@@ -173,16 +246,19 @@ def test_jvp_and_jtvp(lib, shape, at_truth):
     O = case.O_true if at_truth else g.point()
     lib.forward_loss(g.ctx, dev_c64(O), g.P, cache=1)
     pb = case.problem()
+    mdl = fp32_model(case)
     v = synth.to_c64(synth.random_complex(O.shape, seed=15))
     out = torch.empty((K, m, m), dtype=torch.float32, device="cuda")
     lib.jvp(g.ctx, dev_c64(v), out)
     jv_ref = oracle.jvp(pb, O, v)
-    assert rel_err(host(out), jv_ref) <= tol_for(case, lambda A, B: oracle.jvp(pb, A, B), O, v)
+    compare("J v", host(out), jv_ref, case, lambda A, B: oracle.jvp(pb, A, B), (O, v),
+            lambda: evaluations(mdl, "jvp", O, v))
     w = synth.to_f32(synth.random_real((K, m, m), seed=16))
     outO = torch.empty((n, n), dtype=torch.complex64, device="cuda")
     lib.jtvp(g.ctx, dev_f32(w), outO)
     jt_ref = oracle.jtvp(pb, O, w)
-    assert rel_err(host(outO), jt_ref) <= tol_for(case, lambda A: oracle.jtvp(pb, A, w), O)
+    compare("J^T w", host(outO), jt_ref, case, lambda A: oracle.jtvp(pb, A, w), (O,),
+            lambda: evaluations(mdl, "jtvp", O, w))
 
 
 def test_adjoint_identity_on_gpu(lib):
