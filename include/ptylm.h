@@ -232,6 +232,28 @@ ptylm_status ggn_matvec(ptylm_ctx* ctx, const ptylm_c64* vO, const ptylm_c64* vP
 ptylm_status lm_solve(ptylm_ctx* ctx, ptylm_c64* O_inout, ptylm_c64* P_inout,
                       const ptylm_lm_params* prm, ptylm_lm_stats* stats);
 
+/* Resumable state of Algorithm 1 (Sec. 4.2) between calls, for checkpointing a long run:
+ * with the iterate z = O (or (O, P) for joint contexts) it is everything Algorithm 1 carries
+ * from one outer iteration to the next.  The App. E surrogate level s_t follows from t. */
+typedef struct {
+    int t;             /* outer iterations completed so far (>= 0)                         */
+    double mu;         /* damping multiplier (> 0)                                         */
+    ptylm_c64* delta;  /* host or device [L] (L = ny*nx, + my*mx for joint contexts): the last
+                          CG solution, which warm-starts the next solve; NULL: start from zero
+                          and do not return it                                             */
+} ptylm_lm_state;
+
+/* lm_solve continued from `state` (host struct, in/out): the run starts at outer iteration
+ * state->t with damping state->mu and warm start state->delta, runs prm->max_outer more outer
+ * iterations (history entries count from there; the surrogate schedule from state->t), and
+ * writes the state after its last outer iteration back (delta overwritten in place).  A run
+ * split into two calls with the state handed over follows the uninterrupted run (up to the
+ * rounding order of the scatter's float reductions).  lm_solve is lm_solve_resume from
+ * t = 0, mu = prm->mu0, delta = 0.  PTYLM_ERR_ARG for state == NULL, t < 0 or mu not finite
+ * and > 0; on an error return the state is unspecified. */
+ptylm_status lm_solve_resume(ptylm_ctx* ctx, ptylm_c64* O_inout, ptylm_c64* P_inout,
+                             const ptylm_lm_params* prm, ptylm_lm_state* state, ptylm_lm_stats* stats);
+
 /* Expected intensities h = |F diag(P) S_k O|^2 + b for every position (Sec. 2,
  * Eq. expected_count), used to simulate measurements.  O: device [ny][nx]; P: device
  * [my][mx]; h_out: device float [K][my][mx] in natural order.  Changes no context state. */

@@ -267,8 +267,23 @@ DEFAULT_LM = dict(mu0=1e-5, mu_min=1e-8, kappa=4.0, nu=1.0, rho_min=1e-4, mu_max
                   max_outer=50, max_cg=100, target_err=0.0)
 
 
-def lm_solve(pb: Problem, O0, O_ref=None, mask=None, beta=None, **kw):
-    """Algorithm 1 (object-only, D = I).  Returns (O, info dict with the history)."""
+class _LMState(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_int), ("mu", ctypes.c_double), ("delta", ctypes.c_void_p)]
+
+
+def _state_in(state, mu0, L):
+    """(ctypes state, delta buffer) from a state dict {t, mu, delta} or a fresh start."""
+    if state is None:
+        state = {"t": 0, "mu": mu0, "delta": np.zeros(L, np.complex128)}
+    delta = np.ascontiguousarray(np.asarray(state["delta"], np.complex128).reshape(-1)).copy()
+    assert delta.size == L
+    return _LMState(int(state["t"]), float(state["mu"]), delta.ctypes.data), delta
+
+
+def lm_solve(pb: Problem, O0, O_ref=None, mask=None, beta=None, state=None, **kw):
+    """Algorithm 1 (object-only, D = I).  Returns (O, info dict with the history).
+    state: None (fresh start) or a dict {t, mu, delta} from an earlier info["state"]; the run
+    continues from it, and info["state"] is the state after its last outer iteration."""
     prm = dict(DEFAULT_LM)
     prm.update(kw)
     if beta is None:
@@ -283,13 +298,15 @@ def lm_solve(pb: Problem, O0, O_ref=None, mask=None, beta=None, **kw):
     Oref = None if O_ref is None else _c(O_ref)
     m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
     g = pb.geom()
+    cst, delta = _state_in(state, prm["mu0"], O.size)
     st = _load().orc_lm_solve(ctypes.byref(g), _p(O), _p(pb.P), _p(pb.pos), _p(pb.y),
                               ctypes.byref(p), _p(Oref), _p(m), ctypes.byref(n_outer),
                               ctypes.byref(cg_total), _p(hf), _p(hg), _p(hmu), _p(hcg),
-                              _p(herr), _p(hrho), L)
+                              _p(herr), _p(hrho), L, ctypes.byref(cst))
     n = n_outer.value
     return O, dict(status=st, n_outer=n, cg_total=cg_total.value, f=hf[:n], gnorm=hg[:n],
-                   mu=hmu[:n], cg=hcg[:n], err=herr[:n], rho=hrho[:n])
+                   mu=hmu[:n], cg=hcg[:n], err=herr[:n], rho=hrho[:n],
+                   state={"t": cst.t, "mu": cst.mu, "delta": delta.reshape(O.shape)})
 
 
 # ---------------------------------------------------------------------------------------
@@ -373,9 +390,10 @@ DEFAULT_LM2 = dict(DEFAULT_LM, scaled=1, joint=0, projected=0, radius_O=1.0, rad
                    surrogate0=1.0, surrogate_end=1e-4, surrogate_T=0)
 
 
-def lm_solve2(pb: Problem, O0, P0=None, O_ref=None, mask=None, beta=None, **kw):
+def lm_solve2(pb: Problem, O0, P0=None, O_ref=None, mask=None, beta=None, state=None, **kw):
     """Algorithm 1 with D = Dg(G) and Jacobi PCG (scaled), the joint state (joint) and the
-    Algorithm 2 plug-in (projected).  Returns (O, P, info)."""
+    Algorithm 2 plug-in (projected).  Returns (O, P, info).  state as in lm_solve (delta over
+    the whole state z: [ny*nx] or [ny*nx + my*mx] for joint problems)."""
     prm = dict(DEFAULT_LM2)
     prm.update(kw)
     if beta is None:
@@ -397,12 +415,15 @@ def lm_solve2(pb: Problem, O0, P0=None, O_ref=None, mask=None, beta=None, **kw):
     g = pb.geom()
     lib = _load()
     lib.orc_lm_solve2.restype = ctypes.c_int
+    Lz = O.size + (P.size if int(prm["joint"]) else 0)
+    cst, delta = _state_in(state, prm["mu0"], Lz)
     st = lib.orc_lm_solve2(ctypes.byref(g), _p(O), _p(P), _p(pb.pos), _p(pb.y), ctypes.byref(p), _p(Oref),
                            _p(m), ctypes.byref(n_outer), ctypes.byref(cg_total), _p(hf), _p(hg), _p(hmu),
-                           _p(hcg), _p(herr), _p(hrho), L)
+                           _p(hcg), _p(herr), _p(hrho), L, ctypes.byref(cst))
     n = n_outer.value
     return O, P, dict(status=st, n_outer=n, cg_total=cg_total.value, f=hf[:n], gnorm=hg[:n], mu=hmu[:n],
-                      cg=hcg[:n], err=herr[:n], rho=hrho[:n])
+                      cg=hcg[:n], err=herr[:n], rho=hrho[:n],
+                      state={"t": cst.t, "mu": cst.mu, "delta": delta})
 
 
 def object_error_blind(O, O_ref, mask=None, ramp_iterations=3):

@@ -501,7 +501,9 @@ double orc_object_error(long N, const dc* O, const dc* O_ref, const unsigned cha
  * Parameters follow Sec. 5: mu0 = 1e-5, mu_min = 1e-8, nu = 1, rho_min = 1e-4, kappa = 4;
  * beta = 0.1 (Gaussian) or 0.9 (Poisson).  Per outer iteration the history arrays receive
  * f, ||g||, mu, number of CG iterations, accepted flag and (if O_ref) the object error.
- * Returns 0 on normal termination, 6 if mu overflowed (stalled).
+ * Returns 0 on normal termination, 6 if mu overflowed (stalled).  state (may be NULL): the
+ * run starts from it (outer iteration state->t, mu, warm start delta; history entries and
+ * max_outer count from there) and receives the state after the last outer iteration run.
  * ------------------------------------------------------------------------------------ */
 typedef struct {
     double mu0, mu_min, kappa, nu, rho_min, beta, mu_max;
@@ -509,11 +511,23 @@ typedef struct {
     double target_err;   /* stop once the object error <= target_err (if O_ref given) */
 } orc_lm_params;
 
+/* Resumable state of Algorithm 1 (Sec. 4.2) between calls: the outer iterations completed
+ * so far (t; the App. E surrogate level s_t is a function of t), the damping multiplier mu,
+ * and the last CG solution delta, the warm start of the next inner solve (Sec. 4.2, "warm
+ * start"), [N] (object only) or [L] (joint state).  With the iterate z itself this is all
+ * Algorithm 1 carries from one outer iteration to the next, so a run split in two with the
+ * state handed over computes exactly the same iterates as one uninterrupted run. */
+typedef struct {
+    int t;
+    double mu;
+    dc* delta;
+} orc_lm_state;
+
 int orc_lm_solve(const orc_geom* g, dc* O, const dc* P, const int32_t* pos, const double* y,
                  const orc_lm_params* prm, const dc* O_ref, const unsigned char* mask,
                  int* n_outer_out, int* cg_total_out,
                  double* hist_f, double* hist_gnorm, double* hist_mu, int* hist_cg,
-                 double* hist_err, double* hist_rho, int hist_len)
+                 double* hist_err, double* hist_rho, int hist_len, orc_lm_state* state)
 {
     const long N = (long)g->ny * g->nx;
     dc* grad = (dc*)malloc(sizeof(dc) * N);
@@ -522,7 +536,13 @@ int orc_lm_solve(const orc_geom* g, dc* O, const dc* P, const int32_t* pos, cons
     dc* trial = (dc*)malloc(sizeof(dc) * N);
     double mu = prm->mu0;
     int cg_total = 0, status = 0, t = 0;
-    for (t = 0; t < prm->max_outer; ++t) {
+    const int t0 = state ? state->t : 0;   /* history entries are counted from t0 */
+    if (state) {
+        mu = state->mu;
+        if (state->delta) memcpy(delta, state->delta, sizeof(dc) * N);
+    }
+    for (t = t0; t < t0 + prm->max_outer; ++t) {
+        const int h = t - t0;
         double dl2 = 0.0;
         double f = orc_loss(g, O, P, pos, y, &dl2);
         orc_gradient(g, O, P, pos, y, grad, NULL);
@@ -530,8 +550,8 @@ int orc_lm_solve(const orc_geom* g, dc* O, const dc* P, const int32_t* pos, cons
         double eta = fmin(prm->beta, sqrt(gnorm));
         double rho = 0.0;
         int cg_this = 0;
-        if (hist_f && t < hist_len) hist_f[t] = f;
-        if (hist_gnorm && t < hist_len) hist_gnorm[t] = gnorm;
+        if (hist_f && h < hist_len) hist_f[h] = f;
+        if (hist_gnorm && h < hist_len) hist_gnorm[h] = gnorm;
         while (!(rho > prm->rho_min)) {
             double lambda = mu * pow(sqrt(dl2), prm->nu);
             int conv = 0;
@@ -559,18 +579,23 @@ int orc_lm_solve(const orc_geom* g, dc* O, const dc* P, const int32_t* pos, cons
             }
         }
         cg_total += cg_this;
-        if (hist_mu && t < hist_len) hist_mu[t] = mu;
-        if (hist_cg && t < hist_len) hist_cg[t] = cg_this;
-        if (hist_rho && t < hist_len) hist_rho[t] = rho;   /* gain ratio of the step that ended it */
+        if (hist_mu && h < hist_len) hist_mu[h] = mu;
+        if (hist_cg && h < hist_len) hist_cg[h] = cg_this;
+        if (hist_rho && h < hist_len) hist_rho[h] = rho;   /* gain ratio of the step that ended it */
         if (status) { ++t; break; }
         if (O_ref) {
             double e = orc_object_error(N, O, O_ref, mask);
-            if (hist_err && t < hist_len) hist_err[t] = e;
+            if (hist_err && h < hist_len) hist_err[h] = e;
             if (e <= prm->target_err) { ++t; break; }
         }
     }
-    if (n_outer_out) *n_outer_out = t;
+    if (n_outer_out) *n_outer_out = t - t0;
     if (cg_total_out) *cg_total_out = cg_total;
+    if (state) {
+        state->t = t;
+        state->mu = mu;
+        if (state->delta) memcpy(state->delta, delta, sizeof(dc) * N);
+    }
     free(grad); free(delta); free(r); free(trial);
     return status;
 }
@@ -752,11 +777,12 @@ double orc_surrogate_at(const orc_lm2_params* prm, int t)
 }
 
 /* Algorithm 1 with scaling, the joint state and the Algorithm 2 plug-in.
- * O_inout [N], P_inout [M] (updated when joint).  History as in orc_lm_solve. */
+ * O_inout [N], P_inout [M] (updated when joint).  History and state as in orc_lm_solve
+ * (state->t also places the run on the App. E surrogate schedule). */
 int orc_lm_solve2(const orc_geom* g, dc* O_inout, dc* P_inout, const int32_t* pos, const double* y,
                   const orc_lm2_params* prm, const dc* O_ref, const unsigned char* mask,
                   int* n_outer_out, int* cg_total_out, double* hist_f, double* hist_gnorm, double* hist_mu,
-                  int* hist_cg, double* hist_err, double* hist_rho, int hist_len)
+                  int* hist_cg, double* hist_err, double* hist_rho, int hist_len, orc_lm_state* state)
 {
     orc_problem pb = {g, pos, y, prm->joint, P_inout};
     const long N = (long)g->ny * g->nx;
@@ -773,9 +799,15 @@ int orc_lm_solve2(const orc_geom* g, dc* O_inout, dc* P_inout, const int32_t* po
     if (prm->joint) memcpy(z + N, P_inout, sizeof(dc) * M);
     double mu = prm->mu0;
     int cg_total = 0, status = 0, t;
+    const int t0 = state ? state->t : 0;   /* history entries are counted from t0 */
+    if (state) {
+        mu = state->mu;
+        if (state->delta) memcpy(delta, state->delta, sizeof(dc) * L);
+    }
     orc_geom gt = *g;   /* the geometry with the surrogate background of iteration t */
     pb.g = &gt;
-    for (t = 0; t < prm->max_outer; ++t) {
+    for (t = t0; t < t0 + prm->max_outer; ++t) {
+        const int h = t - t0;
         gt.b = g->b + orc_surrogate_at(prm, t);
         double dl2 = 0.0;
         const double f = z_loss(&pb, z, &dl2);
@@ -783,8 +815,8 @@ int orc_lm_solve2(const orc_geom* g, dc* O_inout, dc* P_inout, const int32_t* po
         const double gnorm = sqrt(rdot(grad, grad, L));
         const double eta = fmin(prm->beta, sqrt(gnorm));
         if (D) z_diag(&pb, z, prm->diag_floor, D);
-        if (hist_f && t < hist_len) hist_f[t] = f;
-        if (hist_gnorm && t < hist_len) hist_gnorm[t] = gnorm;
+        if (hist_f && h < hist_len) hist_f[h] = f;
+        if (hist_gnorm && h < hist_len) hist_gnorm[h] = gnorm;
         double rho = 0.0;
         int cg_this = 0;
         while (!(rho > prm->rho_min)) {
@@ -833,20 +865,25 @@ int orc_lm_solve2(const orc_geom* g, dc* O_inout, dc* P_inout, const int32_t* po
             }
         }
         cg_total += cg_this;
-        if (hist_mu && t < hist_len) hist_mu[t] = mu;
-        if (hist_cg && t < hist_len) hist_cg[t] = cg_this;
-        if (hist_rho && t < hist_len) hist_rho[t] = rho;   /* gain ratio of the step that ended it */
+        if (hist_mu && h < hist_len) hist_mu[h] = mu;
+        if (hist_cg && h < hist_len) hist_cg[h] = cg_this;
+        if (hist_rho && h < hist_len) hist_rho[h] = rho;   /* gain ratio of the step that ended it */
         if (status) { ++t; break; }
         if (O_ref) {
             double e = orc_object_error(N, z, O_ref, mask);
-            if (hist_err && t < hist_len) hist_err[t] = e;
+            if (hist_err && h < hist_len) hist_err[h] = e;
             if (e <= prm->target_err) { ++t; break; }
         }
     }
     memcpy(O_inout, z, sizeof(dc) * N);
     if (prm->joint) memcpy(P_inout, z + N, sizeof(dc) * M);
-    if (n_outer_out) *n_outer_out = t;
+    if (n_outer_out) *n_outer_out = t - t0;
     if (cg_total_out) *cg_total_out = cg_total;
+    if (state) {
+        state->t = t;
+        state->mu = mu;
+        if (state->delta) memcpy(state->delta, delta, sizeof(dc) * L);
+    }
     free(z); free(grad); free(delta); free(r); free(trial); free(s); free(D);
     return status;
 }

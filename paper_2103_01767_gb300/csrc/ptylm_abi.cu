@@ -1072,8 +1072,8 @@ ptylm_status ggn_diag(ptylm_ctx* c, float* D_out, double floor_rel) {
     return op_ggn_diag(c, D_out, floor_rel);
 }
 
-ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, const ptylm_lm_params* prm,
-                      ptylm_lm_stats* stats) {
+static ptylm_status lm_solve_impl(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, const ptylm_lm_params* prm,
+                                  ptylm_lm_state* state, ptylm_lm_stats* stats) {
     g_last_error.clear();
     if (!c || !O_inout || !P_inout || !prm) return fail(PTYLM_ERR_ARG, "ctx, O, P and params must be non-NULL");
     if (prm->max_outer < 0 || prm->max_cg < 0 || !(prm->kappa > 1.0) || !(prm->mu0 > 0.0) || prm->wait_polls < 0)
@@ -1128,6 +1128,12 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
     const int nb = vec_blocks(c);
     unsigned* cnt = c->counters + CNT_VEC;
     CUDA_TRY(cudaMemsetAsync(x, 0, zbytes, c->stream));
+    // a resumed run starts from the saved warm start, damping and outer-iteration count
+    const int t0 = state ? state->t : 0;
+    if (state && state->delta)
+        CUDA_TRY(cudaMemcpyAsync(x, state->delta, zbytes,
+                                 is_host_pointer(state->delta) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                 c->stream));
 
     double f_min = 0.0;  // Algorithm 2 compares f - f_min (the Poisson metric can be negative)
     if (prm->projected && c->d.loss == PTYLM_LOSS_POISSON) {
@@ -1147,7 +1153,7 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
         return vec_launched(c);
     };
 
-    double mu = prm->mu0;
+    double mu = state ? state->mu : prm->mu0;
     int cg_total = 0, matvecs = 0, t = 0;
     bool hit_maxit = false;
     ptylm_status status = PTYLM_OK;
@@ -1164,7 +1170,8 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
     };
 
     bool ahead = false;   // the linearisation at z came with the accepted trial point
-    for (t = 0; t < prm->max_outer; ++t) {
+    for (t = t0; t < t0 + prm->max_outer; ++t) {
+        const int h = t - t0;   // history entry of this outer iteration
         const double s_t = surrogate_at(prm, t);
         c->b_eff = (float)(c->d.background + s_t);
         surrogate_guard.used = s_t > 0.0;
@@ -1183,9 +1190,9 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
         const double gnorm = std::sqrt(gg);
         const double eta = std::min(prm->beta, std::sqrt(gnorm));  // Eq. lma_termination_eta
         const double tol = eta * gnorm;                              // Eq. lma_termination_magnitude
-        if (stats && stats->hist_len > t) {
-            if (stats->hist_f) stats->hist_f[t] = f;
-            if (stats->hist_gnorm) stats->hist_gnorm[t] = gnorm;
+        if (stats && stats->hist_len > h) {
+            if (stats->hist_f) stats->hist_f[h] = f;
+            if (stats->hist_gnorm) stats->hist_gnorm[h] = gnorm;
         }
         double rho = 0.0;
         int cg_this = 0;
@@ -1252,7 +1259,7 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
             STATUS_TRY(vec_launched(c));
             // the trial's forward pass doubles as the next linearisation when the next outer
             // iteration exists and uses the same background
-            const bool ahead_here = lookahead && t + 1 < prm->max_outer &&
+            const bool ahead_here = lookahead && t + 1 < t0 + prm->max_outer &&
                                     surrogate_at(prm, t + 1) == s_t;
             if (ahead_here) STATUS_TRY(op_forward_lookahead(c, trial));
             else STATUS_TRY(op_forward(c, trial, probe_of(trial), 0));
@@ -1321,9 +1328,9 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
             }
         }
         cg_total += cg_this;
-        if (stats && stats->hist_len > t) {
-            if (stats->hist_mu) stats->hist_mu[t] = mu;
-            if (stats->hist_cg) stats->hist_cg[t] = cg_this;
+        if (stats && stats->hist_len > h) {
+            if (stats->hist_mu) stats->hist_mu[h] = mu;
+            if (stats->hist_cg) stats->hist_cg[h] = cg_this;
         }
         if (timed_out) {
             status = fail(PTYLM_ERR_TIMEOUT, "a grid-wide wait of the CG iteration gave up at outer iteration %d", t);
@@ -1336,13 +1343,13 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
         }
         if (prm->O_ref) {
             STATUS_TRY(object_error(&err));
-            if (stats && stats->hist_len > t && stats->hist_err) stats->hist_err[t] = err;
+            if (stats && stats->hist_len > h && stats->hist_err) stats->hist_err[h] = err;
             if (err <= prm->target_err) {
                 ++t;
                 break;
             }
-        } else if (stats && stats->hist_len > t && stats->hist_err) {
-            stats->hist_err[t] = NAN;
+        } else if (stats && stats->hist_len > h && stats->hist_err) {
+            stats->hist_err[h] = NAN;
         }
     }
     CUDA_TRY(cudaMemcpyAsync(O_inout, z, sizeof(float2) * N, host_O ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
@@ -1351,8 +1358,15 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
         CUDA_TRY(cudaMemcpyAsync(P_inout, z + N, sizeof(float2) * c->M,
                                  host_P ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (state) {
+        state->t = t;
+        state->mu = mu;
+        if (state->delta)
+            CUDA_TRY(cudaMemcpy(state->delta, x, zbytes,
+                                is_host_pointer(state->delta) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice));
+    }
     if (stats) {
-        stats->n_outer = t;
+        stats->n_outer = t - t0;
         stats->cg_total = cg_total;
         stats->matvecs_total = matvecs;
         stats->f_final = f_cur;
@@ -1360,6 +1374,20 @@ ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, cons
     }
     if (status != PTYLM_OK) return status;
     return hit_maxit ? PTYLM_WARN_CG_MAXIT : PTYLM_OK;
+}
+
+ptylm_status lm_solve(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, const ptylm_lm_params* prm,
+                      ptylm_lm_stats* stats) {
+    return lm_solve_impl(c, O_inout, P_inout, prm, nullptr, stats);
+}
+
+ptylm_status lm_solve_resume(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P_inout, const ptylm_lm_params* prm,
+                             ptylm_lm_state* state, ptylm_lm_stats* stats) {
+    g_last_error.clear();
+    if (!state) return fail(PTYLM_ERR_ARG, "state must be non-NULL (lm_solve starts afresh)");
+    if (state->t < 0 || !(state->mu > 0.0) || !std::isfinite(state->mu))
+        return fail(PTYLM_ERR_ARG, "invalid LM state (t = %d, mu = %g)", state->t, state->mu);
+    return lm_solve_impl(c, O_inout, P_inout, prm, state, stats);
 }
 
 }  // extern "C"

@@ -63,6 +63,10 @@ class LMParams(ctypes.Structure):
                 ("wait_polls", ctypes.c_int)]
 
 
+class LMState(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_int), ("mu", ctypes.c_double), ("delta", ctypes.c_void_p)]
+
+
 class LMStats(ctypes.Structure):
     _fields_ = [("n_outer", ctypes.c_int), ("cg_total", ctypes.c_int),
                 ("matvecs_total", ctypes.c_int), ("f_final", ctypes.c_double),
@@ -93,6 +97,8 @@ def load_library():
             lib.jtvp.argtypes = [vp, vp, vp, vp]
             lib.ggn_matvec.argtypes = [vp, vp, vp, d, vp, vp, vp]
             lib.lm_solve.argtypes = [vp, vp, vp, ctypes.POINTER(LMParams), ctypes.POINTER(LMStats)]
+            lib.lm_solve_resume.argtypes = [vp, vp, vp, ctypes.POINTER(LMParams), ctypes.POINTER(LMState),
+                                            ctypes.POINTER(LMStats)]
             lib.lm_destroy.argtypes = [vp]
             lib.forward_intensity.argtypes = [vp, vp, vp, vp]
             lib.ptylm_set_measurements.argtypes = [vp, vp]
@@ -363,10 +369,13 @@ def default_lm_params(loss: int) -> LMParams:
 
 
 def lm_solve(ctx: Context, O, P, params: LMParams | None = None, hist_len: int = 0,
-             O_ref=None, mask=None, **overrides):
+             O_ref=None, mask=None, state=None, **overrides):
     """Run Algorithm 1 in place on O.  Returns (status, stats dict).  PTYLM_WARN_CG_MAXIT and
     PTYLM_ERR_STALLED (the damping ran away: no step decreases f any more at FP32 resolution)
-    are returned rather than raised; O, P and the history then hold the last iterate."""
+    are returned rather than raised; O, P and the history then hold the last iterate.
+    state: None (fresh start) or a dict {t, mu, delta} (delta a contiguous complex64 tensor or
+    array of the state's length, updated in place); the run continues from it through
+    lm_solve_resume and the dict is updated to the state after the run (also stats["state"])."""
     p = default_lm_params(ctx.desc.loss) if params is None else params
     for k, v in overrides.items():
         setattr(p, k, v)
@@ -379,13 +388,44 @@ def lm_solve(ctx: Context, O, P, params: LMParams | None = None, hist_len: int =
     hcg = np.zeros(max(L, 1), np.int32)
     st = LMStats(0, 0, 0, 0.0, 0.0, L, hf.ctypes.data, hg.ctypes.data, hmu.ctypes.data,
                  hcg.ctypes.data, herr.ctypes.data)
-    status = _check(load_library().lm_solve(ctx.handle, _ptr(O), _ptr(P), ctypes.byref(p),
+    lib = load_library()
+    if state is None:
+        status = _check(lib.lm_solve(ctx.handle, _ptr(O), _ptr(P), ctypes.byref(p), ctypes.byref(st)),
+                        allow=(PTYLM_WARN_CG_MAXIT, PTYLM_ERR_STALLED))
+    else:
+        cs = LMState(int(state["t"]), float(state["mu"]), _ptr(state.get("delta")))
+        status = _check(lib.lm_solve_resume(ctx.handle, _ptr(O), _ptr(P), ctypes.byref(p), ctypes.byref(cs),
                                             ctypes.byref(st)), allow=(PTYLM_WARN_CG_MAXIT, PTYLM_ERR_STALLED))
+        state["t"], state["mu"] = cs.t, cs.mu
     n = min(st.n_outer, L)
     return status, dict(n_outer=st.n_outer, cg_total=st.cg_total, matvecs=st.matvecs_total,
                         f_final=st.f_final, err_final=st.err_final, f=hf[:n].copy(),
                         gnorm=hg[:n].copy(), mu=hmu[:n].copy(), cg=hcg[:n].copy(),
-                        err=herr[:n].copy())
+                        err=herr[:n].copy(), state=state)
+
+
+def new_lm_state(ctx: Context, mu0: float | None = None, device=None):
+    """A fresh resumable state {t: 0, mu: mu0 (the Sec. 5 default), delta: zeros} for ctx;
+    delta is a complex64 CUDA tensor of the state's length."""
+    import torch
+    L = ctx.desc.ny * ctx.desc.nx + (ctx.desc.my * ctx.desc.mx if ctx.desc.joint else 0)
+    mu = default_lm_params(ctx.desc.loss).mu0 if mu0 is None else float(mu0)
+    return {"t": 0, "mu": mu, "delta": torch.zeros(L, dtype=torch.complex64, device=device or "cuda")}
+
+
+def save_lm_checkpoint(path, O, P, state) -> None:
+    """Write the iterate (O, P) and the LM state (t, mu, delta) to an .npz file."""
+    def host(a):
+        return a.detach().cpu().numpy() if hasattr(a, "detach") else np.asarray(a)
+    np.savez(path, O=host(O), P=host(P), t=int(state["t"]), mu=float(state["mu"]), delta=host(state["delta"]))
+
+
+def load_lm_checkpoint(path, device="cuda"):
+    """(O, P, state) from save_lm_checkpoint's file, as complex64 CUDA tensors."""
+    import torch
+    d = np.load(path)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.complex64)).to(device)
+    return t(d["O"]), t(d["P"]), {"t": int(d["t"]), "mu": float(d["mu"]), "delta": t(d["delta"])}
 
 
 # ---------------------------------------------------------------------------------------

@@ -7,9 +7,9 @@ the patches, the orthonormal 2D FFTs (scipy.fft keeps single precision), the per
 metric terms and the overlap scatter-add are all FP32; only the error metric's final sum is
 FP64, as on the CUDA path.  It shares no code with the CUDA kernels or with the FP64 oracle.
 Its use: where an input makes the FP64 oracle's answer sensitive at the level of FP32
-rounding, the CUDA path's error is compared with the error of this evaluation (and of the
-same evaluation with the two FFT axes taken in the other order), both measured against the
-oracle.
+rounding, the CUDA path's error is compared with the worst error of four roundings of this
+evaluation (two FFT implementations -- scipy's pocketfft and a radix-2 transform written
+here -- each taking the two axes in either order), all measured against the oracle.
 
 Conventions as in the library: positions (row, col) of each patch's top-left corner,
 real-coordinate gradients (d/dRe + i d/dIm), y in natural DFT order.
@@ -23,23 +23,43 @@ F32 = np.float32
 C64 = np.complex64
 
 
-def _fft2(x, order):
-    # order 0: scipy's 2D transform; order 1: the two axes one at a time, columns first
+def _radix2(x, inverse):
+    """Radix-2 decimation-in-time DFT over the last axis (a power of two) in complex64, the
+    twiddles exp(-+2 pi i k / n) computed in FP64 and rounded once; orthonormal."""
+    n = x.shape[-1]
+    if n == 1:
+        return x
+    even, odd = _radix2(x[..., 0::2], inverse), _radix2(x[..., 1::2], inverse)
+    sign = 1.0 if inverse else -1.0
+    w = np.exp(sign * 2j * np.pi * np.arange(n // 2) / n).astype(C64)
+    t = w * odd
+    out = np.concatenate([even + t, even - t], axis=-1) * F32(1.0 / np.sqrt(2.0))
+    return out.astype(C64)
+
+
+def _fft2(x, order, inverse=False):
+    """Four single-precision roundings of the orthonormal 2D DFT: scipy's (pocketfft) 2D
+    transform (order 0), scipy's 1D transforms columns first (1), the radix-2 transform rows
+    first (2) and columns first (3)."""
     if order == 0:
-        out = sfft.fft2(x, axes=(-2, -1), norm="ortho")
+        out = (sfft.ifft2 if inverse else sfft.fft2)(x, axes=(-2, -1), norm="ortho")
+    elif order == 1:
+        f = sfft.ifft if inverse else sfft.fft
+        out = f(f(x, axis=-2, norm="ortho"), axis=-1, norm="ortho")
+    elif order == 2:
+        out = np.swapaxes(_radix2(np.swapaxes(_radix2(x, inverse), -1, -2), inverse), -1, -2)
     else:
-        out = sfft.fft(sfft.fft(x, axis=-2, norm="ortho"), axis=-1, norm="ortho")
+        out = _radix2(np.swapaxes(_radix2(np.swapaxes(x, -1, -2), inverse), -1, -2), inverse)
+    out = np.ascontiguousarray(out)
     assert out.dtype == C64
     return out
 
 
 def _ifft2(x, order):
-    if order == 0:
-        out = sfft.ifft2(x, axes=(-2, -1), norm="ortho")
-    else:
-        out = sfft.ifft(sfft.ifft(x, axis=-2, norm="ortho"), axis=-1, norm="ortho")
-    assert out.dtype == C64
-    return out
+    return _fft2(x, order, inverse=True)
+
+
+ORDERS = (0, 1, 2, 3)
 
 
 class Fp32Model:
@@ -119,5 +139,5 @@ class Fp32Model:
 
 
 def evaluations(model: Fp32Model, method: str, *args, **kw):
-    """The quantity in both FFT axis orders (two independent FP32 roundings)."""
-    return [getattr(model, method)(*args, order=o, **kw) for o in (0, 1)]
+    """The quantity under the four FFT roundings of _fft2 (independent FP32 evaluations)."""
+    return [getattr(model, method)(*args, order=o, **kw) for o in ORDERS]

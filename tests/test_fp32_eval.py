@@ -23,7 +23,7 @@ def test_fp32_evaluation_matches_oracle(loss, at_truth):
     f_ref, d_ref = oracle.loss(pb, O, return_dl_norm2=True)
     refs = {"jvp": oracle.jvp(pb, O, v), "jtvp": oracle.jtvp(pb, O, w),
             "ggn_matvec": oracle.ggn_matvec(pb, O, v, lam=0.3)}
-    for order in (0, 1):
+    for order in (0, 1, 2, 3):
         f, d = mdl.loss_value(O, order=order)
         assert abs(f - f_ref) <= 1e-5 * abs(f_ref)
         errs = {"jvp": rel_err(mdl.jvp(O, v, order=order), refs["jvp"]),
@@ -40,11 +40,25 @@ def test_fp32_evaluation_matches_oracle(loss, at_truth):
             assert 1e-9 < e <= (1e-3 if ill else 1e-5), (k, order, e)
 
 
+def test_radix2_transform_is_the_dft():
+    """The hand-written radix-2 transform equals numpy's FP64 DFT to FP32 accuracy."""
+    from tests.fp32_eval import _fft2
+    rng = np.random.default_rng(7)
+    x = (rng.standard_normal((3, 64, 64)) + 1j * rng.standard_normal((3, 64, 64))).astype(np.complex64)
+    ref = np.fft.fft2(x.astype(np.complex128), norm="ortho")
+    for order in (2, 3):
+        got = _fft2(x, order)
+        assert 1e-9 < rel_err(got, ref) <= 1e-6
+        assert rel_err(_fft2(got, order, inverse=True), x.astype(np.complex128)) <= 1e-6
+
+
 def test_fp32_evaluation_orders_round_differently():
     case = make_case(96, 32, K=11, loss=0, seed=55)
     O = synth.to_c64(case.O_true + synth.random_complex(case.O_true.shape, seed=56, scale=0.05))
     v = synth.to_c64(synth.random_complex(O.shape, seed=57))
     mdl = Fp32Model((96, 96), case.P, case.pos, case.y, 0, case.b)
-    a, b = evaluations(mdl, "ggn_matvec", O, v, lam=0.1)
-    assert a.dtype == np.complex64 and b.dtype == np.complex64
-    assert 0.0 < rel_err(a, b) <= 1e-5
+    evs = evaluations(mdl, "ggn_matvec", O, v, lam=0.1)
+    assert len(evs) == 4 and all(e.dtype == np.complex64 for e in evs)
+    for i in range(4):
+        for j in range(i):
+            assert 0.0 < rel_err(evs[i], evs[j]) <= 1e-5, (i, j)

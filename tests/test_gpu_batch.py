@@ -11,7 +11,7 @@ import pytest
 import oracle
 from paper_2103_01767_gb300 import synth
 from tests.problems import make_case, rel_err
-from tests.fp32_eval import evaluations
+from tests.fp32_eval import ORDERS, evaluations
 from tests.test_gpu_parity import compare, fp32_conditioning, fp32_model
 
 torch = pytest.importorskip("torch")
@@ -81,9 +81,9 @@ def test_batch_forward_loss_and_gradient(lib, batch):
         mdl = fp32_model(c)
         f_ref, dl2_ref = oracle.loss(pb, X, return_dl_norm2=True)
         compare(f"f[{b}]", f[b], f_ref, c, lambda A: oracle.loss(pb, A), (X,),
-                lambda: [mdl.loss_value(X, order=o)[0] for o in (0, 1)])
+                lambda: [mdl.loss_value(X, order=o)[0] for o in ORDERS])
         compare(f"||dl||^2[{b}]", dl2[b], dl2_ref, c, lambda A: oracle.loss(pb, A, return_dl_norm2=True)[1], (X,),
-                lambda: [mdl.loss_value(X, order=o)[1] for o in (0, 1)])
+                lambda: [mdl.loss_value(X, order=o)[1] for o in ORDERS])
         g_ref = oracle.gradient(pb, X)
         compare(f"grad f[{b}]", host(gv[b]), g_ref, c, lambda A: oracle.gradient(pb, A), (X,),
                 lambda: evaluations(mdl, "gradient", X))

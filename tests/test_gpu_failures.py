@@ -45,23 +45,31 @@ def _setup(lib, n=192, m=64, K=60, loss=1, seed=41):
 
 
 def test_cg_wait_timeout_is_reported_and_the_context_recovers(lib):
-    case, ctx, pos, y = _setup(lib)
+    """On a tiled scan (patches side by side, no overlaps) every scatter adds one contribution
+    per object pixel, so lm_solve is deterministic: after the timeout the same context must
+    reproduce a fresh context's run bit for bit."""
+    n, m = 256, 64
+    case = make_case(n, m, loss=1, seed=44, grid=n // m, step=m, radius=0.3 * m, peak=1e4)
+    assert case.pos.max() + m == n
+    pos = torch.from_numpy(case.pos).cuda()
+    y = torch.from_numpy(case.y.astype(np.float32)).cuda()
+    ctx = lib.lm_init(n, n, m, m, pos, y, case.loss, case.b)
     P = _c64(case.P)
-    O0 = _c64(synth.flat_object(case.n) * 0.9)
+    O0 = _c64(synth.flat_object(n) * 0.9)
     O = O0.clone()
     with pytest.raises(lib.PtylmError) as e:
         lib.lm_solve(ctx, O, P, max_outer=2, wait_polls=1)
     assert e.value.status == lib.PTYLM_ERR_TIMEOUT, e.value
     # the same context, default waits: the same result as a fresh context
     O1 = O0.clone()
-    st1, info1 = lib.lm_solve(ctx, O1, P, max_outer=3)
-    ctx2 = lib.lm_init(case.n, case.n, case.m, case.m, pos, y, case.loss, case.b)
+    st1, info1 = lib.lm_solve(ctx, O1, P, hist_len=4, max_outer=3)
+    ctx2 = lib.lm_init(n, n, m, m, pos, y, case.loss, case.b)
     O2 = O0.clone()
-    st2, info2 = lib.lm_solve(ctx2, O2, P, max_outer=3)
+    st2, info2 = lib.lm_solve(ctx2, O2, P, hist_len=4, max_outer=3)
     assert st1 == st2 == lib.PTYLM_OK
-    assert info1["n_outer"] == info2["n_outer"] == 3
-    assert abs(info1["f_final"] - info2["f_final"]) <= 1e-5 * abs(info2["f_final"])
-    assert rel_err(O1.cpu().numpy(), O2.cpu().numpy()) <= 1e-4
+    assert info1["n_outer"] == info2["n_outer"] == 3 and info1["cg_total"] == info2["cg_total"] > 0
+    assert np.array_equal(info1["f"], info2["f"])
+    assert torch.equal(O1, O2)
     lib.lm_destroy(ctx)
     lib.lm_destroy(ctx2)
 

@@ -106,8 +106,10 @@ def test_joint_jvp_and_jtvp(lib, shape):
     vP = synth.to_c64(synth.random_complex((m, m), seed=61))
     out = torch.empty((K, m, m), dtype=torch.float32, device="cuda")
     lib.jvp(ctx, c64(vO), out, vP=c64(vP))
-    parity.check("joint J v", host(out), oracle.jvp(pb, O, vO, P=P, vP=vP), TOL)
-    parity.check("joint J v", host(out), oracle.jvp(pb, O, vO, P=P, vP=vP), TOL, norm="max")
+    jv_ref = oracle.jvp(pb, O, vO, P=P, vP=vP)
+    parity.check("joint J v", host(out), jv_ref, TOL)
+    lit_pb = oracle.Problem((n, n), P, case.pos, None, case.loss, case.b)   # the probe of this point
+    parity.check_detector("joint J v", host(out), jv_ref, oracle.intensity(lit_pb, O) - case.b)
     w = synth.to_f32(synth.random_real((K, m, m), seed=62))
     outO = torch.empty((n, n), dtype=torch.complex64, device="cuda")
     outP = torch.empty((m, m), dtype=torch.complex64, device="cuda")

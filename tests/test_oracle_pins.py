@@ -813,3 +813,60 @@ def test_projected_joint_plm_trajectory_equals_dense_algorithm(loss, sigma):
     np.testing.assert_allclose(info["rho"], rho_d, rtol=1e-4)
     assert np.linalg.norm(O_o.ravel() - z[:N]) <= 1e-5 * np.linalg.norm(z[:N])
     assert np.linalg.norm(P_o.ravel() - z[N:]) <= 1e-5 * np.linalg.norm(z[N:])
+
+
+# ------------------------------------------------------------------- checkpoint / resume
+def _npz_roundtrip(tmp_path, name, O, P, state):
+    """Save (z, mu, t, delta) to .npz and read it back, as a checkpoint on disk."""
+    path = os.path.join(str(tmp_path), name)
+    np.savez(path, O=O, P=P, t=state["t"], mu=state["mu"], delta=state["delta"])
+    d = np.load(path)
+    return d["O"], d["P"], {"t": int(d["t"]), "mu": float(d["mu"]), "delta": d["delta"]}
+
+
+def test_lm_resume_reproduces_the_uninterrupted_run_bit_for_bit(tmp_path):
+    """Algorithm 1 carries (z, mu, t, delta) from one outer iteration to the next (Sec. 4.2;
+    delta warm-starts the next CG solve): 7 outer iterations in one run equal 3 + 4 with the
+    state checkpointed to disk in between, bit for bit (iterate, f, mu, CG counts)."""
+    pb, _ = small_poisson_problem()
+    O0 = synth.flat_object(pb.nx)
+    O_all, info_all = oracle.lm_solve(pb, O0, max_outer=7)
+    O_a, info_a = oracle.lm_solve(pb, O0, max_outer=3)
+    O_r, _, st = _npz_roundtrip(tmp_path, "lm.npz", O_a, pb.P, info_a["state"])
+    assert st["t"] == 3 and np.any(st["delta"] != 0)
+    O_b, info_b = oracle.lm_solve(pb, O_r, max_outer=4, state=st)
+    assert np.array_equal(O_b, O_all)
+    for k in ("f", "mu", "cg", "gnorm"):
+        assert np.array_equal(np.concatenate([info_a[k], info_b[k]]), info_all[k]), k
+    assert info_b["state"]["t"] == 7 and info_b["state"]["mu"] == info_all["state"]["mu"]
+    # without the warm start the continuation differs: the state matters
+    O_c, _ = oracle.lm_solve(pb, O_r, max_outer=4, state=dict(st, delta=np.zeros_like(st["delta"])))
+    assert not np.array_equal(O_c, O_all)
+
+
+def test_plm_s_joint_resume_follows_the_surrogate_schedule_bit_for_bit(tmp_path):
+    """The same for PLM-S on the joint state z = (O, P) (Sec. 3.3, App. E): the resumed run
+    picks up the surrogate level s_t at t = state.t, so 2 + 3 iterations across the end of a
+    T = 4 schedule equal 5 uninterrupted ones bit for bit; restarting the schedule (t = 0)
+    does not."""
+    n, m = 96, 32
+    O_true = synth.to_c64(synth.object_texture(n, seed=4))
+    P_true = synth.to_c64(synth.probe_disk_defocus(m, 10.0))
+    pos, _ = synth.raster_positions(n, m, 8, 8, 1, seed=5)
+    pb = oracle.Problem((n, n), P_true, pos, None, 1, 1e-8)
+    pb.y = synth.to_f32(oracle.intensity(pb, O_true) * 50.0)
+    P0 = synth.to_c64(synth.probe_disk_defocus(m, 10.0, phased=False) * np.sqrt(50.0))
+    O0 = synth.flat_object(n) * 0.9
+    # beta = 0.1: with Poisson's 0.9 the warm start alone meets the forcing bound after the
+    # first solve and no CG iteration would run (the state would then hardly matter)
+    kw = dict(scaled=1, joint=1, surrogate0=1.0, surrogate_end=1e-2, surrogate_T=4, beta=0.1)
+    O_all, P_all, i_all = oracle.lm_solve2(pb, O0, P0, max_outer=5, **kw)
+    assert np.all(i_all["cg"] > 0)
+    O_a, P_a, i_a = oracle.lm_solve2(pb, O0, P0, max_outer=2, **kw)
+    O_r, P_r, st = _npz_roundtrip(tmp_path, "plm.npz", O_a, P_a, i_a["state"])
+    assert st["delta"].size == n * n + m * m
+    O_b, P_b, i_b = oracle.lm_solve2(pb, O_r, P_r, max_outer=3, state=st, **kw)
+    assert np.array_equal(O_b, O_all) and np.array_equal(P_b, P_all)
+    assert np.array_equal(np.concatenate([i_a["f"], i_b["f"]]), i_all["f"])
+    O_c, _, _ = oracle.lm_solve2(pb, O_r, P_r, max_outer=3, state=dict(st, t=0), **kw)
+    assert not np.array_equal(O_c, O_all)

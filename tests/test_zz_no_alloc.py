@@ -1,6 +1,7 @@
 """The allocation-free entry point ptylm_forward_loss_noalloc, called through the C-ABI, on two
 calls in a row: against the context-based forward_loss (cache = 0, the call the header says it
-equals, and cache = 1) on the same inputs, and against the FP64 oracle's error metric.
+equals, and cache = 1) on the same inputs at 1e-5, and against the FP64 oracle's error metric
+with the checks of the parity tests (test_gpu_parity.compare).
 
 Callers that must not allocate device memory use this entry point: serving or real-time loops
 that reserve all their memory at start-up (cudaMalloc and cudaFree can synchronise the device
@@ -16,7 +17,10 @@ import pytest
 
 import oracle
 from paper_2103_01767_gb300 import synth
+from tests import parity
+from tests.fp32_eval import ORDERS
 from tests.problems import make_case
+from tests.test_gpu_parity import compare, fp32_model
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -52,7 +56,10 @@ def test_noalloc_loss_matches_context_path_on_two_calls(lib, shape, loss, side_s
     f0, dl2_0 = lib.forward_loss(ctx, O, P, cache=0)
     f1, dl2_1 = lib.forward_loss(ctx, O, P, cache=1)
     lib.lm_destroy(ctx)
-    f_orc, dl2_orc = oracle.loss(case.problem(), O_np, return_dl_norm2=True)
+    pb = case.problem()
+    case.at_truth = False
+    mdl = fp32_model(case)
+    f_orc, dl2_orc = oracle.loss(pb, O_np, return_dl_norm2=True)
     out = torch.empty(2, dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream() if side_stream else None
     if stream is not None:
@@ -67,13 +74,18 @@ def test_noalloc_loss_matches_context_path_on_two_calls(lib, shape, loss, side_s
         else:
             lib.ptylm_forward_loss_noalloc(n, n, m, pos, y, O, P, out, loss, case.b)
         f, dl2 = out.tolist()
-        errs = {"f vs cache=0": abs(f - f0) / abs(f0), "dl2 vs cache=0": abs(dl2 - dl2_0) / abs(dl2_0),
-                "f vs cache=1": abs(f - f1) / abs(f1), "dl2 vs cache=1": abs(dl2 - dl2_1) / abs(dl2_1),
-                "f vs oracle": abs(f - f_orc) / abs(f_orc), "dl2 vs oracle": abs(dl2 - dl2_orc) / abs(dl2_orc)}
-        print(f"noalloc {shape} loss={loss} side_stream={side_stream}: "
-              + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
-        for k, v in errs.items():
-            assert v <= TOL, (k, v)
+        # the existing entry point on the same inputs: the same arithmetic, 1e-5
+        parity.check("noalloc f vs forward_loss(cache=0)", f, f0)
+        parity.check("noalloc ||dl||^2 vs forward_loss(cache=0)", dl2, dl2_0)
+        parity.check("noalloc f vs forward_loss(cache=1)", f, f1)
+        parity.check("noalloc ||dl||^2 vs forward_loss(cache=1)", dl2, dl2_1)
+        # the FP64 oracle, with the checks of the parity tests (Poisson counts away from the
+        # truth: the FP32 conditioning bound and the independent FP32 evaluation)
+        compare("noalloc f vs oracle", f, f_orc, case, lambda A: oracle.loss(pb, A), (O_np,),
+                lambda: [mdl.loss_value(O_np, order=o)[0] for o in ORDERS])
+        compare("noalloc ||dl||^2 vs oracle", dl2, dl2_orc, case,
+                lambda A: oracle.loss(pb, A, return_dl_norm2=True)[1], (O_np,),
+                lambda: [mdl.loss_value(O_np, order=o)[1] for o in ORDERS])
 
 
 def test_noalloc_rejects_out_of_range_positions_and_sizes(lib):
