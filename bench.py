@@ -602,6 +602,82 @@ def learned_vs_plain(ptylm, torch, dev, target=1e-3, pairs=200_000, batch=64, re
     return out, net, idx
 
 
+def autograd_leg(ptylm, torch, dev, reps=10):
+    """The differentiable magnitudes (autograd.far_field_magnitude over the JVP / J^T VP
+    kernels) at the 1024^2 / 128^2 / 3600-position geometry, in both memory modes: the unit
+    phasor psihat / zeta stored by the forward pass (8 K M bytes; one 2D FFT per position per
+    derivative) or the exit waves recomputed in every derivative call (two FFTs, no stored
+    array).  Median of `reps` timings (CUDA events) of the forward pass, a reverse-mode J^T w
+    (backward of sum w zeta) and a forward-mode J v; and a central-difference check of the
+    reverse-mode derivative of L = sum w zeta, w nonzero on the bright pixels of 64 positions."""
+    import torch.autograd.forward_ad as fwAD
+    from paper_2103_01767_gb300 import autograd as ag
+    w_ = synth.LARGE
+    P = torch.from_numpy(synth.probe_disk_defocus(w_.m, w_.radius).astype(np.complex64)).to(dev)
+    pos_np, _ = synth.raster_positions(w_.n, w_.m, w_.grid, w_.step, w_.jitter, seed=1)
+    pos = torch.from_numpy(pos_np).to(dev)
+    O = torch.from_numpy(synth.object_texture(w_.n, seed=0).astype(np.complex64)).to(dev)
+    K, m = pos_np.shape[0], w_.m
+    wts = torch.from_numpy(synth.random_real((K, m, m), seed=5).astype(np.float32)).to(dev)
+    v = torch.from_numpy(synth.random_complex((w_.n, w_.n), seed=6).astype(np.complex64)).to(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    out = {"workload": f"{w_.n}^2 object, {m}^2 probe, {K} positions", "reps": reps}
+    for mode, budget in (("stored_phasor", 1 << 40), ("recompute_exit_waves", 0)):
+        pb = ag.MagnitudeProblem(w_.n, w_.n, m, pos, 1e-8, phasor_budget=budget)
+        Od = O.clone().requires_grad_(True)
+
+        def fwd():
+            pb._point = None
+            return ag.far_field_magnitude(Od, P, pb)
+
+        zeta = fwd()
+
+        def bwd():
+            Od.grad = None
+            torch.autograd.backward(zeta, wts, retain_graph=True)
+
+        def jvp():
+            with fwAD.dual_level():
+                fwAD.unpack_dual(ag.far_field_magnitude(fwAD.make_dual(O, v), P, pb)).tangent
+
+        r = {"stores_phasor": pb.stores_phasor, "phasor_bytes": 8 * K * m * m if pb.stores_phasor else 0,
+             "forward_ms": timed(fwd), "jtvp_ms": timed(bwd), "jvp_ms": timed(jvp)}
+        out[mode] = r
+        del pb, zeta, Od
+        torch.cuda.empty_cache()
+    # central differences of L = sum w zeta (FP64 sums) along v, w on the bright pixels of 64 positions
+    pb = ag.MagnitudeProblem(w_.n, w_.n, m, pos, 1e-8, phasor_budget=0)
+    with torch.no_grad():
+        z0 = ag.far_field_magnitude(O, P, pb)
+    sel = torch.zeros(K, dtype=torch.bool, device=dev)
+    sel[torch.from_numpy(np.random.default_rng(7).choice(K, 64, replace=False)).to(dev)] = True
+    wfd = wts * (z0 > 0.05 * z0.max()).float() * sel[:, None, None].float()
+    Od = O.clone().requires_grad_(True)
+    L = (ag.far_field_magnitude(Od, P, pb).double() * wfd.double()).sum()
+    L.backward()
+    dd = float((torch.view_as_real(Od.grad).double() * torch.view_as_real(v).double()).sum())
+    eps = 1e-3
+    with torch.no_grad():
+        Lp = float((ag.far_field_magnitude(O + eps * v, P, pb).double() * wfd.double()).sum())
+        Lm = float((ag.far_field_magnitude(O - eps * v, P, pb).double() * wfd.double()).sum())
+    fd = (Lp - Lm) / (2 * eps)
+    out["central_difference"] = {"positions": 64, "eps": eps, "fd": fd, "adjoint": dd,
+                                 "rel_diff": abs(fd - dd) / abs(dd)}
+    return out
+
+
 def _object_error(O, O_ref, mask):
     """Phase-aligned relative error over the mask (host arithmetic on the copies; reporting only)."""
     a = O.cpu().numpy().astype(np.complex128)[mask.cpu().numpy().astype(bool)]
@@ -886,7 +962,7 @@ def main():
     N, M, K = w.n * w.n, w.m * w.m, int(pos.shape[0])
 
     clocks = clk.summary()
-    comparison, tta = None, None
+    comparison, tta, autograd = None, None, None
     if rank == 0 and not args.no_extras:
         cufft_us = time_cufft_pair(torch, K, w.m, dev)
         comparison = {"cufft_fwd_inv_us": cufft_us, "matvec_us": 1e6 * (mv_ms / 1e3) / max(mv_n, 1),
@@ -899,6 +975,7 @@ def main():
         tta["learned_vs_plain"], net, idx = learned_vs_plain(ptylm, torch, dev)
         tta["large"] = large_poisson_time_to_accuracy(ptylm, torch, dev, stream, net, idx)
         net.close()
+        autograd = autograd_leg(ptylm, torch, dev)
     avg_mv_s = (mv_ms / 1e3) / max(mv_n, 1)
     flops = matvec_flops(K, M)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
@@ -940,6 +1017,7 @@ def main():
             "kernels": per_kernel,
             "comparison": comparison,
             "time_to_accuracy": tta,
+            "autograd": autograd,
         }
         print(json.dumps(line), flush=True)
     ptylm.lm_destroy(ctx)

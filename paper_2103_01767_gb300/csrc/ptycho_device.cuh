@@ -14,6 +14,15 @@ __device__ __forceinline__ void red_add_c64(float2* addr, float2 v) {
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
 
+// Read-only load that does not allocate in L1: for the object patch values, which each
+// position reads once, so that they do not push the kernel's spilled registers (and other
+// reused lines) out of L1.
+__device__ __forceinline__ float2 ldg_stream(const float2* p) {
+    float2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+
 // Asynchronous bulk prefetch of `bytes` (multiple of 16, 16-byte aligned) into L2.
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
@@ -185,49 +194,68 @@ __device__ __forceinline__ TeamCtx<G> team_setup(const float2* tw_g) {
     return c;
 }
 
+// Where a thread's 32 probe values P[BX*a + b][x] (a = 0..31, pass-1 layout, thread
+// t = x + S*b) come from, 8 at a time (a = a0 .. a0 + 7): plain loads from the probe array
+// (L1 / L2).
+template <class G>
+struct GlobalProbe {
+    const float2* pr;
+    __device__ __forceinline__ GlobalProbe(const float2* P, int tid)
+        : pr(P + (tid >> G::LOG_S) * G::S + (tid & (G::S - 1))) {}
+    __device__ __forceinline__ void load8(float2* pv, int a0) const {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) pv[i] = pr[G::BX * G::S * (a0 + i)];  // plain load: an __ldg is hoisted out of the position loop
+    }
+};
+
 // Pass-1 gather: thread t = x + S*b holds rows y = BX*a + b of column x:
 //   v[a] = P[y][x] * A[r0 + y][c0 + x].
 // Lanes are consecutive columns: each warp load reads 256 contiguous bytes of one row.
-template <class G>
-__device__ __forceinline__ void gather_times_probe(float2* v, const float2* __restrict__ A,
-                                                   const float2* __restrict__ P, int nx, int r0,
-                                                   int c0, int tid) {
+template <class G, class PS>
+__device__ __forceinline__ void gather_times_probe(float2* v, const float2* __restrict__ A, const PS& ps, int nx,
+                                                   int r0, int c0, int tid) {
     const int x = tid & (G::S - 1), b = tid >> G::LOG_S;
     const float2* src = A + (size_t)(r0 + b) * nx + c0 + x;
-    const float2* pr = P + b * G::S + x;
     const size_t row_step = (size_t)G::BX * nx;
 #pragma unroll
     for (int a0 = 0; a0 < 32; a0 += 8) {
         float2 pv[8], av[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            pv[i] = pr[G::BX * G::S * (a0 + i)];  // plain load: an __ldg is hoisted out of the position loop
-            av[i] = __ldg(src + row_step * (a0 + i));
-        }
+        for (int i = 0; i < 8; ++i) av[i] = ldg_stream(src + row_step * (a0 + i));
+        ps.load8(pv, a0);
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[a0 + i] = cmul(pv[i], av[i]);
         sched_fence();
     }
 }
+template <class G>
+__device__ __forceinline__ void gather_times_probe(float2* v, const float2* __restrict__ A,
+                                                   const float2* __restrict__ P, int nx, int r0,
+                                                   int c0, int tid) {
+    gather_times_probe<G>(v, A, GlobalProbe<G>(P, tid), nx, r0, c0, tid);
+}
 
 // Pass-1 scatter: out[r0 + y][c0 + x] += conj(P[y][x]) * v[a], same thread layout.
-template <class G>
-__device__ __forceinline__ void scatter_times_conj_probe(const float2* v, float2* out,
-                                                         const float2* __restrict__ P, int nx,
-                                                         int r0, int c0, int tid) {
+template <class G, class PS>
+__device__ __forceinline__ void scatter_times_conj_probe(const float2* v, float2* out, const PS& ps, int nx, int r0,
+                                                         int c0, int tid) {
     const int x = tid & (G::S - 1), b = tid >> G::LOG_S;
     float2* dst = out + (size_t)(r0 + b) * nx + c0 + x;
-    const float2* pr = P + b * G::S + x;
     const size_t row_step = (size_t)G::BX * nx;
 #pragma unroll
     for (int a0 = 0; a0 < 32; a0 += 8) {
         float2 pv[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) pv[i] = pr[G::BX * G::S * (a0 + i)];
+        ps.load8(pv, a0);
 #pragma unroll
         for (int i = 0; i < 8; ++i) red_add_c64(dst + row_step * (a0 + i), cmulc(v[a0 + i], pv[i]));
         sched_fence();
     }
+}
+template <class G>
+__device__ __forceinline__ void scatter_times_conj_probe(const float2* v, float2* out,
+                                                         const float2* __restrict__ P, int nx,
+                                                         int r0, int c0, int tid) {
+    scatter_times_conj_probe<G>(v, out, GlobalProbe<G>(P, tid), nx, r0, c0, tid);
 }
 
 // Scatter of one position fused with the gather of the next, which share the probe values
@@ -236,29 +264,31 @@ __device__ __forceinline__ void scatter_times_conj_probe(const float2* v, float2
 //   v[a] = P[y][x] A[r1 + y][c1 + x]                  (next position, Eq. exit_wave)
 // and the next position's object loads are in flight while the reductions issue, so the
 // two memory phases cost one round trip per chunk instead of two.
-template <class G>
-__device__ __forceinline__ void scatter_then_gather(float2* v, float2* out, const float2* __restrict__ A,
-                                                    const float2* __restrict__ P, int nx, int r0, int c0,
-                                                    int r1, int c1, int tid) {
+template <class G, class PS>
+__device__ __forceinline__ void scatter_then_gather(float2* v, float2* out, const float2* __restrict__ A, const PS& ps,
+                                                    int nx, int r0, int c0, int r1, int c1, int tid) {
     const int x = tid & (G::S - 1), b = tid >> G::LOG_S;
     float2* dst = out + (size_t)(r0 + b) * nx + c0 + x;
     const float2* src = A + (size_t)(r1 + b) * nx + c1 + x;
-    const float2* pr = P + b * G::S + x;
     const size_t row_step = (size_t)G::BX * nx;
 #pragma unroll
     for (int a0 = 0; a0 < 32; a0 += 8) {
         float2 pv[8], av[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            pv[i] = pr[G::BX * G::S * (a0 + i)];
-            av[i] = __ldg(src + row_step * (a0 + i));
-        }
+        for (int i = 0; i < 8; ++i) av[i] = ldg_stream(src + row_step * (a0 + i));
+        ps.load8(pv, a0);
 #pragma unroll
         for (int i = 0; i < 8; ++i) red_add_c64(dst + row_step * (a0 + i), cmulc(v[a0 + i], pv[i]));
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[a0 + i] = cmul(pv[i], av[i]);
         sched_fence();
     }
+}
+template <class G>
+__device__ __forceinline__ void scatter_then_gather(float2* v, float2* out, const float2* __restrict__ A,
+                                                    const float2* __restrict__ P, int nx, int r0, int c0,
+                                                    int r1, int c1, int tid) {
+    scatter_then_gather<G>(v, out, A, GlobalProbe<G>(P, tid), nx, r0, c0, r1, c1, tid);
 }
 
 // Joint gather (Eq. jac_ampl with both blocks): v[a] = P[y][x] A[r0+y][c0+x] + B[y][x] C[r0+y][c0+x],
