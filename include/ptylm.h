@@ -118,7 +118,8 @@ typedef struct {
 } ptylm_lm_params;
 
 /* Per-call results of lm_solve.  hist_* point to host arrays of hist_len entries (or are
- * NULL); entry t describes outer iteration t. */
+ * NULL); entry t describes outer iteration t.  Each outer iteration is also an NVTX range
+ * ("lm: outer iteration t") with its CG solves and trial points nested inside. */
 typedef struct {
     int n_outer;          /* outer iterations run                                         */
     int cg_total;         /* CG iterations (GGN matvecs inside CG) summed over the run    */
@@ -131,6 +132,10 @@ typedef struct {
     double* hist_mu;      /* mu after iteration t                                         */
     int* hist_cg;         /* CG iterations in iteration t                                 */
     double* hist_err;     /* object error after iteration t (NaN without O_ref)           */
+    double* hist_rho;     /* gain ratio of the step that ended iteration t                */
+    double* hist_lambda;  /* damping lambda of that step                                  */
+    double* hist_time;    /* host wall-clock seconds from the start of the call to the end
+                             of iteration t                                               */
 } ptylm_lm_stats;
 
 /* Create a context for one reconstruction problem (Sec. 2).

@@ -2,8 +2,11 @@
 // LM vector kernels with FP64 reductions, and the truncated LM driver (Algorithm 1 of
 // arXiv 2103.01767, Sec. 4.2).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <chrono>
+#include <optional>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1170,8 +1173,25 @@ static ptylm_status lm_solve_impl(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P
     };
 
     bool ahead = false;   // the linearisation at z came with the accepted trial point
+    const auto t_start = std::chrono::steady_clock::now();
+    struct NvtxOuter {
+        bool open = false;
+        void begin(int t) {
+            end();
+            char name[48];
+            snprintf(name, sizeof name, "lm: outer iteration %d", t);
+            nvtxRangePushA(name);
+            open = true;
+        }
+        void end() {
+            if (open) nvtxRangePop();
+            open = false;
+        }
+        ~NvtxOuter() { end(); }
+    } nvtx_outer;
     for (t = t0; t < t0 + prm->max_outer; ++t) {
         const int h = t - t0;   // history entry of this outer iteration
+        nvtx_outer.begin(t);
         const double s_t = surrogate_at(prm, t);
         c->b_eff = (float)(c->d.background + s_t);
         surrogate_guard.used = s_t > 0.0;
@@ -1194,12 +1214,19 @@ static ptylm_status lm_solve_impl(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P
             if (stats->hist_f) stats->hist_f[h] = f;
             if (stats->hist_gnorm) stats->hist_gnorm[h] = gnorm;
         }
-        double rho = 0.0;
+        double rho = 0.0, lambda_last = NAN;
         int cg_this = 0;
         bool stalled = false, timed_out = false;
+        struct NvtxSolve {   // closed on every exit from this outer iteration
+            NvtxSolve() { nvtxRangePushA("lm: CG solves and trial points"); }
+            ~NvtxSolve() { nvtxRangePop(); }
+        };
+        std::optional<NvtxSolve> nvtx_solve;
+        nvtx_solve.emplace();
         while (!(rho > prm->rho_min)) {
             // lambda = mu ||grad_zeta l||^nu (D = I) or mu (D = Dg(G)), Algorithm 1
             const double lambda = D ? mu : mu * std::pow(std::sqrt(dl2), prm->nu);
+            lambda_last = lambda;
             const float lam32 = (float)lambda;
             // ---- truncated (P)CG on (G + lambda D) x = -g, warm-started from x ----
             STATUS_TRY(op_matvec(c, x, lambda, D, q));                            // q = (G + lambda D) x
@@ -1327,10 +1354,15 @@ static ptylm_status lm_solve_impl(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P
                 break;
             }
         }
+        nvtx_solve.reset();
         cg_total += cg_this;
         if (stats && stats->hist_len > h) {
             if (stats->hist_mu) stats->hist_mu[h] = mu;
             if (stats->hist_cg) stats->hist_cg[h] = cg_this;
+            if (stats->hist_rho) stats->hist_rho[h] = rho;
+            if (stats->hist_lambda) stats->hist_lambda[h] = lambda_last;
+            if (stats->hist_time)
+                stats->hist_time[h] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
         }
         if (timed_out) {
             status = fail(PTYLM_ERR_TIMEOUT, "a grid-wide wait of the CG iteration gave up at outer iteration %d", t);

@@ -73,7 +73,8 @@ class LMStats(ctypes.Structure):
                 ("err_final", ctypes.c_double), ("hist_len", ctypes.c_int),
                 ("hist_f", ctypes.c_void_p), ("hist_gnorm", ctypes.c_void_p),
                 ("hist_mu", ctypes.c_void_p), ("hist_cg", ctypes.c_void_p),
-                ("hist_err", ctypes.c_void_p)]
+                ("hist_err", ctypes.c_void_p), ("hist_rho", ctypes.c_void_p),
+                ("hist_lambda", ctypes.c_void_p), ("hist_time", ctypes.c_void_p)]
 
 
 _lib = None
@@ -369,13 +370,15 @@ def default_lm_params(loss: int) -> LMParams:
 
 
 def lm_solve(ctx: Context, O, P, params: LMParams | None = None, hist_len: int = 0,
-             O_ref=None, mask=None, state=None, **overrides):
+             O_ref=None, mask=None, state=None, log_path=None, **overrides):
     """Run Algorithm 1 in place on O.  Returns (status, stats dict).  PTYLM_WARN_CG_MAXIT and
     PTYLM_ERR_STALLED (the damping ran away: no step decreases f any more at FP32 resolution)
     are returned rather than raised; O, P and the history then hold the last iterate.
     state: None (fresh start) or a dict {t, mu, delta} (delta a contiguous complex64 tensor or
     array of the state's length, updated in place); the run continues from it through
-    lm_solve_resume and the dict is updated to the state after the run (also stats["state"])."""
+    lm_solve_resume and the dict is updated to the state after the run (also stats["state"]).
+    log_path: append one JSON line per outer iteration (t, f, ||grad f||, mu, lambda, gain
+    ratio, CG iterations, accepted, seconds, object error) to this file (needs hist_len)."""
     p = default_lm_params(ctx.desc.loss) if params is None else params
     for k, v in overrides.items():
         setattr(p, k, v)
@@ -384,10 +387,10 @@ def lm_solve(ctx: Context, O, P, params: LMParams | None = None, hist_len: int =
     if mask is not None:
         p.mask = _ptr(mask)
     L = int(hist_len)
-    hf, hg, hmu, herr = (np.full(max(L, 1), math.nan) for _ in range(4))
+    hf, hg, hmu, herr, hrho, hlam, htime = (np.full(max(L, 1), math.nan) for _ in range(7))
     hcg = np.zeros(max(L, 1), np.int32)
     st = LMStats(0, 0, 0, 0.0, 0.0, L, hf.ctypes.data, hg.ctypes.data, hmu.ctypes.data,
-                 hcg.ctypes.data, herr.ctypes.data)
+                 hcg.ctypes.data, herr.ctypes.data, hrho.ctypes.data, hlam.ctypes.data, htime.ctypes.data)
     lib = load_library()
     if state is None:
         status = _check(lib.lm_solve(ctx.handle, _ptr(O), _ptr(P), ctypes.byref(p), ctypes.byref(st)),
@@ -398,10 +401,28 @@ def lm_solve(ctx: Context, O, P, params: LMParams | None = None, hist_len: int =
                                             ctypes.byref(st)), allow=(PTYLM_WARN_CG_MAXIT, PTYLM_ERR_STALLED))
         state["t"], state["mu"] = cs.t, cs.mu
     n = min(st.n_outer, L)
-    return status, dict(n_outer=st.n_outer, cg_total=st.cg_total, matvecs=st.matvecs_total,
-                        f_final=st.f_final, err_final=st.err_final, f=hf[:n].copy(),
-                        gnorm=hg[:n].copy(), mu=hmu[:n].copy(), cg=hcg[:n].copy(),
-                        err=herr[:n].copy(), state=state)
+    out = dict(n_outer=st.n_outer, cg_total=st.cg_total, matvecs=st.matvecs_total,
+               f_final=st.f_final, err_final=st.err_final, f=hf[:n].copy(),
+               gnorm=hg[:n].copy(), mu=hmu[:n].copy(), cg=hcg[:n].copy(),
+               err=herr[:n].copy(), rho=hrho[:n].copy(), lam=hlam[:n].copy(), seconds=htime[:n].copy(),
+               state=state)
+    if log_path is not None:
+        write_lm_log(log_path, out, p)
+    return status, out
+
+
+def write_lm_log(path, info, params) -> None:
+    """One JSON line per outer iteration of an lm_solve history (appended to `path`)."""
+    import json
+    t0 = int(info["state"]["t"]) - int(info["n_outer"]) if info.get("state") else 0
+    with open(path, "a") as fh:
+        for i in range(len(info["f"])):
+            def num(a):
+                return float(a[i]) if math.isfinite(float(a[i])) else None
+            fh.write(json.dumps({"t": t0 + i, "f": num(info["f"]), "grad_norm": num(info["gnorm"]),
+                                 "mu": num(info["mu"]), "lambda": num(info["lam"]), "rho": num(info["rho"]),
+                                 "cg": int(info["cg"][i]), "accepted": bool(info["rho"][i] > params.rho_min),
+                                 "seconds": num(info["seconds"]), "err": num(info["err"])}) + "\n")
 
 
 def new_lm_state(ctx: Context, mu0: float | None = None, device=None):
@@ -555,7 +576,7 @@ def batch_lm_solve(batch: Batch, O, params=None, hist_len: int = 0, O_refs=None,
         hcg = np.zeros(max(L, 1), np.int32)
         hists.append((hf, hg, hmu, hcg, herr))
         stats[b] = LMStats(0, 0, 0, 0.0, 0.0, L, hf.ctypes.data, hg.ctypes.data, hmu.ctypes.data,
-                           hcg.ctypes.data, herr.ctypes.data)
+                           hcg.ctypes.data, herr.ctypes.data, None, None, None)
     status = _check(lib.ptylm_batch_lm_solve(batch.handle, _ptr(O), prm, stats),
                     allow=(PTYLM_WARN_CG_MAXIT, PTYLM_ERR_STALLED))
     out = []
