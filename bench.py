@@ -549,7 +549,7 @@ def learned_vs_plain(ptylm, torch, dev, target=1e-3, pairs=200_000, batch=64, re
     c64 = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.complex64)).to(dev)
     P = c64(synth.probe_disk_defocus(m, R))
     pool = c64(np.stack([synth.object_texture(n, seed=100 + s) for s in range(8)]))
-    widths = (32, 64, 128)
+    widths = (64, 128, 256)
     net = ptylm.net_create(widths, max_batch=batch, seed=1)
     steps = pairs // batch
     torch.cuda.synchronize(dev)

@@ -438,16 +438,22 @@ ptylm_status ptylm_batch_destroy(ptylm_batch* batch);
  * probe), two channels (Re, Im) of [128][128] float.  A 6-layer convolutional encoder-decoder refines it into the object
  * patch: three 3 x 3 stride-2 convolutions 2 -> C1 -> C2 -> C3 (ReLU), then three x2
  * nearest upsamplings each followed by a 3 x 3 convolution C3 -> C2 -> C1 (ReLU) -> 2
- * (linear).  Weights are bfloat16 copies of FP32 master weights; activations and all sums
- * are FP32.  The patch estimates are averaged into the object with weights |P|^2 over
+ * (linear).  Weights are bfloat16 copies of FP32 master weights; sums are FP32.  The
+ * convolutions run on the tensor cores (tcgen05 MMA, BF16 operands, FP32 accumulation in
+ * TMEM): each FP32 activation or gradient is carried as a pair of bfloat16 values
+ * (x = hi + lo, exact to 2^-18 relative), so a product with a bfloat16 weight takes two MMAs
+ * and a weight-gradient product three (hi.hi + hi.lo + lo.hi).  A convolution kernel whose
+ * bounded wait gives up makes the call return PTYLM_ERR_TIMEOUT.  The patch estimates are
+ * averaged into the object with weights |P|^2 over
  * their overlaps (1 where no probe reaches).  Parameter layout (flat float array):
  * W1 b1 W2 b2 ... W6 b6, W_l as [c_out][c_in][3][3].  Arrays are device arrays unless named
  * *_host; images are [N][2][128][128] float.
  * --------------------------------------------------------------------------------------- */
 typedef struct ptylm_net ptylm_net;
 
-/* m must be 128; widths = {C1, C2, C3}, positive multiples of 16; max_batch: patterns per
- * forward / training batch; seed: He-normal initial weights, zero biases. */
+/* m must be 128; widths = {C1, C2, C3}, multiples of 32 in [32, 256] ({64, 128, 256}:
+ * 740,226 parameters); max_batch: patterns per forward / training batch; seed: He-normal
+ * initial weights, zero biases.  PTYLM_ERR_ARG for other sizes. */
 ptylm_status ptylm_net_create(ptylm_net** net, int m, const int* widths, int max_batch, uint64_t seed,
                               void* stream);
 /* Number of floats in the flat parameter array (-1 for NULL). */

@@ -1,0 +1,68 @@
+// conv_tc.h -- tensor-core 3x3 convolutions of the learned initialisation (tcgen05 MMA with
+// BF16 operands and FP32 accumulation in TMEM, operands staged by TMA tiled loads).
+//
+// Feature maps live in HBM as NHWC pairs of bfloat16 tensors (hi, lo) with x = hi + lo,
+// hi = bf16(x), lo = bf16(x - hi): the pair carries an FP32 activation to 2^-18 relative
+// (two MMAs per product against BF16 weights), so the network computes with BF16 weights and
+// FP32-accurate activations.  Weight gradients take the three products hi.hi + hi.lo + lo.hi.
+//
+// Weight copies (bfloat16) are tap-major: forward wf[9][Co][Ci_pad], input gradient
+// wb[9][Ci][Co_pad] (wb[t][c][o] = w[o][c][t]), channels zero-padded to multiples of 16.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace ptylm {
+
+struct Act2 {
+    __nv_bfloat16* hi;
+    __nv_bfloat16* lo;
+    int N, H, W, C;  // batch, height, width, stored channels (multiple of 8)
+};
+
+struct TcLayer {
+    int Ci, Co;          // channels
+    int Ci_pad, Co_pad;  // multiples of 16 >= Ci, Co (K extents of wf and wb)
+    int up;              // 0: stride 2; 1: x2 nearest upsampling, then stride 1
+    int relu;
+    int Hin;             // input side (the low-resolution side for up layers); square maps
+    int Hout() const { return up ? 2 * Hin : Hin / 2; }
+};
+
+// one-time setup (tensor-map encoder entry point, kernel attributes)
+cudaError_t tc_prepare();
+
+// y = relu?(conv(x) + bias): hidden layers write the pair y (NHWC, C = Co); the last layer
+// writes y32 as FP32 planes [N][Co][Hout][Hout].
+cudaError_t tc_conv_forward(const TcLayer& L, const Act2& x, const __nv_bfloat16* wf, const float* bias, const Act2* y,
+                            float* y32, unsigned* err, unsigned spin, int num_sms, cudaStream_t st);
+
+// dx = (d conv / d x)^T dy masked by act > 0 (act: the layer's input, same shape as dx);
+// db_part[i][c] (i < *n_part) are partial sums over pixels of dx (the bias gradient of the
+// layer that produced act).  db_part needs tc_bias_parts(L, N) * Ci floats.
+cudaError_t tc_conv_backward_data(const TcLayer& L, const Act2& dy, const __nv_bfloat16* wb, const Act2& act,
+                                  const Act2& dx, float* db_part, int* n_part, unsigned* err, unsigned spin, int num_sms,
+                                  cudaStream_t st);
+int tc_bias_parts(const TcLayer& L, int N, int num_sms);
+
+// dw[o][c][3][3] = sum over the batch and pixels of dy (.) x at the tap, written (not
+// accumulated); ws: tc_wgrad_workspace(L, N, num_sms) floats.
+cudaError_t tc_conv_wgrad(const TcLayer& L, const Act2& x, const Act2& dy, float* ws, float* dw, unsigned* err,
+                          unsigned spin, int num_sms, cudaStream_t st);
+size_t tc_wgrad_workspace(const TcLayer& L, int N, int num_sms);
+
+// db[c] = sum_i part[i][c] (fixed order)
+cudaError_t tc_bias_reduce(const float* part, int n_part, int C, float* db, cudaStream_t st);
+// wf / wb from the FP32 master weights w[Co][Ci][3][3]
+cudaError_t tc_weights(const TcLayer& L, const float* w32, __nv_bfloat16* wf, __nv_bfloat16* wb, cudaStream_t st);
+// pair x0 (C = 8, channels 2..7 zero) from FP32 planes X[N][2][H][W]
+cudaError_t tc_pack_input(const float* X, const Act2& x0, cudaStream_t st);
+// loss += sum mask (out - t)^2 / n_terms (FP64); g = 2 mask (out - t) / n_terms as the pair
+// g (C = 8, channels 2..7 zero) and db_part[i][2] partial sums of g (FP32).
+cudaError_t tc_mse(const float* out, const float* t, const float* mask, const Act2& g, double n_terms, float* db_part,
+                   int* n_part, double* loss, cudaStream_t st);
+constexpr int kMseBlocks = 256;
+
+}  // namespace ptylm

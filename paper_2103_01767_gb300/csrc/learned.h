@@ -1,7 +1,7 @@
 // learned.h -- kernels of the learned initialisation (a data-driven initial object for
-// Algorithm 1; not part of the paper): the 3x3 convolution layers of the encoder-decoder
-// in forward and backward form (bfloat16 weights, FP32 activations and accumulation), the
-// loss, Adam, the physics input computed with the team FFT, and the overlap stitching.
+// Algorithm 1; not part of the paper) besides its convolutions (conv_tc.h): Adam, the
+// probe-support mask, the physics input computed with the team FFT, and the overlap
+// stitching.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -10,32 +10,7 @@
 
 namespace ptylm {
 
-struct ConvShape {
-    int N, Ci, Co, Hin, Win;  // input batch, channels and side (before any upsampling)
-    int stride, up, relu;     // stride 1 or 2; up: x2 nearest upsampling of the input first
-    int Ho() const { return (up ? 2 * Hin : Hin) / stride; }
-    int Wo() const { return (up ? 2 * Win : Win) / stride; }
-};
-
-// y = conv(x) + bias (ReLU if relu), NCHW FP32, weights bfloat16 [Co][Ci][3][3].
-cudaError_t conv_forward(const ConvShape& s, const float* x, const __nv_bfloat16* w, const float* bias, float* y,
-                         cudaStream_t st);
-// dx (input side, low resolution for upsampled layers) from dy; wt: the weights transposed
-// and flipped ([Ci][Co][3][3], bfloat16), scratch: N*Ci*(2 Hin)*(2 Win) floats for up layers.
-cudaError_t conv_backward_data(const ConvShape& s, const float* dy, const __nv_bfloat16* w,
-                               const __nv_bfloat16* wt, float* dx, float* scratch, cudaStream_t st);
-// dw (FP32, accumulated into: zero it first) and db (written) from x and dy.
-cudaError_t conv_backward_weights(const ConvShape& s, const float* x, const float* dy, float* dw, float* db,
-                                  int num_sms, cudaStream_t st);
-// w16 = bf16(w32) and wt = transposed, flipped bf16 copy.
-cudaError_t weights_to_bf16(const ConvShape& s, const float* w32, __nv_bfloat16* w16, __nv_bfloat16* wt,
-                            cudaStream_t st);
-// g *= (a > 0)
-cudaError_t relu_backward(float* g, const float* a, long n, cudaStream_t st);
-// loss += sum mask (out - t)^2 / n_terms (FP64), g = 2 mask (out - t) / n_terms
-cudaError_t mse_loss(const float* out, const float* t, const float* mask, int N, int HW, double n_terms, float* g,
-                     double* loss, cudaStream_t st);
-// Adam step t (>= 1) on n parameters, then w16 = bf16(w) when w16 != NULL.
+// Adam step t (>= 1) on n parameters.
 cudaError_t adam_step(float* w, float* m, float* v, const float* g, long n, float lr, float b1, float b2, float eps,
                       int t, cudaStream_t st);
 // mask[p] = |P[p]| > 0 as 1/0 floats

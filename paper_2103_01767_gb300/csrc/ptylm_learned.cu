@@ -17,6 +17,7 @@
 
 #include "../../include/ptylm.h"
 #include "kernels.h"
+#include "conv_tc.h"
 #include "learned.h"
 
 using namespace ptylm;
@@ -61,7 +62,7 @@ uint64_t splitmix64(uint64_t& s) {
 
 struct ptylm_net {
     int m = 0, widths[3] = {0, 0, 0}, max_batch = 0, num_sms = 0;
-    int ci[NL], co[NL], stride[NL], up[NL], relu[NL], hin[NL];
+    TcLayer L[NL];
     long w_off[NL], b_off[NL], n_params = 0;
     cudaStream_t stream = nullptr;
     std::vector<void*> allocs;
@@ -70,14 +71,17 @@ struct ptylm_net {
     float* adam_m = nullptr;
     float* adam_v = nullptr;
     int adam_t = 0;
-    __nv_bfloat16* w16[NL] = {};
-    __nv_bfloat16* wt[NL] = {};
+    __nv_bfloat16* wf[NL] = {};        // forward weight copies [9][Co][Ci_pad]
+    __nv_bfloat16* wb[NL] = {};        // input-gradient weight copies [9][Ci][Co_pad]
     float* xin = nullptr;              // [max_batch][2][m][m]
     float* target = nullptr;           // [max_batch][2][m][m]
-    float* act[NL] = {};               // layer outputs
-    float* g0 = nullptr;               // gradient ping-pong buffers
-    float* g1 = nullptr;
-    float* scratch = nullptr;          // high-resolution input gradients of upsampled layers
+    float* out = nullptr;              // network output [max_batch][2][m][m]
+    Act2 x0{};                         // packed input pair, 8 channels
+    Act2 act[NL - 1] = {};             // hidden layer outputs (NHWC pairs)
+    Act2 g[NL] = {};                   // gradient w.r.t. each layer's output (g[NL-1]: 8 channels)
+    float* db_part = nullptr;          // partial sums of the bias gradients
+    float* ws = nullptr;               // weight-gradient partial sums
+    unsigned* err = nullptr;           // bounded-wait failures of the convolution kernels
     float* mask = nullptr;             // [m][m] probe support
     double* loss = nullptr;            // [1]
     float2* tw = nullptr;              // W_m^j
@@ -86,6 +90,8 @@ struct ptylm_net {
 };
 
 namespace {
+
+constexpr unsigned kConvSpin = 1u << 24;   // polls per bounded wait of a convolution kernel
 
 ptylm_status nalloc(ptylm_net* n, void** p, size_t bytes) {
     if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
@@ -102,27 +108,44 @@ ptylm_status nalloc_t(ptylm_net* n, T** p, size_t count) {
     *p = static_cast<T*>(q);
     return s;
 }
-
-ConvShape shape(const ptylm_net* n, int l, int N) {
-    return ConvShape{N, n->ci[l], n->co[l], n->hin[l], n->hin[l], n->stride[l], n->up[l], n->relu[l]};
+ptylm_status nalloc_act(ptylm_net* n, Act2* a, int H, int C) {
+    *a = Act2{nullptr, nullptr, n->max_batch, H, H, C};
+    const size_t count = (size_t)n->max_batch * H * H * C;
+    ptylm_status s;
+    if ((s = nalloc_t(n, &a->hi, count)) != PTYLM_OK) return s;
+    return nalloc_t(n, &a->lo, count);
 }
-
-long out_elems(const ptylm_net* n, int l, int N) {
-    const ConvShape s = shape(n, l, N);
-    return (long)N * s.Co * s.Ho() * s.Wo();
+Act2 batch(Act2 a, int N) {
+    a.N = N;
+    return a;
 }
 
 ptylm_status refresh_bf16(ptylm_net* n) {
-    for (int l = 0; l < NL; ++l)
-        LCUDA_TRY(weights_to_bf16(shape(n, l, 1), n->params + n->w_off[l], n->w16[l], n->wt[l], n->stream));
+    for (int l = 0; l < NL; ++l) LCUDA_TRY(tc_weights(n->L[l], n->params + n->w_off[l], n->wf[l], n->wb[l], n->stream));
+    return PTYLM_OK;
+}
+
+// a bounded wait inside a convolution kernel gave up: report it and clear the flag
+ptylm_status check_conv_wait(ptylm_net* n) {
+    unsigned h = 0;
+    LCUDA_TRY(cudaMemcpyAsync(&h, n->err, sizeof(unsigned), cudaMemcpyDeviceToHost, n->stream));
+    LCUDA_TRY(cudaStreamSynchronize(n->stream));
+    if (h) {
+        LCUDA_TRY(cudaMemset(n->err, 0, sizeof(unsigned)));
+        return lfail(PTYLM_ERR_TIMEOUT, "a bounded wait of a convolution kernel gave up (flags 0x%x)", h);
+    }
     return PTYLM_OK;
 }
 
 ptylm_status forward(ptylm_net* n, const float* X, int N) {
-    const float* in = X;
+    const Act2 x0 = batch(n->x0, N);
+    LCUDA_TRY(tc_pack_input(X, x0, n->stream));
+    Act2 in = x0;
     for (int l = 0; l < NL; ++l) {
-        LCUDA_TRY(conv_forward(shape(n, l, N), in, n->w16[l], n->params + n->b_off[l], n->act[l], n->stream));
-        in = n->act[l];
+        const Act2 y = l < NL - 1 ? batch(n->act[l], N) : Act2{};
+        LCUDA_TRY(tc_conv_forward(n->L[l], in, n->wf[l], n->params + n->b_off[l], l < NL - 1 ? &y : nullptr, n->out, n->err,
+                                  kConvSpin, n->num_sms, n->stream));
+        in = y;
     }
     return PTYLM_OK;
 }
@@ -130,18 +153,17 @@ ptylm_status forward(ptylm_net* n, const float* X, int N) {
 // loss and gradients (into n->grads) for the batch X -> target T
 ptylm_status loss_grad(ptylm_net* n, const float* X, const float* T, int N, double n_terms, double* loss_dev) {
     LSTATUS_TRY(forward(n, X, N));
-    float* g = n->g0;
-    float* gnext = n->g1;
-    LCUDA_TRY(mse_loss(n->act[NL - 1], T, n->mask, N, n->m * n->m, n_terms, g, loss_dev, n->stream));
-    LCUDA_TRY(cudaMemsetAsync(n->grads, 0, sizeof(float) * n->n_params, n->stream));
+    int parts = 0;
+    LCUDA_TRY(tc_mse(n->out, T, n->mask, batch(n->g[NL - 1], N), n_terms, n->db_part, &parts, loss_dev, n->stream));
+    LCUDA_TRY(tc_bias_reduce(n->db_part, parts, n->L[NL - 1].Co, n->grads + n->b_off[NL - 1], n->stream));
     for (int l = NL - 1; l >= 0; --l) {
-        const ConvShape s = shape(n, l, N);
-        if (n->relu[l]) LCUDA_TRY(relu_backward(g, n->act[l], out_elems(n, l, N), n->stream));
-        const float* in = l == 0 ? X : n->act[l - 1];
-        LCUDA_TRY(conv_backward_weights(s, in, g, n->grads + n->w_off[l], n->grads + n->b_off[l], n->num_sms, n->stream));
+        const Act2 in = l == 0 ? batch(n->x0, N) : batch(n->act[l - 1], N);
+        const Act2 g = batch(n->g[l], N);
+        LCUDA_TRY(tc_conv_wgrad(n->L[l], in, g, n->ws, n->grads + n->w_off[l], n->err, kConvSpin, n->num_sms, n->stream));
         if (l > 0) {
-            LCUDA_TRY(conv_backward_data(s, g, n->w16[l], n->wt[l], gnext, n->scratch, n->stream));
-            std::swap(g, gnext);
+            LCUDA_TRY(tc_conv_backward_data(n->L[l], g, n->wb[l], in, batch(n->g[l - 1], N), n->db_part, &parts, n->err,
+                                            kConvSpin, n->num_sms, n->stream));
+            LCUDA_TRY(tc_bias_reduce(n->db_part, parts, n->L[l].Ci, n->grads + n->b_off[l - 1], n->stream));
         }
     }
     return PTYLM_OK;
@@ -179,7 +201,8 @@ ptylm_status ptylm_net_create(ptylm_net** out, int m, const int* widths, int max
     if (m != 128) return lfail(PTYLM_ERR_ARG, "the learned initialisation is built for 128 x 128 patterns");
     if (max_batch < 1) return lfail(PTYLM_ERR_ARG, "max_batch must be >= 1");
     for (int i = 0; i < 3; ++i)
-        if (widths[i] < 16 || widths[i] % 16) return lfail(PTYLM_ERR_ARG, "widths must be positive multiples of 16");
+        if (widths[i] < 32 || widths[i] > 256 || widths[i] % 32)
+            return lfail(PTYLM_ERR_ARG, "widths must be multiples of 32 in [32, 256]");
     ptylm_net* n = new ptylm_net();
     auto bail = [&](ptylm_status s) {
         for (void* p : n->allocs) cudaFree(p);
@@ -195,18 +218,17 @@ ptylm_status ptylm_net_create(ptylm_net** out, int m, const int* widths, int max
         cudaGetLastError();
         return bail(lfail(PTYLM_ERR_CUDA, "no usable CUDA device"));
     }
+    if (tc_prepare() != cudaSuccess) {
+        cudaGetLastError();
+        return bail(lfail(PTYLM_ERR_CUDA, "the tensor-core convolutions need the tensor-map encoder of the driver"));
+    }
     const int c1 = widths[0], c2 = widths[1], c3 = widths[2];
     const int ci[NL] = {2, c1, c2, c3, c2, c1}, co[NL] = {c1, c2, c3, c2, c1, 2};
-    const int st[NL] = {2, 2, 2, 1, 1, 1}, upv[NL] = {0, 0, 0, 1, 1, 1}, rl[NL] = {1, 1, 1, 1, 1, 0};
+    const int upv[NL] = {0, 0, 0, 1, 1, 1}, rl[NL] = {1, 1, 1, 1, 1, 0};
     const int hin[NL] = {m, m / 2, m / 4, m / 8, m / 4, m / 2};
     long off = 0;
     for (int l = 0; l < NL; ++l) {
-        n->ci[l] = ci[l];
-        n->co[l] = co[l];
-        n->stride[l] = st[l];
-        n->up[l] = upv[l];
-        n->relu[l] = rl[l];
-        n->hin[l] = hin[l];
+        n->L[l] = TcLayer{ci[l], co[l], (ci[l] + 15) / 16 * 16, (co[l] + 15) / 16 * 16, upv[l], rl[l], hin[l]};
         n->w_off[l] = off;
         off += (long)co[l] * ci[l] * 9;
         n->b_off[l] = off;
@@ -215,22 +237,29 @@ ptylm_status ptylm_net_create(ptylm_net** out, int m, const int* widths, int max
     n->n_params = off;
     ptylm_status s;
     const size_t img = (size_t)max_batch * 2 * m * m;
-    long max_act = 0, max_scratch = 0;
+    size_t ws = 1, parts = (size_t)kMseBlocks * 2;
     for (int l = 0; l < NL; ++l) {
-        max_act = std::max(max_act, out_elems(n, l, max_batch));
-        if (upv[l]) max_scratch = std::max(max_scratch, (long)max_batch * ci[l] * (2L * hin[l]) * (2L * hin[l]));
+        ws = std::max(ws, tc_wgrad_workspace(n->L[l], max_batch, n->num_sms));
+        if (l > 0) parts = std::max(parts, (size_t)tc_bias_parts(n->L[l], max_batch, n->num_sms) * ci[l]);
     }
     if ((s = nalloc_t(n, &n->params, off)) || (s = nalloc_t(n, &n->grads, off)) || (s = nalloc_t(n, &n->adam_m, off)) ||
         (s = nalloc_t(n, &n->adam_v, off)) || (s = nalloc_t(n, &n->xin, img)) || (s = nalloc_t(n, &n->target, img)) ||
-        (s = nalloc_t(n, &n->g0, std::max<long>(max_act, img))) || (s = nalloc_t(n, &n->g1, std::max<long>(max_act, img))) ||
-        (s = nalloc_t(n, &n->scratch, std::max<long>(1, max_scratch))) || (s = nalloc_t(n, &n->mask, (size_t)m * m)) ||
-        (s = nalloc_t(n, &n->loss, 1)) || (s = nalloc_t(n, &n->tw, m)) || (s = nalloc_t(n, &n->u, (size_t)m * m)) ||
-        (s = nalloc_t(n, &n->P, (size_t)m * m)))
+        (s = nalloc_t(n, &n->out, img)) || (s = nalloc_t(n, &n->db_part, parts)) || (s = nalloc_t(n, &n->ws, ws)) ||
+        (s = nalloc_t(n, &n->err, 1)) || (s = nalloc_t(n, &n->mask, (size_t)m * m)) || (s = nalloc_t(n, &n->loss, 1)) ||
+        (s = nalloc_t(n, &n->tw, m)) || (s = nalloc_t(n, &n->u, (size_t)m * m)) || (s = nalloc_t(n, &n->P, (size_t)m * m)) ||
+        (s = nalloc_act(n, &n->x0, m, 8)) || (s = nalloc_act(n, &n->g[NL - 1], m, 8)))
         return bail(s);
     for (int l = 0; l < NL; ++l) {
-        if ((s = nalloc_t(n, &n->w16[l], (size_t)co[l] * ci[l] * 9)) || (s = nalloc_t(n, &n->wt[l], (size_t)co[l] * ci[l] * 9)) ||
-            (s = nalloc_t(n, &n->act[l], out_elems(n, l, max_batch))))
+        if ((s = nalloc_t(n, &n->wf[l], (size_t)9 * co[l] * n->L[l].Ci_pad)) ||
+            (s = nalloc_t(n, &n->wb[l], (size_t)9 * ci[l] * n->L[l].Co_pad)))
             return bail(s);
+        if (l < NL - 1 &&
+            ((s = nalloc_act(n, &n->act[l], n->L[l].Hout(), co[l])) || (s = nalloc_act(n, &n->g[l], n->L[l].Hout(), co[l]))))
+            return bail(s);
+    }
+    if (cudaMemset(n->err, 0, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(lfail(PTYLM_ERR_CUDA, "initialising the network"));
     }
     // He-normal initial weights (std sqrt(2 / (9 c_in))) by Box-Muller on splitmix64, zero biases
     std::vector<float> h(off, 0.0f);
@@ -288,10 +317,8 @@ ptylm_status ptylm_net_forward(ptylm_net* n, const float* X, int N, float* out) 
     if (!n || !X || !out) return lfail(PTYLM_ERR_ARG, "net, X and out must be non-NULL");
     if (N < 1 || N > n->max_batch) return lfail(PTYLM_ERR_ARG, "N must be in [1, max_batch]");
     LSTATUS_TRY(forward(n, X, N));
-    LCUDA_TRY(cudaMemcpyAsync(out, n->act[NL - 1], sizeof(float) * out_elems(n, NL - 1, N), cudaMemcpyDeviceToDevice,
-                              n->stream));
-    LCUDA_TRY(cudaStreamSynchronize(n->stream));
-    return PTYLM_OK;
+    LCUDA_TRY(cudaMemcpyAsync(out, n->out, sizeof(float) * N * 2 * n->m * n->m, cudaMemcpyDeviceToDevice, n->stream));
+    return check_conv_wait(n);
 }
 
 ptylm_status ptylm_net_loss_grad(ptylm_net* n, const float* X, const float* T, const float* mask, int N, double* loss) {
@@ -310,6 +337,7 @@ ptylm_status ptylm_net_loss_grad(ptylm_net* n, const float* X, const float* T, c
     double h = 0.0;
     LCUDA_TRY(cudaMemcpyAsync(&h, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
     LCUDA_TRY(cudaStreamSynchronize(n->stream));
+    LSTATUS_TRY(check_conv_wait(n));
     if (loss) *loss = h;
     return PTYLM_OK;
 }
@@ -387,6 +415,7 @@ ptylm_status ptylm_net_train(ptylm_net* n, const ptylm_c64* pool, int n_obj, int
         e = cudaStreamSynchronize(n->stream);
         if (e == cudaSuccess && loss_hist) e = cudaMemcpy(loss_hist, dl, sizeof(double) * steps, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) s = lfail(PTYLM_ERR_CUDA, "training: %s", cudaGetErrorString(e));
+        else s = check_conv_wait(n);
     }
     cudaFree(d4);
     cudaFree(dl);
@@ -445,7 +474,7 @@ ptylm_status ptylm_learned_init(ptylm_ctx* ctx, ptylm_net* n, const ptylm_c64* P
                            n->stream);
         if (e == cudaSuccess) s = forward(n, n->xin, nb);
         if (e == cudaSuccess && s == PTYLM_OK)
-            e = stitch_accumulate(n->act[NL - 1], didx + i0, nb, cv.pos, n->P, cv.nx, num, den, n->stream);
+            e = stitch_accumulate(n->out, didx + i0, nb, cv.pos, n->P, cv.nx, num, den, n->stream);
     }
     if (e == cudaSuccess && s == PTYLM_OK) e = stitch_finish(num, den, N, reinterpret_cast<float2*>(O0), n->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
@@ -454,7 +483,7 @@ ptylm_status ptylm_learned_init(ptylm_ctx* ctx, ptylm_net* n, const ptylm_c64* P
     cudaFree(didx);
     if (s != PTYLM_OK) return s;
     LCUDA_TRY(e);
-    return PTYLM_OK;
+    return check_conv_wait(n);
 }
 
 ptylm_status ptylm_net_destroy(ptylm_net* n) {

@@ -617,7 +617,7 @@ class Net:
             pass
 
 
-def net_create(widths=(32, 64, 128), max_batch=64, seed=0, m=128, stream=None) -> Net:
+def net_create(widths=(64, 128, 256), max_batch=64, seed=0, m=128, stream=None) -> Net:
     w = (ctypes.c_int * 3)(*[int(x) for x in widths])
     h = ctypes.c_void_p()
     _check(load_library().ptylm_net_create(ctypes.byref(h), int(m), w, int(max_batch), int(seed), _stream_ptr(stream)))
