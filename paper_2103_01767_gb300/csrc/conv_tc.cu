@@ -4,12 +4,13 @@
 // grid itself, or one parity class of it), i.e. 128 GEMM rows = 128 TMEM lanes, and up to four
 // such accumulators ("phases") of N columns each.  The K loop runs over input channels, 16 per
 // pipeline stage.  Per stage a TMA producer thread loads
-//   * a few "copies" of the input: boxes of (8 channels) x (16 columns) x (rows) from a plain
-//     or stride-2 parity view of the NHWC tensor, each with its own column shift; a tap's
+//   * a few "copies" of the input: boxes of (8 channels) x (16 columns) x (rows) from the map or
+//     one of its parity planes, each with its own column shift (every box row is 256
+//     contiguous bytes of the chunk-major layout); a tap's
 //     operand is a copy started `row` rows down (the canonical no-swizzle K-major layout makes
 //     a row shift a plain descriptor offset, so one copy serves the three taps of a column);
 //     out-of-range coordinates fill zeros, which is the convolution's zero padding;
-//   * the bfloat16 weights of all nine taps for those 16 channels (one 3D box per 8 channels);
+//   * the bfloat16 weights of all nine taps for those 16 channels (18 contiguous bulk copies);
 // and one MMA thread issues, per (phase, tap) group and per split (hi, lo), a 128 x N x 16
 // tcgen05.mma into the phase's accumulator.  Mbarrier rings (full / empty) pipeline the stages.
 //
@@ -49,7 +50,8 @@ constexpr int kOneCtaPerSm = 120 * 1024;  // dynamic request that leaves no room
 enum { EPI_HIDDEN = 0, EPI_LAST = 1, EPI_BWD = 2, EPI_POOL = 3 };
 
 struct Copy {
-    int8_t row0, col;  // box start relative to the tile origin (sub-lattice units of the map)
+    int8_t row0, col;  // box start relative to the tile origin (sub-lattice units)
+    int8_t par;        // parity plane of a parity-split map, -1 for a plain map
 };
 struct Group {
     uint8_t phase, copy, row, tap;
@@ -67,22 +69,27 @@ struct ConvArgs {
     Group group[kMaxGroup];
     int mode, osy, osx;
     int8_t opy[4], opx[4];
-    int oH, oW, oC;  // output tensor (NHWC channels, or FP32 planes for the last layer)
+    int oH, oW, oC;  // output tensor (chunk-major pair, or FP32 planes for the last layer)
+    int out_par;     // layout of (out_hi, out_lo)
     __nv_bfloat16* out_hi;
     __nv_bfloat16* out_lo;
+    __nv_bfloat16* out_phi;  // optional parity-split copy of the output
+    __nv_bfloat16* out_plo;
     float* out32;
+    const __nv_bfloat16* wts;  // weights [9][K/8][R][8]
+    int wK8, wR;
     const float* bias;
     int relu;
     const __nv_bfloat16* m_hi;
     const __nv_bfloat16* m_lo;
+    int m_par;
     float* db_part;
     unsigned* err;
     unsigned spin;
 };
 
 struct ConvParams {
-    CUtensorMap amap[2 * kMaxCopy];  // copy j: amap[j] (hi), amap[n_copy + j] (lo)
-    CUtensorMap bmap;
+    CUtensorMap amap[2];  // the input tensor: hi, lo
     ConvArgs a;
 };
 
@@ -96,27 +103,37 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-__device__ __forceinline__ void store_pair16(__nv_bfloat16* hi, __nv_bfloat16* lo, const float* v) {
-    __align__(16) __nv_bfloat16 h[16], l[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) split_bf16(v[j], h[j], l[j]);
-    uint4* dh = reinterpret_cast<uint4*>(hi);
-    uint4* dl = reinterpret_cast<uint4*>(lo);
-    dh[0] = reinterpret_cast<const uint4*>(h)[0];
-    dh[1] = reinterpret_cast<const uint4*>(h)[1];
-    dl[0] = reinterpret_cast<const uint4*>(l)[0];
-    dl[1] = reinterpret_cast<const uint4*>(l)[1];
+// element offset of 8-channel chunk q at pixel (y, x) of image n in the chunk-major layouts
+__device__ __forceinline__ size_t chunk_at(int par, int C8, int H, int W, int n, int y, int x, int q) {
+    if (!par) return ((((size_t)n * C8 + q) * H + y) * W + x) * 8;
+    return (((((size_t)n * C8 + q) * 4 + ((y & 1) << 1) + (x & 1)) * (H >> 1) + (y >> 1)) * (W >> 1) + (x >> 1)) * 8;
 }
 
-// mask[j] = (hi + lo > 0) of 16 channels
-__device__ __forceinline__ void load_mask16(const __nv_bfloat16* hi, const __nv_bfloat16* lo, bool* m) {
-    __align__(16) __nv_bfloat16 h[16], l[16];
-    reinterpret_cast<uint4*>(h)[0] = reinterpret_cast<const uint4*>(hi)[0];
-    reinterpret_cast<uint4*>(h)[1] = reinterpret_cast<const uint4*>(hi)[1];
-    reinterpret_cast<uint4*>(l)[0] = reinterpret_cast<const uint4*>(lo)[0];
-    reinterpret_cast<uint4*>(l)[1] = reinterpret_cast<const uint4*>(lo)[1];
+__device__ __forceinline__ void store_pair8(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t o, const float* v) {
+    __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) m[j] = __bfloat162float(h[j]) + __bfloat162float(l[j]) > 0.0f;
+    for (int j = 0; j < 8; ++j) split_bf16(v[j], h[j], l[j]);
+    *reinterpret_cast<uint4*>(hi + o) = *reinterpret_cast<const uint4*>(h);
+    *reinterpret_cast<uint4*>(lo + o) = *reinterpret_cast<const uint4*>(l);
+}
+
+// m[j] = (hi + lo > 0) of 8 channels
+__device__ __forceinline__ void load_mask8(const __nv_bfloat16* hi, const __nv_bfloat16* lo, size_t o, bool* m) {
+    __align__(16) __nv_bfloat16 h[8], l[8];
+    *reinterpret_cast<uint4*>(h) = *reinterpret_cast<const uint4*>(hi + o);
+    *reinterpret_cast<uint4*>(l) = *reinterpret_cast<const uint4*>(lo + o);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m[j] = __bfloat162float(h[j]) + __bfloat162float(l[j]) > 0.0f;
+}
+
+// 16 channels from ch0 of pixel (y, x) into the output pair (and its parity copy)
+__device__ __forceinline__ void store_out16(const ConvArgs& a, int n, int y, int x, int ch0, const float* v) {
+    const int C8 = a.oC >> 3;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        store_pair8(a.out_hi, a.out_lo, chunk_at(a.out_par, C8, a.oH, a.oW, n, y, x, (ch0 >> 3) + q), v + 8 * q);
+        if (a.out_phi) store_pair8(a.out_phi, a.out_plo, chunk_at(1, C8, a.oH, a.oW, n, y, x, (ch0 >> 3) + q), v + 8 * q);
+    }
 }
 
 __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__ ConvParams p) {
@@ -154,69 +171,82 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
     const uint32_t sbase = smem_u32(smem);
     const unsigned cmask = a.cmask[pg];
 
-    if (threadIdx.x == 0) {
-        // TMA producer
-        uint32_t bytes = 2u * 9u * a.N * 16u;
-        for (int j = 0; j < a.n_copy; ++j)
-            if (cmask >> j & 1) bytes += (uint32_t)(a.split * 2 * a.a_slot);
-        int ks = 0;
-        for (; ks < a.ksteps; ++ks) {
-            const int s = ks % S, use = ks / S;
-            if (use > 0 && !bar_wait(smem_u32(&empty[s]), (use - 1) & 1, a.spin)) {
-                atomicOr(a.err, 1u);
-                abort_flag = 1;
-                break;
-            }
-            if (*(volatile int*)&abort_flag) break;
-            const uint32_t st = sbase + s * a.stage_bytes;
-            const uint32_t fb = smem_u32(&full[s]);
-            bar_expect_tx(fb, bytes);
-            for (int sp = 0; sp < a.split; ++sp)
-                for (int j = 0; j < a.n_copy; ++j) {
-                    if (!(cmask >> j & 1)) continue;
-                    const uint32_t dst = st + (uint32_t)((sp * a.n_copy + j) * 2 * a.a_slot);
-                    const CUtensorMap* m = &p.amap[sp * a.n_copy + j];
-                    const int x = b0 + a.copy[j].col, y = a0 + a.copy[j].row0;
-                    tma_load_4d(dst, m, ks * 16, x, y, n, fb);
-                    tma_load_4d(dst + a.a_slot, m, ks * 16 + 8, x, y, n, fb);
+    if (warp == 0) {
+        // TMA producer: lane 0 issues, the other lanes wait at the warp barrier
+        if (lane == 0) {
+            const int nb = min(a.N, a.wR - o0);   // weight rows present (the rest is never read into D)
+            uint32_t bytes = 18u * (uint32_t)nb * 16u;
+            for (int j = 0; j < a.n_copy; ++j)
+                if (cmask >> j & 1) bytes += (uint32_t)(a.split * 2 * a.a_slot);
+            int ks = 0;
+            for (; ks < a.ksteps; ++ks) {
+                const int s = ks % S, use = ks / S;
+                if (use > 0 && !bar_wait(smem_u32(&empty[s]), (use - 1) & 1, a.spin)) {
+                    atomicOr(a.err, 1u);
+                    abort_flag = 1;
+                    break;
                 }
-            const uint32_t bdst = st + a.a_bytes;
-            tma_load_3d(bdst, &p.bmap, ks * 16, o0, 0, fb);
-            tma_load_3d(bdst + 9 * a.N * 16, &p.bmap, ks * 16 + 8, o0, 0, fb);
-        }
-        issued = ks;
-    } else if (threadIdx.x == 32) {
-        // MMA issuer
-        const uint32_t idesc = idesc_bf16(128, a.N, 0, 0);
-        const int g0 = a.gstart[pg * a.P], g1 = a.gstart[pg * a.P + a.P];
-        unsigned started = 0;
-        int ks = 0;
-        for (; ks < a.ksteps; ++ks) {
-            const int s = ks % S, use = ks / S;
-            if (!bar_wait(smem_u32(&full[s]), use & 1, a.spin)) {
-                atomicOr(a.err, 2u);
-                abort_flag = 1;
-                break;
+                if (*(volatile int*)&abort_flag) break;
+                const uint32_t st = sbase + s * a.stage_bytes;
+                const uint32_t fb = smem_u32(&full[s]);
+                bar_expect_tx(fb, bytes);
+                for (int sp = 0; sp < a.split; ++sp)
+                    for (int j = 0; j < a.n_copy; ++j) {
+                        if (!(cmask >> j & 1)) continue;
+                        const uint32_t dst = st + (uint32_t)((sp * a.n_copy + j) * 2 * a.a_slot);
+                        const Copy cp = a.copy[j];
+                        const int x = (b0 + cp.col) * 8, y = a0 + cp.row0;
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const int chunk = 2 * ks + q;
+                            tma_load_4d(dst + q * a.a_slot, &p.amap[sp], x, y, cp.par < 0 ? chunk : 4 * chunk + cp.par, n, fb);
+                        }
+                    }
+                const uint32_t bdst = st + a.a_bytes;
+                for (int q = 0; q < 2; ++q)
+                    for (int t = 0; t < 9; ++t) {
+                        const __nv_bfloat16* src = a.wts + (((size_t)t * a.wK8 + 2 * ks + q) * a.wR + o0) * 8;
+                        bulk_load(bdst + (uint32_t)((q * 9 + t) * a.N * 16), src, (uint32_t)nb * 16u, fb);
+                    }
             }
-            fence_after();
-            const uint32_t st = sbase + s * a.stage_bytes;
-            const uint64_t bd0 = sdesc(st + a.a_bytes, 9u * a.N * 16u, 128u);
-            for (int g = g0; g < g1; ++g) {
-                const Group gr = a.group[g];
-                const int ph = gr.phase - pg * a.P;
-                const uint64_t bd = bd0 + (uint64_t)((gr.tap * a.N * 16) >> 4);
-                const uint32_t d = tmem + (uint32_t)(ph * a.N);
-                for (int sp = 0; sp < a.split; ++sp) {
-                    const uint32_t aaddr = st + (uint32_t)((sp * a.n_copy + gr.copy) * 2 * a.a_slot + gr.row * 256);
-                    const uint64_t ad = sdesc(aaddr, (uint32_t)a.a_slot, 128u);
-                    mma_bf16(d, ad, bd, idesc, (started >> ph) & 1u);
-                    started |= 1u << ph;
+            issued = ks;
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // MMA issuer: lane 0 issues, the other lanes wait at the warp barrier
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(128, a.N, 0, 0);
+            const int g0 = a.gstart[pg * a.P], g1 = a.gstart[pg * a.P + a.P];
+            unsigned started = 0;
+            int ks = 0;
+            for (; ks < a.ksteps; ++ks) {
+                const int s = ks % S, use = ks / S;
+                if (!bar_wait(smem_u32(&full[s]), use & 1, a.spin)) {
+                    atomicOr(a.err, 2u);
+                    abort_flag = 1;
+                    break;
                 }
+                fence_after();
+                const uint32_t st = sbase + s * a.stage_bytes;
+                const uint64_t bd0 = sdesc(st + a.a_bytes, 9u * a.N * 16u, 128u);
+                for (int g = g0; g < g1; ++g) {
+                    const Group gr = a.group[g];
+                    const int ph = gr.phase - pg * a.P;
+                    const uint64_t bd = bd0 + (uint64_t)((gr.tap * a.N * 16) >> 4);
+                    const uint32_t d = tmem + (uint32_t)(ph * a.N);
+                    for (int sp = 0; sp < a.split; ++sp) {
+                        const uint32_t aaddr = st + (uint32_t)((sp * a.n_copy + gr.copy) * 2 * a.a_slot + gr.row * 256);
+                        const uint64_t ad = sdesc(aaddr, (uint32_t)a.a_slot, 128u);
+                        mma_bf16(d, ad, bd, idesc, (started >> ph) & 1u);
+                        started |= 1u << ph;
+                    }
+                }
+                mma_commit(smem_u32(&empty[s]));
             }
-            mma_commit(smem_u32(&empty[s]));
+            consumed = ks;
+            mma_commit(smem_u32(&done));
         }
-        consumed = ks;
-        mma_commit(smem_u32(&done));
+        __syncwarp();
     }
     const bool ok = bar_wait(smem_u32(&done), 0, a.spin);
     if (!ok && lane == 0) atomicOr(a.err, 4u);
@@ -245,8 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
                         v[j] += a.bias[ch0 + j];
                         if (a.relu) v[j] = fmaxf(v[j], 0.0f);
                     }
-                    const size_t o = (((size_t)n * a.oH + oy) * a.oW + ox) * a.oC + ch0;
-                    store_pair16(a.out_hi + o, a.out_lo + o, v);
+                    store_out16(a, n, oy, ox, ch0, v);
                 } else if (a.mode == EPI_LAST) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
@@ -265,13 +294,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
                         py = (a0 + r) >> 1;
                         px = (b0 + c) >> 1;
                     }
-                    const size_t o = (((size_t)n * a.oH + py) * a.oW + px) * a.oC + ch0;
                     if (writer) {
                         bool m[16];
-                        load_mask16(a.m_hi + o, a.m_lo + o, m);
+#pragma unroll
+                        for (int q = 0; q < 2; ++q)
+                            load_mask8(a.m_hi, a.m_lo, chunk_at(a.m_par, a.oC >> 3, a.oH, a.oW, n, py, px, (ch0 >> 3) + q),
+                                       m + 8 * q);
 #pragma unroll
                         for (int j = 0; j < 16; ++j) v[j] = m[j] ? v[j] : 0.0f;
-                        store_pair16(a.out_hi + o, a.out_lo + o, v);
+                        store_out16(a, n, py, px, ch0, v);
                     } else {
 #pragma unroll
                         for (int j = 0; j < 16; ++j) v[j] = 0.0f;
@@ -314,6 +345,7 @@ struct WgArgs {
     int n_copy, rows, N, c_tiles, Nc, tmem_cols, n_stage;
     int g_slot, x_slot, g_bytes, x_bytes, stage_bytes;
     int n_split;      // gridDim.x
+    int g_parity;     // 1: dy is read from its parity copy, plane = phase
     Copy copy[6];
     uint8_t grp[4][9][2];  // phase, tap -> copy, row offset
     unsigned cmask[4];
@@ -323,8 +355,8 @@ struct WgArgs {
 };
 
 struct WgParams {
-    CUtensorMap gmap[8];   // [split][phase]
-    CUtensorMap xmap[12];  // [split][copy]
+    CUtensorMap gmap[2];  // dy (or its parity copy): hi, lo
+    CUtensorMap xmap[2];  // the layer input: hi, lo
     WgArgs a;
 };
 
@@ -367,78 +399,90 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
     const uint32_t sbase = smem_u32(smem);
     const int my_tiles = split < a.n_tiles ? (a.n_tiles - 1 - split) / a.n_split + 1 : 0;
 
-    if (threadIdx.x == 0) {
-        int it = 0;
-        for (; it < my_tiles; ++it) {
-            const int tile = split + it * a.n_split;
-            const int nimg = tile / (a.phases * per_phase), rem = tile % (a.phases * per_phase);
-            const int ph = rem / per_phase, tt = rem % per_phase;
-            const int a0 = (tt / a.tiles_x) * a.rows_px, b0 = (tt % a.tiles_x) * 16;
-            const int s = it % S, use = it / S;
-            if (use > 0 && !bar_wait(smem_u32(&empty[s]), (use - 1) & 1, a.spin)) {
-                atomicOr(a.err, 8u);
-                abort_flag = 1;
-                break;
-            }
-            if (*(volatile int*)&abort_flag) break;
-            const unsigned cm = a.cmask[ph];
-            uint32_t bytes = (uint32_t)(2 * a.g_real * a.g_slot);
-            for (int j = 0; j < a.n_copy; ++j)
-                if (cm >> j & 1) bytes += (uint32_t)(2 * a.x_real * a.x_slot);
-            const uint32_t st = sbase + s * a.stage_bytes;
-            const uint32_t fb = smem_u32(&full[s]);
-            bar_expect_tx(fb, bytes);
-            for (int sp = 0; sp < 2; ++sp) {
-                const CUtensorMap* gm = &p.gmap[sp * 4 + (a.phases > 1 ? ph : 0)];
-                for (int q = 0; q < a.g_real; ++q)
-                    tma_load_4d(st + (uint32_t)((sp * a.g_real + q) * a.g_slot), gm, o0 + 8 * q, b0, a0, nimg, fb);
-                for (int j = 0; j < a.n_copy; ++j) {
-                    if (!(cm >> j & 1)) continue;
-                    const CUtensorMap* xm = &p.xmap[sp * a.n_copy + j];
-                    const uint32_t xb = st + (uint32_t)(a.g_bytes + ((sp * a.n_copy + j) * a.x_real) * a.x_slot);
-                    for (int q = 0; q < a.x_real; ++q)
-                        tma_load_4d(xb + (uint32_t)(q * a.x_slot), xm, c0 + 8 * q, b0 + a.copy[j].col, a0 + a.copy[j].row0,
-                                    nimg, fb);
+    if (warp == 0) {
+        // TMA producer: lane 0 issues, the other lanes wait at the warp barrier
+        if (lane == 0) {
+            int it = 0;
+            for (; it < my_tiles; ++it) {
+                const int tile = split + it * a.n_split;
+                const int nimg = tile / (a.phases * per_phase), rem = tile % (a.phases * per_phase);
+                const int ph = rem / per_phase, tt = rem % per_phase;
+                const int a0 = (tt / a.tiles_x) * a.rows_px, b0 = (tt % a.tiles_x) * 16;
+                const int s = it % S, use = it / S;
+                if (use > 0 && !bar_wait(smem_u32(&empty[s]), (use - 1) & 1, a.spin)) {
+                    atomicOr(a.err, 8u);
+                    abort_flag = 1;
+                    break;
                 }
-            }
-        }
-        issued = it;
-    } else if (threadIdx.x == 32) {
-        const uint32_t idesc = idesc_bf16(128, a.N, 1, 1);
-        int it = 0;
-        for (; it < my_tiles; ++it) {
-            const int tile = split + it * a.n_split;
-            const int ph = (tile % (a.phases * per_phase)) / per_phase;
-            const int s = it % S, use = it / S;
-            if (!bar_wait(smem_u32(&full[s]), use & 1, a.spin)) {
-                atomicOr(a.err, 16u);
-                abort_flag = 1;
-                break;
-            }
-            fence_after();
-            const uint32_t st = sbase + s * a.stage_bytes;
-            for (int tap = 0; tap < 9; ++tap) {
-                const int cp = a.grp[ph][tap][0], ro = a.grp[ph][tap][1];
-                const uint32_t d = tmem + (uint32_t)(tap * a.N);
-                const uint32_t x0 = st + (uint32_t)(a.g_bytes + cp * a.x_real * a.x_slot + ro * 256);
-                const uint32_t xstride = (uint32_t)(a.n_copy * a.x_real * a.x_slot);  // split 0 -> 1
-                const uint32_t gstride = (uint32_t)(a.g_real * a.g_slot);
-                for (int k = 0; k < a.rows_px; ++k) {
-#pragma unroll
-                    for (int combo = 0; combo < 3; ++combo) {
-                        const int sg = combo == 2 ? 1 : 0, sx = combo == 1 ? 1 : 0;   // hi.hi, hi.lo, lo.hi
-                        const uint64_t gd = sdesc(st + sg * gstride + k * 256, 128u, (uint32_t)a.g_slot);
-                        const uint64_t xd = sdesc(x0 + sx * xstride + k * 256, 128u, (uint32_t)a.x_slot);
-                        const uint32_t acc = (it > 0 || k > 0 || combo > 0) ? 1u : 0u;
-                        if (a.w2) mma_bf16(d, xd, gd, idesc, acc);
-                        else mma_bf16(d, gd, xd, idesc, acc);
+                if (*(volatile int*)&abort_flag) break;
+                const unsigned cm = a.cmask[ph];
+                uint32_t bytes = (uint32_t)(2 * a.g_real * a.g_slot);
+                for (int j = 0; j < a.n_copy; ++j)
+                    if (cm >> j & 1) bytes += (uint32_t)(2 * a.x_real * a.x_slot);
+                const uint32_t st = sbase + s * a.stage_bytes;
+                const uint32_t fb = smem_u32(&full[s]);
+                bar_expect_tx(fb, bytes);
+                for (int sp = 0; sp < 2; ++sp) {
+                    for (int q = 0; q < a.g_real; ++q) {
+                        const int chunk = (o0 >> 3) + q;
+                        tma_load_4d(st + (uint32_t)((sp * a.g_real + q) * a.g_slot), &p.gmap[sp], b0 * 8, a0,
+                                    a.g_parity ? 4 * chunk + ph : chunk, nimg, fb);
+                    }
+                    for (int j = 0; j < a.n_copy; ++j) {
+                        if (!(cm >> j & 1)) continue;
+                        const Copy cp = a.copy[j];
+                        const uint32_t xb = st + (uint32_t)(a.g_bytes + ((sp * a.n_copy + j) * a.x_real) * a.x_slot);
+                        for (int q = 0; q < a.x_real; ++q) {
+                            const int chunk = (c0 >> 3) + q;
+                            tma_load_4d(xb + (uint32_t)(q * a.x_slot), &p.xmap[sp], (b0 + cp.col) * 8, a0 + cp.row0,
+                                        cp.par < 0 ? chunk : 4 * chunk + cp.par, nimg, fb);
+                        }
                     }
                 }
             }
-            mma_commit(smem_u32(&empty[s]));
+            issued = it;
         }
-        consumed = it;
-        mma_commit(smem_u32(&done));
+        __syncwarp();
+    } else if (warp == 1) {
+        // MMA issuer: lane 0 issues, the other lanes wait at the warp barrier
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(128, a.N, 1, 1);
+            int it = 0;
+            for (; it < my_tiles; ++it) {
+                const int tile = split + it * a.n_split;
+                const int ph = (tile % (a.phases * per_phase)) / per_phase;
+                const int s = it % S, use = it / S;
+                if (!bar_wait(smem_u32(&full[s]), use & 1, a.spin)) {
+                    atomicOr(a.err, 16u);
+                    abort_flag = 1;
+                    break;
+                }
+                fence_after();
+                const uint32_t st = sbase + s * a.stage_bytes;
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int cp = a.grp[ph][tap][0], ro = a.grp[ph][tap][1];
+                    const uint32_t d = tmem + (uint32_t)(tap * a.N);
+                    const uint32_t x0 = st + (uint32_t)(a.g_bytes + cp * a.x_real * a.x_slot + ro * 256);
+                    const uint32_t xstride = (uint32_t)(a.n_copy * a.x_real * a.x_slot);  // split 0 -> 1
+                    const uint32_t gstride = (uint32_t)(a.g_real * a.g_slot);
+                    for (int k = 0; k < a.rows_px; ++k) {
+    #pragma unroll
+                        for (int combo = 0; combo < 3; ++combo) {
+                            const int sg = combo == 2 ? 1 : 0, sx = combo == 1 ? 1 : 0;   // hi.hi, hi.lo, lo.hi
+                            const uint64_t gd = sdesc(st + sg * gstride + k * 256, 128u, (uint32_t)a.g_slot);
+                            const uint64_t xd = sdesc(x0 + sx * xstride + k * 256, 128u, (uint32_t)a.x_slot);
+                            const uint32_t acc = (it > 0 || k > 0 || combo > 0) ? 1u : 0u;
+                            if (a.w2) mma_bf16(d, xd, gd, idesc, acc);
+                            else mma_bf16(d, gd, xd, idesc, acc);
+                        }
+                    }
+                }
+                mma_commit(smem_u32(&empty[s]));
+            }
+            consumed = it;
+            mma_commit(smem_u32(&done));
+        }
+        __syncwarp();
     }
     const bool ok = bar_wait(smem_u32(&done), 0, a.spin);
     if (!ok && lane == 0) atomicOr(a.err, 32u);
@@ -490,70 +534,89 @@ __global__ void k_wgrad_reduce(const float* __restrict__ part, int Co, int Ci, i
     }
 }
 
-__global__ void k_bias_reduce(const float* __restrict__ part, int n_part, int C, float* __restrict__ db) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
-        float s = 0.0f;
-        for (int q = 0; q < n_part; ++q) s += part[(size_t)q * C + c];
-        db[c] = s;
+// bias gradient: slice sums of the partial rows (32 channels x 8 rows of parts per block),
+// then the slices in order; both steps in a fixed order
+__global__ void __launch_bounds__(256) k_bias_slices(const float* __restrict__ part, int n_part, int C, int per_slice,
+                                                     float* __restrict__ tmp) {
+    const int tx = threadIdx.x & 31, r = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + tx;
+    const int q0 = blockIdx.y * per_slice, q1 = min(n_part, q0 + per_slice);
+    float s = 0.0f;
+    if (c < C)
+        for (int q = q0 + r; q < q1; q += 8) s += part[(size_t)q * C + c];
+    __shared__ float red[8][32];
+    red[r][tx] = s;
+    __syncthreads();
+    if (r == 0 && c < C) {
+        float t = 0.0f;
+        for (int k = 0; k < 8; ++k) t += red[k][tx];
+        tmp[(size_t)blockIdx.y * C + c] = t;
     }
 }
 
+__global__ void k_bias_final(const float* __restrict__ tmp, int slices, int C, float* __restrict__ db) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float s = 0.0f;
+    for (int q = 0; q < slices; ++q) s += tmp[(size_t)q * C + c];
+    db[c] = s;
+}
+
+// wf[t][c/8][o][c%8] = w[o][c][t] (c < Ci_pad), wb[t][o/8][c][o%8] = w[o][c][t] (o < Co_pad)
 __global__ void k_weights_tc(const float* __restrict__ w, int Co, int Ci, int Ci_pad, int Co_pad,
                              __nv_bfloat16* __restrict__ wf, __nv_bfloat16* __restrict__ wb) {
     const int total = 9 * Co * Ci_pad + 9 * Ci * Co_pad;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         if (i < 9 * Co * Ci_pad) {
-            const int c = i % Ci_pad, o = (i / Ci_pad) % Co, t = i / (Ci_pad * Co);
+            const int e = i & 7, r = i >> 3, o = r % Co, q = (r / Co) % (Ci_pad >> 3), t = r / Co / (Ci_pad >> 3);
+            const int c = 8 * q + e;
             wf[i] = __float2bfloat16_rn(c < Ci ? w[((size_t)o * Ci + c) * 9 + t] : 0.0f);
         } else {
             const int j = i - 9 * Co * Ci_pad;
-            const int o = j % Co_pad, c = (j / Co_pad) % Ci, t = j / (Co_pad * Ci);
+            const int e = j & 7, r = j >> 3, c = r % Ci, q = (r / Ci) % (Co_pad >> 3), t = r / Ci / (Co_pad >> 3);
+            const int o = 8 * q + e;
             wb[j] = __float2bfloat16_rn(o < Co ? w[((size_t)o * Ci + c) * 9 + t] : 0.0f);
         }
     }
 }
 
-__global__ void k_pack_input(const float* __restrict__ X, int N, int HW, __nv_bfloat16* __restrict__ hi,
+__global__ void k_pack_input(const float* __restrict__ X, int N, int H, int W, int par, __nv_bfloat16* __restrict__ hi,
                              __nv_bfloat16* __restrict__ lo) {
-    const long total = (long)N * HW;
+    const long HW = (long)H * W, total = (long)N * HW;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-        const long n = i / HW, p = i % HW;
-        __align__(16) __nv_bfloat16 h[8], l[8];
+        const int n = (int)(i / HW), y = (int)((i % HW) / W), x = (int)(i % W);
+        float v[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float v = j < 2 ? X[(n * 2 + j) * HW + p] : 0.0f;
-            split_bf16(v, h[j], l[j]);
-        }
-        reinterpret_cast<uint4*>(hi)[i] = *reinterpret_cast<const uint4*>(h);
-        reinterpret_cast<uint4*>(lo)[i] = *reinterpret_cast<const uint4*>(l);
+        for (int j = 0; j < 8; ++j) v[j] = j < 2 ? X[((size_t)n * 2 + j) * HW + (i % HW)] : 0.0f;
+        store_pair8(hi, lo, chunk_at(par, 1, H, W, n, y, x, 0), v);
     }
 }
 
 __global__ void __launch_bounds__(256) k_mse_tc(const float* __restrict__ out, const float* __restrict__ t,
-                                                const float* __restrict__ mask, int N, int HW, float inv_terms,
+                                                const float* __restrict__ mask, int N, int H, int W, float inv_terms,
                                                 __nv_bfloat16* __restrict__ ghi, __nv_bfloat16* __restrict__ glo,
+                                                __nv_bfloat16* __restrict__ gphi, __nv_bfloat16* __restrict__ gplo,
                                                 float* __restrict__ db_part, double* loss) {
     double acc = 0.0;
     float d0 = 0.0f, d1 = 0.0f;
-    const long total = (long)N * HW;
+    const long HW = (long)H * W, total = (long)N * HW;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-        const long n = i / HW, p = i % HW;
+        const int n = (int)(i / HW), p = (int)(i % HW), y = p / W, x = p % W;
         const float mk = mask[p];
-        __align__(16) __nv_bfloat16 h[8], l[8];
-        float g[2];
+        float g[8];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            const long k = (n * 2 + c) * HW + p;
+            const long k = ((long)n * 2 + c) * HW + p;
             const float d = (out[k] - t[k]) * mk;
             acc += (double)d * d;
             g[c] = 2.0f * d * inv_terms;
         }
+#pragma unroll
+        for (int c = 2; c < 8; ++c) g[c] = 0.0f;
         d0 += g[0];
         d1 += g[1];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) split_bf16(j < 2 ? g[j] : 0.0f, h[j], l[j]);
-        reinterpret_cast<uint4*>(ghi)[i] = *reinterpret_cast<const uint4*>(h);
-        reinterpret_cast<uint4*>(glo)[i] = *reinterpret_cast<const uint4*>(l);
+        store_pair8(ghi, glo, chunk_at(0, 1, H, W, n, y, x, 0), g);
+        if (gphi) store_pair8(gphi, gplo, chunk_at(1, 1, H, W, n, y, x, 0), g);
     }
     __shared__ double rl[8];
     __shared__ float r0[8], r1[8];
@@ -593,41 +656,15 @@ EncodeTiledFn g_encode = nullptr;
 bool g_ready = false;
 int g_conv_dyn = 0, g_wg_dyn = 0;   // dynamic shared memory the two kernels may request
 
-// view of an NHWC pair tensor: plain, or the parity class (qy, qx) of a stride-2 lattice
-bool enc_act(CUtensorMap* m, const __nv_bfloat16* base, const Act2& t, bool parity, int qy, int qx, int rows) {
+// map of one half (hi or lo) of a chunk-major tensor; box = 16 pixels x 8 channels x `rows`
+// rows of one chunk (one parity plane of a parity-split tensor: chunk coordinate 4 q + plane)
+bool enc_act(CUtensorMap* m, const __nv_bfloat16* base, const Act2& t, bool parity, int rows) {
     const size_t es = sizeof(__nv_bfloat16);
-    cuuint64_t dims[4], strides[3];
-    const __nv_bfloat16* b = base;
-    if (parity) {
-        b = base + ((size_t)qy * t.W + qx) * t.C;
-        dims[0] = t.C;
-        dims[1] = t.W / 2;
-        dims[2] = t.H / 2;
-        dims[3] = t.N;
-        strides[0] = 2 * t.C * es;
-        strides[1] = 2 * (size_t)t.W * t.C * es;
-    } else {
-        dims[0] = t.C;
-        dims[1] = t.W;
-        dims[2] = t.H;
-        dims[3] = t.N;
-        strides[0] = t.C * es;
-        strides[1] = (size_t)t.W * t.C * es;
-    }
-    strides[2] = (size_t)t.H * t.W * t.C * es;
-    cuuint32_t box[4] = {8, 16, (cuuint32_t)rows, 1}, estr[4] = {1, 1, 1, 1};
-    return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(b), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// weights [9][R][K] bfloat16, box (8, N, 9)
-bool enc_w(CUtensorMap* m, const __nv_bfloat16* w, int K, int R, int N) {
-    const size_t es = sizeof(__nv_bfloat16);
-    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)R, 9};
-    cuuint64_t strides[2] = {(cuuint64_t)K * es, (cuuint64_t)R * K * es};
-    cuuint32_t box[3] = {8, (cuuint32_t)N, 9}, estr[3] = {1, 1, 1};
-    return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(w), dims, strides, box, estr,
+    const int C8 = t.C / 8, H = parity ? t.H / 2 : t.H, W = parity ? t.W / 2 : t.W, planes = parity ? 4 : 1;
+    cuuint64_t dims[4] = {(cuuint64_t)W * 8, (cuuint64_t)H, (cuuint64_t)C8 * planes, (cuuint64_t)t.N};
+    cuuint64_t strides[3] = {(cuuint64_t)W * 8 * es, (cuuint64_t)H * W * 8 * es, (cuuint64_t)C8 * planes * H * W * 8 * es};
+    cuuint32_t box[4] = {128, (cuuint32_t)rows, 1, 1}, estr[4] = {1, 1, 1, 1};
+    return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -741,6 +778,8 @@ cudaError_t tc_conv_forward(const TcLayer& L, const Act2& x, const __nv_bfloat16
     a.split = 2;
     a.ksteps = L.Ci_pad / 16;
     if (!L.up) {
+        // the input is read by parity planes: it must be stored split by parity
+        if (!x.par) return cudaErrorInvalidValue;
         phases = 1;
         a.tiles_y = Ho / 8;
         a.tiles_x = Ho / 16;
@@ -748,13 +787,7 @@ cudaError_t tc_conv_forward(const TcLayer& L, const Act2& x, const __nv_bfloat16
         a.n_copy = 6;
         const int qx[3] = {0, 1, 1}, dx[3] = {0, -1, 0};
         for (int qy = 0; qy < 2; ++qy)
-            for (int var = 0; var < 3; ++var) {
-                const int j = qy * 3 + var;
-                a.copy[j] = Copy{-1, (int8_t)dx[var]};
-                if (!enc_act(&pl.prm.amap[j], x.hi, x, true, qy, qx[var], a.rows) ||
-                    !enc_act(&pl.prm.amap[a.n_copy + j], x.lo, x, true, qy, qx[var], a.rows))
-                    return cudaErrorInvalidValue;
-            }
+            for (int var = 0; var < 3; ++var) a.copy[qy * 3 + var] = Copy{-1, (int8_t)dx[var], (int8_t)(2 * qy + qx[var])};
         for (int u = 0; u < 3; ++u)
             for (int v = 0; v < 3; ++v) {
                 const int qy = u == 1 ? 0 : 1, dy = u == 0 ? -1 : 0, var = v == 1 ? 0 : (v == 0 ? 1 : 2);
@@ -765,14 +798,10 @@ cudaError_t tc_conv_forward(const TcLayer& L, const Act2& x, const __nv_bfloat16
         phases = 4;
         a.tiles_y = L.Hin / 8;
         a.tiles_x = L.Hin / 16;
+        if (x.par) return cudaErrorInvalidValue;
         a.rows = 10;
         a.n_copy = 3;
-        for (int j = 0; j < 3; ++j) {
-            a.copy[j] = Copy{-1, (int8_t)(j - 1)};
-            if (!enc_act(&pl.prm.amap[j], x.hi, x, false, 0, 0, a.rows) ||
-                !enc_act(&pl.prm.amap[3 + j], x.lo, x, false, 0, 0, a.rows))
-                return cudaErrorInvalidValue;
-        }
+        for (int j = 0; j < 3; ++j) a.copy[j] = Copy{-1, (int8_t)(j - 1), -1};
         for (int py = 0; py < 2; ++py)
             for (int px = 0; px < 2; ++px)
                 for (int u = 0; u < 3; ++u)
@@ -789,13 +818,20 @@ cudaError_t tc_conv_forward(const TcLayer& L, const Act2& x, const __nv_bfloat16
     const bool last = y == nullptr;
     const int Ntot = (L.Co + 15) / 16 * 16;
     if ((e = finish_plan(pl, x.N, num_sms, phases, Ntot)) != cudaSuccess) return e;
-    if (!enc_w(&pl.prm.bmap, wf, L.Ci_pad, L.Co, a.N)) return cudaErrorInvalidValue;
+    if (!enc_act(&pl.prm.amap[0], x.hi, x, x.par != 0, a.rows) || !enc_act(&pl.prm.amap[1], x.lo, x, x.par != 0, a.rows))
+        return cudaErrorInvalidValue;
+    a.wts = wf;
+    a.wK8 = L.Ci_pad / 8;
+    a.wR = L.Co;
     a.mode = last ? EPI_LAST : EPI_HIDDEN;
     a.oH = Ho;
     a.oW = Ho;
     a.oC = L.Co;
+    a.out_par = last ? 0 : y->par;
     a.out_hi = last ? nullptr : y->hi;
     a.out_lo = last ? nullptr : y->lo;
+    a.out_phi = last ? nullptr : y->phi;
+    a.out_plo = last ? nullptr : y->plo;
     a.out32 = y32;
     a.bias = bias;
     a.relu = L.relu;
@@ -832,12 +868,7 @@ cudaError_t tc_conv_backward_data(const TcLayer& L, const Act2& dy, const __nv_b
         a.tiles_x = Sd / 16;
         a.rows = 9;
         a.n_copy = 2;
-        for (int j = 0; j < 2; ++j) {
-            a.copy[j] = Copy{0, (int8_t)j};
-            if (!enc_act(&pl.prm.amap[j], dy.hi, dy, false, 0, 0, a.rows) ||
-                !enc_act(&pl.prm.amap[2 + j], dy.lo, dy, false, 0, 0, a.rows))
-                return cudaErrorInvalidValue;
-        }
+        for (int j = 0; j < 2; ++j) a.copy[j] = Copy{0, (int8_t)j, -1};
         for (int qy = 0; qy < 2; ++qy)
             for (int qx = 0; qx < 2; ++qx)
                 for (int u = 0; u < 3; ++u)
@@ -860,25 +891,29 @@ cudaError_t tc_conv_backward_data(const TcLayer& L, const Act2& dy, const __nv_b
         a.tiles_x = Sd / 16;
         a.rows = 10;
         a.n_copy = 3;
-        for (int j = 0; j < 3; ++j) {
-            a.copy[j] = Copy{-1, (int8_t)(j - 1)};
-            if (!enc_act(&pl.prm.amap[j], dy.hi, dy, false, 0, 0, a.rows) ||
-                !enc_act(&pl.prm.amap[3 + j], dy.lo, dy, false, 0, 0, a.rows))
-                return cudaErrorInvalidValue;
-        }
+        for (int j = 0; j < 3; ++j) a.copy[j] = Copy{-1, (int8_t)(j - 1), -1};
         for (int u = 0; u < 3; ++u)
             for (int v = 0; v < 3; ++v) g[ng++] = Group{0, (uint8_t)(2 - v), (uint8_t)(2 - u), (uint8_t)(3 * u + v)};
         a.osy = a.osx = 1;
         a.mode = EPI_POOL;
     }
     sort_groups(a, g, ng, phases);
+    if (dy.par) return cudaErrorInvalidValue;   // both forms read dy by plain rows
     if ((e = finish_plan(pl, dy.N, num_sms, phases, L.Ci)) != cudaSuccess) return e;
-    if (!enc_w(&pl.prm.bmap, wb, L.Co_pad, L.Ci, a.N)) return cudaErrorInvalidValue;
+    if (!enc_act(&pl.prm.amap[0], dy.hi, dy, false, a.rows) || !enc_act(&pl.prm.amap[1], dy.lo, dy, false, a.rows))
+        return cudaErrorInvalidValue;
+    a.wts = wb;
+    a.wK8 = L.Co_pad / 8;
+    a.wR = L.Ci;
     a.oH = L.Hin;
     a.oW = L.Hin;
     a.oC = L.Ci;
+    a.out_par = dx.par;
     a.out_hi = dx.hi;
     a.out_lo = dx.lo;
+    a.out_phi = dx.phi;
+    a.out_plo = dx.plo;
+    a.m_par = act.par;
     a.m_hi = act.hi;
     a.m_lo = act.lo;
     a.db_part = db_part;
@@ -941,12 +976,13 @@ cudaError_t plan_wgrad(WgPlan& pl, const TcLayer& L, const Act2* x, const Act2* 
     a.n_tiles = n_img * a.phases * a.tiles_x * a.tiles_y;
     a.n_split = std::max(1, std::min(a.n_tiles, num_sms / kinds));
     for (int j = 0; j < a.n_copy; ++j) {
-        if (L.up) a.copy[j] = Copy{-1, (int8_t)(j - 1)};
+        if (L.up) a.copy[j] = Copy{-1, (int8_t)(j - 1), -1};
         else {
-            const int dxv[3] = {0, -1, 0};
-            a.copy[j] = Copy{-1, (int8_t)dxv[j % 3]};
+            const int dxv[3] = {0, -1, 0}, qxv[3] = {0, 1, 1};
+            a.copy[j] = Copy{-1, (int8_t)dxv[j % 3], (int8_t)(2 * (j / 3) + qxv[j % 3])};
         }
     }
+    a.g_parity = L.up ? 1 : 0;
     for (int ph = 0; ph < a.phases; ++ph) {
         unsigned m = 0;
         for (int u = 0; u < 3; ++u)
@@ -967,19 +1003,14 @@ cudaError_t plan_wgrad(WgPlan& pl, const TcLayer& L, const Act2* x, const Act2* 
         a.cmask[ph] = m;
     }
     if (x && dy) {
-        const int qxv[3] = {0, 1, 1};
-        for (int sp = 0; sp < 2; ++sp) {
-            const __nv_bfloat16* gb = sp ? dy->lo : dy->hi;
-            const __nv_bfloat16* xb = sp ? x->lo : x->hi;
-            for (int ph = 0; ph < a.phases; ++ph)
-                if (!enc_act(&pl.prm.gmap[sp * 4 + ph], gb, *dy, L.up != 0, ph >> 1, ph & 1, a.rows_px))
-                    return cudaErrorInvalidValue;
-            for (int j = 0; j < a.n_copy; ++j) {
-                const bool ok = L.up ? enc_act(&pl.prm.xmap[sp * a.n_copy + j], xb, *x, false, 0, 0, a.rows)
-                                     : enc_act(&pl.prm.xmap[sp * a.n_copy + j], xb, *x, true, j / 3, qxv[j % 3], a.rows);
-                if (!ok) return cudaErrorInvalidValue;
-            }
-        }
+        // up layers read dy by parity planes (its parity copy), stride-2 layers by plain rows;
+        // the input x of a stride-2 layer is read by parity planes, of an up layer by plain rows
+        if (L.up ? (!dy->phi || x->par) : (dy->par || !x->par)) return cudaErrorInvalidValue;
+        const __nv_bfloat16* ghi = L.up ? dy->phi : dy->hi;
+        const __nv_bfloat16* glo = L.up ? dy->plo : dy->lo;
+        if (!enc_act(&pl.prm.gmap[0], ghi, *dy, L.up != 0, a.rows_px) || !enc_act(&pl.prm.gmap[1], glo, *dy, L.up != 0, a.rows_px) ||
+            !enc_act(&pl.prm.xmap[0], x->hi, *x, x->par != 0, a.rows) || !enc_act(&pl.prm.xmap[1], x->lo, *x, x->par != 0, a.rows))
+            return cudaErrorInvalidValue;
     }
     pl.grid = dim3(a.n_split, kinds, 1);
     pl.smem = a.n_stage * a.stage_bytes + 16 * std::max(a.g_slot, a.x_slot) + 1024;
@@ -1015,8 +1046,11 @@ cudaError_t tc_conv_wgrad(const TcLayer& L, const Act2& x, const Act2& dy, float
     return cudaGetLastError();
 }
 
-cudaError_t tc_bias_reduce(const float* part, int n_part, int C, float* db, cudaStream_t st) {
-    k_bias_reduce<<<(C + 127) / 128, 128, 0, st>>>(part, n_part, C, db);
+cudaError_t tc_bias_reduce(const float* part, int n_part, int C, float* tmp, float* db, cudaStream_t st) {
+    if (n_part < 1 || C < 1) return cudaErrorInvalidValue;
+    const int slices = std::min(kBiasSlices, n_part), per = (n_part + slices - 1) / slices;
+    k_bias_slices<<<dim3((C + 31) / 32, slices), 256, 0, st>>>(part, n_part, C, per, tmp);
+    k_bias_final<<<(C + 127) / 128, 128, 0, st>>>(tmp, slices, C, db);
     return cudaGetLastError();
 }
 
@@ -1029,13 +1063,15 @@ cudaError_t tc_weights(const TcLayer& L, const float* w32, __nv_bfloat16* wf, __
 
 cudaError_t tc_pack_input(const float* X, const Act2& x0, cudaStream_t st) {
     const long total = (long)x0.N * x0.H * x0.W;
-    k_pack_input<<<(int)std::min<long>(2048, (total + 255) / 256), 256, 0, st>>>(X, x0.N, x0.H * x0.W, x0.hi, x0.lo);
+    k_pack_input<<<(int)std::min<long>(2048, (total + 255) / 256), 256, 0, st>>>(X, x0.N, x0.H, x0.W, x0.par, x0.hi, x0.lo);
     return cudaGetLastError();
 }
 
 cudaError_t tc_mse(const float* out, const float* t, const float* mask, const Act2& g, double n_terms, float* db_part,
                    int* n_part, double* loss, cudaStream_t st) {
-    k_mse_tc<<<kMseBlocks, 256, 0, st>>>(out, t, mask, g.N, g.H * g.W, (float)(1.0 / n_terms), g.hi, g.lo, db_part, loss);
+    if (g.par) return cudaErrorInvalidValue;
+    k_mse_tc<<<kMseBlocks, 256, 0, st>>>(out, t, mask, g.N, g.H, g.W, (float)(1.0 / n_terms), g.hi, g.lo, g.phi, g.plo,
+                                         db_part, loss);
     *n_part = kMseBlocks;
     return cudaGetLastError();
 }

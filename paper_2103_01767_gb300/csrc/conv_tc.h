@@ -1,13 +1,20 @@
 // conv_tc.h -- tensor-core 3x3 convolutions of the learned initialisation (tcgen05 MMA with
 // BF16 operands and FP32 accumulation in TMEM, operands staged by TMA tiled loads).
 //
-// Feature maps live in HBM as NHWC pairs of bfloat16 tensors (hi, lo) with x = hi + lo,
+// Feature maps live in HBM as pairs of bfloat16 tensors (hi, lo) with x = hi + lo,
 // hi = bf16(x), lo = bf16(x - hi): the pair carries an FP32 activation to 2^-18 relative
 // (two MMAs per product against BF16 weights), so the network computes with BF16 weights and
 // FP32-accurate activations.  Weight gradients take the three products hi.hi + hi.lo + lo.hi.
 //
-// Weight copies (bfloat16) are tap-major: forward wf[9][Co][Ci_pad], input gradient
-// wb[9][Ci][Co_pad] (wb[t][c][o] = w[o][c][t]), channels zero-padded to multiples of 16.
+// Layout: channel-chunk major, [N][C/8][H][W][8] ("plain"), or split by pixel parity,
+// [N][C/8][2][2][H/2][W/2][8] ("parity"), so that 16 neighbouring pixels of one 8-channel chunk
+// (of the map or of one of its stride-2 sub-lattices) are 256 contiguous bytes: the row of a
+// TMA box.  A tensor may carry a second, parity-split copy (phi, plo) for the kernels that
+// read its stride-2 sub-lattices.
+//
+// Weight copies (bfloat16) are tap- and chunk-major: forward wf[9][Ci_pad/8][Co][8], input
+// gradient wb[9][Co_pad/8][Ci][8] (wb[t][o/8][c][o%8] = w[o][c][t]), channels zero-padded to
+// multiples of 16.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -20,6 +27,9 @@ struct Act2 {
     __nv_bfloat16* hi;
     __nv_bfloat16* lo;
     int N, H, W, C;  // batch, height, width, stored channels (multiple of 8)
+    int par;         // layout of (hi, lo): 0 plain, 1 parity
+    __nv_bfloat16* phi = nullptr;  // optional parity-split copy
+    __nv_bfloat16* plo = nullptr;
 };
 
 struct TcLayer {
@@ -53,14 +63,16 @@ cudaError_t tc_conv_wgrad(const TcLayer& L, const Act2& x, const Act2& dy, float
                           unsigned spin, int num_sms, cudaStream_t st);
 size_t tc_wgrad_workspace(const TcLayer& L, int N, int num_sms);
 
-// db[c] = sum_i part[i][c] (fixed order)
-cudaError_t tc_bias_reduce(const float* part, int n_part, int C, float* db, cudaStream_t st);
+// db[c] = sum_i part[i][c] in a fixed order; tmp: kBiasSlices * C floats
+constexpr int kBiasSlices = 64;
+cudaError_t tc_bias_reduce(const float* part, int n_part, int C, float* tmp, float* db, cudaStream_t st);
 // wf / wb from the FP32 master weights w[Co][Ci][3][3]
 cudaError_t tc_weights(const TcLayer& L, const float* w32, __nv_bfloat16* wf, __nv_bfloat16* wb, cudaStream_t st);
-// pair x0 (C = 8, channels 2..7 zero) from FP32 planes X[N][2][H][W]
+// pair x0 (C = 8, channels 2..7 zero, layout x0.par) from FP32 planes X[N][2][H][W]
 cudaError_t tc_pack_input(const float* X, const Act2& x0, cudaStream_t st);
 // loss += sum mask (out - t)^2 / n_terms (FP64); g = 2 mask (out - t) / n_terms as the pair
-// g (C = 8, channels 2..7 zero) and db_part[i][2] partial sums of g (FP32).
+// g (C = 8, channels 2..7 zero; plain, plus the parity copy when g.phi is set) and
+// db_part[i][2] partial sums of g (FP32).
 cudaError_t tc_mse(const float* out, const float* t, const float* mask, const Act2& g, double n_terms, float* db_part,
                    int* n_part, double* loss, cudaStream_t st);
 constexpr int kMseBlocks = 256;

@@ -77,9 +77,10 @@ struct ptylm_net {
     float* target = nullptr;           // [max_batch][2][m][m]
     float* out = nullptr;              // network output [max_batch][2][m][m]
     Act2 x0{};                         // packed input pair, 8 channels
-    Act2 act[NL - 1] = {};             // hidden layer outputs (NHWC pairs)
+    Act2 act[NL - 1] = {};             // hidden layer outputs (chunk-major pairs)
     Act2 g[NL] = {};                   // gradient w.r.t. each layer's output (g[NL-1]: 8 channels)
     float* db_part = nullptr;          // partial sums of the bias gradients
+    float* db_tmp = nullptr;           // their slice sums (kBiasSlices x 256)
     float* ws = nullptr;               // weight-gradient partial sums
     unsigned* err = nullptr;           // bounded-wait failures of the convolution kernels
     float* mask = nullptr;             // [m][m] probe support
@@ -108,12 +109,15 @@ ptylm_status nalloc_t(ptylm_net* n, T** p, size_t count) {
     *p = static_cast<T*>(q);
     return s;
 }
-ptylm_status nalloc_act(ptylm_net* n, Act2* a, int H, int C) {
-    *a = Act2{nullptr, nullptr, n->max_batch, H, H, C};
+// pair tensor of max_batch maps H x H x C in layout `par`, with a parity-split copy if asked
+ptylm_status nalloc_act(ptylm_net* n, Act2* a, int H, int C, int par, bool parity_copy) {
+    *a = Act2{nullptr, nullptr, n->max_batch, H, H, C, par};
     const size_t count = (size_t)n->max_batch * H * H * C;
     ptylm_status s;
-    if ((s = nalloc_t(n, &a->hi, count)) != PTYLM_OK) return s;
-    return nalloc_t(n, &a->lo, count);
+    if ((s = nalloc_t(n, &a->hi, count)) != PTYLM_OK || (s = nalloc_t(n, &a->lo, count)) != PTYLM_OK) return s;
+    if (parity_copy && ((s = nalloc_t(n, &a->phi, count)) != PTYLM_OK || (s = nalloc_t(n, &a->plo, count)) != PTYLM_OK))
+        return s;
+    return PTYLM_OK;
 }
 Act2 batch(Act2 a, int N) {
     a.N = N;
@@ -155,7 +159,7 @@ ptylm_status loss_grad(ptylm_net* n, const float* X, const float* T, int N, doub
     LSTATUS_TRY(forward(n, X, N));
     int parts = 0;
     LCUDA_TRY(tc_mse(n->out, T, n->mask, batch(n->g[NL - 1], N), n_terms, n->db_part, &parts, loss_dev, n->stream));
-    LCUDA_TRY(tc_bias_reduce(n->db_part, parts, n->L[NL - 1].Co, n->grads + n->b_off[NL - 1], n->stream));
+    LCUDA_TRY(tc_bias_reduce(n->db_part, parts, n->L[NL - 1].Co, n->db_tmp, n->grads + n->b_off[NL - 1], n->stream));
     for (int l = NL - 1; l >= 0; --l) {
         const Act2 in = l == 0 ? batch(n->x0, N) : batch(n->act[l - 1], N);
         const Act2 g = batch(n->g[l], N);
@@ -163,7 +167,7 @@ ptylm_status loss_grad(ptylm_net* n, const float* X, const float* T, int N, doub
         if (l > 0) {
             LCUDA_TRY(tc_conv_backward_data(n->L[l], g, n->wb[l], in, batch(n->g[l - 1], N), n->db_part, &parts, n->err,
                                             kConvSpin, n->num_sms, n->stream));
-            LCUDA_TRY(tc_bias_reduce(n->db_part, parts, n->L[l].Ci, n->grads + n->b_off[l - 1], n->stream));
+            LCUDA_TRY(tc_bias_reduce(n->db_part, parts, n->L[l].Ci, n->db_tmp, n->grads + n->b_off[l - 1], n->stream));
         }
     }
     return PTYLM_OK;
@@ -244,17 +248,20 @@ ptylm_status ptylm_net_create(ptylm_net** out, int m, const int* widths, int max
     }
     if ((s = nalloc_t(n, &n->params, off)) || (s = nalloc_t(n, &n->grads, off)) || (s = nalloc_t(n, &n->adam_m, off)) ||
         (s = nalloc_t(n, &n->adam_v, off)) || (s = nalloc_t(n, &n->xin, img)) || (s = nalloc_t(n, &n->target, img)) ||
-        (s = nalloc_t(n, &n->out, img)) || (s = nalloc_t(n, &n->db_part, parts)) || (s = nalloc_t(n, &n->ws, ws)) ||
+        (s = nalloc_t(n, &n->out, img)) || (s = nalloc_t(n, &n->db_part, parts)) || (s = nalloc_t(n, &n->db_tmp, (size_t)kBiasSlices * 256)) || (s = nalloc_t(n, &n->ws, ws)) ||
         (s = nalloc_t(n, &n->err, 1)) || (s = nalloc_t(n, &n->mask, (size_t)m * m)) || (s = nalloc_t(n, &n->loss, 1)) ||
         (s = nalloc_t(n, &n->tw, m)) || (s = nalloc_t(n, &n->u, (size_t)m * m)) || (s = nalloc_t(n, &n->P, (size_t)m * m)) ||
-        (s = nalloc_act(n, &n->x0, m, 8)) || (s = nalloc_act(n, &n->g[NL - 1], m, 8)))
+        (s = nalloc_act(n, &n->x0, m, 8, 1, false)) || (s = nalloc_act(n, &n->g[NL - 1], m, 8, 0, true)))
         return bail(s);
     for (int l = 0; l < NL; ++l) {
         if ((s = nalloc_t(n, &n->wf[l], (size_t)9 * co[l] * n->L[l].Ci_pad)) ||
             (s = nalloc_t(n, &n->wb[l], (size_t)9 * ci[l] * n->L[l].Co_pad)))
             return bail(s);
-        if (l < NL - 1 &&
-            ((s = nalloc_act(n, &n->act[l], n->L[l].Hout(), co[l])) || (s = nalloc_act(n, &n->g[l], n->L[l].Hout(), co[l]))))
+        // the input of a stride-2 layer is stored split by parity; the output gradient of an
+        // upsampling layer also gets a parity-split copy (its weight gradient reads the four
+        // output phases)
+        if (l < NL - 1 && ((s = nalloc_act(n, &n->act[l], n->L[l].Hout(), co[l], n->L[l + 1].up ? 0 : 1, false)) ||
+                           (s = nalloc_act(n, &n->g[l], n->L[l].Hout(), co[l], 0, n->L[l].up != 0))))
             return bail(s);
     }
     if (cudaMemset(n->err, 0, sizeof(unsigned)) != cudaSuccess) {

@@ -1,6 +1,6 @@
 // tc_common.cuh -- inline-PTX building blocks of the tensor-core convolutions: mbarriers with
-// bounded waits, TMA tiled loads (cp.async.bulk.tensor), tcgen05 shared-memory and instruction
-// descriptors, tcgen05.mma / commit, TMEM allocation and loads.
+// bounded waits, TMA tiled and bulk loads (cp.async.bulk[.tensor]), tcgen05 shared-memory and
+// instruction descriptors, tcgen05.mma / commit, TMEM allocation and loads.
 //
 // Operand layouts are the canonical no-swizzle ones of tcgen05:
 //   K-major:  core matrix = 8 rows (M or N) x 16 bytes of K; LBO = byte stride between core
@@ -41,20 +41,22 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, uint32_t
     return false;
 }
 
-// 4D tiled load: box at (c, x, y, n) of the map into shared memory, completing on `bar`
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c, int x, int y, int n, uint32_t bar) {
+// 4D tiled load: the box at coordinates (c0, c1, c2, c3) (innermost first) of the map into
+// shared memory, completing on `bar`; out-of-range elements read as zero
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
         "[%6];" ::"r"(dst),
-        "l"(map), "r"(c), "r"(x), "r"(y), "r"(n), "r"(bar)
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
         : "memory");
 }
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int k, int r, int t, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
-            dst),
-        "l"(map), "r"(k), "r"(r), "r"(t), "r"(bar)
-        : "memory");
+
+// contiguous copy of `bytes` (multiple of 16, both addresses 16-byte aligned), completing on `bar`
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
 }
 
 // shared-memory matrix descriptor (no swizzle, version 1); the start address occupies the
