@@ -810,7 +810,12 @@ def run_batch(args):
         "e2e": {"value": bt.B / e2e_s, "unit": BATCH_UNIT, "h2d_bytes_per_step": 8 * bt.total,
                 "d2h_bytes_per_step": 8 * bt.total},
         "clocks": clocks, "gpu_launches": int(launches),
-        "schedule": {"chosen": choice, "tune_ms": tune_ms},
+        "schedule": {"chosen": choice, "chosen_desc": ptylm.schedule_desc(choice),
+                     "tune_table": [dict(ptylm.schedule_desc(c), schedule=c, ms=t)
+                                    for c, t in enumerate(tune_ms) if t > 0],
+                     "note": "autotuner over FFT tile (values per thread for the 32^2 / 64^2 problems: "
+                             "32 or 16), work-item order and positions per team per item; each entry is "
+                             "the mean of 3 batched GGN products"},
         "comparison": {"sequential_single_contexts_ms": 1e3 * seq_s, "batched_ms": 1e3 * t_step,
                        "speedup": seq_s / t_step},
         "lm_step_ms": 1e3 * lm_step_s,

@@ -413,13 +413,21 @@ ptylm_status ptylm_batch_ggn_matvec(ptylm_batch* batch, const ptylm_c64* v, ptyl
 ptylm_status ptylm_batch_lm_solve(ptylm_batch* batch, ptylm_c64* O_inout, const ptylm_lm_params* prm,
                                   ptylm_lm_stats* stats);
 
-/* Schedule autotuner: times the batch's GGN product (3 launches after a warm-up) under six
- * schedules -- work items ordered largest patches first (0..2) or round robin over the
- * problems (3..5), with 1, 2 or 4 positions per team per item -- and keeps the fastest.
- * Needs a linearisation point.  choice: index kept; ms: up to n_ms measured times. */
+/* Autotuner (the paper has no counterpart): times the batch's GGN product (3 launches after a
+ * warm-up) under 24 schedules and keeps the fastest.  Schedule c = s + 6 (t32 + 2 t64):
+ *   s = 0..5: work items ordered largest patches first (0..2) or round robin over the
+ *             problems (3..5), with 1, 2 or 4 positions per team per item;
+ *   t32, t64: FFT tile of the problems with 32 x 32 / 64 x 64 probes -- 0: 32 values per
+ *             thread (teams of S^2/32 threads), 1: 16 values per thread (teams of S^2/16
+ *             threads, half the registers per patch, one more exchange for S = 32).
+ * Tiles that no problem of the batch uses are not timed (ms entry -1).  A tile change puts
+ * the affected problems' measurements into that tile's team order and recomputes the
+ * linearisation (cache, gradient, metric) at the same point.  Needs a linearisation point.
+ * choice: index kept; ms: up to n_ms entries of the table (host floats). */
 ptylm_status ptylm_batch_tune(ptylm_batch* batch, int* choice, float* ms, int n_ms);
 
-/* Use schedule `choice` (0..5, as in ptylm_batch_tune) without timing. */
+/* Use schedule `choice` (0..23, as in ptylm_batch_tune) without timing; with a linearisation
+ * point, a tile change recomputes it as in ptylm_batch_tune. */
 ptylm_status ptylm_batch_set_schedule(ptylm_batch* batch, int choice);
 
 /* Kernel launches issued by the batch so far (graph replays count their four kernels). */

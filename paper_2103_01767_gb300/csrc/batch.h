@@ -15,13 +15,13 @@ struct BatchProblem {
     long z_off;          // first element of this problem's object in the batch vectors
     int K, nx, LS, loss;
     float b;             // background b (+ the surrogate s_t inside the batched LM)
-    int pad;
+    int LE;              // log2 of the values per thread of its FFT tile (5, or 4 for S <= 64)
 };
 
 // A work item: positions k0 + team + teams * j (j < per_team) of problem `prob`, where
-// teams = 512 / (S^2 / 32) is the number of thread teams a 512-thread CTA holds for the
-// problem's probe side S (16, 4 and 1 for S = 32, 64, 128).  Every item is the same
-// 16384 * per_team pixels of FFT work.
+// teams = 512 / (S^2 / E) is the number of thread teams a 512-thread CTA holds for the
+// problem's probe side S and values per thread E (16, 4 and 1 for S = 32, 64, 128 with
+// E = 32; 8 and 2 for S = 32, 64 with E = 16).
 struct BatchItem {
     int prob, k0, per_team, pad;
 };
@@ -47,5 +47,10 @@ enum BatchKernel { BK_FWD_LOSS = 0, BK_FWD_CACHE = 1, BK_MATVEC = 2, BK_COUNT = 
 // Opt in to the kernels' shared memory and return how many CTAs of each fit on one SM.
 cudaError_t batch_prepare(int* ctas_per_sm);
 cudaError_t batch_launch(int kernel, const BatchArgs& a, int grid, cudaStream_t stream);
+// Measurements of K positions of side 2^LS from the team-register order of the tile with
+// 2^le_from values per thread to that with 2^le_to (le in {4, 5}, LS in {5, 6}); src and
+// dst must not overlap.
+cudaError_t batch_relayout_measurements(int LS, int le_from, int le_to, const float* src, float* dst, int K, int blocks,
+                                        cudaStream_t stream);
 
 }  // namespace ptylm

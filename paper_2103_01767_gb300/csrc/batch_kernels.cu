@@ -2,13 +2,15 @@
 // uneven object sizes, probe sides (32, 64, 128), scans and losses, each operator as ONE
 // persistent launch.
 //
-// Every CTA has 512 threads and 128 KB of exchange buffers, which hold 16 teams for a
-// 32 x 32 probe, 4 teams for 64 x 64 or one team for 128 x 128 (Geo<LS>): a work item is one
-// problem's positions for all teams of the CTA, and every item is the same 16384 pixels
-// of FFT work per position slot.  CTAs take items from a device counter (largest patches
-// first in the default order), branch once per item on the probe side and run the same
-// team code as the single-problem kernels (gather x probe, team 2D FFT, frequency stage,
-// inverse FFT, x conj(probe) and overlap scatter-add; App. A steps 1-4).  Positions beyond
+// Every CTA has 512 threads and 128 KB of exchange buffers.  A problem's FFT tile is its
+// probe side S with E values per thread (Geo<LS, LE>): E = 32 gives teams of S^2/32 threads
+// (16 teams per CTA for a 32 x 32 probe, 4 for 64 x 64, one for 128 x 128); E = 16, an
+// autotuner choice for sides 32 and 64, gives teams of S^2/16 threads (8 and 2 per CTA),
+// with twice the threads and half the registers per patch.  A work item is one problem's
+// positions for all teams of the CTA.  CTAs take items from a device counter (largest
+// patches first in the default order), branch once per item on the problem's tile and run
+// the same team code as the single-problem kernels (gather x probe, team 2D FFT, frequency
+// stage, inverse FFT, x conj(probe) and overlap scatter-add; App. A steps 1-4).  Positions beyond
 // a problem's K in its last item run the FFT on zeros (the team barriers are CTA-wide) and
 // touch no memory.  The last CTA to finish restores the counters, so the launch can be
 // replayed inside a CUDA graph.
@@ -47,7 +49,7 @@ __device__ __forceinline__ void batch_forward_item(const BatchArgs& a, const Bat
     const float2* O = a.V + p.z_off;
     float2* gout = a.out + p.z_off;
     double acc_l = 0.0, acc_d = 0.0;
-    float2 v[32];
+    float2 v[G::E];
     for (int j = 0; j < it.per_team; ++j) {
         const int k = it.k0 + team + TEAMS * j;
         const bool valid = k < p.K;
@@ -58,7 +60,7 @@ __device__ __forceinline__ void batch_forward_item(const BatchArgs& a, const Bat
             prefetch_tile_l2(p.y + (size_t)k * G::M, sizeof(float) * G::M, tid);
         } else {
 #pragma unroll
-            for (int e = 0; e < 32; ++e) v[e] = make_float2(0.0f, 0.0f);
+            for (int e = 0; e < G::E; ++e) v[e] = make_float2(0.0f, 0.0f);
         }
         float sl = 0.0f, sd = 0.0f, s2;
         LossSums ls;  // loss_pixel: h = |g / S|^2 + b (Eq. expected_count), constant factors at the end
@@ -87,7 +89,7 @@ __device__ __forceinline__ void batch_forward_item(const BatchArgs& a, const Bat
             auto pixels = [&](auto loss_c) {
                 constexpr int LOSS = decltype(loss_c)::value;
 #pragma unroll
-                for (int e = 0; e < 32; ++e) {
+                for (int e = 0; e < G::E; ++e) {
                     float ca, cg;
                     loss_pixel<LOSS, false>(v[e], valid ? __ldg(yk + e * G::T) : 0.0f, p.b, invS, ls, ca, cg);
                 }
@@ -95,8 +97,8 @@ __device__ __forceinline__ void batch_forward_item(const BatchArgs& a, const Bat
             if (p.loss == 0) pixels(std::integral_constant<int, 0>{});
             else pixels(std::integral_constant<int, 1>{});
         }
-        if (p.loss == 0) ls.finish<0>(32, sl, sd, s2);
-        else ls.finish<1>(32, sl, sd, s2);
+        if (p.loss == 0) ls.finish<0>(G::E, sl, sd, s2);
+        else ls.finish<1>(G::E, sl, sd, s2);
         if (valid) {
             acc_l += (double)sl;
             acc_d += (double)sd;
@@ -117,7 +119,7 @@ __device__ __forceinline__ void batch_matvec_item(const BatchArgs& a, const Batc
     const float invM = 1.0f / G::M;
     const float2* V = a.V + p.z_off;
     float2* out = a.out + p.z_off;
-    float2 v[32];
+    float2 v[G::E];
     for (int j = 0; j < it.per_team; ++j) {
         const int k = it.k0 + team + TEAMS * j;
         const bool valid = k < p.K;
@@ -128,7 +130,7 @@ __device__ __forceinline__ void batch_matvec_item(const BatchArgs& a, const Batc
             prefetch_tile_l2(ak, sizeof(float2) * G::M, tid);
         } else {
 #pragma unroll
-            for (int e = 0; e < 32; ++e) v[e] = make_float2(0.0f, 0.0f);
+            for (int e = 0; e < G::E; ++e) v[e] = make_float2(0.0f, 0.0f);
         }
         team_fft_roundtrip<G>(v, sm, tw, tid, [&](float2* g, int jj) {
             float2 av[G::BY];
@@ -149,6 +151,13 @@ __device__ __forceinline__ void batch_matvec_item(const BatchArgs& a, const Batc
     }
 }
 
+template <int KIND, class G>
+__device__ __forceinline__ void batch_item(const BatchArgs& a, const BatchProblem& p, const BatchItem& it,
+                                           float2* smem, const float2* tw) {
+    if constexpr (KIND == BK_MATVEC) batch_matvec_item<G>(a, p, it, smem, tw);
+    else batch_forward_item<G, KIND == BK_FWD_CACHE>(a, p, it, smem, tw);
+}
+
 // The persistent scheduler: take items until none are left, then let the last CTA reset
 // the counters.
 template <int KIND>
@@ -167,19 +176,12 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batch(BatchArgs a) {
         const BatchItem it = a.items[idx];
         if (a.active && !a.active[it.prob]) continue;
         const BatchProblem p = a.probs[it.prob];
-        switch (p.LS) {
-            case 5:
-                if constexpr (KIND == BK_MATVEC) batch_matvec_item<Geo<5>>(a, p, it, smem, tw);
-                else batch_forward_item<Geo<5>, KIND == BK_FWD_CACHE>(a, p, it, smem, tw);
-                break;
-            case 6:
-                if constexpr (KIND == BK_MATVEC) batch_matvec_item<Geo<6>>(a, p, it, smem, tw);
-                else batch_forward_item<Geo<6>, KIND == BK_FWD_CACHE>(a, p, it, smem, tw);
-                break;
-            default:
-                if constexpr (KIND == BK_MATVEC) batch_matvec_item<Geo<7>>(a, p, it, smem, tw);
-                else batch_forward_item<Geo<7>, KIND == BK_FWD_CACHE>(a, p, it, smem, tw);
-                break;
+        switch (p.LS * 8 + p.LE) {
+            case 5 * 8 + 5: batch_item<KIND, Geo<5, 5>>(a, p, it, smem, tw); break;
+            case 5 * 8 + 4: batch_item<KIND, Geo<5, 4>>(a, p, it, smem, tw); break;
+            case 6 * 8 + 5: batch_item<KIND, Geo<6, 5>>(a, p, it, smem, tw); break;
+            case 6 * 8 + 4: batch_item<KIND, Geo<6, 4>>(a, p, it, smem, tw); break;
+            default: batch_item<KIND, Geo<7, 5>>(a, p, it, smem, tw); break;
         }
         __syncthreads();  // the next item may lay its teams out differently in shared memory
     }
@@ -191,6 +193,39 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batch(BatchArgs a) {
             __threadfence();
         }
     }
+}
+
+// Measurements from the team-register order of one FFT tile to that of another (same side):
+// dst[k][e*T + t] = src[k][e'*T' + t'] where (e', t') holds, in the source tile, the
+// frequency (ky, kx) that (e, t) holds in the destination tile.  In a tile G the frequency
+// (ky, kx) sits at thread ky + S*(kx mod BX) and element ((kx / BX) mod G3)*BY + kx / AY.
+template <int LS, int LF, int LT>
+__global__ void k_batch_relayout(const float* __restrict__ src, float* __restrict__ dst, long total) {
+    using GF = Geo<LS, LF>;
+    using GT = Geo<LS, LT>;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const long k = i / GT::M;
+        const int r = (int)(i - k * GT::M);
+        const int e = r / GT::T, t = r % GT::T;
+        const int ky = freq_ky<GT>(t), kx = freq_kx<GT>(t, e);
+        const int tf = ky + GF::S * (kx % GF::BX);
+        const int ef = ((kx / GF::BX) % GF::G3) * GF::BY + kx / GF::AY;
+        dst[i] = src[k * GF::M + ef * GF::T + tf];
+    }
+}
+
+cudaError_t batch_relayout_measurements(int LS, int le_from, int le_to, const float* src, float* dst, int K, int blocks,
+                                        cudaStream_t stream) {
+    const long total = (long)K << (2 * LS);
+    if (total == 0 || le_from == le_to) return cudaSuccess;
+    switch (LS * 8 + le_to) {
+        case 5 * 8 + 4: k_batch_relayout<5, 5, 4><<<blocks, 256, 0, stream>>>(src, dst, total); break;
+        case 5 * 8 + 5: k_batch_relayout<5, 4, 5><<<blocks, 256, 0, stream>>>(src, dst, total); break;
+        case 6 * 8 + 4: k_batch_relayout<6, 5, 4><<<blocks, 256, 0, stream>>>(src, dst, total); break;
+        case 6 * 8 + 5: k_batch_relayout<6, 4, 5><<<blocks, 256, 0, stream>>>(src, dst, total); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 static size_t batch_smem_bytes() { return sizeof(float2) * (BATCH_TW + 16384); }

@@ -194,7 +194,7 @@ __device__ __forceinline__ TeamCtx<G> team_setup(const float2* tw_g) {
     return c;
 }
 
-// Where a thread's 32 probe values P[BX*a + b][x] (a = 0..31, pass-1 layout, thread
+// Where a thread's E probe values P[BX*a + b][x] (a = 0..E-1, pass-1 layout, thread
 // t = x + S*b) come from, 8 at a time (a = a0 .. a0 + 7): plain loads from the probe array
 // (L1 / L2).
 template <class G>
@@ -218,7 +218,7 @@ __device__ __forceinline__ void gather_times_probe(float2* v, const float2* __re
     const float2* src = A + (size_t)(r0 + b) * nx + c0 + x;
     const size_t row_step = (size_t)G::BX * nx;
 #pragma unroll
-    for (int a0 = 0; a0 < 32; a0 += 8) {
+    for (int a0 = 0; a0 < G::E; a0 += 8) {
         float2 pv[8], av[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) av[i] = ldg_stream(src + row_step * (a0 + i));
@@ -243,7 +243,7 @@ __device__ __forceinline__ void scatter_times_conj_probe(const float2* v, float2
     float2* dst = out + (size_t)(r0 + b) * nx + c0 + x;
     const size_t row_step = (size_t)G::BX * nx;
 #pragma unroll
-    for (int a0 = 0; a0 < 32; a0 += 8) {
+    for (int a0 = 0; a0 < G::E; a0 += 8) {
         float2 pv[8];
         ps.load8(pv, a0);
 #pragma unroll
@@ -272,7 +272,7 @@ __device__ __forceinline__ void scatter_then_gather(float2* v, float2* out, cons
     const float2* src = A + (size_t)(r1 + b) * nx + c1 + x;
     const size_t row_step = (size_t)G::BX * nx;
 #pragma unroll
-    for (int a0 = 0; a0 < 32; a0 += 8) {
+    for (int a0 = 0; a0 < G::E; a0 += 8) {
         float2 pv[8], av[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) av[i] = ldg_stream(src + row_step * (a0 + i));
@@ -302,7 +302,7 @@ __device__ __forceinline__ void gather_joint(float2* v, const float2* __restrict
     const int poff = b * G::S + x;
     const size_t row_step = (size_t)G::BX * nx;
 #pragma unroll
-    for (int a0 = 0; a0 < 32; a0 += 8) {
+    for (int a0 = 0; a0 < G::E; a0 += 8) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int a = a0 + i;
@@ -327,7 +327,7 @@ __device__ __forceinline__ void accumulate_probe_adjoint(const float2* v, float2
     const int poff = b * G::S + x;
     const size_t row_step = (size_t)G::BX * nx;
 #pragma unroll
-    for (int a0 = 0; a0 < 32; a0 += 8) {
+    for (int a0 = 0; a0 < G::E; a0 += 8) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int a = a0 + i;

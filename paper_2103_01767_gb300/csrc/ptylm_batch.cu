@@ -311,6 +311,7 @@ struct ptylm_batch {
 
     bool has_lin = false;
     int order = 0, per_team = 1;
+    int le32 = 5, le64 = 5;              // FFT tile (log2 values per thread) of the 32^2 / 64^2 problems
     bool tuned = false;
     std::vector<float> tune_ms;
     cudaGraph_t graph = nullptr;
@@ -360,7 +361,7 @@ std::vector<BatchItem> build_items(const ptylm_batch* bt, int order, int per_tea
     std::vector<std::vector<BatchItem>> per(bt->B);
     for (int b = 0; b < bt->B; ++b) {
         const int S = bt->d[b].my;
-        const int teams = BATCH_THREADS / (S * S / 32);
+        const int teams = BATCH_THREADS / ((S * S) >> bt->hprobs[b].LE);
         const int span = teams * per_team;
         for (int k0 = 0; k0 < bt->d[b].K; k0 += span) per[b].push_back(BatchItem{b, k0, per_team, 0});
     }
@@ -460,6 +461,36 @@ ptylm_status batch_forward(ptylm_batch* bt, const float2* V, int cache, int* mas
         BSTATUS_TRY(vec_ok(bt));
     }
     return launch_batch(bt, cache ? BK_FWD_CACHE : BK_FWD_LOSS, V, cache ? bt->grad : nullptr, mask);
+}
+
+// FFT tiles of the 32^2 and 64^2 problems (log2 of the values per thread, 5 or 4).  A change
+// moves those problems' measurements into the new tile's team-register order (through their
+// cache buffers, which the new tile rewrites anyway) and, when a linearisation point exists,
+// recomputes its cache, gradient and metric at z in the new layout.
+ptylm_status set_tiles(ptylm_batch* bt, int le32, int le64) {
+    bool changed = false;
+    for (int b = 0; b < bt->B; ++b) {
+        BatchProblem& p = bt->hprobs[b];
+        const int want = p.LS == 5 ? le32 : (p.LS == 6 ? le64 : 5);
+        if (p.LE == want) continue;
+        if (p.K > 0) {
+            const size_t bytes = sizeof(float) * ((size_t)p.K << (2 * p.LS));
+            float* tmp = reinterpret_cast<float*>(p.a_cache);
+            BCUDA_TRY(cudaMemcpyAsync(tmp, p.y, bytes, cudaMemcpyDeviceToDevice, bt->stream));
+            const int blocks = std::min(bt->num_sms * 8, std::max(1, (int)(((long)p.K << (2 * p.LS)) / 256)));
+            BCUDA_TRY(batch_relayout_measurements(p.LS, p.LE, want, tmp, const_cast<float*>(p.y), p.K, blocks,
+                                                  bt->stream));
+        }
+        p.LE = want;
+        changed = true;
+    }
+    bt->le32 = le32;
+    bt->le64 = le64;
+    if (!changed) return PTYLM_OK;
+    BSTATUS_TRY(upload_probs(bt));
+    BSTATUS_TRY(upload_items(bt, bt->order, bt->per_team));
+    if (bt->has_lin) BSTATUS_TRY(batch_forward(bt, bt->z, 1, nullptr));
+    return PTYLM_OK;
 }
 
 ptylm_status read_f_and_scalars(ptylm_batch* bt) {
@@ -581,7 +612,9 @@ ptylm_status ptylm_batch_init(ptylm_batch** out, int B, const ptylm_desc* descs,
         bt->off[b + 1] = bt->off[b] + N;
         hfirst[b] = (int)hch.size();
         for (long s = 0; s < N; s += CHUNK) hch.push_back(Chunk{bt->off[b] + s, (int)std::min<long>(CHUNK, N - s), b});
-        const int S = descs[b].my, teams = BATCH_THREADS / (S * S / 32);
+        // the smallest team count of any tile the autotuner may pick for this side (16 values
+        // per thread for sides 32 and 64) bounds the number of items
+        const int S = descs[b].my, teams = BATCH_THREADS / (S * S / (S <= 64 ? 16 : 32));
         max_items += (descs[b].K + teams - 1) / teams;
     }
     hfirst[B] = (int)hch.size();
@@ -641,6 +674,7 @@ ptylm_status ptylm_batch_init(ptylm_batch** out, int B, const ptylm_desc* descs,
         p.LS = LS;
         p.loss = d.loss;
         p.b = d.background;
+        p.LE = 5;
         p.z_off = bt->off[b];
         int2* pos = nullptr;
         float* y = nullptr;
@@ -757,56 +791,79 @@ ptylm_status ptylm_batch_ggn_matvec(ptylm_batch* bt, const ptylm_c64* v, ptylm_c
     return leave(bt);
 }
 
+// Schedules of the autotuner: index = sched + 6 * (t32 + 2 * t64) with sched = (order,
+// positions per team per item) from kSched, t32 / t64 = 1 when the 32^2 / 64^2 problems run
+// the 16-values-per-thread FFT tile.
+constexpr int kSched[6][2] = {{0, 1}, {0, 2}, {0, 4}, {1, 1}, {1, 2}, {1, 4}};
+constexpr int kSchedules = 24;
+
+ptylm_status apply_schedule(ptylm_batch* bt, int c) {
+    const int sched = c % 6, t32 = (c / 6) & 1, t64 = c / 12;
+    bt->order = kSched[sched][0];
+    bt->per_team = kSched[sched][1];
+    BSTATUS_TRY(set_tiles(bt, t32 ? 4 : 5, t64 ? 4 : 5));
+    return upload_items(bt, kSched[sched][0], kSched[sched][1]);
+}
+
 ptylm_status ptylm_batch_tune(ptylm_batch* bt, int* choice, float* ms, int n_ms) {
     set_last_error("");
     if (!bt) return bfail(PTYLM_ERR_ARG, "batch must be non-NULL");
     if (!bt->has_lin) return bfail(PTYLM_ERR_STATE, "no linearisation point (ptylm_batch_forward_loss with cache=1)");
     BSTATUS_TRY(enter(bt));
-    // candidates: (order, positions per team per item)
-    const int cand[6][2] = {{0, 1}, {0, 2}, {0, 4}, {1, 1}, {1, 2}, {1, 4}};
+    bool has32 = false, has64 = false;
+    for (int b = 0; b < bt->B; ++b) {
+        has32 |= bt->hprobs[b].LS == 5 && bt->hprobs[b].K > 0;
+        has64 |= bt->hprobs[b].LS == 6 && bt->hprobs[b].K > 0;
+    }
     cudaEvent_t e0, e1;
     BCUDA_TRY(cudaEventCreate(&e0));
     BCUDA_TRY(cudaEventCreate(&e1));
     int best = 0;
     float best_ms = 1e30f;
-    bt->tune_ms.assign(6, 0.0f);
+    bt->tune_ms.assign(kSchedules, -1.0f);
     ptylm_status s = PTYLM_OK;
-    for (int c = 0; c < 6 && s == PTYLM_OK; ++c) {
-        if ((s = upload_items(bt, cand[c][0], cand[c][1])) != PTYLM_OK) break;
-        if ((s = launch_batch(bt, BK_MATVEC, bt->grad, bt->q, nullptr)) != PTYLM_OK) break;   // warm-up
-        cudaEventRecord(e0, bt->stream);
-        for (int rep = 0; rep < 3 && s == PTYLM_OK; ++rep) s = launch_batch(bt, BK_MATVEC, bt->grad, bt->q, nullptr);
-        cudaEventRecord(e1, bt->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) s = bfail(PTYLM_ERR_CUDA, "timing a schedule");
-        float t = 0.0f;
-        cudaEventElapsedTime(&t, e0, e1);
-        bt->tune_ms[c] = t / 3.0f;
-        if (bt->tune_ms[c] < best_ms) {
-            best_ms = bt->tune_ms[c];
-            best = c;
+    // tiles in the outer loop: a tile change relinearises, a schedule change only rebuilds
+    // the work list; tiles that no problem of the batch uses are not timed (entry -1)
+    for (int tile = 0; tile < 4 && s == PTYLM_OK; ++tile) {
+        if (((tile & 1) && !has32) || ((tile & 2) && !has64)) continue;
+        for (int sched = 0; sched < 6 && s == PTYLM_OK; ++sched) {
+            const int c = sched + 6 * tile;
+            if ((s = apply_schedule(bt, c)) != PTYLM_OK) break;
+            if ((s = launch_batch(bt, BK_MATVEC, bt->grad, bt->q, nullptr)) != PTYLM_OK) break;   // warm-up
+            cudaEventRecord(e0, bt->stream);
+            for (int rep = 0; rep < 3 && s == PTYLM_OK; ++rep) s = launch_batch(bt, BK_MATVEC, bt->grad, bt->q, nullptr);
+            cudaEventRecord(e1, bt->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) s = bfail(PTYLM_ERR_CUDA, "timing a schedule");
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            bt->tune_ms[c] = t / 3.0f;
+            if (bt->tune_ms[c] < best_ms) {
+                best_ms = bt->tune_ms[c];
+                best = c;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     BSTATUS_TRY(s);
-    BSTATUS_TRY(upload_items(bt, cand[best][0], cand[best][1]));
+    BSTATUS_TRY(apply_schedule(bt, best));
     bt->tuned = true;
     if (bt->graph_exec) BSTATUS_TRY(capture_graph(bt));
     if (choice) *choice = best;
-    for (int c = 0; c < n_ms && c < 6; ++c) ms[c] = bt->tune_ms[c];
+    for (int c = 0; c < n_ms && c < kSchedules; ++c) ms[c] = bt->tune_ms[c];
     BCUDA_TRY(cudaStreamSynchronize(bt->stream));
     return leave(bt);
 }
 
 ptylm_status ptylm_batch_set_schedule(ptylm_batch* bt, int choice) {
     set_last_error("");
-    if (!bt || choice < 0 || choice > 5) return bfail(PTYLM_ERR_ARG, "schedule must be 0..5");
-    const int cand[6][2] = {{0, 1}, {0, 2}, {0, 4}, {1, 1}, {1, 2}, {1, 4}};
-    BSTATUS_TRY(upload_items(bt, cand[choice][0], cand[choice][1]));
+    if (!bt || choice < 0 || choice >= kSchedules) return bfail(PTYLM_ERR_ARG, "schedule must be 0..%d", kSchedules - 1);
+    BSTATUS_TRY(enter(bt));
+    BSTATUS_TRY(apply_schedule(bt, choice));
     bt->tuned = true;
     if (bt->graph_exec) BSTATUS_TRY(capture_graph(bt));
     BCUDA_TRY(cudaStreamSynchronize(bt->stream));
-    return PTYLM_OK;
+    return leave(bt);
 }
 
 ptylm_status ptylm_batch_lm_solve(ptylm_batch* bt, ptylm_c64* O_inout, const ptylm_lm_params* prm,

@@ -1,17 +1,18 @@
 // team_fft.cuh -- register/shared-memory 2D FFT for one S x S patch per thread team.
 //
 // The far-field propagator of the model (Sec. 2, Eq. expected_count) is an S x S 2D DFT
-// applied independently at every scan position.  A "team" of T = S*S/32 threads owns one
-// patch; every thread holds 32 complex values in registers and the 2D transform runs as
-// three register passes separated by two shared-memory exchanges.  The first transformed
-// dimension (d1) is the patch row index y, the second (d2) the column index x:
+// applied independently at every scan position.  A "team" of T = S*S/E threads owns one
+// patch; every thread holds E complex values in registers (E = 32 everywhere except the
+// batched kernels, which may run 32^2 and 64^2 patches with E = 16) and the 2D transform
+// runs as three register passes separated by two shared-memory exchanges.  The first
+// transformed dimension (d1) is the patch row index y, the second (d2) the column index x:
 //
-//   d1 = BX*a1 + b1  (32 x BX = S)           d2 = BY*ay + by  (AY x BY = S, AY = 32/BX)
-//   pass 1   DFT_32 over a1          -> k1, twiddle W_S^(b1*k1)     thread t1 = d2 + S*b1
+//   d1 = BX*a1 + b1  (E x BX = S)            d2 = BY*ay + by  (AY x BY = S, AY = E/BX)
+//   pass 1   DFT_E over a1           -> k1, twiddle W_S^(b1*k1)     thread t1 = d2 + S*b1
 //   pass 2   DFT_BX over b1 -> k2;  DFT_AY over ay -> k1y,
-//            twiddle W_S^(by*k1y)                                  thread t2 = k1 + 32*by
+//            twiddle W_S^(by*k1y)                                  thread t2 = k1 + E*by
 //   pass 3   DFT_BY over by          -> k2y                         thread (kd1, k1y)
-//   frequency index (k_d1, k_d2) = (k1 + 32*k2, k1y + AY*k2y)
+//   frequency index (k_d1, k_d2) = (k1 + E*k2, k1y + AY*k2y)
 //
 // In pass 1 the 32 lanes of a warp hold 32 consecutive columns of one row, so the patch
 // gather and the scatter-add touch 256 contiguous bytes per warp instruction.
@@ -22,10 +23,10 @@
 // elements in the "pass-3" layout and computes their frequency index instead.
 //
 // Exchange layouts (units of 8-byte complex words):
-//   ex1 (pass 1 <-> pass 2):  slot(t1, k1) = t1*32 + (k1 ^ (t1 & 31))
+//   ex1 (pass 1 <-> pass 2):  slot(t1, k1) = t1*E + (k1 ^ (t1 & (E-1)))
 //        writers vary t1 across lanes, readers vary k1: the XOR swizzle keeps both
-//        conflict-free.
-//   ex2 (pass 2 <-> pass 3):  slot = ((k2*AY + k1y)*BY + by)*32 + k1
+//        conflict-free (for E = 16 within each half-warp, the unit of a 64-bit access).
+//   ex2 (pass 2 <-> pass 3):  slot = ((k2*AY + k1y)*BY + by)*E + k1
 //        both sides have lanes = k1, so plain row-major is conflict-free.
 //
 // Unnormalised transforms: forward then inverse multiplies by S*S; callers fold the
@@ -181,19 +182,22 @@ __device__ __forceinline__ void dft_strided(float2* v, int base) {
     }
 }
 
-// Geometry of the three-pass decomposition for S = 2^LS.
-template <int LS>
+// Geometry of the three-pass decomposition for S = 2^LS with E = 2^LE values per thread.
+template <int LS, int LE = 5>
 struct Geo {
     static_assert(LS >= 5 && LS <= 7, "supported patch sides: 32, 64, 128");
+    static_assert(LE == 5 || (LE == 4 && LS <= 6), "values per thread: 32, or 16 for sides 32 and 64");
     static constexpr int LOG_S = LS;
+    static constexpr int LOG_E = LE;
     static constexpr int S = 1 << LS;
     static constexpr int M = S * S;
-    static constexpr int E = 32;         // complex values per thread
+    static constexpr int E = 1 << LE;    // complex values per thread
     static constexpr int T = M / E;      // threads per team
-    static constexpr int BX = S / 32;
-    static constexpr int AY = 32 / BX;
+    static constexpr int BX = S / E;
+    static constexpr int AY = E / BX;
     static constexpr int BY = S / AY;
-    static constexpr int G3 = 32 / BY;   // pass-3 groups per thread
+    static constexpr int G3 = E / BY;    // pass-3 groups per thread
+    static_assert(BY <= E, "pass 3 must fit one thread's values");
     static constexpr int TEAMS = (T >= 128) ? 1 : 128 / T;  // teams per CTA
     static constexpr int THREADS = T * TEAMS;
 };
@@ -211,11 +215,11 @@ __device__ __forceinline__ void sched_fence() { asm volatile("" ::: "memory"); }
 
 template <class G>
 __device__ __forceinline__ void pass1_fwd(float2* v, const float2* tw, int t1) {
-    RegDFT<32, false>::run(v);
+    RegDFT<G::E, false>::run(v);
     if constexpr (G::BX > 1) {
         const int bx = (t1 >> G::LOG_S) & (G::BX - 1);
 #pragma unroll
-        for (int k0 = 0; k0 < 32; k0 += 8) {
+        for (int k0 = 0; k0 < G::E; k0 += 8) {
             float2 w[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) w[i] = tw[bx * (k0 + i)];
@@ -229,43 +233,43 @@ __device__ __forceinline__ void pass1_fwd(float2* v, const float2* tw, int t1) {
 
 template <class G>
 __device__ __forceinline__ void pass1_inv(float2* v) {
-    RegDFT<32, true>::run(v);
+    RegDFT<G::E, true>::run(v);
 }
 
 // ---- exchange 1 --------------------------------------------------------------------
 template <class G>
 __device__ __forceinline__ void ex1_store_from_p1(float2* sm, const float2* v, int t1) {
-    const int sw = t1 & 31;
+    const int sw = t1 & (G::E - 1);
 #pragma unroll
-    for (int k = 0; k < 32; ++k) sm[t1 * 32 + (k ^ sw)] = v[k];
+    for (int k = 0; k < G::E; ++k) sm[t1 * G::E + (k ^ sw)] = v[k];
 }
 template <class G>
 __device__ __forceinline__ void ex1_load_to_p1(const float2* sm, float2* v, int t1) {
-    const int sw = t1 & 31;
+    const int sw = t1 & (G::E - 1);
 #pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = sm[t1 * 32 + (k ^ sw)];
+    for (int k = 0; k < G::E; ++k) v[k] = sm[t1 * G::E + (k ^ sw)];
 }
 // pass-2 register layout: v[ay*BX + bx] (before pass 2) / v[k1y*BX + k2x] (after)
 template <class G>
 __device__ __forceinline__ void ex1_load_to_p2(const float2* sm, float2* v, int t2) {
-    const int k1x = t2 & 31, by = (t2 >> 5) & (G::BY - 1);  // t2 < T = 32 BY: the mask states the range
+    const int k1x = t2 & (G::E - 1), by = (t2 >> G::LOG_E) & (G::BY - 1);  // t2 < T = E BY: the mask states the range
 #pragma unroll
     for (int ay = 0; ay < G::AY; ++ay)
 #pragma unroll
         for (int bx = 0; bx < G::BX; ++bx) {
             const int t1 = (G::BY * ay + by) + G::S * bx;
-            v[ay * G::BX + bx] = sm[t1 * 32 + (k1x ^ (t1 & 31))];
+            v[ay * G::BX + bx] = sm[t1 * G::E + (k1x ^ (t1 & (G::E - 1)))];
         }
 }
 template <class G>
 __device__ __forceinline__ void ex1_store_from_p2(float2* sm, const float2* v, int t2) {
-    const int k1x = t2 & 31, by = (t2 >> 5) & (G::BY - 1);  // t2 < T = 32 BY: the mask states the range
+    const int k1x = t2 & (G::E - 1), by = (t2 >> G::LOG_E) & (G::BY - 1);  // t2 < T = E BY: the mask states the range
 #pragma unroll
     for (int ay = 0; ay < G::AY; ++ay)
 #pragma unroll
         for (int bx = 0; bx < G::BX; ++bx) {
             const int t1 = (G::BY * ay + by) + G::S * bx;
-            sm[t1 * 32 + (k1x ^ (t1 & 31))] = v[ay * G::BX + bx];
+            sm[t1 * G::E + (k1x ^ (t1 & (G::E - 1)))] = v[ay * G::BX + bx];
         }
 }
 
@@ -277,7 +281,7 @@ __device__ __forceinline__ void pass2_fwd(float2* v, const float2* tw, int t2) {
 #pragma unroll
     for (int k2x = 0; k2x < G::BX; ++k2x) dft_strided<G::AY, G::BX, false>(v, k2x);
     if constexpr (G::BY > 1) {
-        const int by = (t2 >> 5) & (G::BY - 1);  // t2 < T = 32 BY: the mask states the range
+        const int by = (t2 >> G::LOG_E) & (G::BY - 1);  // t2 < T = E BY: the mask states the range
 #pragma unroll
         for (int k1y = 1; k1y < G::AY; ++k1y) {
             const float2 w = tw[by * k1y];
@@ -289,9 +293,9 @@ __device__ __forceinline__ void pass2_fwd(float2* v, const float2* tw, int t2) {
 
 template <class G>
 __device__ __forceinline__ void pass2_inv(float2* v, const float2* tw, int t2) {
-    const int k1x = t2 & 31;
+    const int k1x = t2 & (G::E - 1);
     if constexpr (G::BY > 1) {
-        const int by = (t2 >> 5) & (G::BY - 1);  // t2 < T = 32 BY: the mask states the range
+        const int by = (t2 >> G::LOG_E) & (G::BY - 1);  // t2 < T = E BY: the mask states the range
 #pragma unroll
         for (int k1y = 1; k1y < G::AY; ++k1y) {
             const float2 w = tw[by * k1y];
@@ -316,11 +320,11 @@ __device__ __forceinline__ void pass2_inv(float2* v, const float2* tw, int t2) {
 // ---- exchange 2 (skipped when BY == 1: the data already sits in the right thread) -----
 template <class G>
 __device__ __forceinline__ int ex2_slot(int k2x, int k1y, int by, int k1x) {
-    return ((k2x * G::AY + k1y) * G::BY + by) * 32 + k1x;
+    return ((k2x * G::AY + k1y) * G::BY + by) * G::E + k1x;
 }
 template <class G>
 __device__ __forceinline__ void ex2_store_from_p2(float2* sm, const float2* v, int t2) {
-    const int k1x = t2 & 31, by = (t2 >> 5) & (G::BY - 1);  // t2 < T = 32 BY: the mask states the range
+    const int k1x = t2 & (G::E - 1), by = (t2 >> G::LOG_E) & (G::BY - 1);  // t2 < T = E BY: the mask states the range
 #pragma unroll
     for (int k1y = 0; k1y < G::AY; ++k1y)
 #pragma unroll
@@ -329,7 +333,7 @@ __device__ __forceinline__ void ex2_store_from_p2(float2* sm, const float2* v, i
 }
 template <class G>
 __device__ __forceinline__ void ex2_load_to_p2(const float2* sm, float2* v, int t2) {
-    const int k1x = t2 & 31, by = (t2 >> 5) & (G::BY - 1);  // t2 < T = 32 BY: the mask states the range
+    const int k1x = t2 & (G::E - 1), by = (t2 >> G::LOG_E) & (G::BY - 1);  // t2 < T = E BY: the mask states the range
 #pragma unroll
     for (int k1y = 0; k1y < G::AY; ++k1y)
 #pragma unroll
@@ -339,7 +343,7 @@ __device__ __forceinline__ void ex2_load_to_p2(const float2* sm, float2* v, int 
 // pass-3 register layout: v[j*BY + by] (before pass 3) / v[j*BY + k2y] (after)
 template <class G>
 __device__ __forceinline__ void ex2_load_to_p3(const float2* sm, float2* v, int t3) {
-    const int k1x = t3 & 31, k2x = (t3 & (G::S - 1)) >> 5, k1y0 = t3 >> G::LOG_S;
+    const int k1x = t3 & (G::E - 1), k2x = (t3 & (G::S - 1)) >> G::LOG_E, k1y0 = t3 >> G::LOG_S;
 #pragma unroll
     for (int j = 0; j < G::G3; ++j)
 #pragma unroll
@@ -348,7 +352,7 @@ __device__ __forceinline__ void ex2_load_to_p3(const float2* sm, float2* v, int 
 }
 template <class G>
 __device__ __forceinline__ void ex2_store_from_p3(float2* sm, const float2* v, int t3) {
-    const int k1x = t3 & 31, k2x = (t3 & (G::S - 1)) >> 5, k1y0 = t3 >> G::LOG_S;
+    const int k1x = t3 & (G::E - 1), k2x = (t3 & (G::S - 1)) >> G::LOG_E, k1y0 = t3 >> G::LOG_S;
 #pragma unroll
     for (int j = 0; j < G::G3; ++j)
 #pragma unroll
@@ -445,18 +449,18 @@ __device__ __forceinline__ void team_fft_roundtrip(float2* v, float2* sm, const 
         ex2_store_from_p2<G>(sm, v, tid);
         before_pass3();
         team_sync<G>();
-        const int k1x = tid & 31, k2x = (tid & (G::S - 1)) >> 5, k1y0 = (tid >> G::LOG_S) & (G::BX - 1);
+        const int k1x = tid & (G::E - 1), k2x = (tid & (G::S - 1)) >> G::LOG_E, k1y0 = (tid >> G::LOG_S) & (G::BX - 1);
 #pragma unroll 1
         for (int j = 0; j < G::G3; ++j) {
             float2 g[G::BY];
             const int base = ex2_slot<G>(k2x, k1y0 + G::BX * j, 0, k1x);
 #pragma unroll
-            for (int by = 0; by < G::BY; ++by) g[by] = sm[base + by * 32];
+            for (int by = 0; by < G::BY; ++by) g[by] = sm[base + by * G::E];
             RegDFT<G::BY, false>::run(g);
             stage(g, j);
             RegDFT<G::BY, true>::run(g);
 #pragma unroll
-            for (int by = 0; by < G::BY; ++by) sm[base + by * 32] = g[by];
+            for (int by = 0; by < G::BY; ++by) sm[base + by * G::E] = g[by];
         }
         team_sync<G>();
         ex2_load_to_p2<G>(sm, v, tid);

@@ -452,7 +452,18 @@ def load_lm_checkpoint(path, device="cuda"):
 # ---------------------------------------------------------------------------------------
 # Batches of independent reconstructions
 # ---------------------------------------------------------------------------------------
-N_SCHEDULES = 6
+N_SCHEDULES = 24
+
+
+def schedule_desc(choice: int) -> dict:
+    """What batch schedule `choice` (0 .. N_SCHEDULES - 1) sets: the work-item order
+    (0: largest patches first, 1: round robin), the positions each team handles per item,
+    and the FFT tile of the 32^2 and 64^2 problems as values per thread (teams of
+    S^2 / values threads)."""
+    sched, tile = choice % 6, choice // 6
+    order, per_team = ((0, 1), (0, 2), (0, 4), (1, 1), (1, 2), (1, 4))[sched]
+    return {"order": order, "positions_per_team": per_team,
+            "values_per_thread_32": 16 if tile & 1 else 32, "values_per_thread_64": 16 if tile & 2 else 32}
 
 
 class Batch:
@@ -529,7 +540,8 @@ def batch_ggn_matvec(batch: Batch, v, out, lam=None) -> None:
 
 
 def batch_tune(batch: Batch):
-    """Returns (chosen schedule, measured ms per schedule)."""
+    """Returns (chosen schedule, measured ms per schedule); a schedule whose FFT tile no
+    problem of the batch uses is not timed and reads -1."""
     choice = ctypes.c_int(-1)
     ms = (ctypes.c_float * N_SCHEDULES)()
     _check(load_library().ptylm_batch_tune(batch.handle, ctypes.byref(choice), ms, N_SCHEDULES))
