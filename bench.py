@@ -602,6 +602,48 @@ def learned_vs_plain(ptylm, torch, dev, target=1e-3, pairs=200_000, batch=64, re
     return out, net, idx
 
 
+def net_layer_flops(widths, m=128):
+    """Algorithmic forward flops per pattern of the 6-layer encoder-decoder:
+    2 * H_out^2 * C_in * C_out * 9 summed over its 3x3 convolutions."""
+    c1, c2, c3 = widths
+    ci, co = [2, c1, c2, c3, c2, c1], [c1, c2, c3, c2, c1, 2]
+    ho = [m // 2, m // 4, m // 8, m // 4, m // 2, m]
+    return [2 * h * h * o * i * 9 for i, o, h in zip(ci, co, ho)]
+
+
+def net_timing(ptylm, torch, dev, widths=(64, 128, 256), batch_fwd=256, batch_train=64, reps=20):
+    """Throughput of the learned initialisation's network on the tensor cores: forward at
+    batch_fwd and loss + gradient (forward, input and weight gradients of every layer) at
+    batch_train, median wall time of `reps` calls each (device synchronised around every
+    call), random inputs.  Algorithmic flops: forward as net_layer_flops, loss + gradient
+    three times that."""
+    m = 128
+    net = ptylm.net_create(widths, max_batch=max(batch_fwd, batch_train), seed=1)
+    g = torch.Generator(device="cpu").manual_seed(1)
+    X = torch.randn((batch_fwd, 2, m, m), generator=g).to(dev)
+    T = torch.randn((batch_train, 2, m, m), generator=g).to(dev)
+    mask = torch.from_numpy((np.abs(synth.probe_disk_defocus(m, 40.0)) > 0).astype(np.float32)).to(dev)
+    out = torch.empty((batch_fwd, 2, m, m), dtype=torch.float32, device=dev)
+    per = float(sum(net_layer_flops(widths, m)))
+    res = {"widths": list(widths), "params": net.num_params, "flops_forward_per_pattern": per}
+    for name, fn, n, mult in (("forward", lambda: ptylm.net_forward(net, X, out), batch_fwd, 1),
+                              ("loss_grad", lambda: ptylm.net_loss_grad(net, X[:batch_train], T, mask),
+                               batch_train, 3)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize(dev)
+            ts.append(time.perf_counter() - t0)
+        ms = 1e3 * statistics.median(ts)
+        res[name] = {"batch": n, "ms": ms, "tflops": mult * per * n / (ms * 1e-3) / 1e12}
+    net.close()
+    return res
+
+
 def autograd_leg(ptylm, torch, dev, reps=10):
     """The differentiable magnitudes (autograd.far_field_magnitude over the JVP / J^T VP
     kernels) at the 1024^2 / 128^2 / 3600-position geometry, in both memory modes: the unit
@@ -837,7 +879,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the cuFFT comparison and the LM time-to-accuracy runs")
+    ap.add_argument("--net-timing", action="store_true",
+                    help="only time the learned initialisation's network (forward, loss + gradient)")
     args = ap.parse_args()
+    if args.net_timing:
+        import torch
+        from paper_2103_01767_gb300 import build as _build
+        _build.build()
+        from paper_2103_01767_gb300 import ptylm
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        torch.cuda.set_device(dev)
+        print(json.dumps({"impl": args.impl, "net_timing": net_timing(ptylm, torch, dev)}), flush=True)
+        return 0
     if args.workload == synth.BATCH64:
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle has no batched form; "
@@ -978,6 +1031,7 @@ def main():
         if oracle_tta is not None:
             tta["small"]["oracle"] = oracle_tta
         tta["learned_vs_plain"], net, idx = learned_vs_plain(ptylm, torch, dev)
+        tta["learned_vs_plain"]["network"]["timing"] = net_timing(ptylm, torch, dev)
         tta["large"] = large_poisson_time_to_accuracy(ptylm, torch, dev, stream, net, idx)
         net.close()
         autograd = autograd_leg(ptylm, torch, dev)
