@@ -400,8 +400,11 @@ ptylm_status ptylm_batch_gradient(ptylm_batch* batch, ptylm_c64* g);
 ptylm_status ptylm_batch_ggn_matvec(ptylm_batch* batch, const ptylm_c64* v, ptylm_c64* out,
                                     const double* lambda);
 
-/* Algorithm 1 with D = I for every problem, in place on the batch vector O_inout.
- * prm: B parameter sets (scaled and projected must be 0; the App. E surrogate schedule is
+/* Algorithm 1 for every problem, in place on the batch vector O_inout: LM (D = I) or, for
+ * problems with prm[b].scaled = 1, PLM (D = Dg(G) from the closed form of App. B at every
+ * linearisation, floored at diag_floor times its maximum; lambda = mu; Jacobi PCG with
+ * (1 + lambda) D; the predicted reduction with Delta^T D Delta), as lm_solve does for one
+ * problem.  prm: B parameter sets (projected must be 0; the App. E surrogate schedule is
  * honoured; O_ref / mask point to problem b's own reference object and mask).  stats: B
  * entries or NULL.  All problems advance together: each outer step linearises the problems
  * whose last step was accepted, runs the truncated CG of all unfinished problems (one CG
@@ -412,6 +415,13 @@ ptylm_status ptylm_batch_ggn_matvec(ptylm_batch* batch, const ptylm_c64* v, ptyl
  * finishing the others, else PTYLM_WARN_CG_MAXIT if any CG solve hit max_cg. */
 ptylm_status ptylm_batch_lm_solve(ptylm_batch* batch, ptylm_c64* O_inout, const ptylm_lm_params* prm,
                                   ptylm_lm_stats* stats);
+
+/* Closed-form GGN diagonal of every problem at the batch's linearisation point (App. B, Eqs.
+ * ggn_diag_elem_final, ggn_diag_mat; as ggn_diag): D_out[z_off_b + n] = sum over problem b's
+ * positions k whose patch holds n of |P_b[n - r_k]|^2 tr_k / (2M_b), tr_k = sum_m d2l_km,
+ * then raised to floor_rel times problem b's maximum.  D_out: host or device float [total].
+ * PTYLM_ERR_STATE without a linearisation point, PTYLM_ERR_ARG for floor_rel outside [0, 1). */
+ptylm_status ptylm_batch_ggn_diag(ptylm_batch* batch, float* D_out, double floor_rel);
 
 /* Autotuner (the paper has no counterpart): times the batch's GGN product (3 launches after a
  * warm-up) under 24 schedules and keeps the fastest.  Schedule c = s + 6 (t32 + 2 t64):

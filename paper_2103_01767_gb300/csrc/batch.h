@@ -11,6 +11,7 @@ struct BatchProblem {
     const int2* pos;     // [K] (row, column) of each patch
     const float* y;      // [K][M] measurements in team-register order (sqrt(y) for Gaussian)
     float2* a_cache;     // [K][M] cache a = psihat (d2l)^(1/2) / zeta of the last linearisation
+    float* trp;          // [K][T] per-thread sums of d2l of the last linearisation (T = M / E)
     const float2* P;     // [M] probe
     long z_off;          // first element of this problem's object in the batch vectors
     int K, nx, LS, loss;
@@ -47,6 +48,14 @@ enum BatchKernel { BK_FWD_LOSS = 0, BK_FWD_CACHE = 1, BK_MATVEC = 2, BK_COUNT = 
 // Opt in to the kernels' shared memory and return how many CTAs of each fit on one SM.
 cudaError_t batch_prepare(int* ctas_per_sm);
 cudaError_t batch_launch(int kernel, const BatchArgs& a, int grid, cudaStream_t stream);
+// Closed-form diagonal of every problem's GGN in real coordinates at its linearisation point
+// (App. B; the single-problem k_diag_object): D[z_off + n] += sum over the positions k of
+// problem b whose patch holds n of |P[n - r_k]|^2 tr_k / (2M), tr_k = sum of trp[k][.],
+// for the problems with mask[b] != 0 (D zeroed there beforehand).  pos_first: [B + 1]
+// prefix sums of the position counts; one block per position of the whole batch.
+cudaError_t batch_diag_launch(const BatchProblem* probs, const int* pos_first, int B, int total_positions,
+                              const int* mask, float* D, cudaStream_t stream);
+
 // Measurements of K positions of side 2^LS from the team-register order of the tile with
 // 2^le_from values per thread to that with 2^le_to (le in {4, 5}, LS in {5, 6}); src and
 // dst must not overlap.

@@ -19,6 +19,7 @@
 #include "batch.h"
 #include "ptycho_device.cuh"
 #include "team_fft.cuh"
+#include "reduce.cuh"
 
 namespace ptylm {
 
@@ -102,6 +103,7 @@ __device__ __forceinline__ void batch_forward_item(const BatchArgs& a, const Bat
         if (valid) {
             acc_l += (double)sl;
             acc_d += (double)sd;
+            if constexpr (CACHE) p.trp[(size_t)k * G::T + tid] = s2;   // for the closed-form diagonal
         }
         team_sync<G>();
     }
@@ -225,6 +227,44 @@ cudaError_t batch_relayout_measurements(int LS, int le_from, int le_to, const fl
         case 6 * 8 + 5: k_batch_relayout<6, 4, 5><<<blocks, 256, 0, stream>>>(src, dst, total); break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+// The closed-form diagonal (see batch.h): block g handles the g-th position of the batch.
+__global__ void __launch_bounds__(256) k_batch_diag(const BatchProblem* __restrict__ probs,
+                                                    const int* __restrict__ pos_first, int B,
+                                                    const int* __restrict__ mask, float* D) {
+    const int g = blockIdx.x;
+    int lo = 0, hi = B;   // the problem b with pos_first[b] <= g < pos_first[b + 1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pos_first[mid] <= g) lo = mid;
+        else hi = mid;
+    }
+    const int b = lo;
+    if (mask && !mask[b]) return;
+    const BatchProblem p = probs[b];
+    const int k = g - pos_first[b];
+    const int S = 1 << p.LS, M = S * S, T = M >> p.LE;
+    double s[1] = {0.0};
+    for (int t = threadIdx.x; t < T; t += blockDim.x) s[0] += (double)p.trp[(size_t)k * T + t];
+    block_sum<1>(s);
+    __shared__ float scale;
+    if (threadIdx.x == 0) scale = (float)s[0] / (2.0f * (float)M);
+    __syncthreads();
+    const int2 rc = p.pos[k];
+    float* Db = D + p.z_off;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const int y = m >> p.LS, x = m & (S - 1);
+        const float2 pv = p.P[m];
+        atomicAdd(Db + (size_t)(rc.x + y) * p.nx + rc.y + x, (pv.x * pv.x + pv.y * pv.y) * scale);
+    }
+}
+
+cudaError_t batch_diag_launch(const BatchProblem* probs, const int* pos_first, int B, int total_positions,
+                              const int* mask, float* D, cudaStream_t stream) {
+    if (total_positions <= 0) return cudaSuccess;
+    k_batch_diag<<<total_positions, 256, 0, stream>>>(probs, pos_first, B, mask, D);
     return cudaGetLastError();
 }
 

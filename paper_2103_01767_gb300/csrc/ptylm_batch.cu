@@ -64,17 +64,50 @@ __device__ __forceinline__ float brdot(float2 a, float2 b) { return a.x * b.x + 
 
 #define CHUNK_LOOP(c, g) for (long g = (c).begin + threadIdx.x; g < (c).begin + (c).len; g += blockDim.x)
 
-// out = lambda_b v over the chunks of problems with mask[b] (the damping term of the GGN
+// Scaling of a batch vector: problems with scaled[b] use the diagonal D (PLM, D = Dg(G)),
+// the others the identity (LM).
+struct Scale {
+    const float* D;      // [total] or NULL
+    const int* scaled;   // [B] or NULL
+    __device__ __forceinline__ bool on(int b) const { return D && scaled && scaled[b]; }
+};
+
+// out = lambda_b D_b v over the chunks of problems with mask[b] (the damping term of the GGN
 // product, written before the per-position kernel accumulates into out).
 __global__ void kb_damp(const Chunk* ch, const int* mask, const float* lam, const float2* __restrict__ v,
-                        float2* __restrict__ out) {
+                        float2* __restrict__ out, Scale sc) {
     const Chunk c = ch[blockIdx.x];
     if (mask && !mask[c.prob]) return;
     const float l = lam ? lam[c.prob] : 0.0f;
+    const bool dsc = sc.on(c.prob);
     CHUNK_LOOP(c, g) {
         const float2 x = v[g];
-        out[g] = make_float2(l * x.x, l * x.y);
+        const float w = dsc ? l * sc.D[g] : l;
+        out[g] = make_float2(w * x.x, w * x.y);
     }
+}
+
+// D over the chunks of problems with mask[b]: zero; per-problem maximum (non-negative floats
+// compare as their bit patterns); floor at floor_rel * that maximum (reading C10).
+__global__ void kb_dzero(const Chunk* ch, const int* mask, float* D) {
+    const Chunk c = ch[blockIdx.x];
+    if (mask && !mask[c.prob]) return;
+    CHUNK_LOOP(c, g) D[g] = 0.0f;
+}
+__global__ void kb_dmax(const Chunk* ch, const int* mask, const float* __restrict__ D, unsigned* dmax) {
+    const Chunk c = ch[blockIdx.x];
+    if (mask && !mask[c.prob]) return;
+    float m = 0.0f;
+    CHUNK_LOOP(c, g) m = fmaxf(m, D[g]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(dmax + c.prob, __float_as_uint(m));
+}
+__global__ void kb_dfloor(const Chunk* ch, const int* mask, const unsigned* __restrict__ dmax,
+                          const float* __restrict__ floor_rel, float* D) {
+    const Chunk c = ch[blockIdx.x];
+    if (mask && !mask[c.prob]) return;
+    const float fl = floor_rel[c.prob] * __uint_as_float(dmax[c.prob]);
+    CHUNK_LOOP(c, g) D[g] = fmaxf(D[g], fl);
 }
 
 // z = x + d (mask), z = x (copy mask), z = 0 (mask)
@@ -111,6 +144,7 @@ struct DotArgs {
     const double* tol2;       // [B] stop when r.r <= tol2
     const int* max_cg;        // [B]
     int* any_active;          // number of problems still iterating
+    Scale w0;                 // kb_dots: weight D on the first product of scaled problems
 };
 
 // Per chunk partial sums -> per problem FP64 sums (chunk order) -> op and CG bookkeeping.
@@ -174,8 +208,9 @@ __global__ void kb_dots(DotArgs d, const float2* __restrict__ a0, const float2* 
 #pragma unroll
     for (int w = 0; w < W; ++w) f[w] = 0.0f;
     if (!d.mask || d.mask[c.prob]) {
+        const bool dsc = d.w0.on(c.prob);
         CHUNK_LOOP(c, g) {
-            f[0] += brdot(a0[g], b0[g]);
+            f[0] += dsc ? d.w0.D[g] * brdot(a0[g], b0[g]) : brdot(a0[g], b0[g]);
             if constexpr (W > 1) f[1] += brdot(a1[g], b1[g]);
             if constexpr (W > 2) f[2] += brdot(a2[g], b2[g]);
         }
@@ -186,33 +221,43 @@ __global__ void kb_dots(DotArgs d, const float2* __restrict__ a0, const float2* 
     batch_finish<W>(d, s);
 }
 
-// CG start (D = I): r = -g - q, p = r, q = lambda p; r.r -> slots, mask = r.r > tol2.
+// (P)CG start: r = -g - q, p = z = M^-1 r with the Jacobi preconditioner M = (1 + lambda) D
+// of (G + lambda D) for scaled problems (M = I otherwise), q = lambda D p; r.z and r.r ->
+// slots, mask = r.r > tol2.
 __global__ void kb_cg_start(DotArgs d, const float2* __restrict__ g, float2* __restrict__ q, float2* __restrict__ r,
-                            float2* __restrict__ p, const float* __restrict__ lam) {
+                            float2* __restrict__ p, const float* __restrict__ lam, Scale sc) {
     const Chunk c = d.ch[blockIdx.x];
-    float f = 0.0f;
+    float frz = 0.0f, frr = 0.0f;
     if (!d.lm_active || d.lm_active[c.prob]) {
         const float l = lam[c.prob];
+        const bool dsc = sc.on(c.prob);
         CHUNK_LOOP(c, i) {
             const float2 gi = g[i], qi = q[i];
             const float2 ri = make_float2(-gi.x - qi.x, -gi.y - qi.y);
+            const float di = dsc ? sc.D[i] : 1.0f;
+            const float m = dsc ? 1.0f / ((1.0f + l) * di) : 1.0f;
+            const float2 zi = make_float2(m * ri.x, m * ri.y);
             r[i] = ri;
-            p[i] = ri;
-            q[i] = make_float2(l * ri.x, l * ri.y);
-            f += brdot(ri, ri);
+            p[i] = zi;
+            q[i] = make_float2(l * di * zi.x, l * di * zi.y);
+            frz += brdot(ri, zi);
+            frr += brdot(ri, ri);
         }
     }
-    double s[2] = {f, f};
+    double s[2] = {frz, frr};
     batch_finish<2>(d, s);
 }
 
-// x += alpha p, r -= alpha q; new r.r -> beta, mask = r.r > tol2 and iterations < max.
+// x += alpha p, r -= alpha q; new r.z (z = M^-1 r) and r.r -> beta, mask = r.r > tol2 and
+// iterations < max.
 __global__ void kb_cg_update(DotArgs d, float2* __restrict__ x, float2* __restrict__ r, const float2* __restrict__ p,
-                             const float2* __restrict__ q) {
+                             const float2* __restrict__ q, const float* __restrict__ lam, Scale sc) {
     const Chunk c = d.ch[blockIdx.x];
-    float f = 0.0f;
+    float frz = 0.0f, frr = 0.0f;
     if (d.mask[c.prob]) {
         const float alpha = (float)d.sc[(size_t)c.prob * S_COUNT + S_ALPHA];
+        const float l1 = 1.0f + lam[c.prob];
+        const bool dsc = sc.on(c.prob);
         CHUNK_LOOP(c, i) {
             const float2 pi = p[i], qi = q[i];
             float2 xi = x[i], ri = r[i];
@@ -222,25 +267,31 @@ __global__ void kb_cg_update(DotArgs d, float2* __restrict__ x, float2* __restri
             ri.y -= alpha * qi.y;
             x[i] = xi;
             r[i] = ri;
-            f += brdot(ri, ri);
+            const float rr = brdot(ri, ri);
+            frr += rr;
+            frz += dsc ? rr / (l1 * sc.D[i]) : rr;
         }
     }
-    double s[2] = {f, f};
+    double s[2] = {frz, frr};
     batch_finish<2>(d, s);
 }
 
-// p = r + beta p, q = lambda p (the next product's damping term).
+// p = M^-1 r + beta p, q = lambda D p (the next product's damping term).
 __global__ void kb_cg_direction(const Chunk* ch, const int* mask, const double* sc, const float2* __restrict__ r,
-                                float2* __restrict__ p, float2* __restrict__ q, const float* __restrict__ lam) {
+                                float2* __restrict__ p, float2* __restrict__ q, const float* __restrict__ lam,
+                                Scale dsc_) {
     const Chunk c = ch[blockIdx.x];
     if (!mask[c.prob]) return;
     const float beta = (float)sc[(size_t)c.prob * S_COUNT + S_BETA];
     const float l = lam[c.prob];
+    const bool dsc = dsc_.on(c.prob);
     CHUNK_LOOP(c, i) {
         const float2 ri = r[i], pi = p[i];
-        const float2 pn = make_float2(ri.x + beta * pi.x, ri.y + beta * pi.y);
+        const float di = dsc ? dsc_.D[i] : 1.0f;
+        const float m = dsc ? 1.0f / ((1.0f + l) * di) : 1.0f;
+        const float2 pn = make_float2(m * ri.x + beta * pi.x, m * ri.y + beta * pi.y);
         p[i] = pn;
-        q[i] = make_float2(l * pn.x, l * pn.y);
+        q[i] = make_float2(l * di * pn.x, l * di * pn.y);
     }
 }
 
@@ -303,6 +354,12 @@ struct ptylm_batch {
     float2 *z = nullptr, *grad = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *trial = nullptr;
     float2* ref = nullptr;               // concatenated reference objects (lm_solve)
     uint8_t* pix = nullptr;              // concatenated error masks (lm_solve)
+    float* D = nullptr;                  // [total] closed-form GGN diagonals (PLM scaling)
+    unsigned* dmax = nullptr;            // [B] their maxima (float bits)
+    int* scaled = nullptr;               // [B] problems whose LM runs with D = Dg(G)
+    float* dfloor = nullptr;             // [B] floor of each problem's diagonal, relative to its maximum
+    int* pos_first = nullptr;            // [B + 1] prefix sums of the position counts
+    int total_pos = 0;
 
     // pinned host mirrors
     double* h_scal = nullptr;            // [B][S_COUNT]
@@ -444,8 +501,11 @@ DotArgs dot_args(ptylm_batch* bt, int* mask, int dst, int op, int post = POST_NO
     d.tol2 = bt->tol2;
     d.max_cg = bt->max_cg;
     d.any_active = bt->any_active;
+    d.w0 = Scale{nullptr, nullptr};
     return d;
 }
+
+Scale scale_of(ptylm_batch* bt) { return Scale{bt->D, bt->scaled}; }
 
 ptylm_status vec_ok(ptylm_batch* bt) {
     ++bt->launches;
@@ -493,6 +553,23 @@ ptylm_status set_tiles(ptylm_batch* bt, int le32, int le64) {
     return PTYLM_OK;
 }
 
+// Closed-form Dg(G) of the problems in `mask` at their linearisation point, each floored at
+// floors[b] times its maximum (host array of B values; 0: no floor).
+ptylm_status batch_diag(ptylm_batch* bt, const int* mask, const std::vector<float>& floors) {
+    kb_dzero<<<bt->n_chunks, BVEC_THREADS, 0, bt->stream>>>(bt->chunks, mask, bt->D);
+    BSTATUS_TRY(vec_ok(bt));
+    BCUDA_TRY(batch_diag_launch(bt->probs, bt->pos_first, bt->B, bt->total_pos, mask, bt->D, bt->stream));
+    ++bt->launches;
+    BCUDA_TRY(cudaMemcpyAsync(bt->dfloor, floors.data(), sizeof(float) * bt->B, cudaMemcpyHostToDevice, bt->stream));
+    BCUDA_TRY(cudaMemsetAsync(bt->dmax, 0, sizeof(unsigned) * bt->B, bt->stream));
+    kb_dmax<<<bt->n_chunks, BVEC_THREADS, 0, bt->stream>>>(bt->chunks, mask, bt->D, bt->dmax);
+    BSTATUS_TRY(vec_ok(bt));
+    kb_dfloor<<<bt->n_chunks, BVEC_THREADS, 0, bt->stream>>>(bt->chunks, mask, bt->dmax, bt->dfloor, bt->D);
+    BSTATUS_TRY(vec_ok(bt));
+    BCUDA_TRY(cudaStreamSynchronize(bt->stream));   // floors is a pageable host buffer
+    return PTYLM_OK;
+}
+
 ptylm_status read_f_and_scalars(ptylm_batch* bt) {
     BCUDA_TRY(cudaMemcpyAsync(bt->h_f, bt->f, sizeof(double) * 2 * bt->B, cudaMemcpyDeviceToHost, bt->stream));
     BCUDA_TRY(cudaMemcpyAsync(bt->h_scal, bt->scal, sizeof(double) * S_COUNT * bt->B, cudaMemcpyDeviceToHost,
@@ -508,10 +585,10 @@ ptylm_status cg_iteration(ptylm_batch* bt) {
                                                               bt->q, nullptr, nullptr, nullptr, nullptr);
     BSTATUS_TRY(vec_ok(bt));                                                             // alpha
     kb_cg_update<<<bt->n_chunks, BVEC_THREADS, 0, bt->stream>>>(dot_args(bt, bt->cg_active, 0, OP_BETA, POST_UPDATE),
-                                                                bt->x, bt->r, bt->p, bt->q);
+                                                                bt->x, bt->r, bt->p, bt->q, bt->lam, scale_of(bt));
     BSTATUS_TRY(vec_ok(bt));                                                             // x, r, beta
     kb_cg_direction<<<bt->n_chunks, BVEC_THREADS, 0, bt->stream>>>(bt->chunks, bt->cg_active, bt->scal, bt->r, bt->p,
-                                                                   bt->q, bt->lam);
+                                                                   bt->q, bt->lam, scale_of(bt));
     return vec_ok(bt);                                                                   // p, q = lambda p
 }
 
@@ -649,6 +726,11 @@ ptylm_status ptylm_batch_init(ptylm_batch** out, int B, const ptylm_desc* descs,
     BA(bt->p, bt->total, "CG p");
     BA(bt->q, bt->total, "CG q");
     BA(bt->trial, bt->total, "trial point");
+    BA(bt->D, bt->total, "GGN diagonals");
+    BA(bt->dmax, B, "diagonal maxima");
+    BA(bt->scaled, B, "scaling flags");
+    BA(bt->dfloor, B, "diagonal floors");
+    BA(bt->pos_first, B + 1, "position offsets");
 #undef BA
     if (cudaMallocHost((void**)&bt->h_scal, sizeof(double) * S_COUNT * B) != cudaSuccess ||
         cudaMallocHost((void**)&bt->h_f, sizeof(double) * 2 * B) != cudaSuccess ||
@@ -682,6 +764,11 @@ ptylm_status ptylm_batch_init(ptylm_batch** out, int B, const ptylm_desc* descs,
         if ((s = balloc_t(bt, &pos, std::max(1, d.K), "positions")) != PTYLM_OK) return bail(s);
         if ((s = balloc_t(bt, &y, (size_t)std::max(1, d.K) * M, "measurements")) != PTYLM_OK) return bail(s);
         if ((s = balloc_t(bt, &ac, (size_t)std::max(1, d.K) * M, "frequency cache")) != PTYLM_OK) return bail(s);
+        // per-thread d2l sums: T = M / E threads per position, E >= 16 for every tile
+        float* trp = nullptr;
+        if ((s = balloc_t(bt, &trp, (size_t)std::max(1, d.K) * (M / 16), "diagonal partials")) != PTYLM_OK)
+            return bail(s);
+        p.trp = trp;
         if ((s = balloc_t(bt, &P, M, "probe")) != PTYLM_OK) return bail(s);
         std::vector<int32_t> hp(2 * (size_t)std::max(1, d.K), 0);
         if (d.K > 0 && cudaMemcpy(hp.data(), positions_dev[b], sizeof(int32_t) * 2 * d.K, cudaMemcpyDefault) != cudaSuccess) {
@@ -708,6 +795,9 @@ ptylm_status ptylm_batch_init(ptylm_batch** out, int B, const ptylm_desc* descs,
         p.a_cache = ac;
         p.P = P;
     }
+    std::vector<int> hpf(B + 1, 0);
+    for (int b = 0; b < B; ++b) hpf[b + 1] = hpf[b] + descs[b].K;
+    bt->total_pos = hpf[B];
     std::vector<float2> htw(BATCH_TW);
     int o = 0;
     for (int S : {32, 64, 128})
@@ -719,7 +809,9 @@ ptylm_status ptylm_batch_init(ptylm_batch** out, int B, const ptylm_desc* descs,
         cudaMemcpyAsync(bt->chunks, hch.data(), sizeof(Chunk) * hch.size(), cudaMemcpyHostToDevice, bt->stream) != cudaSuccess ||
         cudaMemcpyAsync(bt->chunk_first, hfirst.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice, bt->stream) != cudaSuccess ||
         cudaMemsetAsync(bt->counters, 0, sizeof(unsigned) * 3, bt->stream) != cudaSuccess ||
-        cudaMemsetAsync(bt->scal, 0, sizeof(double) * S_COUNT * B, bt->stream) != cudaSuccess) {
+        cudaMemsetAsync(bt->scal, 0, sizeof(double) * S_COUNT * B, bt->stream) != cudaSuccess ||
+        cudaMemcpyAsync(bt->pos_first, hpf.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice, bt->stream) != cudaSuccess ||
+        cudaMemsetAsync(bt->scaled, 0, sizeof(int) * B, bt->stream) != cudaSuccess) {
         cudaGetLastError();
         return bail(bfail(PTYLM_ERR_CUDA, "uploading batch tables"));
     }
@@ -784,10 +876,21 @@ ptylm_status ptylm_batch_ggn_matvec(ptylm_batch* bt, const ptylm_c64* v, ptylm_c
     BCUDA_TRY(cudaMemcpyAsync(bt->lam, hl.data(), sizeof(float) * bt->B, cudaMemcpyHostToDevice, bt->stream));
     const float2* V = reinterpret_cast<const float2*>(v);
     float2* O = reinterpret_cast<float2*>(out);
-    kb_damp<<<bt->n_chunks, BVEC_THREADS, 0, bt->stream>>>(bt->chunks, nullptr, bt->lam, V, O);
+    kb_damp<<<bt->n_chunks, BVEC_THREADS, 0, bt->stream>>>(bt->chunks, nullptr, bt->lam, V, O, Scale{nullptr, nullptr});
     BSTATUS_TRY(vec_ok(bt));
     BSTATUS_TRY(launch_batch(bt, BK_MATVEC, V, O, nullptr));
     BCUDA_TRY(cudaStreamSynchronize(bt->stream));   // hl is a pageable host buffer
+    return leave(bt);
+}
+
+ptylm_status ptylm_batch_ggn_diag(ptylm_batch* bt, float* D_out, double floor_rel) {
+    set_last_error("");
+    if (!bt || !D_out) return bfail(PTYLM_ERR_ARG, "batch and D_out must be non-NULL");
+    if (!(floor_rel >= 0.0) || !(floor_rel < 1.0)) return bfail(PTYLM_ERR_ARG, "floor_rel must be in [0, 1)");
+    if (!bt->has_lin) return bfail(PTYLM_ERR_STATE, "no linearisation point (ptylm_batch_forward_loss with cache=1)");
+    BSTATUS_TRY(enter(bt));
+    BSTATUS_TRY(batch_diag(bt, nullptr, std::vector<float>(bt->B, (float)floor_rel)));
+    BCUDA_TRY(cudaMemcpyAsync(D_out, bt->D, sizeof(float) * bt->total, cudaMemcpyDefault, bt->stream));
     return leave(bt);
 }
 
@@ -876,7 +979,9 @@ ptylm_status ptylm_batch_lm_solve(ptylm_batch* bt, ptylm_c64* O_inout, const pty
         const ptylm_lm_params& q = prm[b];
         if (q.max_outer < 0 || q.max_cg < 0 || !(q.kappa > 1.0) || !(q.mu0 > 0.0))
             return bfail(PTYLM_ERR_ARG, "problem %d: invalid LM parameters", b);
-        if (q.scaled || q.projected) return bfail(PTYLM_ERR_ARG, "problem %d: batches run Algorithm 1 with D = I", b);
+        if (q.projected) return bfail(PTYLM_ERR_ARG, "problem %d: batches run Algorithm 1 without Algorithm 2", b);
+        if (q.scaled && !(q.diag_floor >= 0.0 && q.diag_floor < 1.0))
+            return bfail(PTYLM_ERR_ARG, "problem %d: diag_floor must be in [0, 1)", b);
         if (q.surrogate_T < 0 || (q.surrogate_T > 0 && (!(q.surrogate0 > 0.0) || !(q.surrogate_end > 0.0))))
             return bfail(PTYLM_ERR_ARG, "problem %d: invalid surrogate schedule", b);
         if (q.O_ref) want_err = true;
@@ -884,6 +989,16 @@ ptylm_status ptylm_batch_lm_solve(ptylm_batch* bt, ptylm_c64* O_inout, const pty
     BSTATUS_TRY(enter(bt));
     const size_t zbytes = sizeof(float2) * bt->total;
     BCUDA_TRY(cudaMemcpyAsync(bt->z, O_inout, zbytes, cudaMemcpyDeviceToDevice, bt->stream));
+    // PLM problems (D = Dg(G), lambda = mu, Jacobi PCG; reading C10) next to LM ones (D = I)
+    std::vector<int> scaled_h(B);
+    std::vector<float> floors_h(B, 0.0f);
+    bool any_scaled = false;
+    for (int b = 0; b < B; ++b) {
+        scaled_h[b] = prm[b].scaled ? 1 : 0;
+        floors_h[b] = prm[b].scaled ? (float)prm[b].diag_floor : 0.0f;
+        any_scaled |= scaled_h[b] != 0;
+    }
+    BSTATUS_TRY(upload_mask(bt, bt->scaled, scaled_h));
     BCUDA_TRY(cudaMemsetAsync(bt->x, 0, zbytes, bt->stream));
     if (want_err) {
         if (!bt->ref) {
@@ -951,6 +1066,18 @@ ptylm_status ptylm_batch_lm_solve(ptylm_batch* bt, ptylm_c64* O_inout, const pty
             kb_dots<1><<<bt->n_chunks, BVEC_THREADS, 0, bt->stream>>>(dot_args(bt, bt->relin, S_GG, OP_STORE), bt->grad,
                                                                       bt->grad, nullptr, nullptr, nullptr, nullptr);
             BSTATUS_TRY(vec_ok(bt));
+            if (any_scaled) {
+                std::vector<int> rs(B);
+                bool any_rs = false;
+                for (int b = 0; b < B; ++b) {
+                    rs[b] = relin[b] && scaled_h[b];
+                    any_rs |= rs[b] != 0;
+                }
+                if (any_rs) {   // Dg(G) at the new linearisation point (the accept mask is free here)
+                    BSTATUS_TRY(upload_mask(bt, bt->accept, rs));
+                    BSTATUS_TRY(batch_diag(bt, bt->accept, floors_h));
+                }
+            }
             BSTATUS_TRY(read_f_and_scalars(bt));
             for (int b = 0; b < B; ++b) {
                 if (!relin[b]) continue;
@@ -980,7 +1107,8 @@ ptylm_status ptylm_batch_lm_solve(ptylm_batch* bt, ptylm_c64* O_inout, const pty
                 hm[b] = 0;
                 continue;
             }
-            lambda[b] = mu[b] * std::pow(std::sqrt(dl2[b]), prm[b].nu);
+            // lambda = mu ||grad_zeta l||^nu (D = I) or mu (D = Dg(G)), Algorithm 1
+            lambda[b] = scaled_h[b] ? mu[b] : mu[b] * std::pow(std::sqrt(dl2[b]), prm[b].nu);
             hl[b] = (float)lambda[b];
             const double gnorm = std::sqrt(gg[b]);
             const double tol = std::min(prm[b].beta, std::sqrt(gnorm)) * gnorm;
@@ -992,12 +1120,13 @@ ptylm_status ptylm_batch_lm_solve(ptylm_batch* bt, ptylm_c64* O_inout, const pty
         BCUDA_TRY(cudaMemcpyAsync(bt->tol2, ht.data(), sizeof(double) * B, cudaMemcpyHostToDevice, bt->stream));
         BCUDA_TRY(cudaMemcpyAsync(bt->max_cg, hm.data(), sizeof(int) * B, cudaMemcpyHostToDevice, bt->stream));
         // ---- truncated CG on (G + lambda I) x = -g, warm-started from x (C8) ----
-        kb_damp<<<bt->n_chunks, BVEC_THREADS, 0, bt->stream>>>(bt->chunks, bt->lm_active, bt->lam, bt->x, bt->q);
+        kb_damp<<<bt->n_chunks, BVEC_THREADS, 0, bt->stream>>>(bt->chunks, bt->lm_active, bt->lam, bt->x, bt->q,
+                                                               scale_of(bt));
         BSTATUS_TRY(vec_ok(bt));
         BSTATUS_TRY(launch_batch(bt, BK_MATVEC, bt->x, bt->q, bt->lm_active));              // q = (G + lambda) x
         for (int b = 0; b < B; ++b) matvecs[b] += active[b];
         kb_cg_start<<<bt->n_chunks, BVEC_THREADS, 0, bt->stream>>>(dot_args(bt, bt->cg_active, 0, OP_START, POST_START),
-                                                                   bt->grad, bt->q, bt->r, bt->p, bt->lam);
+                                                                   bt->grad, bt->q, bt->r, bt->p, bt->lam, scale_of(bt));
         BSTATUS_TRY(vec_ok(bt));
         for (int it = 0; it < max_cg_all;) {
             BCUDA_TRY(cudaMemcpyAsync(bt->h_int, bt->any_active, sizeof(int), cudaMemcpyDeviceToHost, bt->stream));
@@ -1022,7 +1151,9 @@ ptylm_status ptylm_batch_lm_solve(ptylm_batch* bt, ptylm_c64* O_inout, const pty
         kb_axpy<<<bt->n_chunks, BVEC_THREADS, 0, bt->stream>>>(bt->chunks, bt->lm_active, bt->z, bt->x, bt->trial);
         BSTATUS_TRY(vec_ok(bt));
         BSTATUS_TRY(batch_forward(bt, bt->trial, 0, bt->lm_active));
-        kb_dots<3><<<bt->n_chunks, BVEC_THREADS, 0, bt->stream>>>(dot_args(bt, bt->lm_active, S_DD, OP_STORE), bt->x,
+        DotArgs dd_args = dot_args(bt, bt->lm_active, S_DD, OP_STORE);
+        dd_args.w0 = scale_of(bt);   // Delta^T D Delta for the scaled problems
+        kb_dots<3><<<bt->n_chunks, BVEC_THREADS, 0, bt->stream>>>(dd_args, bt->x,
                                                                   bt->x, bt->x, bt->grad, bt->x, bt->r);
         BSTATUS_TRY(vec_ok(bt));
         BSTATUS_TRY(read_f_and_scalars(bt));

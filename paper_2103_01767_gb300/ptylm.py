@@ -124,6 +124,7 @@ def load_library():
             lib.ptylm_batch_lm_solve.argtypes = [vp, vp, P(LMParams), P(LMStats)]
             lib.ptylm_batch_tune.argtypes = [vp, P(i), P(ctypes.c_float), i]
             lib.ptylm_batch_set_schedule.argtypes = [vp, i]
+            lib.ptylm_batch_ggn_diag.argtypes = [vp, vp, d]
             lib.ptylm_batch_profile_read.argtypes = [vp, P(ctypes.c_longlong)]
             lib.ptylm_batch_destroy.argtypes = [vp]
             u64 = ctypes.c_uint64
@@ -145,7 +146,8 @@ def load_library():
                 getattr(lib, name).restype = i
             for name in ("ptylm_batch_init", "ptylm_batch_forward_loss", "ptylm_batch_gradient",
                          "ptylm_batch_ggn_matvec", "ptylm_batch_lm_solve", "ptylm_batch_tune",
-                         "ptylm_batch_set_schedule", "ptylm_batch_profile_read", "ptylm_batch_destroy"):
+                         "ptylm_batch_set_schedule", "ptylm_batch_profile_read", "ptylm_batch_destroy",
+                         "ptylm_batch_ggn_diag"):
                 getattr(lib, name).restype = i
             for name in ("lm_init", "forward_loss", "gradient", "jvp", "jtvp", "ggn_matvec",
                          "lm_solve", "lm_destroy", "forward_intensity", "ptylm_set_measurements",
@@ -546,6 +548,15 @@ def batch_tune(batch: Batch):
     ms = (ctypes.c_float * N_SCHEDULES)()
     _check(load_library().ptylm_batch_tune(batch.handle, ctypes.byref(choice), ms, N_SCHEDULES))
     return choice.value, list(ms)
+
+
+def batch_ggn_diag(batch: Batch, D_out, floor_rel: float = 0.0) -> None:
+    """Closed-form GGN diagonal of every problem at the batch's linearisation point into the
+    float32 vector D_out (batch layout, total elements)."""
+    import torch
+    if not isinstance(D_out, torch.Tensor) or D_out.dtype != torch.float32 or D_out.numel() < batch.total:
+        raise ValueError("D_out must be a float32 tensor of at least batch.total elements")
+    _check(load_library().ptylm_batch_ggn_diag(batch.handle, _ptr(D_out), float(floor_rel)))
 
 
 def batch_set_schedule(batch: Batch, choice: int) -> None:

@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 from paper_2103_01767_gb300 import synth
+from tests import parity
 from tests.problems import make_case, rel_err
 from tests.fp32_eval import ORDERS, evaluations
 from tests.test_gpu_parity import compare, fp32_conditioning, fp32_model
@@ -150,6 +151,70 @@ def test_every_schedule_gives_the_same_product(lib, batch):
         for s in (0, 6, 12, 18):
             compare(f"(G + 0.2 I) v[{b}] schedule {s}", views[s][b], ref, c,
                     lambda A, B: oracle.ggn_matvec(pb, A, B, lam=0.2), (X, vb), lambda: ev)
+
+
+@pytest.mark.parametrize("schedule", TILES)
+def test_batch_ggn_diag(lib, batch, schedule):
+    """App. B closed form per problem (FP32 sums and float atomics, per-problem floor) against
+    the oracle's orc_ggn_diag, under both FFT tiles (the per-thread d2l sums follow the tile)."""
+    bt, cases, points, O = batch
+    lib.batch_set_schedule(bt, schedule)
+    lib.batch_forward_loss(bt, O, cache=1)
+    for floor in (0.0, 1e-6):
+        D = torch.empty(bt.total, dtype=torch.float32, device="cuda")
+        lib.batch_ggn_diag(bt, D, floor)
+        Dh = D.cpu().numpy().astype(np.float64)
+        for b, (c, X) in enumerate(zip(cases, points)):
+            pb = c.problem()
+            diag_at = lambda A: oracle.ggn_diag(pb, A, floor_rel=floor)[0].ravel()
+            ref = diag_at(X)
+            got = Dh[bt.offsets[b]:bt.offsets[b + 1]]
+            if c.loss == 0:
+                parity.check(f"batch Dg(G)[{b}] (floor {floor})", got, ref)
+                parity.check(f"batch Dg(G)[{b}] (floor {floor})", got, ref, norm="max")
+            else:
+                tol = max(TOL, 2.0 * fp32_conditioning(diag_at, c.m, X))
+                parity.check(f"batch Dg(G)[{b}] (floor {floor})", got, ref, tol, basis="2 x FP32 conditioning")
+
+
+def test_batch_plm_reaches_accuracy_like_single_problem_plm(lib):
+    """PLM (D = Dg(G), lambda = mu, Jacobi PCG) next to LM in one batch: the scaled problems
+    reach 1e-3 object error in a number of outer iterations within 3 of the single-problem
+    lm_solve(scaled=1) and of the oracle's PLM for the smallest; the LM problem of the same
+    batch still matches its single-problem run."""
+    specs = [(128, 32, 8, 8), (192, 64, 6, 16), (256, 128, 4, 32)]
+    scaled = [1, 1, 0]
+    cases, probs, O0, refs, masks = [], [], [], [], []
+    for i, (n, m, grid, step) in enumerate(specs):
+        c = make_case(n, m, loss=0, seed=140 + i, grid=grid, step=step, radius=0.3125 * m)
+        cases.append(c)
+        probs.append(dict(ny=n, nx=n, m=m, positions=torch.from_numpy(c.pos).cuda(), y=f32(c.y), probe=c64(c.P),
+                          loss=0, background=c.b))
+        O0.append(synth.flat_object(n))
+        refs.append(c64(c.O_true))
+        masks.append(torch.from_numpy(synth.illumination_mask(n, c.P, c.pos, 0.1).astype(np.uint8)).cuda())
+    bt = lib.batch_init(probs)
+    O = torch.cat([c64(o).reshape(-1) for o in O0])
+    params = []
+    for b in range(len(specs)):
+        p = lib.default_lm_params(0)
+        p.scaled = scaled[b]
+        params.append(p)
+    st, infos = lib.batch_lm_solve(bt, O, params, hist_len=80, O_refs=refs, masks=masks, max_outer=80,
+                                   target_err=1e-3)
+    ov = bt.views(O)
+    for b, c in enumerate(cases):
+        mask = synth.illumination_mask(c.n, c.P, c.pos, 0.1)
+        assert oracle.object_error(host(ov[b]), c.O_true, mask) <= 1e-3, b
+        ctx = lib.lm_init(c.n, c.n, c.m, c.m, torch.from_numpy(c.pos).cuda(), f32(c.y), 0, c.b)
+        _, single = lib.lm_solve(ctx, c64(O0[b]), c64(c.P), hist_len=80, O_ref=refs[b], mask=masks[b], max_outer=80,
+                                 target_err=1e-3, scaled=scaled[b])
+        assert abs(infos[b]["n_outer"] - single["n_outer"]) <= 3, (b, infos[b]["n_outer"], single["n_outer"])
+        assert infos[b]["err"][-1] <= 1e-3
+    mask0 = synth.illumination_mask(128, cases[0].P, cases[0].pos, 0.1)
+    _, _, info_ref = oracle.lm_solve2(cases[0].problem(), O0[0], O_ref=cases[0].O_true, mask=mask0, scaled=1,
+                                      max_outer=80, target_err=1e-3)
+    assert abs(infos[0]["n_outer"] - info_ref["n_outer"]) <= 3, (infos[0]["n_outer"], info_ref["n_outer"])
 
 
 def test_batch_lm_reaches_accuracy_like_single_problem_lm(lib):
