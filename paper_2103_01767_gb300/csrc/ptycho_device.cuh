@@ -202,9 +202,31 @@ struct GlobalProbe {
     const float2* pr;
     __device__ __forceinline__ GlobalProbe(const float2* P, int tid)
         : pr(P + (tid >> G::LOG_S) * G::S + (tid & (G::S - 1))) {}
-    __device__ __forceinline__ void load8(float2* pv, int a0) const {
+    template <class Dep>
+    __device__ __forceinline__ void load8(float2* pv, int a0, const Dep*) const {
 #pragma unroll
         for (int i = 0; i < 8; ++i) pv[i] = pr[G::BX * G::S * (a0 + i)];  // plain load: an __ldg is hoisted out of the position loop
+    }
+};
+
+// The same probe values through read-only loads written as non-volatile inline PTX whose
+// extra operand is an address of the current position (`dep`): they cannot be hoisted out
+// of the position loop, but the compiler schedules them freely.  In the error-metric kernels
+// this ordering is faster than GlobalProbe's (trial loss 252 -> 226 us, linearisation
+// 442 -> 432 us at 1024^2 / 128^2 / 3600); in the GGN product it is slower (325 -> 340 us),
+// so the product keeps GlobalProbe.
+template <class G>
+struct ScheduledProbe {
+    const float2* pr;
+    __device__ __forceinline__ ScheduledProbe(const float2* P, int tid)
+        : pr(P + (tid >> G::LOG_S) * G::S + (tid & (G::S - 1))) {}
+    template <class Dep>
+    __device__ __forceinline__ void load8(float2* pv, int a0, const Dep* dep) const {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float2* q = pr + G::BX * G::S * (a0 + i);
+            asm("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(pv[i].x), "=f"(pv[i].y) : "l"(q), "l"(dep));
+        }
     }
 };
 
@@ -222,7 +244,7 @@ __device__ __forceinline__ void gather_times_probe(float2* v, const float2* __re
         float2 pv[8], av[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) av[i] = ldg_stream(src + row_step * (a0 + i));
-        ps.load8(pv, a0);
+        ps.load8(pv, a0, src);
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[a0 + i] = cmul(pv[i], av[i]);
         sched_fence();
@@ -245,7 +267,7 @@ __device__ __forceinline__ void scatter_times_conj_probe(const float2* v, float2
 #pragma unroll
     for (int a0 = 0; a0 < G::E; a0 += 8) {
         float2 pv[8];
-        ps.load8(pv, a0);
+        ps.load8(pv, a0, dst);
 #pragma unroll
         for (int i = 0; i < 8; ++i) red_add_c64(dst + row_step * (a0 + i), cmulc(v[a0 + i], pv[i]));
         sched_fence();
@@ -276,7 +298,7 @@ __device__ __forceinline__ void scatter_then_gather(float2* v, float2* out, cons
         float2 pv[8], av[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) av[i] = ldg_stream(src + row_step * (a0 + i));
-        ps.load8(pv, a0);
+        ps.load8(pv, a0, src);
 #pragma unroll
         for (int i = 0; i < 8; ++i) red_add_c64(dst + row_step * (a0 + i), cmulc(v[a0 + i], pv[i]));
 #pragma unroll

@@ -97,19 +97,20 @@ k_forward(FwdArgs a) {
     // before the FFT, instead of waiting on 32 dependent loads per thread after it.
     constexpr bool STAGE_Y = forward_stages_y<LS, CACHE, INTENSITY, JOINT, MAG>();
     float* sy = reinterpret_cast<float*>(c.sm + G::M);
+    const ScheduledProbe<G> probe(a.P, c.tid);
     float2 v[32];
     int k = blockIdx.x * G::TEAMS + c.team;
     if constexpr (FUSED) {
         if (k < a.K) {
             const int2 rc = a.pos[k];
-            gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
+            gather_times_probe<G>(v, a.O, probe, a.nx, rc.x, rc.y, c.tid);
         }
     }
     for (; k < a.K; k += stride) {
         const int2 rc = a.pos[k];
         const float* yk = a.y + (size_t)k * G::M + c.tid;  // measurements in team-register order
         // the gather's loads go first: the measurement copies are only waited for after the FFT
-        if constexpr (!FUSED) gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
+        if constexpr (!FUSED) gather_times_probe<G>(v, a.O, probe, a.nx, rc.x, rc.y, c.tid);
         if constexpr (STAGE_Y) cp_async_tile(sy, a.y + (size_t)k * G::M, sizeof(float) * G::M, c.tid, G::T);
         else if constexpr (!INTENSITY && !MAG) prefetch_tile_l2(a.y + (size_t)k * G::M, sizeof(float) * G::M, c.tid);
         float sl = 0.0f, sd = 0.0f;
@@ -149,12 +150,12 @@ k_forward(FwdArgs a) {
                 const int kn = k + stride;
                 if (kn < a.K) {
                     const int2 rn = a.pos[kn];
-                    scatter_then_gather<G>(v, a.out, a.O, a.P, a.nx, rc.x, rc.y, rn.x, rn.y, c.tid);
+                    scatter_then_gather<G>(v, a.out, a.O, probe, a.nx, rc.x, rc.y, rn.x, rn.y, c.tid);
                 } else {
-                    scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
+                    scatter_times_conj_probe<G>(v, a.out, probe, a.nx, rc.x, rc.y, c.tid);
                 }
             } else {
-                scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
+                scatter_times_conj_probe<G>(v, a.out, probe, a.nx, rc.x, rc.y, c.tid);
             }
             if constexpr (JOINT)
                 accumulate_probe_adjoint<G>(v, a.outP_part + (size_t)(blockIdx.x * G::TEAMS + c.team) * G::M,
