@@ -313,6 +313,40 @@ __device__ __forceinline__ void scatter_then_gather(float2* v, float2* out, cons
     scatter_then_gather<G>(v, out, A, GlobalProbe<G>(P, tid), nx, r0, c0, r1, c1, tid);
 }
 
+// Per-detector-pixel values between a thread's pass-3 layout (element e of thread t is the
+// frequency (freq_ky(t), freq_kx(t, e))) and natural [S][S] order in global memory, through the
+// team's exchange buffer viewed as S rows of S + 1 floats: a warp's lanes hold consecutive
+// rows, so the padding keeps the scattered shared-memory accesses conflict-free, and the
+// global side moves whole rows (coalesced) instead of one float per row and lane.
+// Both start with a team barrier (the buffer must be free) and end with one; the caller
+// synchronises the team again before the buffer's next use.
+template <class G>
+__device__ __forceinline__ void store_natural(const float* val, float* smf, float* out_k, int tid) {
+    team_sync<G>();
+    const int ky = freq_ky<G>(tid);
+#pragma unroll
+    for (int e = 0; e < G::E; ++e) smf[ky * (G::S + 1) + freq_kx<G>(tid, e)] = val[e];
+    team_sync<G>();
+#pragma unroll 8
+    for (int i = 0; i < G::E; ++i) {
+        const int idx = i * G::T + tid;
+        out_k[idx] = smf[(idx >> G::LOG_S) * (G::S + 1) + (idx & (G::S - 1))];
+    }
+}
+template <class G>
+__device__ __forceinline__ void load_natural(const float* __restrict__ in_k, float* smf, float* val, int tid) {
+    team_sync<G>();
+#pragma unroll 8
+    for (int i = 0; i < G::E; ++i) {
+        const int idx = i * G::T + tid;
+        smf[(idx >> G::LOG_S) * (G::S + 1) + (idx & (G::S - 1))] = __ldg(in_k + idx);
+    }
+    team_sync<G>();
+    const int ky = freq_ky<G>(tid);
+#pragma unroll
+    for (int e = 0; e < G::E; ++e) val[e] = smf[ky * (G::S + 1) + freq_kx<G>(tid, e)];
+}
+
 // Joint gather (Eq. jac_ampl with both blocks): v[a] = P[y][x] A[r0+y][c0+x] + B[y][x] C[r0+y][c0+x],
 // i.e. P . S_k dO + dP . S_k O for the direction (A, B) = (dO, dP) at the object C.
 template <class G>

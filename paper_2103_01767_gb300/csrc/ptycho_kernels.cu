@@ -167,6 +167,7 @@ k_forward(FwdArgs a) {
                 __syncthreads();
             }
             if constexpr (MAG || INTENSITY) {
+                float hv[32];
 #pragma unroll
                 for (int e = 0; e < 32; ++e) {
                     const float2 ps = v[e] * invS;
@@ -174,12 +175,13 @@ k_forward(FwdArgs a) {
                     if constexpr (MAG) {
                         // zeta in natural order; the unit phasor u = psihat / zeta in team order
                         const float r = rsqrtf(h);
-                        a.out_real[(size_t)k * G::M + ky * G::S + freq_kx<G>(c.tid, e)] = h * r;
+                        hv[e] = h * r;
                         if (a.a_cache) a.a_cache[(size_t)k * G::M + e * G::T + c.tid] = ps * r;
                     } else {
-                        a.out_real[(size_t)k * G::M + ky * G::S + freq_kx<G>(c.tid, e)] = h;
+                        hv[e] = h;
                     }
                 }
+                store_natural<G>(hv, reinterpret_cast<float*>(c.sm), a.out_real + (size_t)k * G::M, c.tid);
             } else {
                 auto pixels = [&](auto loss_c) {
                     constexpr int LOSS = decltype(loss_c)::value;
@@ -320,15 +322,15 @@ k_jvp(AdjArgs a) {
         if constexpr (JOINT) gather_joint<G>(v, a.V, a.P, a.VP, a.O, a.nx, rc.x, rc.y, c.tid);
         else gather_times_probe<G>(v, a.V, a.P, a.nx, rc.x, rc.y, c.tid);
         team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
-        float* ok = a.out_real + (size_t)k * G::M + freq_ky<G>(c.tid) * G::S;
+        float jv[32];
 #pragma unroll
         for (int e = 0; e < 32; ++e) {
-            const int kx = freq_kx<G>(c.tid, e);
             const float2 ps = slot[e * G::T] * invS;
             const float2 dps = v[e] * invS;
             const float inv_zeta = rsqrtf(ps.x * ps.x + ps.y * ps.y + a.b);
-            ok[kx] = (ps.x * dps.x + ps.y * dps.y) * inv_zeta;
+            jv[e] = (ps.x * dps.x + ps.y * dps.y) * inv_zeta;
         }
+        store_natural<G>(jv, reinterpret_cast<float*>(c.sm), a.out_real + (size_t)k * G::M, c.tid);
         team_sync<G>();
     }
 }
@@ -384,13 +386,14 @@ k_jvp_phasor(AdjArgs a, const float2* __restrict__ u) {
         if constexpr (JOINT) gather_joint<G>(v, a.V, a.P, a.VP, a.O, a.nx, rc.x, rc.y, c.tid);
         else gather_times_probe<G>(v, a.V, a.P, a.nx, rc.x, rc.y, c.tid);
         team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
-        float* ok = a.out_real + (size_t)k * G::M + freq_ky<G>(c.tid) * G::S;
         const float2* uk = u + (size_t)k * G::M + c.tid;
+        float jv[32];
 #pragma unroll
         for (int e = 0; e < 32; ++e) {
             const float2 ue = __ldg(uk + e * G::T);
-            ok[freq_kx<G>(c.tid, e)] = (ue.x * v[e].x + ue.y * v[e].y) * invS;
+            jv[e] = (ue.x * v[e].x + ue.y * v[e].y) * invS;
         }
+        store_natural<G>(jv, reinterpret_cast<float*>(c.sm), a.out_real + (size_t)k * G::M, c.tid);
         team_sync<G>();
     }
 }
@@ -404,11 +407,12 @@ k_jtvp_phasor(AdjArgs a, const float2* __restrict__ u) {
     float2 v[32];
     for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
         const int2 rc = a.pos[k];
-        const float* wk = a.w + (size_t)k * G::M + freq_ky<G>(c.tid) * G::S;
         const float2* uk = u + (size_t)k * G::M + c.tid;
+        float wv[32];
+        load_natural<G>(a.w + (size_t)k * G::M, reinterpret_cast<float*>(c.sm), wv, c.tid);
 #pragma unroll
-        for (int e = 0; e < 32; ++e) v[e] = __ldg(uk + e * G::T) * (__ldg(wk + freq_kx<G>(c.tid, e)) * invS);
-        team_sync<G>();  // the previous position's last shared-memory reads are done
+        for (int e = 0; e < 32; ++e) v[e] = __ldg(uk + e * G::T) * (wv[e] * invS);
+        team_sync<G>();  // every thread's reads of the staged w are done
         team_fft_inv<G>(v, c.sm, c.tw, c.tid);
         scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
         if constexpr (JOINT)
