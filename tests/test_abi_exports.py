@@ -93,3 +93,30 @@ def test_noalloc_wrapper_rejects_bad_arguments_before_the_library():
     # well-typed host tensors are rejected too: the kernels would read host pointers
     with pytest.raises(ValueError, match="CUDA"):
         ptylm.ptylm_forward_loss_noalloc(n, n, m, good["positions"], good["y"], good["O"], good["P"], good["out"])
+
+
+def test_batch_schedule_table():
+    """The 24 autotuner schedules: index = order/positions schedule + 6 x (tile of the 32^2
+    problems + 2 x tile of the 64^2 problems), every combination once."""
+    from paper_2103_01767_gb300 import ptylm
+    seen = set()
+    for c in range(ptylm.N_SCHEDULES):
+        d = ptylm.schedule_desc(c)
+        assert d["order"] in (0, 1) and d["positions_per_team"] in (1, 2, 4)
+        assert d["values_per_thread_32"] in (16, 32) and d["values_per_thread_64"] in (16, 32)
+        seen.add(tuple(sorted(d.items())))
+    assert len(seen) == ptylm.N_SCHEDULES == 24
+    assert ptylm.schedule_desc(0) == {"order": 0, "positions_per_team": 1, "values_per_thread_32": 32,
+                                      "values_per_thread_64": 32}
+    assert ptylm.schedule_desc(18)["values_per_thread_32"] == 16 and ptylm.schedule_desc(18)["values_per_thread_64"] == 16
+
+
+def test_batch_calls_reject_null_handles():
+    """The batch entry points check their handles and arguments on the host."""
+    import ctypes
+    from paper_2103_01767_gb300 import build, ptylm
+    build.build()
+    lib = ptylm.load_library()
+    assert lib.ptylm_batch_ggn_diag(None, None, ctypes.c_double(0.0)) == ptylm.PTYLM_ERR_ARG
+    assert lib.ptylm_batch_set_schedule(None, 0) == ptylm.PTYLM_ERR_ARG
+    assert lib.ptylm_batch_tune(None, None, None, 0) == ptylm.PTYLM_ERR_ARG
