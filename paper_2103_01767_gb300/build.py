@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB_DIR = os.path.join(HERE, "_lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(LIB_DIR, "libptylm.so")
-SOURCES = ["ptycho_kernels.cu", "ptylm_abi.cu", "ptylm_noalloc.cu", "batch_kernels.cu", "ptylm_batch.cu", "learned_kernels.cu", "ptylm_learned.cu", "ptylm_peak.cu", "conv_tc.cu"]
+SOURCES = ["ptycho_kernels.cu", "ptylm_abi.cu", "ptylm_noalloc.cu", "batch_kernels.cu", "ptylm_batch.cu", "learned_kernels.cu", "ptylm_learned.cu", "ptylm_peak.cu", "conv_tc.cu", "conv_last.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

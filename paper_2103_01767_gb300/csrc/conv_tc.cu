@@ -103,29 +103,6 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// element offset of 8-channel chunk q at pixel (y, x) of image n in the chunk-major layouts
-__device__ __forceinline__ size_t chunk_at(int par, int C8, int H, int W, int n, int y, int x, int q) {
-    if (!par) return ((((size_t)n * C8 + q) * H + y) * W + x) * 8;
-    return (((((size_t)n * C8 + q) * 4 + ((y & 1) << 1) + (x & 1)) * (H >> 1) + (y >> 1)) * (W >> 1) + (x >> 1)) * 8;
-}
-
-__device__ __forceinline__ void store_pair8(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t o, const float* v) {
-    __align__(16) __nv_bfloat16 h[8], l[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) split_bf16(v[j], h[j], l[j]);
-    *reinterpret_cast<uint4*>(hi + o) = *reinterpret_cast<const uint4*>(h);
-    *reinterpret_cast<uint4*>(lo + o) = *reinterpret_cast<const uint4*>(l);
-}
-
-// m[j] = (hi + lo > 0) of 8 channels
-__device__ __forceinline__ void load_mask8(const __nv_bfloat16* hi, const __nv_bfloat16* lo, size_t o, bool* m) {
-    __align__(16) __nv_bfloat16 h[8], l[8];
-    *reinterpret_cast<uint4*>(h) = *reinterpret_cast<const uint4*>(hi + o);
-    *reinterpret_cast<uint4*>(l) = *reinterpret_cast<const uint4*>(lo + o);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) m[j] = __bfloat162float(h[j]) + __bfloat162float(l[j]) > 0.0f;
-}
-
 // 16 channels from ch0 of pixel (y, x) into the output pair (and its parity copy)
 __device__ __forceinline__ void store_out16(const ConvArgs& a, int n, int y, int x, int ch0, const float* v) {
     const int C8 = a.oC >> 3;

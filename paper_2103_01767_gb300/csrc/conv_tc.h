@@ -63,6 +63,22 @@ cudaError_t tc_conv_wgrad(const TcLayer& L, const Act2& x, const Act2& dy, float
                           unsigned spin, int num_sms, cudaStream_t st);
 size_t tc_wgrad_workspace(const TcLayer& L, int N, int num_sms);
 
+// The decoder's last layer (x2 nearest upsampling, 3x3 convolution to Co <= 2 channels) on
+// the CUDA cores, with the same operands and results as the tc_conv_* calls above: forward
+// into FP32 planes y32[N][Co][2H][2W]; input gradient dx (plain pair, plus its parity copy
+// when dx.phi is set) masked by act > 0, with tc_last_bias_parts(L, N) partial sums of dx
+// per channel in db_part[i][Ci]; weight gradient dw[Co][Ci][3][3] through ws
+// (tc_last_wgrad_workspace(L, N) floats).  tc_last_supported: the shapes these kernels take
+// (Co <= 2, Ci a power of two in 8 .. 256, input side a multiple of 16).
+bool tc_last_supported(const TcLayer& L);
+cudaError_t tc_last_forward(const TcLayer& L, const Act2& x, const __nv_bfloat16* wf, const float* bias, float* y32,
+                            cudaStream_t st);
+cudaError_t tc_last_backward_data(const TcLayer& L, const Act2& dy, const __nv_bfloat16* wf, const Act2& act,
+                                  const Act2& dx, float* db_part, int* n_part, cudaStream_t st);
+int tc_last_bias_parts(const TcLayer& L, int N);
+cudaError_t tc_last_wgrad(const TcLayer& L, const Act2& x, const Act2& dy, float* ws, float* dw, cudaStream_t st);
+size_t tc_last_wgrad_workspace(const TcLayer& L, int N);
+
 // db[c] = sum_i part[i][c] in a fixed order; tmp: kBiasSlices * C floats
 constexpr int kBiasSlices = 64;
 cudaError_t tc_bias_reduce(const float* part, int n_part, int C, float* tmp, float* db, cudaStream_t st);

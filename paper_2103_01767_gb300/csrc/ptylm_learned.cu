@@ -63,6 +63,7 @@ uint64_t splitmix64(uint64_t& s) {
 struct ptylm_net {
     int m = 0, widths[3] = {0, 0, 0}, max_batch = 0, num_sms = 0;
     TcLayer L[NL];
+    bool last_cuda_cores = false;      // the last layer runs on the CUDA cores (conv_last.cu)
     long w_off[NL], b_off[NL], n_params = 0;
     cudaStream_t stream = nullptr;
     std::vector<void*> allocs;
@@ -147,8 +148,11 @@ ptylm_status forward(ptylm_net* n, const float* X, int N) {
     Act2 in = x0;
     for (int l = 0; l < NL; ++l) {
         const Act2 y = l < NL - 1 ? batch(n->act[l], N) : Act2{};
-        LCUDA_TRY(tc_conv_forward(n->L[l], in, n->wf[l], n->params + n->b_off[l], l < NL - 1 ? &y : nullptr, n->out, n->err,
-                                  kConvSpin, n->num_sms, n->stream));
+        if (l == NL - 1 && n->last_cuda_cores)
+            LCUDA_TRY(tc_last_forward(n->L[l], in, n->wf[l], n->params + n->b_off[l], n->out, n->stream));
+        else
+            LCUDA_TRY(tc_conv_forward(n->L[l], in, n->wf[l], n->params + n->b_off[l], l < NL - 1 ? &y : nullptr, n->out,
+                                      n->err, kConvSpin, n->num_sms, n->stream));
         in = y;
     }
     return PTYLM_OK;
@@ -163,10 +167,16 @@ ptylm_status loss_grad(ptylm_net* n, const float* X, const float* T, int N, doub
     for (int l = NL - 1; l >= 0; --l) {
         const Act2 in = l == 0 ? batch(n->x0, N) : batch(n->act[l - 1], N);
         const Act2 g = batch(n->g[l], N);
-        LCUDA_TRY(tc_conv_wgrad(n->L[l], in, g, n->ws, n->grads + n->w_off[l], n->err, kConvSpin, n->num_sms, n->stream));
+        const bool cc = l == NL - 1 && n->last_cuda_cores;
+        if (cc) LCUDA_TRY(tc_last_wgrad(n->L[l], in, g, n->ws, n->grads + n->w_off[l], n->stream));
+        else LCUDA_TRY(tc_conv_wgrad(n->L[l], in, g, n->ws, n->grads + n->w_off[l], n->err, kConvSpin, n->num_sms, n->stream));
         if (l > 0) {
-            LCUDA_TRY(tc_conv_backward_data(n->L[l], g, n->wb[l], in, batch(n->g[l - 1], N), n->db_part, &parts, n->err,
-                                            kConvSpin, n->num_sms, n->stream));
+            if (cc)
+                LCUDA_TRY(tc_last_backward_data(n->L[l], g, n->wf[l], in, batch(n->g[l - 1], N), n->db_part, &parts,
+                                                n->stream));
+            else
+                LCUDA_TRY(tc_conv_backward_data(n->L[l], g, n->wb[l], in, batch(n->g[l - 1], N), n->db_part, &parts,
+                                                n->err, kConvSpin, n->num_sms, n->stream));
             LCUDA_TRY(tc_bias_reduce(n->db_part, parts, n->L[l].Ci, n->db_tmp, n->grads + n->b_off[l - 1], n->stream));
         }
     }
@@ -239,12 +249,17 @@ ptylm_status ptylm_net_create(ptylm_net** out, int m, const int* widths, int max
         off += co[l];
     }
     n->n_params = off;
+    n->last_cuda_cores = tc_last_supported(n->L[NL - 1]);
     ptylm_status s;
     const size_t img = (size_t)max_batch * 2 * m * m;
     size_t ws = 1, parts = (size_t)kMseBlocks * 2;
     for (int l = 0; l < NL; ++l) {
         ws = std::max(ws, tc_wgrad_workspace(n->L[l], max_batch, n->num_sms));
         if (l > 0) parts = std::max(parts, (size_t)tc_bias_parts(n->L[l], max_batch, n->num_sms) * ci[l]);
+        if (l == NL - 1 && n->last_cuda_cores) {
+            ws = std::max(ws, tc_last_wgrad_workspace(n->L[l], max_batch));
+            parts = std::max(parts, (size_t)tc_last_bias_parts(n->L[l], max_batch) * ci[l]);
+        }
     }
     if ((s = nalloc_t(n, &n->params, off)) || (s = nalloc_t(n, &n->grads, off)) || (s = nalloc_t(n, &n->adam_m, off)) ||
         (s = nalloc_t(n, &n->adam_v, off)) || (s = nalloc_t(n, &n->xin, img)) || (s = nalloc_t(n, &n->target, img)) ||

@@ -115,5 +115,38 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
+// Feature-map pairs (hi, lo), channel-chunk major: [N][C/8][H][W][8] ("plain", par = 0) or
+// split by pixel parity, [N][C/8][2][2][H/2][W/2][8] (par = 1).
+// element offset of 8-channel chunk q at pixel (y, x) of image n
+__device__ __forceinline__ size_t chunk_at(int par, int C8, int H, int W, int n, int y, int x, int q) {
+    if (!par) return ((((size_t)n * C8 + q) * H + y) * W + x) * 8;
+    return (((((size_t)n * C8 + q) * 4 + ((y & 1) << 1) + (x & 1)) * (H >> 1) + (y >> 1)) * (W >> 1) + (x >> 1)) * 8;
+}
+
+__device__ __forceinline__ void store_pair8(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t o, const float* v) {
+    __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) split_bf16(v[j], h[j], l[j]);
+    *reinterpret_cast<uint4*>(hi + o) = *reinterpret_cast<const uint4*>(h);
+    *reinterpret_cast<uint4*>(lo + o) = *reinterpret_cast<const uint4*>(l);
+}
+
+// v[j] = hi + lo of the 8 channels of one chunk
+__device__ __forceinline__ void load_pair8(const __nv_bfloat16* hi, const __nv_bfloat16* lo, size_t o, float* v) {
+    __align__(16) __nv_bfloat16 h[8], l[8];
+    *reinterpret_cast<uint4*>(h) = __ldg(reinterpret_cast<const uint4*>(hi + o));
+    *reinterpret_cast<uint4*>(l) = __ldg(reinterpret_cast<const uint4*>(lo + o));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __bfloat162float(h[j]) + __bfloat162float(l[j]);
+}
+
+// m[j] = (hi + lo > 0) of 8 channels
+__device__ __forceinline__ void load_mask8(const __nv_bfloat16* hi, const __nv_bfloat16* lo, size_t o, bool* m) {
+    float v[8];
+    load_pair8(hi, lo, o, v);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m[j] = v[j] > 0.0f;
+}
+
 }  // namespace tc
 }  // namespace ptylm
