@@ -262,13 +262,23 @@ __global__ void __launch_bounds__(kThreads) k_last_wgrad(const __nv_bfloat16* __
     }
 }
 
-// dw[i] = sum over blocks of ws[block][i], in block order
-__global__ void k_last_wgrad_sum(const float* __restrict__ ws, int blocks, int count, float* __restrict__ dw) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
+// dw[i] = sum over blocks q of ws[q][i]: warp w of a block sums the rows q = w (mod 8) for
+// 32 consecutive i (coalesced), then the eight warp sums are added in warp order
+__global__ void __launch_bounds__(256) k_last_wgrad_sum(const float* __restrict__ ws, int blocks, int count,
+                                                        float* __restrict__ dw) {
+    __shared__ float part[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
     float s = 0.0f;
-    for (int q = 0; q < blocks; ++q) s += ws[(size_t)q * count + i];
-    dw[i] = s;
+    if (i < count)
+        for (int q = w; q < blocks; q += 8) s += ws[(size_t)q * count + i];
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && i < count) {
+        float t = 0.0f;
+        for (int k = 0; k < 8; ++k) t += part[k][lane];
+        dw[i] = t;
+    }
 }
 
 bool last_layer_shape_ok(const TcLayer& L, int H) {
@@ -324,7 +334,7 @@ cudaError_t tc_last_wgrad(const TcLayer& L, const Act2& x, const Act2& dy, float
     k_last_wgrad<<<blocks, kThreads, smem, st>>>(x.hi, x.lo, dy.hi, dy.lo, x.H, x.W, L.Ci, L.Co, ws);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_last_wgrad_sum<<<(count + 255) / 256, 256, 0, st>>>(ws, blocks, count, dw);
+    k_last_wgrad_sum<<<(count + 31) / 32, 256, 0, st>>>(ws, blocks, count, dw);
     return cudaGetLastError();
 }
 
