@@ -482,6 +482,12 @@ ptylm_status ptylm_net_set_params(ptylm_net* net, const float* params_host);
 ptylm_status ptylm_net_get_params(ptylm_net* net, float* params_host, float* grads_host);
 /* out = network(X) for N <= max_batch images. */
 ptylm_status ptylm_net_forward(ptylm_net* net, const float* X, int N, float* out);
+/* Output of hidden layer `layer` (1..5, after its ReLU) of the first N images of the last
+ * forward pass (ptylm_net_forward, ptylm_net_loss_grad or training), as the FP32 value of
+ * the stored bfloat16 pair: out device float [N][C_layer][H_layer][H_layer].  For
+ * inspection and for taking the ReLU decisions of a reference evaluation from the network
+ * itself (the paper has no counterpart).  Synchronises the network's stream. */
+ptylm_status ptylm_net_activation(ptylm_net* net, int layer, int N, float* out);
 /* Loss L = sum mask (out - T)^2 / (2 N sum mask) (mask [128][128] broadcast over channels
  * and batch) and its gradients (kept in the network, read with ptylm_net_get_params). */
 ptylm_status ptylm_net_loss_grad(ptylm_net* net, const float* X, const float* T, const float* mask, int N,

@@ -95,9 +95,13 @@ def net_forward(params, x, widths=(32, 64, 128)):
     return acts
 
 
-def net_loss_and_grads(params, x, target, mask, widths=(32, 64, 128)):
+def net_loss_and_grads(params, x, target, mask, widths=(32, 64, 128), relu_masks=None):
     """L = sum(mask * (out - target)^2) / (2 sum(mask)) over both channels and the batch
-    (mask [H, W] broadcast), and dL/dW, dL/db per layer."""
+    (mask [H, W] broadcast), and dL/dW, dL/db per layer.  relu_masks: optional list of the
+    five hidden layers' ReLU decisions (boolean arrays shaped like their outputs) to use in
+    the backward pass instead of acts > 0 -- the decisions a lower-precision evaluation of
+    the same network took (a pre-activation within its rounding of zero can fall on either
+    side of the kink)."""
     acts = net_forward(params, x, widths)
     out = acts[-1]
     n_terms = 2.0 * x.shape[0] * float(mask.sum())
@@ -110,7 +114,7 @@ def net_loss_and_grads(params, x, target, mask, widths=(32, 64, 128)):
         W, b = params[l]
         _, _, s, up, relu = specs[l]
         if relu:
-            g = g * (acts[l + 1] > 0.0)
+            g = g * (relu_masks[l] if relu_masks is not None else (acts[l + 1] > 0.0))
         dx, dW, db = conv3x3_backward(acts[l], W, g, s, up)
         grads[l] = (dW, db)
         g = dx

@@ -569,6 +569,17 @@ __global__ void k_pack_input(const float* __restrict__ X, int N, int H, int W, i
     }
 }
 
+// out[n][c][y][x] = hi + lo of channel c < C_real of the pair a (any layout)
+__global__ void k_unpack_act(const __nv_bfloat16* __restrict__ hi, const __nv_bfloat16* __restrict__ lo, int N, int H,
+                             int W, int C8, int par, int C_real, float* __restrict__ out) {
+    const long HW = (long)H * W, total = (long)N * C_real * HW;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const int n = (int)(i / (C_real * HW)), c = (int)((i / HW) % C_real), y = (int)((i % HW) / W), x = (int)(i % W);
+        const size_t o = chunk_at(par, C8, H, W, n, y, x, c >> 3) + (c & 7);
+        out[i] = __bfloat162float(hi[o]) + __bfloat162float(lo[o]);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_mse_tc(const float* __restrict__ out, const float* __restrict__ t,
                                                 const float* __restrict__ mask, int N, int H, int W, float inv_terms,
                                                 __nv_bfloat16* __restrict__ ghi, __nv_bfloat16* __restrict__ glo,
@@ -1041,6 +1052,15 @@ cudaError_t tc_weights(const TcLayer& L, const float* w32, __nv_bfloat16* wf, __
 cudaError_t tc_pack_input(const float* X, const Act2& x0, cudaStream_t st) {
     const long total = (long)x0.N * x0.H * x0.W;
     k_pack_input<<<(int)std::min<long>(2048, (total + 255) / 256), 256, 0, st>>>(X, x0.N, x0.H, x0.W, x0.par, x0.hi, x0.lo);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_unpack(const Act2& a, int C_real, float* out, cudaStream_t st) {
+    if (C_real < 1 || C_real > a.C) return cudaErrorInvalidValue;
+    const long total = (long)a.N * C_real * a.H * a.W;
+    if (total == 0) return cudaSuccess;
+    const int blocks = (int)std::min<long>((total + 255) / 256, 4096);
+    k_unpack_act<<<blocks, 256, 0, st>>>(a.hi, a.lo, a.N, a.H, a.W, a.C >> 3, a.par, C_real, out);
     return cudaGetLastError();
 }
 

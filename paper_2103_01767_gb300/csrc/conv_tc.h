@@ -86,6 +86,8 @@ cudaError_t tc_bias_reduce(const float* part, int n_part, int C, float* tmp, flo
 cudaError_t tc_weights(const TcLayer& L, const float* w32, __nv_bfloat16* wf, __nv_bfloat16* wb, cudaStream_t st);
 // pair x0 (C = 8, channels 2..7 zero, layout x0.par) from FP32 planes X[N][2][H][W]
 cudaError_t tc_pack_input(const float* X, const Act2& x0, cudaStream_t st);
+// out[n][c][y][x] = hi + lo of the first C_real channels of the pair a (FP32, [N][C_real][H][W])
+cudaError_t tc_unpack(const Act2& a, int C_real, float* out, cudaStream_t st);
 // loss += sum mask (out - t)^2 / n_terms (FP64); g = 2 mask (out - t) / n_terms as the pair
 // g (C = 8, channels 2..7 zero; plain, plus the parity copy when g.phi is set) and
 // db_part[i][2] partial sums of g (FP32).

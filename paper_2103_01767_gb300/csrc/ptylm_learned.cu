@@ -334,6 +334,16 @@ ptylm_status ptylm_net_get_params(ptylm_net* n, float* host, float* grads_host) 
     return PTYLM_OK;
 }
 
+ptylm_status ptylm_net_activation(ptylm_net* n, int layer, int N, float* out) {
+    set_last_error("");
+    if (!n || !out) return lfail(PTYLM_ERR_ARG, "net and out must be non-NULL");
+    if (layer < 1 || layer > NL - 1) return lfail(PTYLM_ERR_ARG, "layer must be in [1, %d]", NL - 1);
+    if (N < 1 || N > n->max_batch) return lfail(PTYLM_ERR_ARG, "N must be in [1, max_batch]");
+    LCUDA_TRY(tc_unpack(batch(n->act[layer - 1], N), n->L[layer - 1].Co, out, n->stream));
+    LCUDA_TRY(cudaStreamSynchronize(n->stream));
+    return PTYLM_OK;
+}
+
 ptylm_status ptylm_net_forward(ptylm_net* n, const float* X, int N, float* out) {
     set_last_error("");
     if (!n || !X || !out) return lfail(PTYLM_ERR_ARG, "net, X and out must be non-NULL");

@@ -134,6 +134,7 @@ def load_library():
             lib.ptylm_net_set_params.argtypes = [vp, vp]
             lib.ptylm_net_get_params.argtypes = [vp, vp, vp]
             lib.ptylm_net_forward.argtypes = [vp, vp, i, vp]
+            lib.ptylm_net_activation.argtypes = [vp, i, i, vp]
             lib.ptylm_net_loss_grad.argtypes = [vp, vp, vp, vp, i, P(d)]
             lib.ptylm_net_pairs.argtypes = [vp, vp, i, vp, i, vp, vp, vp]
             lib.ptylm_net_train.argtypes = [vp, vp, i, i, vp, i, i, d, u64, vp]
@@ -142,7 +143,7 @@ def load_library():
             lib.ptylm_net_destroy.argtypes = [vp]
             for name in ("ptylm_net_create", "ptylm_net_set_params", "ptylm_net_get_params", "ptylm_net_forward",
                          "ptylm_net_loss_grad", "ptylm_net_pairs", "ptylm_net_train", "ptylm_learned_inputs",
-                         "ptylm_learned_init", "ptylm_net_destroy"):
+                         "ptylm_learned_init", "ptylm_net_destroy", "ptylm_net_activation"):
                 getattr(lib, name).restype = i
             for name in ("ptylm_batch_init", "ptylm_batch_forward_loss", "ptylm_batch_gradient",
                          "ptylm_batch_ggn_matvec", "ptylm_batch_lm_solve", "ptylm_batch_tune",
@@ -619,10 +620,11 @@ def batch_lm_solve(batch: Batch, O, params=None, hist_len: int = 0, O_refs=None,
 class Net:
     """Owns one C network (ptylm_net_create ... ptylm_net_destroy)."""
 
-    def __init__(self, handle, widths, max_batch):
+    def __init__(self, handle, widths, max_batch, m=128):
         self.handle = handle
         self.widths = tuple(widths)
         self.max_batch = max_batch
+        self.m = m
 
     @property
     def num_params(self):
@@ -644,7 +646,7 @@ def net_create(widths=(64, 128, 256), max_batch=64, seed=0, m=128, stream=None) 
     w = (ctypes.c_int * 3)(*[int(x) for x in widths])
     h = ctypes.c_void_p()
     _check(load_library().ptylm_net_create(ctypes.byref(h), int(m), w, int(max_batch), int(seed), _stream_ptr(stream)))
-    return Net(h, widths, max_batch)
+    return Net(h, widths, max_batch, int(m))
 
 
 def net_set_params(net: Net, params) -> None:
@@ -665,6 +667,19 @@ def net_get_params(net: Net):
 def net_forward(net: Net, X, out, N=None) -> None:
     N = int(X.shape[0]) if N is None else int(N)
     _check(load_library().ptylm_net_forward(net.handle, _ptr(X), N, _ptr(out)))
+
+
+def net_activation(net: Net, layer: int, N: int):
+    """Output of hidden layer `layer` (1..5) of the first N images of the last forward pass,
+    as a float32 CUDA tensor [N, C, H, H]."""
+    import torch
+    m = net.m
+    c1, c2, c3 = net.widths
+    C = (c1, c2, c3, c2, c1)[layer - 1]
+    H = (m // 2, m // 4, m // 8, m // 4, m // 2)[layer - 1]
+    out = torch.empty((N, C, H, H), dtype=torch.float32, device="cuda")
+    _check(load_library().ptylm_net_activation(net.handle, int(layer), int(N), _ptr(out)))
+    return out
 
 
 def net_loss_grad(net: Net, X, T, mask, N=None) -> float:

@@ -108,8 +108,24 @@ def test_network_forward_and_gradients_match_the_oracle(lib, widths, N):
     parity.check(f"{tag} output", out.cpu().numpy(), acts[-1], 1e-4, basis="1e-4 (network)")
     parity.check(f"{tag} output", out.cpu().numpy(), acts[-1], 1e-4, norm="max", basis="1e-4 (network)")
     loss = lib.net_loss_grad(net, f32(X), f32(T), f32(mask))
+    # Hidden activations: each layer against the oracle, and the ReLU decisions.  Activations
+    # travel between layers as bfloat16 pairs (2^-18 relative), so a pre-activation within that
+    # precision of zero can land on the other side of the kink than in FP64; the backward pass
+    # of the oracle takes the network's own decisions (a discrete choice made in the kernel's
+    # precision), after checking that every disagreement sits at such a near-zero value.
+    relu_masks = []
+    for l in range(1, 6):
+        a_gpu = lib.net_activation(net, l, N).cpu().numpy().astype(np.float64)
+        a_ref = acts[l]
+        parity.check(f"{tag} activation {l}", a_gpu, a_ref, 1e-4, basis="1e-4 (network)")
+        m_gpu, m_ref = a_gpu > 0.0, a_ref > 0.0
+        diff = m_gpu != m_ref
+        if diff.any():
+            near = np.maximum(np.abs(a_gpu[diff]), np.abs(a_ref[diff])).max() / np.abs(a_ref).max()
+            assert near <= 1e-4, (l, int(diff.sum()), near)
+        relu_masks.append(m_gpu)
     loss_ref, grads_ref = L.net_loss_and_grads(pb, X.astype(np.float64), T.astype(np.float64), mask.astype(np.float64),
-                                               widths)
+                                               widths, relu_masks=relu_masks)
     parity.check(f"{tag} loss", loss, loss_ref, 1e-4, basis="1e-4 (network)")
     _, g = lib.net_get_params(net)
     off = 0
