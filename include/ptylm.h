@@ -80,7 +80,7 @@ typedef struct {
     int max_outer;     /* outer LM iterations                                              */
     int max_cg;        /* CG iterations per solve (PTYLM_WARN_CG_MAXIT when reached)       */
     int fixed_cg;      /* > 0: run exactly this many CG iterations per solve (benchmarking) */
-    double target_err; /* stop once the object error <= target_err (needs O_ref)           */
+    double target_err; /* stop once the object error <= target_err (needs O_ref; 0: none)  */
     const ptylm_c64* O_ref; /* optional device reference object for the error metric       */
     const uint8_t* mask;    /* optional device [ny][nx] mask of pixels the error compares   */
     int scaled;        /* 1: D = Dg(G) (closed form, App. B), lambda = mu, Jacobi PCG with

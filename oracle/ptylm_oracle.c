@@ -508,7 +508,7 @@ double orc_object_error(long N, const dc* O, const dc* O_ref, const unsigned cha
 typedef struct {
     double mu0, mu_min, kappa, nu, rho_min, beta, mu_max;
     int max_outer, max_cg;
-    double target_err;   /* stop once the object error <= target_err (if O_ref given) */
+    double target_err;   /* stop once the object error <= target_err (if O_ref given; 0: no target) */
 } orc_lm_params;
 
 /* Resumable state of Algorithm 1 (Sec. 4.2) between calls: the outer iterations completed
@@ -586,7 +586,7 @@ int orc_lm_solve(const orc_geom* g, dc* O, const dc* P, const int32_t* pos, cons
         if (O_ref) {
             double e = orc_object_error(N, O, O_ref, mask);
             if (hist_err && h < hist_len) hist_err[h] = e;
-            if (e <= prm->target_err) { ++t; break; }
+            if (prm->target_err > 0.0 && e <= prm->target_err) { ++t; break; }
         }
     }
     if (n_outer_out) *n_outer_out = t - t0;
@@ -872,7 +872,7 @@ int orc_lm_solve2(const orc_geom* g, dc* O_inout, dc* P_inout, const int32_t* po
         if (O_ref) {
             double e = orc_object_error(N, z, O_ref, mask);
             if (hist_err && h < hist_len) hist_err[h] = e;
-            if (e <= prm->target_err) { ++t; break; }
+            if (prm->target_err > 0.0 && e <= prm->target_err) { ++t; break; }
         }
     }
     memcpy(O_inout, z, sizeof(dc) * N);

@@ -1376,7 +1376,7 @@ static ptylm_status lm_solve_impl(ptylm_ctx* c, ptylm_c64* O_inout, ptylm_c64* P
         if (prm->O_ref) {
             STATUS_TRY(object_error(&err));
             if (stats && stats->hist_len > h && stats->hist_err) stats->hist_err[h] = err;
-            if (err <= prm->target_err) {
+            if (prm->target_err > 0.0 && err <= prm->target_err) {
                 ++t;
                 break;
             }

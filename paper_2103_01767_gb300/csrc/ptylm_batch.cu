@@ -1207,7 +1207,7 @@ ptylm_status ptylm_batch_lm_solve(ptylm_batch* bt, ptylm_c64* O_inout, const pty
                 stats[b].hist_err[t[b]] = NAN;
             }
             ++t[b];
-            if (t[b] >= prm[b].max_outer || (prm[b].O_ref && err[b] <= prm[b].target_err)) done[b] = 1;
+            if (t[b] >= prm[b].max_outer || (prm[b].O_ref && prm[b].target_err > 0.0 && err[b] <= prm[b].target_err)) done[b] = 1;
         }
     }
     // restore the true backgrounds; a linearisation under a surrogate level is dropped
