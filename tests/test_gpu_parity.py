@@ -330,7 +330,9 @@ def test_lm_host_buffers(lib):
     Od = dev_c64(synth.flat_object(w.n))
     st2, info2 = lib.lm_solve(g.ctx, Od, g.P, max_outer=3)
     assert rel_err(O, host(Od)) <= 1e-5
-    assert info["cg_total"] == info2["cg_total"]
+    # the overlapping scan's scatter rounds differently from run to run, which can move a CG
+    # stopping test by one iteration
+    assert abs(info["cg_total"] - info2["cg_total"]) <= 1
 
 
 def test_zero_positions(lib):
