@@ -262,6 +262,58 @@ def test_batch_lm_fixed_cg_counts(lib, batch):
         assert np.all(info["cg"] % 5 == 0)
 
 
+def test_batch_with_an_empty_member_and_a_border_scan(lib):
+    """A member with no positions next to one whose patches all touch the object's border:
+    the empty member's error metric and gradient are zero and its product is lambda v; the
+    others match the oracle; the batched LM finishes the empty member at once and solves
+    the others; the autotuner times only the tiles the batch uses (128^2 and 32^2 here)."""
+    from tests.problems import Case
+    n, m = 128, 32
+    e = n - m
+    pos = np.array([(0, 0), (0, e), (e, 0), (e, e), (0, 40), (40, e), (e, 17), (63, 0)], np.int32)
+    O_true = synth.to_c64(synth.object_texture(n, seed=210))
+    P = synth.to_c64(synth.probe_disk_defocus(m, 10.0))
+    y = oracle.intensity(oracle.Problem((n, n), P, pos, None, 0, 1e-8), O_true)
+    border = Case(n, m, pos, O_true, P, synth.to_f32(y), 0, 1e-8)
+    big = make_case(160, 128, K=4, loss=0, seed=211)
+    cases = [border, None, big]
+    empty = dict(ny=64, nx=64, m=32, positions=torch.zeros((0, 2), dtype=torch.int32).cuda(),
+                 y=torch.zeros((0, 32, 32), dtype=torch.float32).cuda(), probe=c64(P), loss=0, background=1e-8)
+    probs = [dict(ny=c.n, nx=c.n, m=c.m, positions=torch.from_numpy(c.pos).cuda(), y=f32(c.y), probe=c64(c.P),
+                  loss=0, background=c.b) if c is not None else empty for c in cases]
+    bt = lib.batch_init(probs)
+    assert [bt.offsets[i + 1] - bt.offsets[i] for i in range(3)] == [n * n, 64 * 64, 160 * 160]
+    X = [synth.to_c64(border.O_true + synth.random_complex((n, n), seed=212, scale=0.05)),
+         synth.to_c64(synth.random_complex((64, 64), seed=213)),
+         synth.to_c64(big.O_true + synth.random_complex((160, 160), seed=214, scale=0.05))]
+    O = torch.cat([c64(x).reshape(-1) for x in X])
+    f, dl2 = lib.batch_forward_loss(bt, O, cache=1)
+    g = torch.empty_like(O)
+    lib.batch_gradient(bt, g)
+    gv = bt.views(g)
+    assert f[1] == 0.0 and dl2[1] == 0.0 and float(gv[1].abs().max()) == 0.0
+    vs = [synth.to_c64(synth.random_complex(x.shape, seed=220 + i)) for i, x in enumerate(X)]
+    v = torch.cat([c64(x).reshape(-1) for x in vs])
+    out = torch.empty_like(v)
+    lam = np.array([0.2, 0.7, 0.0])
+    lib.batch_ggn_matvec(bt, v, out, lam)
+    ov = bt.views(out)
+    assert rel_err(host(ov[1]), 0.7 * vs[1]) <= 1e-6
+    for b in (0, 2):
+        c = cases[b]
+        pb = c.problem()
+        parity.check(f"edge batch f[{b}]", f[b], oracle.loss(pb, X[b]))
+        parity.check(f"edge batch grad f[{b}]", host(gv[b]), oracle.gradient(pb, X[b]))
+        parity.check(f"edge batch grad f[{b}]", host(gv[b]), oracle.gradient(pb, X[b]), norm="max")
+        ref = oracle.ggn_matvec(pb, X[b], vs[b], lam=lam[b])
+        parity.check(f"edge batch (G + lam I) v[{b}]", host(ov[b]), ref)
+        parity.check(f"edge batch (G + lam I) v[{b}]", host(ov[b]), ref, norm="max")
+    choice, ms = lib.batch_tune(bt)
+    assert all(t > 0 for t in ms[:12]) and all(t == -1.0 for t in ms[12:]) and choice < 12
+    st, infos = lib.batch_lm_solve(bt, O, hist_len=4, max_outer=3)
+    assert infos[1]["n_outer"] == 0 and infos[0]["n_outer"] >= 1 and infos[2]["n_outer"] >= 1
+
+
 def test_batch_argument_errors(lib):
     c = make_case(96, 32, K=10, loss=0, seed=1)
     good = dict(ny=96, nx=96, m=32, positions=torch.from_numpy(c.pos).cuda(), y=f32(c.y), probe=c64(c.P), loss=0)
