@@ -119,3 +119,28 @@ def test_bf16_rounding_matches_torch():
     v = np.concatenate([rng(13).standard_normal(1000), [1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, -2.5, 0.0]])
     ref = torch.tensor(v, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(L.to_bf16(v), ref)
+
+
+def test_given_relu_masks_select_the_backward_branches():
+    """relu_masks equal to the forward's own decisions change nothing; a mask that switches
+    every unit of the last hidden layer off cuts the gradient of all earlier layers and
+    leaves the last layer's (which the masks do not enter)."""
+    widths = (3, 4, 5)
+    params = L.init_params(widths, seed=8)
+    params = [(W, 0.1 * rng(40 + l).standard_normal(b.shape)) for l, (W, b) in enumerate(params)]
+    x = rng(9).standard_normal((1, 2, 16, 16))
+    t = rng(10).standard_normal((1, 2, 16, 16))
+    mask = np.ones((16, 16))
+    acts = L.net_forward(params, x, widths)
+    own = [a > 0.0 for a in acts[1:6]]
+    _, g0 = L.net_loss_and_grads(params, x, t, mask, widths)
+    _, g1 = L.net_loss_and_grads(params, x, t, mask, widths, relu_masks=own)
+    for (a, b), (c, d) in zip(g0, g1):
+        assert np.array_equal(a, c) and np.array_equal(b, d)
+    # masking every unit of the last hidden layer off cuts the gradient of all earlier layers
+    off = [m.copy() for m in own]
+    off[4][:] = False
+    _, g2 = L.net_loss_and_grads(params, x, t, mask, widths, relu_masks=off)
+    for l in range(5):
+        assert not np.any(g2[l][0]) and not np.any(g2[l][1])
+    assert np.allclose(g2[5][0], g0[5][0]) and np.allclose(g2[5][1], g0[5][1])
