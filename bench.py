@@ -833,6 +833,14 @@ def run_batch(args):
     Ob.copy_(O0)
     _, infos = ptylm.batch_lm_solve(bt, Ob, max_outer=1, fixed_cg=10)
     lm_step_s = time.perf_counter() - t0
+    # the same step as PLM for every member (D = Dg(G) per problem, Jacobi PCG)
+    Ob.copy_(O0)
+    ptylm.batch_lm_solve(bt, Ob, max_outer=1, fixed_cg=10, scaled=1)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    Ob.copy_(O0)
+    ptylm.batch_lm_solve(bt, Ob, max_outer=1, fixed_cg=10, scaled=1)
+    plm_step_s = time.perf_counter() - t0
     line = {
         "metric": BATCH_METRIC, "value": value, "unit": BATCH_UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
@@ -861,6 +869,7 @@ def run_batch(args):
         "comparison": {"sequential_single_contexts_ms": 1e3 * seq_s, "batched_ms": 1e3 * t_step,
                        "speedup": seq_s / t_step},
         "lm_step_ms": 1e3 * lm_step_s,
+        "plm_step_ms": 1e3 * plm_step_s,
     }
     print(json.dumps(line), flush=True)
     bt.close()
