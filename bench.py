@@ -483,6 +483,64 @@ def snapshot_errors(torch, snaps, ref, mask):
     return np.array(out)
 
 
+def blind_errors(torch, snaps, ref, mask, ramp_iterations=3):
+    """Object error of every snapshot against ref for the blind problem (C14: solutions are
+    unique only up to a complex scale and a linear phase ramp): the ramp a0 + a1 y + a2 x is
+    fitted by weighted least squares (weights |o| |r|) to the phase of r conj(o) over the
+    mask, the fit repeated so that wrapped phases settle, then the closed-form complex scale
+    c = <o, r> / <o, o>; error ||c o - r|| / ||r||.  FP64 on the device, after the runs."""
+    m = mask.bool()
+    yy, xx = torch.nonzero(m, as_tuple=True)
+    A = torch.stack([torch.ones_like(yy), yy, xx], dim=1).to(torch.float64)
+    r = ref[m].to(torch.complex128)
+    nr = torch.linalg.vector_norm(r)
+    out = []
+    for s in snaps:
+        o = s[m].to(torch.complex128)
+        for _ in range(ramp_iterations):
+            w = (o.abs() * r.abs()).to(torch.float64)
+            ph = torch.angle(r * torch.conj(o))
+            Aw = A * w[:, None]   # normal equations of the 3-parameter weighted fit
+            coef = torch.linalg.solve(Aw.T @ Aw, Aw.T @ (ph * w))
+            o = o * torch.exp(1j * (A @ coef))
+        c = torch.vdot(o, r) / torch.vdot(o, o)
+        out.append(float(torch.linalg.vector_norm(c * o - r) / nr))
+    return np.array(out)
+
+
+def joint_time_to_accuracy(ptylm, torch, dev, stream, target=1e-3, max_outer=200):
+    """Time to object error <= target on the blind 256^2 / 64^2 / 400-position Poisson 1e4
+    workload, against the converged plain-LM reconstruction of the joint state z = (O, P)
+    (Algorithm 1 with D = I from the flat object and the unphased disk, until the damping
+    runs away or max_outer iterations; C15), errors after blind alignment (C14).  Runs: plain
+    LM, and PLM-J (D = Dg(G) with Algorithm 2's projections), each also against its own last
+    iterate."""
+    w = synth.WORKLOADS["obj256_probe64_pos400_poisson_1e4"]
+    ctx, O0, P0, y, posd, _ = setup_workload(ptylm, torch, w, dev, stream)
+    mask = torch.from_numpy(synth.illumination_mask(w.n, P0.cpu().numpy(), posd.cpu().numpy(), 0.1)
+                            .astype(np.uint8)).to(dev)
+    runs = {}
+    for name, kw in (("LM", dict(scaled=0, projected=0)), ("PLM-J", dict(scaled=1, projected=1))):
+        runs[name] = converge_with_snapshots(ptylm, torch, dev, ctx, O0, P0.clone(), max_outer, **kw)
+    out = {"workload": "256^2 object / 64^2 probe / 400 positions, joint object and probe, Poisson 1e4 photons peak",
+           "target": target, "error": "blind alignment (complex scale and linear phase ramp) on the illuminated pixels",
+           "timing": "per-iteration lm_solve_resume calls with a D2D snapshot after each (upper bounds)"}
+    O_ref = runs["LM"][0][-1]
+    for name, (snaps, times, status, cg) in runs.items():
+        e_ref = blind_errors(torch, snaps, O_ref, mask)
+        e_own = blind_errors(torch, snaps, snaps[-1], mask)
+        s_ref, t_ref = first_below(e_ref, times, target)
+        s_own, t_own = first_below(e_own[:-1], times[:-1], target)
+        out[name] = {"outer": len(times), "cg": int(cg), "status": int(status), "total_s": float(times[-1]),
+                     "vs_plain": {"seconds": s_ref, "outer": t_ref, "err_final": float(e_ref[-1])},
+                     "vs_own_limit": {"seconds": s_own, "outer": t_own}}
+        del snaps
+    out["reference"] = (f"plain LM on z = (O, P) from the flat start, {runs['LM'][0].shape[0]} outer iterations "
+                        f"({'the damping ran away' if runs['LM'][2] == ptylm.PTYLM_ERR_STALLED else 'iteration limit'})")
+    ptylm.lm_destroy(ctx)
+    return out
+
+
 def first_below(errs, times, target):
     idx = np.flatnonzero(errs <= target)
     return (float(times[idx[0]]), int(idx[0]) + 1) if idx.size else (None, None)
@@ -1042,6 +1100,7 @@ def main():
         tta["learned_vs_plain"], net, idx = learned_vs_plain(ptylm, torch, dev)
         tta["learned_vs_plain"]["network"]["timing"] = net_timing(ptylm, torch, dev)
         tta["large"] = large_poisson_time_to_accuracy(ptylm, torch, dev, stream, net, idx)
+        tta["joint"] = joint_time_to_accuracy(ptylm, torch, dev, stream)
         net.close()
         autograd = autograd_leg(ptylm, torch, dev)
     avg_mv_s = (mv_ms / 1e3) / max(mv_n, 1)

@@ -33,3 +33,26 @@ def test_recorded_traffic_is_tied_to_the_kernel_sources():
     # code measured 495.9 and 511.2 MB against 497.2 MB algorithmic, so the record is held
     # to 5 %
     assert abs(float(value) - bench.matvec_bytes(3600, 128 * 128, 1024 * 1024)) < 0.05 * float(value)
+
+
+def test_blind_error_of_the_bench_matches_the_oracle():
+    """bench.py's blind-alignment object error (torch, used on the device after the timed
+    runs) equals the oracle's object_error_blind, and is zero for a scaled, ramped copy."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(5)
+    n = 24
+    R = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))).astype(np.complex64)
+    yy, xx = np.mgrid[0:n, 0:n]
+    ramp = np.exp(1j * (0.3 + 0.05 * yy - 0.02 * xx))
+    O_same = (0.7 - 0.4j) * ramp * R
+    O_noisy = O_same + 0.05 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    mask = np.zeros((n, n), np.uint8)
+    mask[3:21, 2:22] = 1
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.complex64))
+    errs = bench.blind_errors(torch, torch.stack([t(O_same), t(O_noisy)]), t(R), torch.from_numpy(mask))
+    assert errs[0] < 1e-5
+    ref = oracle.object_error_blind(O_noisy.astype(np.complex64), R, mask.astype(bool))
+    assert abs(errs[1] - ref) <= 1e-5 * ref
