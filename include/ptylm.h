@@ -66,6 +66,10 @@ typedef struct {
     float background;         /* b > 0, added to every detector pixel (Eq. expected_count) */
     int joint;                /* 0: object only (SPR, Eq. cdp); 1: object + probe (BPR)  */
     size_t workspace_budget;  /* max bytes the context may allocate; 0 = unlimited       */
+    int values_per_thread;    /* FFT tile of the single-problem kernels: 32, or 16 for     */
+                              /* probe sides 32 and 64 (teams of S^2/16 threads); 0 picks  */
+                              /* 16 when the positions would fill less than half of the   */
+                              /* GPU with teams of S^2/32 threads (ignored by batches)     */
 } ptylm_desc;
 
 /* Parameters of Algorithm 1 (Sec. 4.2; values used in the paper: Sec. 5). */

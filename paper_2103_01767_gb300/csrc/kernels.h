@@ -44,22 +44,24 @@ enum KernelId {
 // Closed-form GGN diagonal (App. B, Eqs. ggn_diag_mat and ggn_joint_diag) from the per-thread
 // d2l sums of the last linearisation: D_O += |P|^2 tr_k / (2M) over each patch (one CTA per
 // position, D_O zeroed first) and, when D_P != NULL, D_P[m] = sum_k |O[r_k + m]|^2 tr_k / (2M).
-cudaError_t launch_ggn_diag(int LS, const float* trp, const int2* pos, int K, const float2* O,
+cudaError_t launch_ggn_diag(int LS, int LE, const float* trp, const int2* pos, int K, const float2* O,
                             const float2* P, int nx, float* D_O, float* D_P, float* tr, cudaStream_t stream);
 
-// Threads per CTA and teams (positions in flight) per CTA for a patch side 2^LS.
-int cta_threads(int LS);
-int cta_teams(int LS);
-size_t cta_smem_bytes(int LS);
+// FFT tile of a single-problem context: patch side 2^LS with 2^LE values per thread (LE = 5,
+// or 4 for sides 32 and 64: teams of S^2/16 threads).  Threads per CTA and teams (positions
+// in flight) per CTA for that tile.
+int cta_threads(int LS, int LE);
+int cta_teams(int LS, int LE);
+size_t cta_smem_bytes(int LS, int LE);
 
 // Opt in to the kernel's dynamic shared memory and report how many CTAs fit on one SM.
-cudaError_t kernel_prepare(int LS, int kid, int* ctas_per_sm);
+cudaError_t kernel_prepare(int LS, int LE, int kid, int* ctas_per_sm);
 
 // Copy measurements from natural [K][S][S] order into the kernels' team-register order
 // (square roots when take_sqrt: the Gaussian metric only uses sqrt(y)).  When `bad` is not
 // NULL, *bad |= 1 if any entry is negative, infinite or NaN (the caller zeroes it first);
 // y_perm == NULL only checks.
-cudaError_t permute_measurements(int LS, const float* y, float* y_perm, int K, int take_sqrt, int blocks,
+cudaError_t permute_measurements(int LS, int LE, const float* y, float* y_perm, int K, int take_sqrt, int blocks,
                                  cudaStream_t stream, unsigned* bad);
 
 // Record the thread-local message that ptylm_last_error() returns (shared by all entry points).
@@ -76,7 +78,7 @@ struct CtxView {
 };
 bool ctx_view(const struct ptylm_ctx* c, CtxView* v);
 
-// Launch kernel `kid` for patch side 2^LS on `grid` CTAs.
-cudaError_t kernel_launch(int LS, int kid, const PtyArgs& a, int grid, cudaStream_t stream);
+// Launch kernel `kid` for the tile (2^LS side, 2^LE values per thread) on `grid` CTAs.
+cudaError_t kernel_launch(int LS, int LE, int kid, const PtyArgs& a, int grid, cudaStream_t stream);
 
 }  // namespace ptylm

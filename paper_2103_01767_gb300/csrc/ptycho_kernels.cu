@@ -80,10 +80,10 @@ struct AdjArgs {          // J^T w and J v
 template <int LS, bool CACHE, bool INTENSITY, bool JOINT, bool MAG>
 __host__ __device__ constexpr bool forward_stages_y() { return LS == 7 && !INTENSITY && !JOINT && !MAG; }
 
-template <int LS, bool CACHE, bool INTENSITY = false, bool JOINT = false, bool MAG = false>
-__global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
+template <int LS, int LE, bool CACHE, bool INTENSITY = false, bool JOINT = false, bool MAG = false>
+__global__ void __launch_bounds__(Geo<LS, LE>::THREADS, 512 / Geo<LS, LE>::THREADS)
 k_forward(FwdArgs a) {
-    using G = Geo<LS>;
+    using G = Geo<LS, LE>;
     TeamCtx<G> c = team_setup<G>(a.tw);
     const float invS = 1.0f / G::S;
     double acc_l = 0.0, acc_d = 0.0;
@@ -98,7 +98,7 @@ k_forward(FwdArgs a) {
     constexpr bool STAGE_Y = forward_stages_y<LS, CACHE, INTENSITY, JOINT, MAG>();
     float* sy = reinterpret_cast<float*>(c.sm + G::M);
     const ScheduledProbe<G> probe(a.P, c.tid);
-    float2 v[32];
+    float2 v[G::E];
     int k = blockIdx.x * G::TEAMS + c.team;
     if constexpr (FUSED) {
         if (k < a.K) {
@@ -143,8 +143,8 @@ k_forward(FwdArgs a) {
                     if constexpr (STAGE_Y) cp_async_wait_all();   // the pass-3 barrier follows
                 });
             float s2;  // sum of d2l over this thread's pixels (closed-form diagonal)
-            if (a.loss == 0) ls.finish<0>(32, sl, sd, s2);
-            else ls.finish<1>(32, sl, sd, s2);
+            if (a.loss == 0) ls.finish<0>(G::E, sl, sd, s2);
+            else ls.finish<1>(G::E, sl, sd, s2);
             if (a.trp) a.trp[(size_t)k * G::T + c.tid] = s2;
             if constexpr (FUSED) {
                 const int kn = k + stride;
@@ -167,9 +167,9 @@ k_forward(FwdArgs a) {
                 __syncthreads();
             }
             if constexpr (MAG || INTENSITY) {
-                float hv[32];
+                float hv[G::E];
 #pragma unroll
-                for (int e = 0; e < 32; ++e) {
+                for (int e = 0; e < G::E; ++e) {
                     const float2 ps = v[e] * invS;
                     const float h = ps.x * ps.x + ps.y * ps.y + a.b;
                     if constexpr (MAG) {
@@ -186,13 +186,13 @@ k_forward(FwdArgs a) {
                 auto pixels = [&](auto loss_c) {
                     constexpr int LOSS = decltype(loss_c)::value;
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
+                    for (int e = 0; e < G::E; ++e) {
                         float ca, cg;
                         loss_pixel<LOSS, false>(v[e], STAGE_Y ? sy[e * G::T + c.tid] : __ldg(yk + e * G::T), a.b,
                                                 invS, ls, ca, cg);
                     }
                     float s2;
-                    ls.finish<LOSS>(32, sl, sd, s2);
+                    ls.finish<LOSS>(G::E, sl, sd, s2);
                 };
                 if (a.loss == 0) pixels(std::integral_constant<int, 0>{});
                 else pixels(std::integral_constant<int, 1>{});
@@ -211,10 +211,10 @@ k_forward(FwdArgs a) {
 // chihat = a t (App. A steps 2-4; the closed-form diagonal Hessian of step 3(ii) is folded
 // into a).  out must hold lambda D v (or zero) on entry.
 // ---------------------------------------------------------------------------------------
-template <int LS, bool JOINT = false>
-__global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
+template <int LS, int LE, bool JOINT = false>
+__global__ void __launch_bounds__(Geo<LS, LE>::THREADS, 512 / Geo<LS, LE>::THREADS)
 k_ggn_matvec(MatvecArgs a) {
-    using G = Geo<LS>;
+    using G = Geo<LS, LE>;
     if (a.skip && __ldcg(a.skip) != 0.0) return;  // every CTA reads the same value
     TeamCtx<G> c = team_setup<G>(a.tw);
     const float invM = 1.0f / G::M;
@@ -223,7 +223,7 @@ k_ggn_matvec(MatvecArgs a) {
     // (one probe load serves both); elsewhere the registers this keeps live across the
     // loop would spill.
     constexpr bool FUSED = LS == 7 && !JOINT;
-    float2 v[32];
+    float2 v[G::E];
     int k = blockIdx.x * G::TEAMS + c.team;
     if constexpr (FUSED) {
         if (k < a.K) {
@@ -270,14 +270,14 @@ k_ggn_matvec(MatvecArgs a) {
 // ---------------------------------------------------------------------------------------
 // J^T w: chihat = psihat w / zeta, recomputing psihat from (O, P).  out += result.
 // ---------------------------------------------------------------------------------------
-template <int LS, bool JOINT = false>
-__global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
+template <int LS, int LE, bool JOINT = false>
+__global__ void __launch_bounds__(Geo<LS, LE>::THREADS, 512 / Geo<LS, LE>::THREADS)
 k_jtvp(AdjArgs a) {
-    using G = Geo<LS>;
+    using G = Geo<LS, LE>;
     TeamCtx<G> c = team_setup<G>(a.tw);
     const float invS = 1.0f / G::S;
     const int ky = freq_ky<G>(c.tid);
-    float2 v[32];
+    float2 v[G::E];
     for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
         const int2 rc = a.pos[k];
         gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
@@ -304,27 +304,27 @@ k_jtvp(AdjArgs a) {
 // J v = Re(conj(psihat) F(P S_k v)) / zeta, written in natural [K][S][S] order.  psihat is
 // recomputed and parked in a per-team global scratch slot while the direction is transformed.
 // ---------------------------------------------------------------------------------------
-template <int LS, bool JOINT = false>
-__global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
+template <int LS, int LE, bool JOINT = false>
+__global__ void __launch_bounds__(Geo<LS, LE>::THREADS, 512 / Geo<LS, LE>::THREADS)
 k_jvp(AdjArgs a) {
-    using G = Geo<LS>;
+    using G = Geo<LS, LE>;
     TeamCtx<G> c = team_setup<G>(a.tw);
     const float invS = 1.0f / G::S;
     float2* slot = a.scratch + (size_t)(blockIdx.x * G::TEAMS + c.team) * G::M + c.tid;
-    float2 v[32];
+    float2 v[G::E];
     for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
         const int2 rc = a.pos[k];
         gather_times_probe<G>(v, a.O, a.P, a.nx, rc.x, rc.y, c.tid);
         team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
 #pragma unroll
-        for (int e = 0; e < 32; ++e) slot[e * G::T] = v[e];
+        for (int e = 0; e < G::E; ++e) slot[e * G::T] = v[e];
         team_sync<G>();
         if constexpr (JOINT) gather_joint<G>(v, a.V, a.P, a.VP, a.O, a.nx, rc.x, rc.y, c.tid);
         else gather_times_probe<G>(v, a.V, a.P, a.nx, rc.x, rc.y, c.tid);
         team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
-        float jv[32];
+        float jv[G::E];
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
+        for (int e = 0; e < G::E; ++e) {
             const float2 ps = slot[e * G::T] * invS;
             const float2 dps = v[e] * invS;
             const float inv_zeta = rsqrtf(ps.x * ps.x + ps.y * ps.y + a.b);
@@ -340,10 +340,10 @@ k_jvp(AdjArgs a) {
 // y_perm[k][e*T + t] = y[k][ky(t)][kx(t, e)] (its square root for the Gaussian metric,
 // whose terms only use sqrt(y)).
 // ---------------------------------------------------------------------------------------
-template <int LS>
+template <int LS, int LE>
 __global__ void k_permute_measurements(const float* __restrict__ y, float* __restrict__ y_perm, long total,
                                        int take_sqrt, unsigned* bad) {
-    using G = Geo<LS>;
+    using G = Geo<LS, LE>;
     bool ok = true;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
         const long k = i / G::M;
@@ -356,14 +356,18 @@ __global__ void k_permute_measurements(const float* __restrict__ y, float* __res
     if (bad && !ok) atomicOr(bad, 1u);
 }
 
-cudaError_t permute_measurements(int LS, const float* y, float* y_perm, int K, int take_sqrt, int blocks,
+// the FFT tiles a single-problem context may use: (side, log2 values per thread)
+#define PTYLM_TILE_CASES(X) X(5, 5) X(5, 4) X(6, 5) X(6, 4) X(7, 5)
+
+cudaError_t permute_measurements(int LS, int LE, const float* y, float* y_perm, int K, int take_sqrt, int blocks,
                                  cudaStream_t stream, unsigned* bad) {
     const long total = (long)K << (2 * LS);
     if (total == 0) return cudaSuccess;
-    switch (LS) {
-        case 5: k_permute_measurements<5><<<blocks, 256, 0, stream>>>(y, y_perm, total, take_sqrt, bad); break;
-        case 6: k_permute_measurements<6><<<blocks, 256, 0, stream>>>(y, y_perm, total, take_sqrt, bad); break;
-        case 7: k_permute_measurements<7><<<blocks, 256, 0, stream>>>(y, y_perm, total, take_sqrt, bad); break;
+    switch (LS * 8 + LE) {
+#define PTYLM_PERMUTE(ls, le) \
+    case ls * 8 + le: k_permute_measurements<ls, le><<<blocks, 256, 0, stream>>>(y, y_perm, total, take_sqrt, bad); break;
+        PTYLM_TILE_CASES(PTYLM_PERMUTE)
+#undef PTYLM_PERMUTE
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -374,22 +378,22 @@ cudaError_t permute_measurements(int LS, const float* y, float* y_perm, int K, i
 //   J v = Re(conj(u) F(P S_k vO + vP S_k O)),   J^T w = S_k^T conj(P) F^H(u w)  (+ probe part)
 // one 2D FFT per position instead of two (psihat is not recomputed).
 // ---------------------------------------------------------------------------------------
-template <int LS, bool JOINT = false>
-__global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
+template <int LS, int LE, bool JOINT = false>
+__global__ void __launch_bounds__(Geo<LS, LE>::THREADS, 512 / Geo<LS, LE>::THREADS)
 k_jvp_phasor(AdjArgs a, const float2* __restrict__ u) {
-    using G = Geo<LS>;
+    using G = Geo<LS, LE>;
     TeamCtx<G> c = team_setup<G>(a.tw);
     const float invS = 1.0f / G::S;
-    float2 v[32];
+    float2 v[G::E];
     for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
         const int2 rc = a.pos[k];
         if constexpr (JOINT) gather_joint<G>(v, a.V, a.P, a.VP, a.O, a.nx, rc.x, rc.y, c.tid);
         else gather_times_probe<G>(v, a.V, a.P, a.nx, rc.x, rc.y, c.tid);
         team_fft_fwd<G>(v, c.sm, c.tw, c.tid);
         const float2* uk = u + (size_t)k * G::M + c.tid;
-        float jv[32];
+        float jv[G::E];
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
+        for (int e = 0; e < G::E; ++e) {
             const float2 ue = __ldg(uk + e * G::T);
             jv[e] = (ue.x * v[e].x + ue.y * v[e].y) * invS;
         }
@@ -398,20 +402,20 @@ k_jvp_phasor(AdjArgs a, const float2* __restrict__ u) {
     }
 }
 
-template <int LS, bool JOINT = false>
-__global__ void __launch_bounds__(Geo<LS>::THREADS, 512 / Geo<LS>::THREADS)
+template <int LS, int LE, bool JOINT = false>
+__global__ void __launch_bounds__(Geo<LS, LE>::THREADS, 512 / Geo<LS, LE>::THREADS)
 k_jtvp_phasor(AdjArgs a, const float2* __restrict__ u) {
-    using G = Geo<LS>;
+    using G = Geo<LS, LE>;
     TeamCtx<G> c = team_setup<G>(a.tw);
     const float invS = 1.0f / G::S;
-    float2 v[32];
+    float2 v[G::E];
     for (int k = blockIdx.x * G::TEAMS + c.team; k < a.K; k += gridDim.x * G::TEAMS) {
         const int2 rc = a.pos[k];
         const float2* uk = u + (size_t)k * G::M + c.tid;
-        float wv[32];
+        float wv[G::E];
         load_natural<G>(a.w + (size_t)k * G::M, reinterpret_cast<float*>(c.sm), wv, c.tid);
 #pragma unroll
-        for (int e = 0; e < 32; ++e) v[e] = __ldg(uk + e * G::T) * (wv[e] * invS);
+        for (int e = 0; e < G::E; ++e) v[e] = __ldg(uk + e * G::T) * (wv[e] * invS);
         team_sync<G>();  // every thread's reads of the staged w are done
         team_fft_inv<G>(v, c.sm, c.tw, c.tid);
         scatter_times_conj_probe<G>(v, a.out, a.P, a.nx, rc.x, rc.y, c.tid);
@@ -426,11 +430,11 @@ k_jtvp_phasor(AdjArgs a, const float2* __restrict__ u) {
 // in real coordinates: D_O[n] = sum_{k: n in patch k} |P[n - r_k]|^2 tr_k / (2M) and
 // D_P[m] = sum_k |O[r_k + m]|^2 tr_k / (2M), tr_k = sum_m d2l_km.
 // ---------------------------------------------------------------------------------------
-template <int LS>
-__global__ void __launch_bounds__(Geo<LS>::T)
+template <int LS, int LE>
+__global__ void __launch_bounds__(Geo<LS, LE>::T)
 k_diag_object(const float* __restrict__ trp, const int2* __restrict__ pos, const float2* __restrict__ P, int nx,
               float* D_O, float* tr) {
-    using G = Geo<LS>;
+    using G = Geo<LS, LE>;
     const int k = blockIdx.x, tid = threadIdx.x;
     double s[1] = {(double)trp[(size_t)k * G::T + tid]};
     block_sum<1>(s);
@@ -444,17 +448,17 @@ k_diag_object(const float* __restrict__ trp, const int2* __restrict__ pos, const
     const int2 rc = pos[k];
     const int x = tid & (G::S - 1), b = tid >> G::LOG_S;
 #pragma unroll 8
-    for (int a = 0; a < 32; ++a) {
+    for (int a = 0; a < G::E; ++a) {
         const int y = G::BX * a + b;
         const float2 p = P[y * G::S + x];
         atomicAdd(D_O + (size_t)(rc.x + y) * nx + rc.y + x, (p.x * p.x + p.y * p.y) * scale);
     }
 }
 
-template <int LS>
+template <int LS, int LE>
 __global__ void k_diag_probe(const float* __restrict__ tr, const int2* __restrict__ pos, int K,
                              const float2* __restrict__ O, int nx, float* D_P) {
-    using G = Geo<LS>;
+    using G = Geo<LS, LE>;
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < G::M; m += gridDim.x * blockDim.x) {
         const int y = m >> G::LOG_S, x = m & (G::S - 1);
         float acc = 0.0f;
@@ -467,22 +471,17 @@ __global__ void k_diag_probe(const float* __restrict__ tr, const int2* __restric
     }
 }
 
-cudaError_t launch_ggn_diag(int LS, const float* trp, const int2* pos, int K, const float2* O, const float2* P,
+cudaError_t launch_ggn_diag(int LS, int LE, const float* trp, const int2* pos, int K, const float2* O, const float2* P,
                             int nx, float* D_O, float* D_P, float* tr, cudaStream_t stream) {
     if (K == 0) return cudaSuccess;
-    switch (LS) {
-        case 5:
-            k_diag_object<5><<<K, Geo<5>::T, 0, stream>>>(trp, pos, P, nx, D_O, tr);
-            if (D_P) k_diag_probe<5><<<(Geo<5>::M + 255) / 256, 256, 0, stream>>>(tr, pos, K, O, nx, D_P);
-            break;
-        case 6:
-            k_diag_object<6><<<K, Geo<6>::T, 0, stream>>>(trp, pos, P, nx, D_O, tr);
-            if (D_P) k_diag_probe<6><<<(Geo<6>::M + 255) / 256, 256, 0, stream>>>(tr, pos, K, O, nx, D_P);
-            break;
-        case 7:
-            k_diag_object<7><<<K, Geo<7>::T, 0, stream>>>(trp, pos, P, nx, D_O, tr);
-            if (D_P) k_diag_probe<7><<<(Geo<7>::M + 255) / 256, 256, 0, stream>>>(tr, pos, K, O, nx, D_P);
-            break;
+    switch (LS * 8 + LE) {
+#define PTYLM_DIAG(ls, le)                                                                                  \
+    case ls * 8 + le:                                                                                         \
+        k_diag_object<ls, le><<<K, Geo<ls, le>::T, 0, stream>>>(trp, pos, P, nx, D_O, tr);                   \
+        if (D_P) k_diag_probe<ls, le><<<(Geo<ls, le>::M + 255) / 256, 256, 0, stream>>>(tr, pos, K, O, nx, D_P); \
+        break;
+        PTYLM_TILE_CASES(PTYLM_DIAG)
+#undef PTYLM_DIAG
         default:
             return cudaErrorInvalidValue;
     }
@@ -492,83 +491,83 @@ cudaError_t launch_ggn_diag(int LS, const float* trp, const int2* pos, int K, co
 // ---------------------------------------------------------------------------------------
 // Host-side dispatch.
 // ---------------------------------------------------------------------------------------
-int cta_threads(int LS) {
-    switch (LS) {
-        case 5: return Geo<5>::THREADS;
-        case 6: return Geo<6>::THREADS;
-        case 7: return Geo<7>::THREADS;
+int cta_threads(int LS, int LE) {
+    switch (LS * 8 + LE) {
+#define PTYLM_THREADS(ls, le) case ls * 8 + le: return Geo<ls, le>::THREADS;
+        PTYLM_TILE_CASES(PTYLM_THREADS)
+#undef PTYLM_THREADS
     }
     return 0;
 }
 
-int cta_teams(int LS) {
-    switch (LS) {
-        case 5: return Geo<5>::TEAMS;
-        case 6: return Geo<6>::TEAMS;
-        case 7: return Geo<7>::TEAMS;
+int cta_teams(int LS, int LE) {
+    switch (LS * 8 + LE) {
+#define PTYLM_TEAMS(ls, le) case ls * 8 + le: return Geo<ls, le>::TEAMS;
+        PTYLM_TILE_CASES(PTYLM_TEAMS)
+#undef PTYLM_TEAMS
     }
     return 0;
 }
 
-size_t cta_smem_bytes(int LS) {
-    switch (LS) {
-        case 5: return sizeof(float2) * (Geo<5>::S + Geo<5>::TEAMS * Geo<5>::M);
-        case 6: return sizeof(float2) * (Geo<6>::S + Geo<6>::TEAMS * Geo<6>::M);
-        case 7: return sizeof(float2) * (Geo<7>::S + Geo<7>::TEAMS * Geo<7>::M);
+size_t cta_smem_bytes(int LS, int LE) {
+    switch (LS * 8 + LE) {
+#define PTYLM_SMEM(ls, le) case ls * 8 + le: return sizeof(float2) * (Geo<ls, le>::S + Geo<ls, le>::TEAMS * Geo<ls, le>::M);
+        PTYLM_TILE_CASES(PTYLM_SMEM)
+#undef PTYLM_SMEM
     }
     return 0;
 }
 
-template <int LS>
+template <int LS, int LE>
 static const void* kernel_ptr(int kid) {
     switch (kid) {
-        case KID_FWD_LOSS: return (const void*)k_forward<LS, false>;
-        case KID_FWD_CACHE: return (const void*)k_forward<LS, true>;
-        case KID_MATVEC: return (const void*)k_ggn_matvec<LS>;
-        case KID_JTVP: return (const void*)k_jtvp<LS>;
-        case KID_JVP: return (const void*)k_jvp<LS>;
-        case KID_FWD_INTENSITY: return (const void*)k_forward<LS, false, true>;
-        case KID_FWD_CACHE_J: return (const void*)k_forward<LS, true, false, true>;
-        case KID_MATVEC_J: return (const void*)k_ggn_matvec<LS, true>;
-        case KID_JTVP_J: return (const void*)k_jtvp<LS, true>;
-        case KID_JVP_J: return (const void*)k_jvp<LS, true>;
-        case KID_FWD_MAG: return (const void*)k_forward<LS, false, false, false, true>;
-        case KID_JVP_U: return (const void*)k_jvp_phasor<LS, false>;
-        case KID_JVP_U_J: return (const void*)k_jvp_phasor<LS, true>;
-        case KID_JTVP_U: return (const void*)k_jtvp_phasor<LS, false>;
-        case KID_JTVP_U_J: return (const void*)k_jtvp_phasor<LS, true>;
+        case KID_FWD_LOSS: return (const void*)k_forward<LS, LE, false>;
+        case KID_FWD_CACHE: return (const void*)k_forward<LS, LE, true>;
+        case KID_MATVEC: return (const void*)k_ggn_matvec<LS, LE>;
+        case KID_JTVP: return (const void*)k_jtvp<LS, LE>;
+        case KID_JVP: return (const void*)k_jvp<LS, LE>;
+        case KID_FWD_INTENSITY: return (const void*)k_forward<LS, LE, false, true>;
+        case KID_FWD_CACHE_J: return (const void*)k_forward<LS, LE, true, false, true>;
+        case KID_MATVEC_J: return (const void*)k_ggn_matvec<LS, LE, true>;
+        case KID_JTVP_J: return (const void*)k_jtvp<LS, LE, true>;
+        case KID_JVP_J: return (const void*)k_jvp<LS, LE, true>;
+        case KID_FWD_MAG: return (const void*)k_forward<LS, LE, false, false, false, true>;
+        case KID_JVP_U: return (const void*)k_jvp_phasor<LS, LE, false>;
+        case KID_JVP_U_J: return (const void*)k_jvp_phasor<LS, LE, true>;
+        case KID_JTVP_U: return (const void*)k_jtvp_phasor<LS, LE, false>;
+        case KID_JTVP_U_J: return (const void*)k_jtvp_phasor<LS, LE, true>;
     }
     return nullptr;
 }
 
-static const void* kernel_for(int LS, int kid) {
-    switch (LS) {
-        case 5: return kernel_ptr<5>(kid);
-        case 6: return kernel_ptr<6>(kid);
-        case 7: return kernel_ptr<7>(kid);
+static const void* kernel_for(int LS, int LE, int kid) {
+    switch (LS * 8 + LE) {
+#define PTYLM_KERNEL(ls, le) case ls * 8 + le: return kernel_ptr<ls, le>(kid);
+        PTYLM_TILE_CASES(PTYLM_KERNEL)
+#undef PTYLM_KERNEL
     }
     return nullptr;
 }
 
 // Dynamic shared memory of kernel `kid`: the team buffers, plus the staged measurements of
 // the 128^2 error-metric kernel.
-static size_t kernel_smem_bytes(int LS, int kid) {
+static size_t kernel_smem_bytes(int LS, int LE, int kid) {
     const bool stage = LS == 7 && ((kid == KID_FWD_LOSS && forward_stages_y<7, false, false, false, false>()) ||
                                    (kid == KID_FWD_CACHE && forward_stages_y<7, true, false, false, false>()));
-    return cta_smem_bytes(LS) + (stage ? sizeof(float) * Geo<7>::M : 0);
+    return cta_smem_bytes(LS, LE) + (stage ? sizeof(float) * Geo<7>::M : 0);
 }
 
-cudaError_t kernel_prepare(int LS, int kid, int* ctas_per_sm) {
-    const void* fn = kernel_for(LS, kid);
+cudaError_t kernel_prepare(int LS, int LE, int kid, int* ctas_per_sm) {
+    const void* fn = kernel_for(LS, LE, kid);
     if (!fn) return cudaErrorInvalidValue;
-    const size_t smem = kernel_smem_bytes(LS, kid);
+    const size_t smem = kernel_smem_bytes(LS, LE, kid);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, cta_threads(LS), smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, cta_threads(LS, LE), smem);
 }
 
-cudaError_t kernel_launch(int LS, int kid, const PtyArgs& a, int grid, cudaStream_t stream) {
-    const void* fn = kernel_for(LS, kid);
+cudaError_t kernel_launch(int LS, int LE, int kid, const PtyArgs& a, int grid, cudaStream_t stream) {
+    const void* fn = kernel_for(LS, LE, kid);
     if (!fn || grid <= 0) return cudaErrorInvalidValue;
     FwdArgs fa{a.O, a.P, a.pos, a.y, a.a_cache, a.out, a.out_real, a.partials, a.counter, a.scal, a.tw,
                a.trp, a.outP_part, a.K, a.nx, a.b, a.loss};
@@ -584,7 +583,7 @@ cudaError_t kernel_launch(int LS, int kid, const PtyArgs& a, int grid, cudaStrea
         default: arg = &ja; break;
     }
     void* args[] = {arg, &u};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(cta_threads(LS)), args, kernel_smem_bytes(LS, kid), stream);
+    return cudaLaunchKernel(fn, dim3(grid), dim3(cta_threads(LS, LE)), args, kernel_smem_bytes(LS, LE, kid), stream);
 }
 
 }  // namespace ptylm

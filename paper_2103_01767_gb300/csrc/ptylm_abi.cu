@@ -265,7 +265,7 @@ static_assert(PROF_CG == PTYLM_KERNEL_CG_ITERATION, "profile ids follow the kern
 struct ptylm_ctx {
     ptylm_desc d;
     unsigned cg_spin_limit = kCoopSpinLimit;  // polls per bounded wait of the CG iteration
-    int LS = 0, S = 0, M = 0;
+    int LS = 0, LE = 5, S = 0, M = 0;   // FFT tile: side 2^LS, 2^LE values per thread
     long N = 0;
     long L = 0;                    // length of the state z: N, or N + M for joint contexts
     cudaStream_t stream = nullptr;
@@ -388,7 +388,7 @@ static ptylm_status prof_end(ptylm_ctx* c, int id, cudaEvent_t e0, cudaEvent_t e
 static ptylm_status launch(ptylm_ctx* c, int kid, const PtyArgs& a) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     STATUS_TRY(prof_begin(c, kid, &e0, &e1));
-    CUDA_TRY(kernel_launch(c->LS, kid, a, c->grid[kid], c->stream));
+    CUDA_TRY(kernel_launch(c->LS, c->LE, kid, a, c->grid[kid], c->stream));
     ++c->launches;
     return prof_end(c, kid, e0, e1);
 }
@@ -489,14 +489,14 @@ static bool joint(const ptylm_ctx* c) { return c->d.joint != 0; }
 
 // Sum the probe accumulators of `kid`'s teams into out [M] (overwrite or add).
 static ptylm_status probe_reduce(ptylm_ctx* c, int kid, float2* out, bool accumulate) {
-    const int slots = c->grid[kid] * cta_teams(c->LS);
+    const int slots = c->grid[kid] * cta_teams(c->LS, c->LE);
     k_probe_reduce<<<(c->M + VEC_THREADS - 1) / VEC_THREADS, VEC_THREADS, 0, c->stream>>>(c->probe_part, slots, c->M,
                                                                                         out, accumulate ? 1 : 0);
     return vec_launched(c);
 }
 
 static ptylm_status clear_probe_part(ptylm_ctx* c, int kid) {
-    const size_t slots = (size_t)c->grid[kid] * cta_teams(c->LS);
+    const size_t slots = (size_t)c->grid[kid] * cta_teams(c->LS, c->LE);
     CUDA_TRY(cudaMemsetAsync(c->probe_part, 0, sizeof(float2) * slots * c->M, c->stream));
     return PTYLM_OK;
 }
@@ -586,7 +586,7 @@ static bool lookahead_set(ptylm_ctx* c) {
     if (c->trp_b) return true;
     if (c->lookahead_failed) return false;
     const size_t need = sizeof(float2) * ((size_t)c->d.K * c->M + c->L + c->N) +
-                        sizeof(float) * (size_t)c->d.K * (c->M / 32);
+                        sizeof(float) * (size_t)c->d.K * (c->M >> c->LE);
     // room is kept for the buffers a later PLM or projected solve would still take
     const size_t reserve = (c->Dg ? 0 : sizeof(float) * c->L) + (c->ls_dir ? 0 : sizeof(float2) * c->L);
     if (c->d.workspace_budget && c->allocated + need + reserve > c->d.workspace_budget) {
@@ -596,7 +596,7 @@ static bool lookahead_set(ptylm_ctx* c) {
     if (ctx_alloc_t(c, &c->a_cache_b, (size_t)c->d.K * c->M, "look-ahead cache") != PTYLM_OK ||
         ctx_alloc_t(c, &c->grad_b, c->L, "look-ahead gradient") != PTYLM_OK ||
         ctx_alloc_t(c, &c->O_lin_b, c->N, "look-ahead point") != PTYLM_OK ||
-        ctx_alloc_t(c, &c->trp_b, (size_t)c->d.K * (c->M / 32), "look-ahead d2l sums") != PTYLM_OK) {
+        ctx_alloc_t(c, &c->trp_b, (size_t)c->d.K * (c->M >> c->LE), "look-ahead d2l sums") != PTYLM_OK) {
         c->lookahead_failed = true;   // a partial set stays allocated until the context is freed
         g_last_error.clear();
         return false;
@@ -646,7 +646,7 @@ static ptylm_status op_matvec(ptylm_ctx* c, const float2* v, double lambda, cons
 // Closed-form Dg(G) over z at the linearisation point, floored at floor_rel * max.
 static ptylm_status op_ggn_diag(ptylm_ctx* c, float* D, double floor_rel) {
     CUDA_TRY(cudaMemsetAsync(D, 0, sizeof(float) * c->L, c->stream));
-    CUDA_TRY(launch_ggn_diag(c->LS, c->trp, c->pos, c->d.K, c->O_lin, c->P_lin, c->d.nx, D,
+    CUDA_TRY(launch_ggn_diag(c->LS, c->LE, c->trp, c->pos, c->d.K, c->O_lin, c->P_lin, c->d.nx, D,
                              joint(c) ? D + c->N : nullptr, c->tr, c->stream));
     c->launches += joint(c) ? 2 : 1;
     if (floor_rel > 0.0) {
@@ -744,6 +744,8 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
     if (d.joint != 0 && d.joint != 1) return fail(PTYLM_ERR_ARG, "joint must be 0 or 1");
     if (d.K > 0 && (!positions_dev || !y_dev)) return fail(PTYLM_ERR_ARG, "positions and y must be non-NULL when K > 0");
     if ((long)d.ny * d.nx > (1L << 31)) return fail(PTYLM_ERR_ARG, "object too large");
+    if (d.values_per_thread != 0 && d.values_per_thread != 32 && !(d.values_per_thread == 16 && LS <= 6))
+        return fail(PTYLM_ERR_ARG, "values_per_thread must be 0, 32, or 16 for probe sides 32 and 64");
 
     // Validate positions on the host before anything is allocated or launched.
     std::vector<int32_t> hpos((size_t)d.K * 2);
@@ -777,10 +779,16 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
         cudaGetLastError();
         return bail(fail(PTYLM_ERR_CUDA, "no usable CUDA device"));
     }
-    const int teams = cta_teams(LS);
+    // FFT tile: 32 values per thread, or 16 for sides 32 and 64 when teams of S^2/32 threads
+    // would fill less than half of the GPU's thread slots (few positions): twice the threads
+    // per patch halve each position's dependent chain of FFT passes
+    if (d.values_per_thread == 16) c->LE = 4;
+    else if (d.values_per_thread == 32) c->LE = 5;
+    else c->LE = (LS <= 6 && (long)d.K * (c->M / 32) < (long)c->num_sms * 1024) ? 4 : 5;
+    const int teams = cta_teams(LS, c->LE);
     for (int kid = 0; kid < KID_COUNT; ++kid) {
         int per_sm = 0;
-        cudaError_t e = kernel_prepare(LS, kid, &per_sm);
+        cudaError_t e = kernel_prepare(LS, c->LE, kid, &per_sm);
         if (e != cudaSuccess || per_sm <= 0)
             return bail(fail(PTYLM_ERR_CUDA, "kernel %d for side %d cannot launch: %s", kid, c->S,
                              e != cudaSuccess ? cudaGetErrorString(e) : "zero occupancy"));
@@ -812,7 +820,7 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
     if ((s = ctx_alloc_t(c, &c->a_cache, (size_t)d.K * c->M, "frequency cache")) != PTYLM_OK) return bail(s);
     if ((s = ctx_alloc_t(c, &c->y_perm, (size_t)d.K * c->M, "measurements")) != PTYLM_OK) return bail(s);
     if ((s = ctx_alloc_t(c, &c->grad, c->L, "gradient")) != PTYLM_OK) return bail(s);
-    if ((s = ctx_alloc_t(c, &c->trp, (size_t)std::max(1, d.K) * (c->M / 32), "d2l sums")) != PTYLM_OK) return bail(s);
+    if ((s = ctx_alloc_t(c, &c->trp, (size_t)std::max(1, d.K) * (c->M >> c->LE), "d2l sums")) != PTYLM_OK) return bail(s);
     if ((s = ctx_alloc_t(c, &c->tr, std::max(1, d.K), "per-position d2l sums")) != PTYLM_OK) return bail(s);
     if (d.joint && (s = ctx_alloc_t(c, &c->probe_part, (size_t)c->probe_slots * c->M, "probe accumulators")) != PTYLM_OK)
         return bail(s);
@@ -844,7 +852,7 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
         return bail(fail(PTYLM_ERR_CUDA, "uploading context tables: %s", cudaGetErrorString(e)));
     }
     if (d.K > 0) {
-        cudaError_t e = permute_measurements(LS, y_dev, c->y_perm, d.K, d.loss == PTYLM_LOSS_GAUSSIAN, c->vec_grid,
+        cudaError_t e = permute_measurements(LS, c->LE, y_dev, c->y_perm, d.K, d.loss == PTYLM_LOSS_GAUSSIAN, c->vec_grid,
                                              c->stream, c->counters + CNT_YBAD);
         unsigned bad = 0;
         if (e == cudaSuccess)
@@ -865,7 +873,7 @@ ptylm_status lm_init(ptylm_ctx** out, const ptylm_desc* desc, const int32_t* pos
 // context stream, then a wait for the flag.
 static ptylm_status check_measurements(ptylm_ctx* c, const float* y_dev) {
     CUDA_TRY(cudaMemsetAsync(c->counters + CNT_YBAD, 0, sizeof(unsigned), c->stream));
-    CUDA_TRY(permute_measurements(c->LS, y_dev, nullptr, c->d.K, 0, c->vec_grid, c->stream, c->counters + CNT_YBAD));
+    CUDA_TRY(permute_measurements(c->LS, c->LE, y_dev, nullptr, c->d.K, 0, c->vec_grid, c->stream, c->counters + CNT_YBAD));
     ++c->launches;
     unsigned bad = 0;
     CUDA_TRY(cudaMemcpyAsync(&c->scal_host[0], c->counters + CNT_YBAD, sizeof(unsigned), cudaMemcpyDeviceToHost,
@@ -887,7 +895,7 @@ ptylm_status ptylm_set_measurements(ptylm_ctx* c, const float* y_dev) {
     }
     STATUS_TRY(check_measurements(c, y_dev));  // rejected data leave the context as it was
     c->has_lin = false;  // the loss cache depends on y; the point and the phasor do not
-    CUDA_TRY(permute_measurements(c->LS, y_dev, c->y_perm, c->d.K, c->d.loss == PTYLM_LOSS_GAUSSIAN, c->vec_grid,
+    CUDA_TRY(permute_measurements(c->LS, c->LE, y_dev, c->y_perm, c->d.K, c->d.loss == PTYLM_LOSS_GAUSSIAN, c->vec_grid,
                                   c->stream, nullptr));
     ++c->launches;
     return PTYLM_OK;
@@ -1000,7 +1008,7 @@ ptylm_status jvp(ptylm_ctx* c, const ptylm_c64* vO, const ptylm_c64* vP, float* 
     if (c->d.K == 0) return PTYLM_OK;
     const int kid = c->u_valid ? (vP ? KID_JVP_U_J : KID_JVP_U) : (vP ? KID_JVP_J : KID_JVP);
     if (!c->u_valid && !c->jvp_scratch) {
-        const size_t slots = (size_t)std::max(c->grid[KID_JVP], c->grid[KID_JVP_J]) * cta_teams(c->LS);
+        const size_t slots = (size_t)std::max(c->grid[KID_JVP], c->grid[KID_JVP_J]) * cta_teams(c->LS, c->LE);
         STATUS_TRY(ctx_alloc_t(c, &c->jvp_scratch, slots * c->M, "jvp scratch"));
     }
     PtyArgs a = base_args(c);

@@ -785,7 +785,7 @@ ptylm_status ptylm_batch_init(ptylm_batch** out, int B, const ptylm_desc* descs,
             return bail(bfail(PTYLM_ERR_CUDA, "problem %d: copying positions / probe", b));
         }
         if (d.K > 0) {
-            cudaError_t e = permute_measurements(LS, y_dev[b], y, d.K, d.loss == PTYLM_LOSS_GAUSSIAN,
+            cudaError_t e = permute_measurements(LS, 5, y_dev[b], y, d.K, d.loss == PTYLM_LOSS_GAUSSIAN,
                                                  std::min(bt->num_sms * 8, std::max(1, (int)((long)d.K * M / 256))),
                                                  bt->stream, bt->counters + 3);
             if (e != cudaSuccess) return bail(bfail(PTYLM_ERR_CUDA, "problem %d: measurements: %s", b, cudaGetErrorString(e)));

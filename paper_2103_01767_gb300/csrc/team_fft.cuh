@@ -198,7 +198,9 @@ struct Geo {
     static constexpr int BY = S / AY;
     static constexpr int G3 = E / BY;    // pass-3 groups per thread
     static_assert(BY <= E, "pass 3 must fit one thread's values");
-    static constexpr int TEAMS = (T >= 128) ? 1 : 128 / T;  // teams per CTA
+    // teams per CTA of the single-problem kernels: several only for one-warp teams, whose
+    // barriers are warp-local (teams in one CTA may run different numbers of positions)
+    static constexpr int TEAMS = (T > 32) ? 1 : 128 / T;
     static constexpr int THREADS = T * TEAMS;
 };
 

@@ -44,7 +44,7 @@ class Desc(ctypes.Structure):
     _fields_ = [("ny", ctypes.c_int), ("nx", ctypes.c_int), ("my", ctypes.c_int),
                 ("mx", ctypes.c_int), ("K", ctypes.c_int), ("loss", ctypes.c_int),
                 ("background", ctypes.c_float), ("joint", ctypes.c_int),
-                ("workspace_budget", ctypes.c_size_t)]
+                ("workspace_budget", ctypes.c_size_t), ("values_per_thread", ctypes.c_int)]
 
 
 class LMParams(ctypes.Structure):
@@ -216,12 +216,13 @@ class Context:
 
 
 def lm_init(ny, nx, my, mx, positions, y, loss=LOSS_GAUSSIAN, background=1e-8, joint=0,
-            workspace_budget=0, stream=None) -> Context:
-    """positions: device int32 [K, 2]; y: device float32 [K, my, mx] (copied)."""
+            workspace_budget=0, stream=None, values_per_thread=0) -> Context:
+    """positions: device int32 [K, 2]; y: device float32 [K, my, mx] (copied).
+    values_per_thread: FFT tile (0 automatic, 32, or 16 for probe sides 32 and 64)."""
     lib = load_library()
     K = 0 if positions is None else int(positions.shape[0])
     desc = Desc(int(ny), int(nx), int(my), int(mx), K, int(loss), float(background), int(joint),
-                int(workspace_budget))
+                int(workspace_budget), int(values_per_thread))
     h = ctypes.c_void_p()
     _check(lib.lm_init(ctypes.byref(h), ctypes.byref(desc), _ptr(positions), _ptr(y),
                        _stream_ptr(stream)))

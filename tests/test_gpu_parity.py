@@ -101,12 +101,13 @@ def host(t):
 
 
 class GpuCase:
-    def __init__(self, lib, case):
+    def __init__(self, lib, case, values_per_thread=0):
         self.lib, self.case = lib, case
         self.pos = dev_i32(case.pos)
         self.y = dev_f32(case.y)
         self.P = dev_c64(case.P)
-        self.ctx = lib.lm_init(case.n, case.n, case.m, case.m, self.pos, self.y, case.loss, case.b)
+        self.ctx = lib.lm_init(case.n, case.n, case.m, case.m, self.pos, self.y, case.loss, case.b,
+                               values_per_thread=values_per_thread)
 
     def point(self, seed=5, scale=0.05):
         O = synth.to_c64(self.case.O_true + synth.random_complex(self.case.O_true.shape, seed=seed, scale=scale))
@@ -267,6 +268,81 @@ def test_jvp_and_jtvp(lib, shape, at_truth):
     jt_ref = oracle.jtvp(pb, O, w)
     compare("J^T w", host(outO), jt_ref, case, lambda A: oracle.jtvp(pb, A, w), (O,),
             lambda: evaluations(mdl, "jtvp", O, w))
+
+
+SMALL_PROBE_SHAPES = [s for s in SHAPES if s[1] <= 64]
+
+
+@pytest.mark.parametrize("vpt", [16, 32])
+@pytest.mark.parametrize("shape", SMALL_PROBE_SHAPES)
+def test_fft_tiles_at_small_probes(lib, shape, vpt):
+    """Probe sides 32 and 64 run on either FFT tile (16 or 32 values per thread; the context
+    picks one from the number of positions): f, ||grad_zeta l||^2, grad f (Gaussian metric,
+    perturbed point), (G + lambda I) v, J v and J^T w (that and Poisson data at the truth)
+    against the oracle at 1e-5 on both."""
+    n, m, K = shape
+    for kind in [(0, False, False), (1, False, True)]:
+        case = kind_case(n, m, K, kind[:2], 21, kind[2])
+        g = GpuCase(lib, case, values_per_thread=vpt)
+        O = case.O_true if kind[2] else g.point()
+        pb = case.problem()
+        tag = f" [E={vpt}]"
+        f, dl2 = lib.forward_loss(g.ctx, dev_c64(O), g.P, cache=1)
+        gd = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+        if not kind[2]:   # the metric and its gradient vanish at the truth
+            f_ref, dl2_ref = oracle.loss(pb, O, return_dl_norm2=True)
+            parity.check("f" + tag, f, f_ref)
+            parity.check("||dl||^2" + tag, dl2, dl2_ref)
+            lib.gradient(g.ctx, gd)
+            gr = oracle.gradient(pb, O)
+            parity.check("grad f" + tag, host(gd), gr)
+            parity.check("grad f" + tag, host(gd), gr, norm="max")
+        v = synth.to_c64(synth.random_complex(O.shape, seed=22))
+        out = torch.empty_like(gd)
+        lib.ggn_matvec(g.ctx, dev_c64(v), out, 0.37)
+        ref = oracle.ggn_matvec(pb, O, v, lam=0.37)
+        parity.check("(G + 0.37 I) v" + tag, host(out), ref)
+        parity.check("(G + 0.37 I) v" + tag, host(out), ref, norm="max")
+        jv = torch.empty((K, m, m), dtype=torch.float32, device="cuda")
+        lib.jvp(g.ctx, dev_c64(v), jv)
+        parity.check_detector("J v" + tag, host(jv), oracle.jvp(pb, O, v), oracle.intensity(pb, O) - case.b, None)
+        w = synth.to_f32(synth.random_real((K, m, m), seed=23))
+        lib.jtvp(g.ctx, dev_f32(w), out)
+        parity.check("J^T w" + tag, host(out), oracle.jtvp(pb, O, w))
+        lib.lm_destroy(g.ctx)
+
+
+@pytest.mark.parametrize("shape", SMALL_PROBE_SHAPES)
+def test_fft_tile_choice(lib, shape):
+    """values_per_thread selects the kernels' FFT tile: the automatic choice for these position
+    counts (at most 3000 patches of 32^2, 1000 of 64^2: under half of the GPU with the 32-value
+    tile) is the 16-value tile, bit for bit on the per-position J v; the 32-value tile rounds
+    its transforms differently.  Other values and 16 at probe side 128 are rejected."""
+    n, m, K = shape
+    case = make_case(n, m, K=K, loss=0, seed=24)
+    O = dev_c64(synth.to_c64(case.O_true + synth.random_complex(case.O_true.shape, seed=25, scale=0.05)))
+    v = dev_c64(synth.random_complex((n, n), seed=26))
+    jv = {}
+    for vpt in (0, 16, 32):
+        g = GpuCase(lib, case, values_per_thread=vpt)
+        lib.forward_loss(g.ctx, O, g.P, cache=1)
+        out = torch.empty((K, m, m), dtype=torch.float32, device="cuda")
+        lib.jvp(g.ctx, v, out)
+        jv[vpt] = out.cpu()
+        lib.lm_destroy(g.ctx)
+    assert torch.equal(jv[0], jv[16])
+    assert not torch.equal(jv[16], jv[32])
+    assert rel_err(jv[16].numpy(), jv[32].numpy()) <= 2e-6
+    pos, y = dev_i32(case.pos), dev_f32(case.y)
+    for bad in (8, 24, 64, -1):
+        with pytest.raises(lib.PtylmError):
+            lib.lm_init(n, n, m, m, pos, y, values_per_thread=bad)
+
+
+def test_fft_tile_16_rejected_at_probe_128(lib):
+    case = make_case(288, 128, K=3, loss=0, seed=27)
+    with pytest.raises(lib.PtylmError):
+        lib.lm_init(288, 288, 128, 128, dev_i32(case.pos), dev_f32(case.y), values_per_thread=16)
 
 
 def test_adjoint_identity_on_gpu(lib):
