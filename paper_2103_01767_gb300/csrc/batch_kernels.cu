@@ -23,7 +23,20 @@
 
 namespace ptylm {
 
-__device__ __forceinline__ int batch_tw_offset(int LS) { return LS == 5 ? 0 : (LS == 6 ? 32 : 96); }
+// Shared-memory twiddles of the five tiles back to back (fill_twiddles: 2S entries each),
+// built from the S-entry tables of sides 32, 64, 128 (a.tw, at 0, 32, 96).
+template <class G>
+__device__ __forceinline__ constexpr int batch_tw_offset() {
+    return G::LOG_S == 5 ? (G::LOG_E == 5 ? 0 : 64) : G::LOG_S == 6 ? (G::LOG_E == 5 ? 128 : 256) : 384;
+}
+constexpr int kBatchTwWords = 640;
+__device__ __forceinline__ void batch_fill_twiddles(float2* tw, const float2* w_all) {
+    fill_twiddles<Geo<5, 5>>(tw + batch_tw_offset<Geo<5, 5>>(), w_all, threadIdx.x, blockDim.x);
+    fill_twiddles<Geo<5, 4>>(tw + batch_tw_offset<Geo<5, 4>>(), w_all, threadIdx.x, blockDim.x);
+    fill_twiddles<Geo<6, 5>>(tw + batch_tw_offset<Geo<6, 5>>(), w_all + 32, threadIdx.x, blockDim.x);
+    fill_twiddles<Geo<6, 4>>(tw + batch_tw_offset<Geo<6, 4>>(), w_all + 32, threadIdx.x, blockDim.x);
+    fill_twiddles<Geo<7, 5>>(tw + batch_tw_offset<Geo<7, 5>>(), w_all + 96, threadIdx.x, blockDim.x);
+}
 
 // Sum two per-thread doubles over the warp and add them to f[0], f[1].
 __device__ __forceinline__ void warp_add_to(double* f, double x, double y) {
@@ -44,8 +57,8 @@ __device__ __forceinline__ void batch_forward_item(const BatchArgs& a, const Bat
                                                    float2* smem, const float2* tw_all) {
     constexpr int TEAMS = BATCH_THREADS / G::T;
     const int team = threadIdx.x / G::T, tid = threadIdx.x % G::T;
-    float2* sm = smem + team * G::M;
-    const float2* tw = tw_all + batch_tw_offset(G::LOG_S);
+    float2* sm = smem + team * G::EXW;
+    const float2* tw = tw_all + batch_tw_offset<G>();
     const float invS = 1.0f / G::S;
     const float2* O = a.V + p.z_off;
     float2* gout = a.out + p.z_off;
@@ -116,8 +129,8 @@ __device__ __forceinline__ void batch_matvec_item(const BatchArgs& a, const Batc
                                                   float2* smem, const float2* tw_all) {
     constexpr int TEAMS = BATCH_THREADS / G::T;
     const int team = threadIdx.x / G::T, tid = threadIdx.x % G::T;
-    float2* sm = smem + team * G::M;
-    const float2* tw = tw_all + batch_tw_offset(G::LOG_S);
+    float2* sm = smem + team * G::EXW;
+    const float2* tw = tw_all + batch_tw_offset<G>();
     const float invM = 1.0f / G::M;
     const float2* V = a.V + p.z_off;
     float2* out = a.out + p.z_off;
@@ -166,9 +179,9 @@ template <int KIND>
 __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batch(BatchArgs a) {
     extern __shared__ float4 dyn_smem_f4[];
     float2* tw = reinterpret_cast<float2*>(dyn_smem_f4);
-    float2* smem = tw + BATCH_TW;
+    float2* smem = tw + kBatchTwWords;
     __shared__ int s_item;
-    for (int i = threadIdx.x; i < BATCH_TW; i += blockDim.x) tw[i] = a.tw[i];
+    batch_fill_twiddles(tw, a.tw);
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(a.work, 1u);
         __syncthreads();  // also orders the twiddle stores before the first item
@@ -199,8 +212,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batch(BatchArgs a) {
 
 // Measurements from the team-register order of one FFT tile to that of another (same side):
 // dst[k][e*T + t] = src[k][e'*T' + t'] where (e', t') holds, in the source tile, the
-// frequency (ky, kx) that (e, t) holds in the destination tile.  In a tile G the frequency
-// (ky, kx) sits at thread ky + S*(kx mod BX) and element ((kx / BX) mod G3)*BY + kx / AY.
+// frequency (ky, kx) that (e, t) holds in the destination tile (freq_place).
 template <int LS, int LF, int LT>
 __global__ void k_batch_relayout(const float* __restrict__ src, float* __restrict__ dst, long total) {
     using GF = Geo<LS, LF>;
@@ -209,9 +221,8 @@ __global__ void k_batch_relayout(const float* __restrict__ src, float* __restric
         const long k = i / GT::M;
         const int r = (int)(i - k * GT::M);
         const int e = r / GT::T, t = r % GT::T;
-        const int ky = freq_ky<GT>(t), kx = freq_kx<GT>(t, e);
-        const int tf = ky + GF::S * (kx % GF::BX);
-        const int ef = ((kx / GF::BX) % GF::G3) * GF::BY + kx / GF::AY;
+        int tf, ef;
+        freq_place<GF>(freq_ky<GT>(t), freq_kx<GT>(t, e), tf, ef);
         dst[i] = src[k * GF::M + ef * GF::T + tf];
     }
 }
@@ -268,7 +279,14 @@ cudaError_t batch_diag_launch(const BatchProblem* probs, const int* pos_first, i
     return cudaGetLastError();
 }
 
-static size_t batch_smem_bytes() { return sizeof(float2) * (BATCH_TW + 16384); }
+// exchange words of a CTA: BATCH_THREADS / T teams of the widest tile's padded buffer
+template <class G>
+constexpr int batch_ex_words() { return (BATCH_THREADS / G::T) * G::EXW; }
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+constexpr int kBatchExWords = cmax(cmax(cmax(batch_ex_words<Geo<5, 5>>(), batch_ex_words<Geo<5, 4>>()),
+                                        cmax(batch_ex_words<Geo<6, 5>>(), batch_ex_words<Geo<6, 4>>())),
+                                   batch_ex_words<Geo<7, 5>>());
+static size_t batch_smem_bytes() { return sizeof(float2) * (kBatchTwWords + kBatchExWords); }
 
 static const void* batch_kernel_ptr(int kernel) {
     switch (kernel) {

@@ -160,7 +160,7 @@ int blocks_for(long n) { return (int)std::min<long>(4096, std::max<long>(1, (n +
 bool team_smem_ready = false;
 cudaError_t prepare_team_kernels() {
     if (team_smem_ready) return cudaSuccess;
-    const int smem = (int)(sizeof(float2) * (G7::S + G7::M));
+    const int smem = (int)(sizeof(float2) * (G7::TW_WORDS + G7::EXW));
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_probe_phasor, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_learn_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
@@ -168,7 +168,7 @@ cudaError_t prepare_team_kernels() {
     team_smem_ready = true;
     return cudaSuccess;
 }
-size_t team_smem() { return sizeof(float2) * (G7::S + G7::M); }
+size_t team_smem() { return sizeof(float2) * (G7::TW_WORDS + G7::EXW); }
 
 }  // namespace
 

@@ -186,10 +186,10 @@ __device__ __forceinline__ TeamCtx<G> team_setup(const float2* tw_g) {
     float2* dyn = reinterpret_cast<float2*>(dyn_smem_f4);
     TeamCtx<G> c;
     c.tw = dyn;
-    for (int i = threadIdx.x; i < G::S; i += blockDim.x) c.tw[i] = tw_g[i];
+    fill_twiddles<G>(c.tw, tw_g, threadIdx.x, blockDim.x);
     c.team = threadIdx.x / G::T;
     c.tid = threadIdx.x % G::T;
-    c.sm = dyn + G::S + c.team * G::M;
+    c.sm = dyn + G::TW_WORDS + c.team * G::EXW;
     __syncthreads();
     return c;
 }

@@ -96,7 +96,8 @@ k_forward(FwdArgs a) {
     // position's measurements (64 KB) in shared memory with asynchronous copies issued
     // before the FFT, instead of waiting on 32 dependent loads per thread after it.
     constexpr bool STAGE_Y = forward_stages_y<LS, CACHE, INTENSITY, JOINT, MAG>();
-    float* sy = reinterpret_cast<float*>(c.sm + G::M);
+    static_assert((G::TW_WORDS + G::EXW) % 2 == 0, "staged measurements must start 16-byte aligned");
+    float* sy = reinterpret_cast<float*>(c.sm + G::EXW);
     const ScheduledProbe<G> probe(a.P, c.tid);
     float2 v[G::E];
     int k = blockIdx.x * G::TEAMS + c.team;
@@ -511,7 +512,7 @@ int cta_teams(int LS, int LE) {
 
 size_t cta_smem_bytes(int LS, int LE) {
     switch (LS * 8 + LE) {
-#define PTYLM_SMEM(ls, le) case ls * 8 + le: return sizeof(float2) * (Geo<ls, le>::S + Geo<ls, le>::TEAMS * Geo<ls, le>::M);
+#define PTYLM_SMEM(ls, le) case ls * 8 + le: return sizeof(float2) * (Geo<ls, le>::TW_WORDS + Geo<ls, le>::TEAMS * Geo<ls, le>::EXW);
         PTYLM_TILE_CASES(PTYLM_SMEM)
 #undef PTYLM_SMEM
     }

@@ -101,9 +101,9 @@ const void* kernel_for(int LS) {
 
 size_t smem_bytes(int LS) {
     switch (LS) {
-        case 5: return sizeof(float2) * (Geo<5>::S + Geo<5>::TEAMS * Geo<5>::M);
-        case 6: return sizeof(float2) * (Geo<6>::S + Geo<6>::TEAMS * Geo<6>::M);
-        case 7: return sizeof(float2) * (Geo<7>::S + Geo<7>::TEAMS * Geo<7>::M);
+        case 5: return sizeof(float2) * (Geo<5>::TW_WORDS + Geo<5>::TEAMS * Geo<5>::EXW);
+        case 6: return sizeof(float2) * (Geo<6>::TW_WORDS + Geo<6>::TEAMS * Geo<6>::EXW);
+        case 7: return sizeof(float2) * (Geo<7>::TW_WORDS + Geo<7>::TEAMS * Geo<7>::EXW);
     }
     return 0;
 }

@@ -10,9 +10,17 @@
 //   d1 = BX*a1 + b1  (E x BX = S)            d2 = BY*ay + by  (AY x BY = S, AY = E/BX)
 //   pass 1   DFT_E over a1           -> k1, twiddle W_S^(b1*k1)     thread t1 = d2 + S*b1
 //   pass 2   DFT_BX over b1 -> k2;  DFT_AY over ay -> k1y,
-//            twiddle W_S^(by*k1y)                                  thread t2 = k1 + E*by
-//   pass 3   DFT_BY over by          -> k2y                         thread (kd1, k1y)
+//            twiddle W_S^(by*k1y)                                  thread t2 = by + BY*k1
+//   pass 3   DFT_BY over by          -> k2y      thread t3 = (k2, k1y0, k1), BY = BX^2 threads
+//            per k1, for the G3 = E/BY values k1y = k1y0 + BX*j, j < G3
 //   frequency index (k_d1, k_d2) = (k1 + E*k2, k1y + AY*k2y)
+//
+// Exchange 2 only moves data between the threads that share k1: BY pass-2 threads and BY
+// pass-3 threads, which the maps above place in one warp (32/BY values of k1 per warp).
+// Each pass-2 thread writes its exchange-2 values into the very slots it read in exchange 1,
+// so exchange 2 needs no team barrier, only a warp barrier: a position's round trip
+// (forward, spectral stage, inverse) passes two team barriers, both at exchange 1, and the
+// warps run the rest of it without waiting for one another.
 //
 // In pass 1 the 32 lanes of a warp hold 32 consecutive columns of one row, so the patch
 // gather and the scatter-add touch 256 contiguous bytes per warp instruction.
@@ -22,12 +30,17 @@
 // exchanges and no transposition back to natural order: the frequency stage sees its
 // elements in the "pass-3" layout and computes their frequency index instead.
 //
-// Exchange layouts (units of 8-byte complex words):
-//   ex1 (pass 1 <-> pass 2):  slot(t1, k1) = t1*E + (k1 ^ (t1 & (E-1)))
-//        writers vary t1 across lanes, readers vary k1: the XOR swizzle keeps both
-//        conflict-free (for E = 16 within each half-warp, the unit of a 64-bit access).
-//   ex2 (pass 2 <-> pass 3):  slot = ((k2*AY + k1y)*BY + by)*E + k1
-//        both sides have lanes = k1, so plain row-major is conflict-free.
+// Exchange layout (units of 8-byte complex words), shared by both exchanges: a padded
+// array word(by, ay, bx, k) = A*by + B*ay + C*bx + k for pass-1 row t1 = BY*ay + by + S*bx
+// and k < E; exchange 2 puts the value (k2, k1y, by, k1) at word(by, k1y, k2, k1), the word
+// its pass-2 thread read the input (ay = k1y, bx = k2) from.  Every access is a per-thread
+// base plus a compile-time offset.  A 64-bit access is served per half-warp, so the strides'
+// residues mod 16 are chosen to give each half-warp's 16 words distinct bank pairs in all
+// three patterns: pass 1 (lanes vary t1's low bits), pass 2 (lanes vary by and k1's low
+// bits) and pass 3 (lanes vary k2, k1y0 and k1's low bits):
+//   BY = 16: A, B, C = 1, 1, 4 (mod 16);  BY = 4: A, B, C = 4, 1, 8, with the pass-3
+//   half-warps taking the k1 of one parity;  BY = 1: B odd.
+// The padding costs 3 % (S = 128) to 26 % (S = 32, E = 16) of the unpadded S*S words.
 //
 // Unnormalised transforms: forward then inverse multiplies by S*S; callers fold the
 // orthonormal 1/S factors into their frequency-domain stage.
@@ -182,6 +195,9 @@ __device__ __forceinline__ void dft_strided(float2* v, int base) {
     }
 }
 
+// smallest integer >= x congruent to r mod 16
+__host__ __device__ constexpr int ex_up16(int x, int r) { return x + (((r - x) % 16) + 16) % 16; }
+
 // Geometry of the three-pass decomposition for S = 2^LS with E = 2^LE values per thread.
 template <int LS, int LE = 5>
 struct Geo {
@@ -197,12 +213,35 @@ struct Geo {
     static constexpr int AY = E / BX;
     static constexpr int BY = S / AY;
     static constexpr int G3 = E / BY;    // pass-3 groups per thread
+    static constexpr int LOG_BX = LS - LE;
+    static constexpr int LOG_BY = 2 * LOG_BX;
     static_assert(BY <= E, "pass 3 must fit one thread's values");
+    static_assert(BY == BX * BX && (BY == 1 || BY == 4 || BY == 16), "pass-3 thread map");
+    // exchange strides (see the layout above) and the words one team's buffer takes
+    static constexpr int EX_A = BY == 16 ? ex_up16(E, 1) : BY == 4 ? ex_up16(E, 4) : E;
+    static constexpr int EX_B = ex_up16((BY - 1) * EX_A + E, 1);
+    static constexpr int EX_C = BX > 1 ? ex_up16((AY - 1) * EX_B + (BY - 1) * EX_A + E, BY == 16 ? 4 : 8) : AY * EX_B;
+    // (rounded up to an even count, so that every team's buffer starts 16-byte aligned)
+    static constexpr int EXW = ((BX - 1) * EX_C + (AY - 1) * EX_B + (BY - 1) * EX_A + E + 1) & ~1;
+    static_assert(EXW >= M, "exchange buffer");
+    static constexpr int TW_WORDS = 2 * S;   // shared-memory twiddles (fill_twiddles)
     // teams per CTA of the single-problem kernels: several only for one-warp teams, whose
     // barriers are warp-local (teams in one CTA may run different numbers of positions)
     static constexpr int TEAMS = (T > 32) ? 1 : 128 / T;
     static constexpr int THREADS = T * TEAMS;
 };
+
+// Twiddles in shared memory, TW_WORDS = 2S entries per tile: tw[j] = W_S^j (j < S) and
+// tw[S + BY*k1y + by] = W_S^(by*k1y), pass 2's twiddles laid out so that its lanes (which
+// vary by) read consecutive words.  Filled from the S-entry table w_s by threads
+// i0, i0 + step, ...
+template <class G>
+__device__ __forceinline__ void fill_twiddles(float2* tw, const float2* w_s, int i0, int step) {
+    for (int i = i0; i < G::S; i += step) {
+        tw[i] = w_s[i];
+        tw[G::S + i] = w_s[(i % G::BY) * (i / G::BY)];
+    }
+}
 
 template <class G>
 __device__ __forceinline__ void team_sync() {
@@ -238,41 +277,65 @@ __device__ __forceinline__ void pass1_inv(float2* v) {
     RegDFT<G::E, true>::run(v);
 }
 
+// ---- exchange layout and thread maps -------------------------------------------------
+template <class G>
+__device__ __forceinline__ int ex_word(int by, int ay, int bx, int k) {
+    return G::EX_A * by + G::EX_B * ay + G::EX_C * bx + k;
+}
+// pass-1 row t1 = BY*ay + by + S*bx;  pass-2 thread t2 = by + BY*k1x;  pass-3 thread
+// t3 = k2x + BX*k1y0 + BY*k1x (BY = 16, 1) or, for BY = 4, k2x + 2*k1y0 + 4*m + 16*h + 32*w
+// with k1x = 8w + 2m + h.  t < T = E*BY: the masks state the ranges.
+template <class G>
+__device__ __forceinline__ int p1_base(int t1) {
+    return ex_word<G>(t1 & (G::BY - 1), (t1 >> G::LOG_BY) & (G::AY - 1), (t1 >> G::LOG_S) & (G::BX - 1), 0);
+}
+template <class G>
+__device__ __forceinline__ int p2_k1x(int t2) { return (t2 >> G::LOG_BY) & (G::E - 1); }
+template <class G>
+__device__ __forceinline__ int p2_by(int t2) { return t2 & (G::BY - 1); }
+template <class G>
+__device__ __forceinline__ int p3_k1x(int t3) {
+    if constexpr (G::BY == 4) return (((t3 >> 5) << 3) | (((t3 >> 2) & 3) << 1) | ((t3 >> 4) & 1)) & (G::E - 1);
+    else return (t3 >> G::LOG_BY) & (G::E - 1);
+}
+template <class G>
+__device__ __forceinline__ int p3_k2x(int t3) { return t3 & (G::BX - 1); }
+template <class G>
+__device__ __forceinline__ int p3_k1y0(int t3) { return (t3 >> G::LOG_BX) & (G::BX - 1); }
+
 // ---- exchange 1 --------------------------------------------------------------------
 template <class G>
 __device__ __forceinline__ void ex1_store_from_p1(float2* sm, const float2* v, int t1) {
-    const int sw = t1 & (G::E - 1);
+    float2* row = sm + p1_base<G>(t1);
 #pragma unroll
-    for (int k = 0; k < G::E; ++k) sm[t1 * G::E + (k ^ sw)] = v[k];
+    for (int k = 0; k < G::E; ++k) row[k] = v[k];
 }
 template <class G>
 __device__ __forceinline__ void ex1_load_to_p1(const float2* sm, float2* v, int t1) {
-    const int sw = t1 & (G::E - 1);
+    const float2* row = sm + p1_base<G>(t1);
 #pragma unroll
-    for (int k = 0; k < G::E; ++k) v[k] = sm[t1 * G::E + (k ^ sw)];
+    for (int k = 0; k < G::E; ++k) v[k] = row[k];
 }
 // pass-2 register layout: v[ay*BX + bx] (before pass 2) / v[k1y*BX + k2x] (after)
 template <class G>
+__device__ __forceinline__ const float2* p2_words(const float2* sm, int t2) {
+    return sm + ex_word<G>(p2_by<G>(t2), 0, 0, p2_k1x<G>(t2));
+}
+template <class G>
 __device__ __forceinline__ void ex1_load_to_p2(const float2* sm, float2* v, int t2) {
-    const int k1x = t2 & (G::E - 1), by = (t2 >> G::LOG_E) & (G::BY - 1);  // t2 < T = E BY: the mask states the range
+    const float2* q = p2_words<G>(sm, t2);
 #pragma unroll
     for (int ay = 0; ay < G::AY; ++ay)
 #pragma unroll
-        for (int bx = 0; bx < G::BX; ++bx) {
-            const int t1 = (G::BY * ay + by) + G::S * bx;
-            v[ay * G::BX + bx] = sm[t1 * G::E + (k1x ^ (t1 & (G::E - 1)))];
-        }
+        for (int bx = 0; bx < G::BX; ++bx) v[ay * G::BX + bx] = q[G::EX_B * ay + G::EX_C * bx];
 }
 template <class G>
 __device__ __forceinline__ void ex1_store_from_p2(float2* sm, const float2* v, int t2) {
-    const int k1x = t2 & (G::E - 1), by = (t2 >> G::LOG_E) & (G::BY - 1);  // t2 < T = E BY: the mask states the range
+    float2* q = const_cast<float2*>(p2_words<G>(sm, t2));
 #pragma unroll
     for (int ay = 0; ay < G::AY; ++ay)
 #pragma unroll
-        for (int bx = 0; bx < G::BX; ++bx) {
-            const int t1 = (G::BY * ay + by) + G::S * bx;
-            sm[t1 * G::E + (k1x ^ (t1 & (G::E - 1)))] = v[ay * G::BX + bx];
-        }
+        for (int bx = 0; bx < G::BX; ++bx) q[G::EX_B * ay + G::EX_C * bx] = v[ay * G::BX + bx];
 }
 
 // ---- pass 2 ----------------------------------------------------------------------------
@@ -283,10 +346,10 @@ __device__ __forceinline__ void pass2_fwd(float2* v, const float2* tw, int t2) {
 #pragma unroll
     for (int k2x = 0; k2x < G::BX; ++k2x) dft_strided<G::AY, G::BX, false>(v, k2x);
     if constexpr (G::BY > 1) {
-        const int by = (t2 >> G::LOG_E) & (G::BY - 1);  // t2 < T = E BY: the mask states the range
+        const int by = p2_by<G>(t2);
 #pragma unroll
         for (int k1y = 1; k1y < G::AY; ++k1y) {
-            const float2 w = tw[by * k1y];
+            const float2 w = tw[G::S + G::BY * k1y + by];   // W_S^(by*k1y), lanes vary by
 #pragma unroll
             for (int k2x = 0; k2x < G::BX; ++k2x) v[k1y * G::BX + k2x] = cmul(v[k1y * G::BX + k2x], w);
         }
@@ -295,12 +358,12 @@ __device__ __forceinline__ void pass2_fwd(float2* v, const float2* tw, int t2) {
 
 template <class G>
 __device__ __forceinline__ void pass2_inv(float2* v, const float2* tw, int t2) {
-    const int k1x = t2 & (G::E - 1);
+    const int k1x = p2_k1x<G>(t2);
     if constexpr (G::BY > 1) {
-        const int by = (t2 >> G::LOG_E) & (G::BY - 1);  // t2 < T = E BY: the mask states the range
+        const int by = p2_by<G>(t2);
 #pragma unroll
         for (int k1y = 1; k1y < G::AY; ++k1y) {
-            const float2 w = tw[by * k1y];
+            const float2 w = tw[G::S + G::BY * k1y + by];   // W_S^(by*k1y), lanes vary by
 #pragma unroll
             for (int k2x = 0; k2x < G::BX; ++k2x) v[k1y * G::BX + k2x] = cmulc(v[k1y * G::BX + k2x], w);
         }
@@ -320,46 +383,37 @@ __device__ __forceinline__ void pass2_inv(float2* v, const float2* tw, int t2) {
 }
 
 // ---- exchange 2 (skipped when BY == 1: the data already sits in the right thread) -----
-template <class G>
-__device__ __forceinline__ int ex2_slot(int k2x, int k1y, int by, int k1x) {
-    return ((k2x * G::AY + k1y) * G::BY + by) * G::E + k1x;
-}
+// Value (k2x, k1y, by, k1x) sits in the word pass-2 thread (by, k1x) read its input
+// (ay = k1y, bx = k2x) from in exchange 1.
 template <class G>
 __device__ __forceinline__ void ex2_store_from_p2(float2* sm, const float2* v, int t2) {
-    const int k1x = t2 & (G::E - 1), by = (t2 >> G::LOG_E) & (G::BY - 1);  // t2 < T = E BY: the mask states the range
-#pragma unroll
-    for (int k1y = 0; k1y < G::AY; ++k1y)
-#pragma unroll
-        for (int k2x = 0; k2x < G::BX; ++k2x)
-            sm[ex2_slot<G>(k2x, k1y, by, k1x)] = v[k1y * G::BX + k2x];
+    ex1_store_from_p2<G>(sm, v, t2);   // same words, the pass-2 output in the input's place
 }
 template <class G>
 __device__ __forceinline__ void ex2_load_to_p2(const float2* sm, float2* v, int t2) {
-    const int k1x = t2 & (G::E - 1), by = (t2 >> G::LOG_E) & (G::BY - 1);  // t2 < T = E BY: the mask states the range
-#pragma unroll
-    for (int k1y = 0; k1y < G::AY; ++k1y)
-#pragma unroll
-        for (int k2x = 0; k2x < G::BX; ++k2x)
-            v[k1y * G::BX + k2x] = sm[ex2_slot<G>(k2x, k1y, by, k1x)];
+    ex1_load_to_p2<G>(sm, v, t2);
 }
-// pass-3 register layout: v[j*BY + by] (before pass 3) / v[j*BY + k2y] (after)
+// pass-3 register layout: v[j*BY + by] (before pass 3) / v[j*BY + k2y] (after); the words
+// of group j start at p3_words(sm, t3) + EX_B*BX*j, one every EX_A
+template <class G, class W>
+__device__ __forceinline__ W* p3_words(W* sm, int t3) {
+    return sm + ex_word<G>(0, p3_k1y0<G>(t3), p3_k2x<G>(t3), p3_k1x<G>(t3));
+}
 template <class G>
 __device__ __forceinline__ void ex2_load_to_p3(const float2* sm, float2* v, int t3) {
-    const int k1x = t3 & (G::E - 1), k2x = (t3 & (G::S - 1)) >> G::LOG_E, k1y0 = t3 >> G::LOG_S;
+    const float2* q = p3_words<G>(sm, t3);
 #pragma unroll
     for (int j = 0; j < G::G3; ++j)
 #pragma unroll
-        for (int by = 0; by < G::BY; ++by)
-            v[j * G::BY + by] = sm[ex2_slot<G>(k2x, k1y0 + G::BX * j, by, k1x)];
+        for (int by = 0; by < G::BY; ++by) v[j * G::BY + by] = q[G::EX_B * G::BX * j + G::EX_A * by];
 }
 template <class G>
 __device__ __forceinline__ void ex2_store_from_p3(float2* sm, const float2* v, int t3) {
-    const int k1x = t3 & (G::E - 1), k2x = (t3 & (G::S - 1)) >> G::LOG_E, k1y0 = t3 >> G::LOG_S;
+    float2* q = p3_words<G>(sm, t3);
 #pragma unroll
     for (int j = 0; j < G::G3; ++j)
 #pragma unroll
-        for (int by = 0; by < G::BY; ++by)
-            sm[ex2_slot<G>(k2x, k1y0 + G::BX * j, by, k1x)] = v[j * G::BY + by];
+        for (int by = 0; by < G::BY; ++by) q[G::EX_B * G::BX * j + G::EX_A * by] = v[j * G::BY + by];
 }
 
 // ---- pass 3 ----------------------------------------------------------------------------
@@ -377,11 +431,20 @@ __device__ __forceinline__ void pass3_inv(float2* v) {
 // Frequency index (row ky, column kx) of register element e in the pass-3 layout of
 // thread t3: the row frequency comes from the first transformed dimension.
 template <class G>
-__device__ __forceinline__ int freq_ky(int t3) { return t3 & (G::S - 1); }
+__device__ __forceinline__ int freq_ky(int t3) { return p3_k1x<G>(t3) + G::E * p3_k2x<G>(t3); }
 template <class G>
 __device__ __forceinline__ int freq_kx(int t3, int e) {
     const int j = e / G::BY, k2y = e % G::BY;
-    return (t3 >> G::LOG_S) + G::BX * j + G::AY * k2y;
+    return p3_k1y0<G>(t3) + G::BX * j + G::AY * k2y;
+}
+// The inverse: thread t3 and element e of the pass-3 layout that hold frequency (ky, kx).
+template <class G>
+__host__ __device__ __forceinline__ void freq_place(int ky, int kx, int& t3, int& e) {
+    const int k1x = ky & (G::E - 1), k2x = ky >> G::LOG_E;
+    const int k1y = kx % G::AY, k2y = kx / G::AY, k1y0 = k1y % G::BX, j = k1y / G::BX;
+    e = j * G::BY + k2y;
+    if constexpr (G::BY == 4) t3 = k2x + 2 * k1y0 + 4 * ((k1x >> 1) & 3) + 16 * (k1x & 1) + 32 * (k1x >> 3);
+    else t3 = k2x + G::BX * k1y0 + G::BY * k1x;
 }
 
 // ---- whole transforms ------------------------------------------------------------------
@@ -394,9 +457,8 @@ __device__ __forceinline__ void team_fft_fwd(float2* v, float2* sm, const float2
     ex1_load_to_p2<G>(sm, v, tid);
     pass2_fwd<G>(v, tw, tid);
     if constexpr (G::BY > 1) {
-        team_sync<G>();  // all ex1 reads done before ex2 overwrites
-        ex2_store_from_p2<G>(sm, v, tid);
-        team_sync<G>();
+        ex2_store_from_p2<G>(sm, v, tid);  // into the slots this thread has just read
+        __syncwarp();
         ex2_load_to_p3<G>(sm, v, tid);
         pass3_fwd<G>(v);
     }
@@ -405,15 +467,15 @@ __device__ __forceinline__ void team_fft_fwd(float2* v, float2* sm, const float2
 // Inverse: v in pass-3 layout (spectrum)  ->  v in pass-1 layout (spatial data).
 // Its first shared-memory writes go to exactly the slots the same thread read last in
 // team_fft_fwd, so it may follow team_fft_fwd without a barrier; after any other use of
-// sm the caller synchronises the team first.
+// sm the caller synchronises the team first.  Exchange 2 stays within each warp, and the
+// exchange-1 stores that follow it go to the slots the same thread has just read.
 template <class G>
 __device__ __forceinline__ void team_fft_inv(float2* v, float2* sm, const float2* tw, int tid) {
     if constexpr (G::BY > 1) {
         pass3_inv<G>(v);
         ex2_store_from_p3<G>(sm, v, tid);
-        team_sync<G>();
+        __syncwarp();
         ex2_load_to_p2<G>(sm, v, tid);
-        team_sync<G>();  // all ex2 reads done before ex1 overwrites
     }
     pass2_inv<G>(v, tw, tid);
     ex1_store_from_p2<G>(sm, v, tid);
@@ -428,45 +490,55 @@ __device__ __forceinline__ void team_fft_inv(float2* v, float2* sm, const float2
 // group (2*BY registers) plus whatever it loads: `stage(g, j)` receives the group's BY
 // spectral values g[k2y] (element e = j*BY + k2y of the pass-3 layout) and overwrites them
 // with the values to transform back.
+template <class G, bool TEAM_PRE, class Stage, class Pre>
+__device__ __forceinline__ void team_fft_roundtrip_impl(float2* v, float2* sm, const float2* tw, int tid,
+                                                        Stage&& stage, Pre&& before_pass3);
+
 template <class G, class Stage>
 __device__ __forceinline__ void team_fft_roundtrip(float2* v, float2* sm, const float2* tw, int tid,
                                                    Stage&& stage) {
-    team_fft_roundtrip<G>(v, sm, tw, tid, stage, [] {});
+    team_fft_roundtrip_impl<G, false>(v, sm, tw, tid, stage, [] {});
 }
 
-// As above, with `before_pass3()` run by every thread just before the barrier that precedes
-// pass 3 when BY > 1 (so data the spectral stage reads from shared memory, written
-// asynchronously, can be waited for there); when BY == 1 it runs before the first stage
-// call with no barrier after it.
+// As above, with `before_pass3()` run by every thread just before pass 3 when BY > 1,
+// followed by a team barrier (so data the spectral stage reads from shared memory, written
+// asynchronously by the whole team, can be waited for there); when BY == 1 it runs before
+// the first stage call with no barrier after it.  Without it (the overload above) exchange
+// 2 and pass 3 need only warp barriers.
 template <class G, class Stage, class Pre>
 __device__ __forceinline__ void team_fft_roundtrip(float2* v, float2* sm, const float2* tw, int tid,
                                                    Stage&& stage, Pre&& before_pass3) {
+    team_fft_roundtrip_impl<G, true>(v, sm, tw, tid, stage, before_pass3);
+}
+
+template <class G, bool TEAM_PRE, class Stage, class Pre>
+__device__ __forceinline__ void team_fft_roundtrip_impl(float2* v, float2* sm, const float2* tw, int tid,
+                                                        Stage&& stage, Pre&& before_pass3) {
     pass1_fwd<G>(v, tw, tid);
     ex1_store_from_p1<G>(sm, v, tid);
     team_sync<G>();
     ex1_load_to_p2<G>(sm, v, tid);
     pass2_fwd<G>(v, tw, tid);
     if constexpr (G::BY > 1) {
-        team_sync<G>();  // all ex1 reads done before ex2 overwrites
-        ex2_store_from_p2<G>(sm, v, tid);
+        ex2_store_from_p2<G>(sm, v, tid);  // into the slots this thread has just read
         before_pass3();
-        team_sync<G>();
-        const int k1x = tid & (G::E - 1), k2x = (tid & (G::S - 1)) >> G::LOG_E, k1y0 = (tid >> G::LOG_S) & (G::BX - 1);
+        if constexpr (TEAM_PRE) team_sync<G>();
+        else __syncwarp();
+        float2* q3 = p3_words<G>(sm, tid);
 #pragma unroll 1
         for (int j = 0; j < G::G3; ++j) {
             float2 g[G::BY];
-            const int base = ex2_slot<G>(k2x, k1y0 + G::BX * j, 0, k1x);
+            float2* q = q3 + G::EX_B * G::BX * j;
 #pragma unroll
-            for (int by = 0; by < G::BY; ++by) g[by] = sm[base + by * G::E];
+            for (int by = 0; by < G::BY; ++by) g[by] = q[G::EX_A * by];
             RegDFT<G::BY, false>::run(g);
             stage(g, j);
             RegDFT<G::BY, true>::run(g);
 #pragma unroll
-            for (int by = 0; by < G::BY; ++by) sm[base + by * G::E] = g[by];
+            for (int by = 0; by < G::BY; ++by) q[G::EX_A * by] = g[by];
         }
-        team_sync<G>();
-        ex2_load_to_p2<G>(sm, v, tid);
-        team_sync<G>();  // all ex2 reads done before ex1 overwrites
+        __syncwarp();
+        ex2_load_to_p2<G>(sm, v, tid);   // the exchange-1 stores below go to these same slots
     } else {
         // BY == 1: the pass-2 registers already hold the spectrum, one value per group.
         before_pass3();
