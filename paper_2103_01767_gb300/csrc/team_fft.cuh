@@ -279,29 +279,29 @@ __device__ __forceinline__ void pass1_inv(float2* v) {
 
 // ---- exchange layout and thread maps -------------------------------------------------
 template <class G>
-__device__ __forceinline__ int ex_word(int by, int ay, int bx, int k) {
+__host__ __device__ __forceinline__ int ex_word(int by, int ay, int bx, int k) {
     return G::EX_A * by + G::EX_B * ay + G::EX_C * bx + k;
 }
 // pass-1 row t1 = BY*ay + by + S*bx;  pass-2 thread t2 = by + BY*k1x;  pass-3 thread
 // t3 = k2x + BX*k1y0 + BY*k1x (BY = 16, 1) or, for BY = 4, k2x + 2*k1y0 + 4*m + 16*h + 32*w
 // with k1x = 8w + 2m + h.  t < T = E*BY: the masks state the ranges.
 template <class G>
-__device__ __forceinline__ int p1_base(int t1) {
+__host__ __device__ __forceinline__ int p1_base(int t1) {
     return ex_word<G>(t1 & (G::BY - 1), (t1 >> G::LOG_BY) & (G::AY - 1), (t1 >> G::LOG_S) & (G::BX - 1), 0);
 }
 template <class G>
-__device__ __forceinline__ int p2_k1x(int t2) { return (t2 >> G::LOG_BY) & (G::E - 1); }
+__host__ __device__ __forceinline__ int p2_k1x(int t2) { return (t2 >> G::LOG_BY) & (G::E - 1); }
 template <class G>
-__device__ __forceinline__ int p2_by(int t2) { return t2 & (G::BY - 1); }
+__host__ __device__ __forceinline__ int p2_by(int t2) { return t2 & (G::BY - 1); }
 template <class G>
-__device__ __forceinline__ int p3_k1x(int t3) {
+__host__ __device__ __forceinline__ int p3_k1x(int t3) {
     if constexpr (G::BY == 4) return (((t3 >> 5) << 3) | (((t3 >> 2) & 3) << 1) | ((t3 >> 4) & 1)) & (G::E - 1);
     else return (t3 >> G::LOG_BY) & (G::E - 1);
 }
 template <class G>
-__device__ __forceinline__ int p3_k2x(int t3) { return t3 & (G::BX - 1); }
+__host__ __device__ __forceinline__ int p3_k2x(int t3) { return t3 & (G::BX - 1); }
 template <class G>
-__device__ __forceinline__ int p3_k1y0(int t3) { return (t3 >> G::LOG_BX) & (G::BX - 1); }
+__host__ __device__ __forceinline__ int p3_k1y0(int t3) { return (t3 >> G::LOG_BX) & (G::BX - 1); }
 
 // ---- exchange 1 --------------------------------------------------------------------
 template <class G>
@@ -431,9 +431,9 @@ __device__ __forceinline__ void pass3_inv(float2* v) {
 // Frequency index (row ky, column kx) of register element e in the pass-3 layout of
 // thread t3: the row frequency comes from the first transformed dimension.
 template <class G>
-__device__ __forceinline__ int freq_ky(int t3) { return p3_k1x<G>(t3) + G::E * p3_k2x<G>(t3); }
+__host__ __device__ __forceinline__ int freq_ky(int t3) { return p3_k1x<G>(t3) + G::E * p3_k2x<G>(t3); }
 template <class G>
-__device__ __forceinline__ int freq_kx(int t3, int e) {
+__host__ __device__ __forceinline__ int freq_kx(int t3, int e) {
     const int j = e / G::BY, k2y = e % G::BY;
     return p3_k1y0<G>(t3) + G::BX * j + G::AY * k2y;
 }
