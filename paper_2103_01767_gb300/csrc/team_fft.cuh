@@ -2,9 +2,9 @@
 //
 // The far-field propagator of the model (Sec. 2, Eq. expected_count) is an S x S 2D DFT
 // applied independently at every scan position.  A "team" of T = S*S/E threads owns one
-// patch; every thread holds E complex values in registers (E = 32 everywhere except the
-// batched kernels, which may run 32^2 and 64^2 patches with E = 16) and the 2D transform
-// runs as three register passes separated by two shared-memory exchanges.  The first
+// patch; every thread holds E complex values in registers (E = 32, or E = 16 for 32^2 and
+// 64^2 patches, chosen per context or per batch schedule) and the 2D transform runs as
+// three register passes separated by two shared-memory exchanges.  The first
 // transformed dimension (d1) is the patch row index y, the second (d2) the column index x:
 //
 //   d1 = BX*a1 + b1  (E x BX = S)            d2 = BY*ay + by  (AY x BY = S, AY = E/BX)
